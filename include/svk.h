@@ -1,0 +1,186 @@
+/*
+ * svk.h -- C ABI of the spatially-varying kernel (SVK) image-subtraction library.
+ *
+ * The library computes the difference image of Optimal Image Subtraction,
+ *     D = (R (x) K_{x,y}) - I                                   (Eq. 1)
+ *     K_{x,y} = sum_k a_k(x,y) B_k                               (Eq. 2)
+ *     a_k(x,y) = sum_t c[k][t] m_t(xt, yt)                       (Eq. 3, order d)
+ * on one GB300 GPU (sm_103a), with hand-written CUDA kernels, and fits the
+ * coefficients c by least squares over star stamps (Sec. 2).
+ *
+ * Conventions shared by every entry point:
+ *   - Images are row-major float32, x = column (contiguous), y = row; pitches are in
+ *     ELEMENTS and must be >= W.
+ *   - Kernel size L is odd, h = (L - 1) / 2; basis stamps are stored
+ *     basis[k][v + h][u + h] (row = y offset v, column = x offset u), float32.
+ *   - (x) is a true convolution: (R (x) K)(x,y) = sum_{u,v} K(u,v) R(x - u, y - v),
+ *     R is zero outside the frame, and the kernel is formed at the OUTPUT pixel.
+ *   - Polynomial coordinates are normalised over the frame:
+ *     xt = (2x - (W - 1)) / (W - 1) (0 when W == 1), likewise yt with H.
+ *   - Monomials m_t = xt^i yt^j with i + j <= d, i outer, j inner; T = (d+1)(d+2)/2.
+ *     For d = 2 this is 1, yt, yt^2, xt, xt yt, xt^2 (the terms of Eq. 3).
+ *   - Coefficients are float32 c[N][T] (row-major) on the device.
+ *   - Every pointer named "device" must be device memory of the current CUDA device;
+ *     the caller owns all buffers; the library never frees them.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *     asynchronous on that stream unless its comment says otherwise.
+ *   - Return value: SVK_OK or an error code; svk_last_error() gives a message
+ *     (thread-local).  Argument errors are detected on the host before any launch
+ *     and leave outputs untouched.
+ */
+#ifndef SVK_H
+#define SVK_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define SVK_API __attribute__((visibility("default")))
+#else
+#define SVK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SVK_VERSION 1
+
+/* status codes */
+#define SVK_OK 0
+#define SVK_ERR_ARG 1         /* invalid argument (host-side check)                      */
+#define SVK_ERR_CUDA 2        /* a CUDA runtime/driver call failed                        */
+#define SVK_ERR_NOT_SPD 3     /* normal matrix not positive definite (info = pivot)       */
+#define SVK_ERR_TIMEOUT 4     /* a bounded device-side wait ran out                       */
+#define SVK_ERR_UNSUPPORTED 5 /* valid request this build does not implement              */
+#define SVK_ERR_WORKSPACE 6   /* caller workspace too small                               */
+
+/* basis kinds (Sec. 2: Gaussian function basis and Dirac delta function basis) */
+#define SVK_BASIS_GAUSS 0
+#define SVK_BASIS_DELTA 1
+
+/* basis normalisation */
+#define SVK_NORM_NONE 0  /* raw stamps                                                    */
+#define SVK_NORM_ALARD 1 /* GAUSS: B_0 unit sum; even-even stamps made zero-sum by        */
+                         /* subtracting (sum) B_0; stamps k >= 1 scaled to unit L2 norm.  */
+                         /* DELTA: stamps other than the centre tap become                */
+                         /* delta_k - delta_centre.                                       */
+
+/* convolution methods */
+#define SVK_METHOD_DIRECT 0 /* kernel formed per pixel on the CUDA cores (FP32 FFMA)      */
+#define SVK_METHOD_BASIS 1  /* R (x) B_k for all k as an implicit-im2col GEMM on the       */
+                            /* tensor cores (tcgen05, TMEM accumulators), then a fused     */
+                            /* polynomial epilogue sum_k a_k(x,y) C_k(x,y) (- I)           */
+
+/* arithmetic of the contraction */
+#define SVK_PREC_FP32 0   /* DIRECT only: FP32 FFMA                                       */
+#define SVK_PREC_BF16X3 1 /* BASIS: R and B split hi + lo in BF16, hi*hi + hi*lo + lo*hi, */
+                          /* FP32 accumulation                                            */
+#define SVK_PREC_FP16X3 2 /* BASIS: the same split in FP16 (power-of-two prescaled)       */
+#define SVK_PREC_BF16 3   /* BASIS: plain BF16 operands, FP32 accumulation (one MMA)       */
+
+#define SVK_EDGE_ZERO 0 /* R is zero outside the frame (the only mode)                    */
+
+/* Message of the last error on this host thread ("" if none). */
+SVK_API const char *svk_last_error(void);
+
+/* SVK_VERSION of the loaded library. */
+SVK_API int svk_version(void);
+
+/* Number of Gaussian-basis stamps for n_gauss Gaussians of polynomial degrees deg[]
+ * (sum of (d+1)(d+2)/2), or -1 on bad arguments.  Host only, no CUDA call. */
+SVK_API int svk_gauss_basis_count(int n_gauss, const int *deg);
+
+/*
+ * Tabulate basis stamps B_k on the L x L grid (Sec. 2, Eq. 2; the Gaussian basis of
+ * Alard & Lupton and the delta basis of Miller et al.), in FP64 on the device,
+ * stored as float32.
+ *   kind        SVK_BASIS_GAUSS: for Gaussian g (sigma[g] px) and (p, q) with
+ *               p + q <= deg[g] (p outer, q inner),
+ *               B(u,v) = exp(-(u^2 + v^2) / (2 sigma_g^2)) u^p v^q;
+ *               N = svk_gauss_basis_count(n_gauss, deg), Gaussian-major.
+ *               SVK_BASIS_DELTA: N = L*L, B_k = delta at tap k = (v+h) L + (u+h);
+ *               sigma / deg / n_gauss ignored.
+ *   L           odd kernel size, 1 <= L <= 63.
+ *   sigma, deg  HOST arrays of n_gauss entries (sigma > 0, 0 <= deg <= 10).
+ *   normalize   SVK_NORM_NONE or SVK_NORM_ALARD.
+ *   basis_out   device float32 [N][L][L]; must hold N*L*L floats.
+ *   n_basis_out HOST int receiving N (may be NULL).
+ */
+SVK_API int svk_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg,
+                    int normalize, float *basis_out, int *n_basis_out, void *stream);
+
+/*
+ * Bytes of device workspace that svk_convolve / svk_difference need for this request.
+ * A call may pass workspace == NULL with ws_bytes == 0, in which case the library makes
+ * a stream-ordered allocation of this size for the duration of the call.
+ */
+SVK_API size_t svk_workspace_size(int method, int precision, int W, int H, int N, int L, int degree);
+
+/*
+ * out = R (x) K_{x,y}  (Eq. 1 without the subtraction; Eq. 2 and 3 for K).
+ *   R        device float32 [H][pitch_R]
+ *   W, H     frame size (>= 1 each; W, H <= 65535)
+ *   basis    device float32 [N][L][L] (1 <= N <= 4096, odd 1 <= L <= 31)
+ *   coeffs   device float32 [N][T], T = (degree+1)(degree+2)/2, 0 <= degree <= 3
+ *   method   SVK_METHOD_DIRECT (precision SVK_PREC_FP32) or SVK_METHOD_BASIS
+ *            (precision SVK_PREC_BF16X3 / FP16X3 / BF16; N <= 256)
+ *   edge     SVK_EDGE_ZERO
+ *   out      device float32 [H][pitch_out]; must not overlap R
+ *   workspace, ws_bytes   device scratch of at least svk_workspace_size() bytes, or
+ *            NULL / 0 (library allocates on `stream`).
+ * Errors: SVK_ERR_ARG (bad sizes, even L, NULL pointers, pitch < W),
+ * SVK_ERR_UNSUPPORTED (method/precision pair not built), SVK_ERR_WORKSPACE,
+ * SVK_ERR_CUDA.
+ */
+SVK_API int svk_convolve(const float *R, int W, int H, int pitch_R, const float *basis, int N, int L,
+                 const float *coeffs, int degree, int method, int precision, int edge,
+                 float *out, int pitch_out, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * D = (R (x) K_{x,y}) - I  (Eq. 1), the subtraction fused into the convolution.
+ * Arguments as svk_convolve, plus I (device float32 [H][pitch_I]) and D (device
+ * float32 [H][pitch_D]; must not overlap R or I).
+ */
+SVK_API int svk_difference(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
+                   const float *basis, int N, int L, const float *coeffs, int degree, int method,
+                   int precision, int edge, float *D, int pitch_D, void *workspace,
+                   size_t ws_bytes, void *stream);
+
+/*
+ * Bytes of device workspace svk_fit_coeffs needs.
+ */
+SVK_API size_t svk_fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree,
+                              int bg_degree);
+
+/*
+ * Optimal Image Subtraction least-squares fit of the coefficients (Sec. 2: least squares
+ * on Eq. 1 over isolated-star stamps, K decomposed on the basis).  Model at a stamp
+ * pixel:  sum_k sum_t c[k][t] m_t(xt,yt) C_k(x,y) + sum_j g_j m_j(xt,yt),  with
+ * C_k = R (x) B_k (computed in FP32 on the device); minimise
+ * sum w (model - I)^2 through the normal equations A c = b, accumulated in FP64, and
+ * solve them by an FP64 Cholesky factorisation on the device.
+ *   R, I       device float32 [H][pitch] (same pitch)
+ *   stamp_xy   device int32 [n_stamps][2] = (x, y) centres; stamps are
+ *              stamp_size x stamp_size (odd); pixels outside the frame are skipped
+ *   basis      device float32 [N][L][L]; degree 0..3; bg_degree -1 (none) .. 3
+ *   weight     device float32 [H][pitch] per-pixel weight, or NULL (unit weight)
+ *   coeffs_out device double [M], M = N*T + Tbg: c[k][t] at k*T + t, then g_j
+ *   chi2_out   device double [1] (nullable): sum w (model - I)^2 at the solution
+ *   info_out   device int [1]: -1 on success, else the first non-positive pivot
+ *   workspace  device scratch of svk_fit_workspace_size() bytes, or NULL / 0.
+ * Limits: 1 <= M <= 1024, n_stamps >= 1, stamp_size <= 127.
+ * The factorisation outcome is only known on the device: this call returns SVK_OK
+ * once the work is queued; *info_out >= 0 after the stream completes means the normal
+ * matrix was not positive definite (coeffs_out is then left at zero).  When `sync` is
+ * non-zero the call synchronises the stream and returns SVK_ERR_NOT_SPD in that case.
+ */
+SVK_API int svk_fit_coeffs(const float *R, const float *I, int W, int H, int pitch, const int *stamp_xy,
+                   int n_stamps, int stamp_size, const float *basis, int N, int L, int degree,
+                   int bg_degree, const float *weight, double *coeffs_out, double *chi2_out,
+                   int *info_out, void *workspace, size_t ws_bytes, int sync, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVK_H */

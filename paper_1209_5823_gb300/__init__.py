@@ -1,0 +1,200 @@
+"""Python binding of the SVK C ABI (include/svk.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes torch tensors
+on the current CUDA device; all arithmetic runs in the CUDA kernels of ``libsvk.so``.
+There is no fallback: if the library is missing, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsvk.so")
+
+SVK_OK = 0
+SVK_ERR_ARG = 1
+SVK_ERR_CUDA = 2
+SVK_ERR_NOT_SPD = 3
+SVK_ERR_TIMEOUT = 4
+SVK_ERR_UNSUPPORTED = 5
+SVK_ERR_WORKSPACE = 6
+
+SVK_BASIS_GAUSS = 0
+SVK_BASIS_DELTA = 1
+SVK_NORM_NONE = 0
+SVK_NORM_ALARD = 1
+SVK_METHOD_DIRECT = 0
+SVK_METHOD_BASIS = 1
+SVK_PREC_FP32 = 0
+SVK_PREC_BF16X3 = 1
+SVK_PREC_FP16X3 = 2
+SVK_PREC_BF16 = 3
+SVK_EDGE_ZERO = 0
+
+# every symbol include/svk.h declares (checked by the tests)
+EXPORTS = (
+    "svk_last_error", "svk_version", "svk_gauss_basis_count", "svk_build_basis", "svk_workspace_size",
+    "svk_convolve", "svk_difference", "svk_fit_workspace_size", "svk_fit_coeffs",
+)
+
+
+class SvkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"svk status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libsvk.so (built by paper_1209_5823_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(p)
+    vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    sig = {
+        "svk_last_error": (ctypes.c_char_p, []),
+        "svk_version": (i, []),
+        "svk_gauss_basis_count": (i, [i, vp]),
+        "svk_build_basis": (i, [i, i, i, vp, vp, i, vp, vp, vp]),
+        "svk_workspace_size": (sz, [i, i, i, i, i, i, i]),
+        "svk_convolve": (i, [vp, i, i, i, vp, i, i, vp, i, i, i, i, vp, i, vp, sz, vp]),
+        "svk_difference": (i, [vp, i, vp, i, i, i, vp, i, i, vp, i, i, i, i, vp, i, vp, sz, vp]),
+        "svk_fit_workspace_size": (sz, [i, i, i, i, i, i]),
+        "svk_fit_coeffs": (i, [vp, vp, i, i, i, vp, i, i, vp, i, i, i, i, vp, vp, vp, vp, vp, sz, i, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != SVK_OK:
+        raise SvkError(status, load_library().svk_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _img(t, name):
+    import torch
+    if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be a CUDA float32 [H][pitch] tensor with unit column stride")
+    return t.shape[0], t.shape[1], t.stride(0)
+
+
+def n_terms(degree: int) -> int:
+    return 0 if degree < 0 else (degree + 1) * (degree + 2) // 2
+
+
+def svk_version() -> int:
+    return int(load_library().svk_version())
+
+
+def svk_gauss_basis_count(deg) -> int:
+    arr = (ctypes.c_int * len(deg))(*deg)
+    return int(load_library().svk_gauss_basis_count(len(deg), arr))
+
+
+def svk_build_basis(kind: int, L: int, sigma=(0.7, 1.5, 2.5), deg=(6, 4, 2), normalize: int = SVK_NORM_ALARD,
+                    out=None, stream=None):
+    """Tabulate the basis stamps on the device; returns a float32 [N][L][L] tensor."""
+    import torch
+    lib = load_library()
+    sg = (ctypes.c_double * len(sigma))(*sigma)
+    dg = (ctypes.c_int * len(deg))(*deg)
+    if kind == SVK_BASIS_GAUSS:
+        N = int(lib.svk_gauss_basis_count(len(deg), dg))
+        if N < 0:
+            raise ValueError("bad degree list")
+    else:
+        N = L * L
+    if out is None:
+        out = torch.empty((N, L, L), dtype=torch.float32, device="cuda")
+    nb = ctypes.c_int(0)
+    _check(lib.svk_build_basis(int(kind), int(L), len(sigma), sg, dg, int(normalize), _ptr(out),
+                               ctypes.byref(nb), _stream(stream)))
+    return out
+
+
+def svk_workspace_size(method: int, precision: int, W: int, H: int, N: int, L: int, degree: int) -> int:
+    return int(load_library().svk_workspace_size(method, precision, W, H, N, L, degree))
+
+
+def svk_convolve(R, basis, coeffs, degree: int, method: int = SVK_METHOD_DIRECT, precision: int = SVK_PREC_FP32,
+                 out=None, workspace=None, stream=None, edge: int = SVK_EDGE_ZERO):
+    """out = R (x) K_{x,y} (Eq. 1-3); all tensors on the CUDA device."""
+    import torch
+    H, W, pR = _img(R, "R")
+    N, L = basis.shape[0], basis.shape[1]
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=R.device)
+    _, _, pO = _img(out, "out")
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_convolve(_ptr(R), W, H, pR, _ptr(basis), N, L, _ptr(coeffs), int(degree), int(method),
+                                       int(precision), int(edge), _ptr(out), pO, _ptr(workspace), ws_bytes,
+                                       _stream(stream)))
+    return out
+
+
+def svk_difference(R, I, basis, coeffs, degree: int, method: int = SVK_METHOD_DIRECT,
+                   precision: int = SVK_PREC_FP32, out=None, workspace=None, stream=None, edge: int = SVK_EDGE_ZERO):
+    """D = (R (x) K_{x,y}) - I (Eq. 1); all tensors on the CUDA device."""
+    import torch
+    H, W, pR = _img(R, "R")
+    H2, W2, pI = _img(I, "I")
+    if (H2, W2) != (H, W):
+        raise ValueError("R and I differ in size")
+    N, L = basis.shape[0], basis.shape[1]
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=R.device)
+    _, _, pD = _img(out, "D")
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_difference(_ptr(R), pR, _ptr(I), pI, W, H, _ptr(basis), N, L, _ptr(coeffs),
+                                         int(degree), int(method), int(precision), int(edge), _ptr(out), pD,
+                                         _ptr(workspace), ws_bytes, _stream(stream)))
+    return out
+
+
+def svk_fit_workspace_size(n_stamps: int, stamp_size: int, N: int, L: int, degree: int, bg_degree: int) -> int:
+    return int(load_library().svk_fit_workspace_size(n_stamps, stamp_size, N, L, degree, bg_degree))
+
+
+def svk_fit_coeffs(R, I, stamp_xy, stamp_size: int, basis, degree: int, bg_degree: int = -1, weight=None,
+                   workspace=None, sync: bool = False, stream=None):
+    """OIS least-squares fit on the device; returns (coeffs[M] f64, chi2[1] f64, info[1] i32) tensors."""
+    import torch
+    H, W, p = _img(R, "R")
+    _, _, pI = _img(I, "I")
+    if pI != p or (weight is not None and weight.stride(0) != p):
+        raise ValueError("R, I and weight must share one pitch")
+    N, L = basis.shape[0], basis.shape[1]
+    M = N * n_terms(degree) + n_terms(bg_degree)
+    coeffs = torch.zeros(M, dtype=torch.float64, device=R.device)
+    chi2 = torch.zeros(1, dtype=torch.float64, device=R.device)
+    info = torch.zeros(1, dtype=torch.int32, device=R.device)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    st = stamp_xy.to(torch.int32).contiguous()
+    _check(load_library().svk_fit_coeffs(_ptr(R), _ptr(I), W, H, p, _ptr(st), st.shape[0], int(stamp_size),
+                                         _ptr(basis), N, L, int(degree), int(bg_degree), _ptr(weight), _ptr(coeffs),
+                                         _ptr(chi2), _ptr(info), _ptr(workspace), ws_bytes, int(bool(sync)),
+                                         _stream(stream)))
+    return coeffs, chi2, info

@@ -1,0 +1,225 @@
+// svk_api.cu -- the C ABI entry points declared in include/svk.h: argument checks on the
+// host, workspace handling and dispatch to the kernels of the other translation units.
+#include <cudaTypedefs.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "svk_common.cuh"
+#include "svk_internal.h"
+
+namespace svk {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int status, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+int cuda_status(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return SVK_OK;
+  return set_error(SVK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+const char *last_error() { return g_err; }
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool encode_tmap_2d_f32(CUtensorMap *map, const float *base, int W, int H, int pitch, int box_w,
+                        int box_h) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 || ((size_t)pitch * 4) % 16 != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+  cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int ScopedWorkspace::acquire(size_t bytes, void *user_ws, size_t user_bytes, cudaStream_t s) {
+  if (bytes == 0) return SVK_OK;
+  if (user_ws) {
+    if (user_bytes < bytes)
+      return set_error(SVK_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", user_bytes, bytes);
+    ptr = user_ws;
+    return SVK_OK;
+  }
+  if (user_bytes != 0) return set_error(SVK_ERR_ARG, "ws_bytes > 0 with a NULL workspace");
+  stream = s;
+  cudaError_t e = cudaMallocAsync(&ptr, bytes, s);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    return cuda_status(e, "cudaMallocAsync(workspace)");
+  }
+  owned = true;
+  return SVK_OK;
+}
+
+ScopedWorkspace::~ScopedWorkspace() {
+  if (owned && ptr) cudaFreeAsync(ptr, stream);
+}
+
+}  // namespace svk
+
+using namespace svk;
+
+static int check_conv_args(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
+                           const float *basis, int N, int L, const float *coeffs, int degree,
+                           int method, int precision, int edge, const float *out, int pitch_out,
+                           bool need_I) {
+  if (!R || !basis || !coeffs || !out || (need_I && !I))
+    return set_error(SVK_ERR_ARG, "NULL image, basis, coefficient or output pointer");
+  if (W < 1 || H < 1 || W > 65535 || H > 65535) return set_error(SVK_ERR_ARG, "bad frame size %dx%d", W, H);
+  if (pitch_R < W || pitch_out < W || (need_I && pitch_I < W))
+    return set_error(SVK_ERR_ARG, "pitch smaller than W");
+  if (L < 1 || L > 31 || (L % 2) == 0) return set_error(SVK_ERR_ARG, "kernel size L=%d must be odd in [1,31]", L);
+  if (N < 1 || N > 4096) return set_error(SVK_ERR_ARG, "N=%d out of range", N);
+  if (degree < 0 || degree > 3) return set_error(SVK_ERR_ARG, "degree=%d out of range [0,3]", degree);
+  if (edge != SVK_EDGE_ZERO) return set_error(SVK_ERR_ARG, "unknown edge mode %d", edge);
+  if (method == SVK_METHOD_DIRECT) {
+    if (precision != SVK_PREC_FP32)
+      return set_error(SVK_ERR_UNSUPPORTED, "the direct method computes in FP32 only");
+  } else if (method == SVK_METHOD_BASIS) {
+    if (precision != SVK_PREC_BF16X3 && precision != SVK_PREC_FP16X3 && precision != SVK_PREC_BF16)
+      return set_error(SVK_ERR_UNSUPPORTED, "basis method precision %d not built", precision);
+    if (N > 256) return set_error(SVK_ERR_UNSUPPORTED, "basis method supports N <= 256 (got %d)", N);
+  } else {
+    return set_error(SVK_ERR_ARG, "unknown method %d", method);
+  }
+  return SVK_OK;
+}
+
+static int run_conv(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
+                    const float *basis, int N, int L, const float *coeffs, int degree, int method,
+                    int precision, int edge, float *out, int pitch_out, void *ws, size_t ws_bytes,
+                    void *stream, bool need_I) {
+  int st = check_conv_args(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, method, precision,
+                           edge, out, pitch_out, need_I);
+  if (st != SVK_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (method == SVK_METHOD_DIRECT)
+    return launch_direct(R, pitch_R, need_I ? I : nullptr, pitch_I, W, H, basis, N, L, coeffs, degree, out,
+                         pitch_out, s);
+  ScopedWorkspace w;
+  st = w.acquire(tc_workspace_size(precision, N, L), ws, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  return launch_tc(R, pitch_R, need_I ? I : nullptr, pitch_I, W, H, basis, N, L, coeffs, degree, precision,
+                   out, pitch_out, w.ptr, tc_workspace_size(precision, N, L), s);
+}
+
+extern "C" {
+
+const char *svk_last_error(void) { return svk::last_error(); }
+
+int svk_version(void) { return SVK_VERSION; }
+
+int svk_gauss_basis_count(int n_gauss, const int *deg) {
+  if (n_gauss < 1 || !deg) return -1;
+  int n = 0;
+  for (int g = 0; g < n_gauss; ++g) {
+    if (deg[g] < 0 || deg[g] > 10) return -1;
+    n += (deg[g] + 1) * (deg[g] + 2) / 2;
+  }
+  return n;
+}
+
+int svk_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg, int normalize,
+                    float *basis_out, int *n_basis_out, void *stream) {
+  if (!basis_out) return set_error(SVK_ERR_ARG, "NULL basis_out");
+  if (L < 1 || L > 63 || (L % 2) == 0) return set_error(SVK_ERR_ARG, "L=%d must be odd in [1,63]", L);
+  if (normalize != SVK_NORM_NONE && normalize != SVK_NORM_ALARD)
+    return set_error(SVK_ERR_ARG, "unknown normalisation %d", normalize);
+  int N;
+  if (kind == SVK_BASIS_GAUSS) {
+    if (n_gauss < 1 || n_gauss > 16 || !sigma || !deg) return set_error(SVK_ERR_ARG, "bad Gaussian list");
+    for (int g = 0; g < n_gauss; ++g)
+      if (!(sigma[g] > 0.0) || deg[g] < 0 || deg[g] > 10) return set_error(SVK_ERR_ARG, "bad sigma/deg[%d]", g);
+    N = svk_gauss_basis_count(n_gauss, deg);
+  } else if (kind == SVK_BASIS_DELTA) {
+    N = L * L;
+  } else {
+    return set_error(SVK_ERR_ARG, "unknown basis kind %d", kind);
+  }
+  if (n_basis_out) *n_basis_out = N;
+  return launch_build_basis(kind, L, n_gauss, sigma, deg, normalize, basis_out, N,
+                            static_cast<cudaStream_t>(stream));
+}
+
+size_t svk_workspace_size(int method, int precision, int W, int H, int N, int L, int degree) {
+  (void)W;
+  (void)H;
+  (void)degree;
+  if (method == SVK_METHOD_BASIS) return tc_workspace_size(precision, N, L);
+  return 0;
+}
+
+int svk_convolve(const float *R, int W, int H, int pitch_R, const float *basis, int N, int L,
+                 const float *coeffs, int degree, int method, int precision, int edge, float *out,
+                 int pitch_out, void *workspace, size_t ws_bytes, void *stream) {
+  return run_conv(R, pitch_R, nullptr, 0, W, H, basis, N, L, coeffs, degree, method, precision, edge, out,
+                  pitch_out, workspace, ws_bytes, stream, false);
+}
+
+int svk_difference(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
+                   const float *basis, int N, int L, const float *coeffs, int degree, int method,
+                   int precision, int edge, float *D, int pitch_D, void *workspace, size_t ws_bytes,
+                   void *stream) {
+  return run_conv(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, method, precision, edge, D,
+                  pitch_D, workspace, ws_bytes, stream, true);
+}
+
+size_t svk_fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree, int bg_degree) {
+  return fit_workspace_size(n_stamps, stamp_size, N, L, degree, bg_degree);
+}
+
+int svk_fit_coeffs(const float *R, const float *I, int W, int H, int pitch, const int *stamp_xy,
+                   int n_stamps, int stamp_size, const float *basis, int N, int L, int degree,
+                   int bg_degree, const float *weight, double *coeffs_out, double *chi2_out,
+                   int *info_out, void *workspace, size_t ws_bytes, int sync, void *stream) {
+  if (!R || !I || !stamp_xy || !basis || !coeffs_out || !info_out)
+    return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  if (W < 1 || H < 1 || W > 65535 || H > 65535 || pitch < W) return set_error(SVK_ERR_ARG, "bad frame size/pitch");
+  if (n_stamps < 1 || stamp_size < 1 || stamp_size > 127 || (stamp_size % 2) == 0)
+    return set_error(SVK_ERR_ARG, "bad stamp list (n=%d, size=%d)", n_stamps, stamp_size);
+  if (L < 1 || L > 31 || (L % 2) == 0) return set_error(SVK_ERR_ARG, "L=%d must be odd in [1,31]", L);
+  if (degree < 0 || degree > 3 || bg_degree < -1 || bg_degree > 3)
+    return set_error(SVK_ERR_ARG, "degree %d / bg_degree %d out of range", degree, bg_degree);
+  const int M = N * n_terms(degree) + n_terms(bg_degree);
+  if (N < 1 || M > 1024) return set_error(SVK_ERR_ARG, "M=%d unknowns out of range [1,1024]", M);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScopedWorkspace w;
+  const size_t need = fit_workspace_size(n_stamps, stamp_size, N, L, degree, bg_degree);
+  int st = w.acquire(need, workspace, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  st = launch_fit(R, I, W, H, pitch, stamp_xy, n_stamps, stamp_size, basis, N, L, degree, bg_degree, weight,
+                  coeffs_out, chi2_out, info_out, w.ptr, need, s);
+  if (st != SVK_OK || !sync) return st;
+  st = cuda_status(cudaStreamSynchronize(s), "svk_fit_coeffs sync");
+  if (st != SVK_OK) return st;
+  int info = -1;
+  st = cuda_status(cudaMemcpy(&info, info_out, sizeof(int), cudaMemcpyDeviceToHost), "read info");
+  if (st != SVK_OK) return st;
+  if (info >= 0) return set_error(SVK_ERR_NOT_SPD, "normal matrix not positive definite at pivot %d", info);
+  return SVK_OK;
+}
+
+}  // extern "C"

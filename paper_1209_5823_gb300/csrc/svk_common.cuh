@@ -1,0 +1,122 @@
+// svk_common.cuh -- helpers shared by the SVK CUDA translation units: host-side error
+// reporting, tensor-map encoding through the driver entry point, and thin inline-PTX
+// wrappers for mbarriers, TMA (cp.async.bulk) and bounded waits.  Written for sm_103a.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "svk.h"
+
+namespace svk {
+
+// ------------------------------------------------------------------ host side
+int set_error(int status, const char *fmt, ...);  // records the message, returns status
+int cuda_status(cudaError_t e, const char *what); // SVK_OK or SVK_ERR_CUDA with message
+const char *last_error();
+
+// 2-D float32 tensor map over an image [H][pitch] with a (box_w x box_h) box, zero fill
+// out of bounds.  Returns false when the driver refuses (alignment, sizes).
+bool encode_tmap_2d_f32(CUtensorMap *map, const float *base, int W, int H, int pitch,
+                        int box_w, int box_h);
+
+// Device-memory allocation on a stream for calls that received no workspace.
+struct ScopedWorkspace {
+  void *ptr = nullptr;
+  cudaStream_t stream = nullptr;
+  bool owned = false;
+  int acquire(size_t bytes, void *user_ws, size_t user_bytes, cudaStream_t s);
+  ~ScopedWorkspace();
+};
+
+inline int n_terms(int d) { return d < 0 ? 0 : (d + 1) * (d + 2) / 2; }
+
+// Device status word written by kernels with bounded waits (0 = fine).
+enum DeviceStatus : uint32_t { kDevOk = 0, kDevTimeout = 1 };
+
+// ------------------------------------------------------------------ device side
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` for at most `limit_ns` nanoseconds.  On expiry the
+// wait records kDevTimeout in *status (if given) and returns false; the caller then
+// unwinds without touching the data the barrier guards.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t *status,
+                                                  uint64_t limit_ns = 2000000000ull) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > limit_ns) {
+      if (status) atomicExch(status, (uint32_t)kDevTimeout);
+      return false;
+    }
+  }
+}
+
+// 2-D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+}  // namespace svk

@@ -1,0 +1,215 @@
+// svk_direct.cu -- direct form of the spatially-varying convolution (Eq. 1-3) on the
+// CUDA cores: the kernel K_{x,y} = sum_k a_k(x,y) B_k is formed at every output pixel
+// (Sec. 3: the best kernel at every pixel; Sec. 4: one kernel per output pixel) and
+// applied to the reference image, FP32 FFMA.
+//
+// Layout of one CTA (256 threads, 32 x 8):
+//   * output tile 128 x 8 pixels; thread (tx, ty) owns pixels x0 + tx + 32 p (p < 4) of
+//     row y0 + ty, so every shared-memory read of R is conflict-free and every global
+//     store is coalesced;
+//   * the R tile plus an h-pixel halo is staged in shared memory by one 2-D TMA load
+//     (out-of-frame pixels arrive as zeros -- the zero-padding edge convention);
+//     the box starts on a 16-byte boundary, so its x origin is rounded down by xoff;
+//   * the basis is consumed NC stamps at a time from a [tap][NC] table in shared
+//     memory (uniform broadcast reads), together with the chunk's coefficients;
+//   * per tap: K_p = sum_j a_j(p) B_j(tap) for the chunk, acc_p += K_p * R(x_p - u, y - v).
+#include "svk_common.cuh"
+#include "svk_internal.h"
+
+namespace svk {
+namespace {
+
+constexpr int kTX = 32, kTY = 8, kP = 4, kTileW = kTX * kP;
+constexpr int kThreads = kTX * kTY;
+
+__host__ __device__ inline int round_up4(int v) { return (v + 3) & ~3; }
+__host__ __device__ inline int box_w(int h) { return round_up4(kTileW + 2 * h + 3); }
+__host__ __device__ inline int box_h(int h) { return kTY + 2 * h; }
+
+template <int NC>
+struct Cfg {
+  static constexpr int NCP = (NC + 3) & ~3;  // table row stride (16-byte rows)
+};
+
+template <int NC>
+size_t direct_smem_bytes(int L) {
+  const int h = (L - 1) / 2;
+  size_t b = (size_t)box_w(h) * box_h(h) * 4;                 // R tile
+  b += (size_t)L * L * Cfg<NC>::NCP * 4;                      // basis chunk [tap][NCP]
+  b += (size_t)NC * 10 * 4;                                   // coefficient chunk
+  b += 16;                                                    // mbarrier
+  return b + 128;                                             // alignment slack
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kThreads, 1)
+    direct_kernel(const __grid_constant__ CUtensorMap tmR, int use_tma, const float *__restrict__ R,
+                  int pitch_R, const float *__restrict__ I, int pitch_I, int W, int H,
+                  const float *__restrict__ basis, int N, int L, const float *__restrict__ coeffs,
+                  int degree, float *__restrict__ out, int pitch_out, uint32_t *status) {
+  constexpr int NCP = Cfg<NC>::NCP;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const int h = (L - 1) / 2, LL = L * L, T = (degree + 1) * (degree + 2) / 2;
+  const int BW = box_w(h), BH = box_h(h);
+  float *Rs = reinterpret_cast<float *>(smem);
+  float *Bs = Rs + BW * BH;
+  float *Cs = Bs + LL * NCP;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uintptr_t>(Cs + NC * 10 + 1) & ~uintptr_t(7));
+
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTY;
+  const int xs = ((x0 - h) >> 2) << 2;  // floor to a multiple of 4 (16-byte TMA origin)
+  const int xoff = (x0 - h) - xs;
+
+  // ---- stage the R tile + halo
+  if (use_tma) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+      mbar_arrive_expect_tx(bar, (uint32_t)(BW * BH * 4));
+      tma_load_2d(Rs, &tmR, bar, xs, y0 - h);
+    }
+  } else {
+    for (int i = tid; i < BW * BH; i += kThreads) {
+      const int r = i / BW, c = i % BW, gy = y0 - h + r, gx = xs + c;
+      Rs[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? R[(size_t)gy * pitch_R + gx] : 0.0f;
+    }
+  }
+
+  // ---- normalised coordinates of the thread's pixels
+  const int tx = threadIdx.x, ty = threadIdx.y, y = y0 + ty;
+  const float yt = H > 1 ? (2.0f * (float)y - (float)(H - 1)) / (float)(H - 1) : 0.0f;
+  float xt[kP];
+#pragma unroll
+  for (int p = 0; p < kP; ++p) {
+    const int x = x0 + tx + 32 * p;
+    xt[p] = W > 1 ? (2.0f * (float)x - (float)(W - 1)) / (float)(W - 1) : 0.0f;
+  }
+
+  float acc[kP];
+#pragma unroll
+  for (int p = 0; p < kP; ++p) acc[p] = 0.0f;
+
+  bool tile_ready = !use_tma;
+  for (int k0 = 0; k0 < N; k0 += NC) {
+    __syncthreads();  // previous chunk consumed (and, first time, mbarrier initialised)
+    for (int i = tid; i < LL * NCP; i += kThreads) {
+      const int tap = i / NCP, j = i % NCP;
+      Bs[i] = (j < NC && k0 + j < N) ? basis[(size_t)(k0 + j) * LL + tap] : 0.0f;
+    }
+    for (int i = tid; i < NC * 10; i += kThreads) {
+      const int j = i / 10, t = i % 10;
+      Cs[i] = (k0 + j < N && t < T) ? coeffs[(size_t)(k0 + j) * T + t] : 0.0f;
+    }
+    __syncthreads();
+    if (!tile_ready) {
+      if (!mbar_wait_bounded(bar, 0, status)) return;  // TMA never landed: give up cleanly
+      tile_ready = true;
+    }
+    // a_j(x_p, y) = sum_t c[k0+j][t] xt^i yt^j for the chunk (Eq. 3, order <= 3)
+    float a[NC][kP];
+#pragma unroll
+    for (int p = 0; p < kP; ++p) {
+      float mon[10];
+      int t = 0;
+      float xi = 1.0f;
+#pragma unroll
+      for (int i = 0; i <= 3; ++i) {
+        float yj = 1.0f;
+#pragma unroll
+        for (int jj = 0; jj <= 3 - i; ++jj) {
+          mon[t++] = (i + jj <= degree) ? xi * yj : 0.0f;
+          yj *= yt;
+        }
+        xi *= xt[p];
+      }
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        // coefficient slots are packed in the same (i outer, j inner) order, skipping
+        // terms above `degree`
+        float s = 0.0f;
+        int tt = 0, q = 0;
+#pragma unroll
+        for (int i = 0; i <= 3; ++i)
+#pragma unroll
+          for (int jj = 0; jj <= 3 - i; ++jj, ++q)
+            if (i + jj <= degree) s = fmaf(Cs[j * 10 + tt++], mon[q], s);
+        a[j][p] = s;
+      }
+    }
+    for (int vi = 0; vi < L; ++vi) {
+      // smem row of image row y - v with v = vi - h; smem column of x - u with u = ui - h
+      const float *rrow = Rs + (ty + 2 * h - vi) * BW + tx + 2 * h + xoff;
+      const float4 *brow = reinterpret_cast<const float4 *>(Bs + vi * L * NCP);
+#pragma unroll 1
+      for (int ui = 0; ui < L; ++ui) {
+        float r[kP];
+#pragma unroll
+        for (int p = 0; p < kP; ++p) r[p] = rrow[32 * p - ui];
+        float k0s[kP], k1s[kP];
+#pragma unroll
+        for (int p = 0; p < kP; ++p) k0s[p] = k1s[p] = 0.0f;
+        const float4 *bt = brow + ui * (NCP / 4);
+#pragma unroll
+        for (int q = 0; q < NCP / 4; ++q) {
+          const float4 b = bt[q];
+          const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int j = 4 * q + e;
+            if (j < NC) {
+#pragma unroll
+              for (int p = 0; p < kP; ++p) {
+                if (j & 1) k1s[p] = fmaf(a[j][p], bv[e], k1s[p]);
+                else k0s[p] = fmaf(a[j][p], bv[e], k0s[p]);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < kP; ++p) acc[p] = fmaf(k0s[p] + k1s[p], r[p], acc[p]);
+      }
+    }
+  }
+
+  if (y < H) {
+#pragma unroll
+    for (int p = 0; p < kP; ++p) {
+      const int x = x0 + tx + 32 * p;
+      if (x < W) {
+        float v = acc[p];
+        if (I) v -= I[(size_t)y * pitch_I + x];
+        out[(size_t)y * pitch_out + x] = v;
+      }
+    }
+  }
+}
+
+template <int NC>
+int launch_nc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis,
+              int N, int L, const float *coeffs, int degree, float *out, int pitch_out, cudaStream_t s) {
+  const int h = (L - 1) / 2;
+  const size_t smem = direct_smem_bytes<NC>(L);
+  cudaError_t e = cudaFuncSetAttribute(direct_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_status(e, "direct_kernel smem attribute");
+  CUtensorMap tm;
+  memset(&tm, 0, sizeof(tm));
+  const int use_tma = encode_tmap_2d_f32(&tm, R, W, H, pitch_R, box_w(h), box_h(h)) ? 1 : 0;
+  dim3 grid((W + kTileW - 1) / kTileW, (H + kTY - 1) / kTY), block(kTX, kTY);
+  direct_kernel<NC><<<grid, block, smem, s>>>(tm, use_tma, R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs,
+                                             degree, out, pitch_out, nullptr);
+  return cuda_status(cudaGetLastError(), "direct_kernel launch");
+}
+
+}  // namespace
+
+int launch_direct(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis,
+                  int N, int L, const float *coeffs, int degree, float *out, int pitch_out, cudaStream_t s) {
+  if (N <= 4) return launch_nc<4>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, s);
+  if (N <= 8) return launch_nc<8>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, s);
+  if (N <= 16) return launch_nc<16>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, s);
+  return launch_nc<25>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, s);
+}
+
+}  // namespace svk

@@ -1,0 +1,32 @@
+// svk_internal.h -- launchers behind the C ABI (one translation unit each).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace svk {
+
+// Direct form (svk_direct.cu): kernel of Eq. 2 formed at every output pixel, FP32 FFMA.
+// I may be NULL (plain convolution).  Arguments already validated.
+int launch_direct(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
+                  const float *basis, int N, int L, const float *coeffs, int degree, float *out,
+                  int pitch_out, cudaStream_t s);
+
+// Basis tabulation (svk_basis.cu).
+int launch_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg,
+                       int normalize, float *basis_out, int N, cudaStream_t s);
+
+// Tensor-core basis form (svk_tc.cu).
+size_t tc_workspace_size(int precision, int N, int L);
+int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
+              const float *basis, int N, int L, const float *coeffs, int degree, int precision,
+              float *out, int pitch_out, void *ws, size_t ws_bytes, cudaStream_t s);
+
+// Least-squares fit (svk_fit.cu).
+size_t fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree, int bg_degree);
+int launch_fit(const float *R, const float *I, int W, int H, int pitch, const int *stamp_xy,
+               int n_stamps, int stamp_size, const float *basis, int N, int L, int degree,
+               int bg_degree, const float *weight, double *coeffs_out, double *chi2_out,
+               int *info_out, void *ws, size_t ws_bytes, cudaStream_t s);
+
+}  // namespace svk

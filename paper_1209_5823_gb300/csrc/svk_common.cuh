@@ -30,7 +30,7 @@ struct ScopedWorkspace {
   ~ScopedWorkspace();
 };
 
-inline int n_terms(int d) { return d < 0 ? 0 : (d + 1) * (d + 2) / 2; }
+__host__ __device__ inline int n_terms(int d) { return d < 0 ? 0 : (d + 1) * (d + 2) / 2; }
 
 // Device status word written by kernels with bounded waits (0 = fine).
 enum DeviceStatus : uint32_t { kDevOk = 0, kDevTimeout = 1 };

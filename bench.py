@@ -1,0 +1,353 @@
+"""Throughput of the spatially-varying convolution + difference image on one GB300.
+
+One step = one pass of the hot path over one synthetic CCD frame (2048 rows x 4096
+columns, ~20k stars, kernel 19 x 19, 49-stamp Gaussian basis, quadratic spatial
+variation): basis tabulation on the device, then D = (R (x) K_{x,y}) - I by the
+tensor-core basis form (BF16 hi+lo split, FP32 accumulation) through the C ABI.
+
+Printed JSON line (rank 0): value = Mpixel/s of D with inputs resident in HBM; e2e =
+the same through the C ABI with pinned host buffers (copies timed); roofline of the
+dominant kernel (algorithmic FLOP / CUDA-event launch time vs the measured bf16 peak);
+the direct form's throughput beside it; the FP64 oracle timed on the host cores on a
+band of rows (cpu_baseline), whose output also gives the measured max relative error
+of both GPU forms on that band.
+
+`--impl reference` times the FP64 oracle alone (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s spatially-varying conv, TC basis form vs direct, at stated max rel err"
+UNIT = "Mpixel/s"
+WORKLOAD = "ccd_2048x4096_L19_d2"
+L2_BYTES = 129 * 2 ** 20
+NROT = 4  # rotating input frames: 4 x (R, I, D) = 384 MB > L2
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("bf16_tflops", 1900.0), d.get("hbm_gbs", 6800.0), "measured"
+    return 1900.0, 6800.0, "fallback"
+
+
+def _algo_flops_per_px(N, L, degree):
+    T = (degree + 1) * (degree + 2) // 2
+    # basis contraction 2 N L^2, coefficient polynomials 2 N T, combination 2 N, subtraction 1
+    return 2 * N * L * L + 2 * N * T + 2 * N + 1
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _frame():
+    import numpy as np
+    import starfield
+    spec = starfield.CONFIGS[1]
+    R, I, _ = starfield.frame_pair(spec)
+    c = starfield.planted_coeffs(49, spec.degree, starfield.rng(spec.seed + 7))
+    return spec, R.astype(np.float32), I.astype(np.float32), c.astype(np.float32)
+
+
+def _oracle_band(R, I, basis32, c32, degree, budget_s=12.0):
+    """Time the FP64 oracle on a band of rows sized to ~budget_s of host CPU time."""
+    import numpy as np
+    import oracle
+    H, W = R.shape
+    R64, B64, C64 = R.astype(np.float64), basis32.astype(np.float64), c32.astype(np.float64)
+    y0 = H // 2
+    t = time.perf_counter()
+    oracle.convolve(R64, B64, C64, degree, rows=(y0, y0 + 1))
+    per_row = max(time.perf_counter() - t, 1e-4)
+    nrows = int(max(1, min(H - y0, budget_s / per_row)))
+    t = time.perf_counter()
+    ref = oracle.convolve(R64, B64, C64, degree, rows=(y0, y0 + nrows))
+    dt = time.perf_counter() - t
+    return ref, (y0, y0 + nrows), dt, oracle.get_threads()
+
+
+def run_reference(args, rank):
+    """Reference arm: the FP64 oracle on the host cores, same metric and workload."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import starfield
+    spec, R, I, c = _frame()
+    B = oracle.gauss_basis(spec.L).astype(np.float32)  # the same basis stamps, tabulated by the oracle
+    H, W = R.shape
+    # size each step so that (warmup + steps) steps take about two minutes in total
+    y0 = H // 2
+    R64, B64, C64 = R.astype(np.float64), B.astype(np.float64), c.astype(np.float64)
+    t = time.perf_counter()
+    oracle.convolve(R64, B64, C64, spec.degree, rows=(y0, y0 + 1))
+    per_row = max(time.perf_counter() - t, 1e-4)
+    rows = int(max(1, min(64, 120.0 / (args.steps + args.warmup) / per_row)))
+    for _ in range(args.warmup):
+        oracle.convolve(R64, B64, C64, spec.degree, rows=(y0, y0 + rows))
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        out = oracle.convolve(R64, B64, C64, spec.degree, rows=(y0, y0 + rows))
+        _ = out - I[y0:y0 + rows]
+    dt = time.perf_counter() - t
+    px = args.steps * rows * W
+    v = px / dt / 1e6
+    cores = oracle.get_threads()
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "W": W, "H": H, "L": spec.L, "N": 49,
+                                             "degree": spec.degree},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{rows} rows x {W} px of the frame per step (rows {y0}..{y0 + rows - 1})"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="svk", choices=["svk", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    if args.impl == "reference":
+        # rank 0 alone runs the oracle; the other ranks of a torchrun launch exit at once
+        run_reference(args, int(os.environ.get("RANK", "0")))
+        return
+    dist, rank, world, local_rank = _dist()
+
+    import numpy as np
+    import torch
+    import paper_1209_5823_gb300 as svk
+    from paper_1209_5823_gb300 import build as svk_build
+
+    if rank == 0:
+        svk_build.build()
+    if dist:
+        dist.barrier()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prec = {"bf16x3": svk.SVK_PREC_BF16X3, "fp16x3": svk.SVK_PREC_FP16X3, "bf16": svk.SVK_PREC_BF16}[args.precision]
+    spec, R, I, c = _frame()
+    H, W, L, d = spec.H, spec.W, spec.L, spec.degree
+    N = 49
+    stream = torch.cuda.current_stream()
+
+    Rs = [torch.from_numpy(R).to(dev) for _ in range(NROT)]
+    Is = [torch.from_numpy(I).to(dev) for _ in range(NROT)]
+    Ds = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in range(NROT)]
+    ct = torch.from_numpy(c).to(dev)
+    basis = torch.empty((N, L, L), dtype=torch.float32, device=dev)
+    ws = torch.empty(svk.svk_workspace_size(svk.SVK_METHOD_BASIS, prec, W, H, N, L, d), dtype=torch.uint8, device=dev)
+
+    def step(i, ev=None):
+        svk.svk_build_basis(svk.SVK_BASIS_GAUSS, L, out=basis)
+        if ev is not None:
+            ev[0].record(stream)
+        svk.svk_difference(Rs[i % NROT], Is[i % NROT], basis, ct, d, method=svk.SVK_METHOD_BASIS, precision=prec,
+                           out=Ds[i % NROT], workspace=ws)
+        if ev is not None:
+            ev[1].record(stream)
+
+    launches_per_step = 3  # basis tabulation, table preparation, tensor-core kernel
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = ClockSampler(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else 0)
+    clk.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        step(i, evs[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = t0.elapsed_time(t1)
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+    # e2e through the C ABI with pinned host buffers: H2D of R and I, D2H of D, every step
+    Rh = torch.from_numpy(R).pin_memory()
+    Ih = torch.from_numpy(I).pin_memory()
+    Dh = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    n_e2e = max(10, args.steps // 4)
+    for i in range(3):
+        Rs[0].copy_(Rh, non_blocking=True)
+        Is[0].copy_(Ih, non_blocking=True)
+        step(0)
+        Dh.copy_(Ds[0], non_blocking=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(n_e2e):
+        Rs[0].copy_(Rh, non_blocking=True)
+        Is[0].copy_(Ih, non_blocking=True)
+        step(0)
+        Dh.copy_(Ds[0], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
+
+    # the direct form on the same frame, for the "vs direct" half of the metric
+    n_dir = max(5, min(50, args.steps // 20))
+    Dd = torch.empty((H, W), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        svk.svk_difference(Rs[0], Is[0], basis, ct, d, method=svk.SVK_METHOD_DIRECT, out=Dd)
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for i in range(n_dir):
+        svk.svk_difference(Rs[i % NROT], Is[i % NROT], basis, ct, d, method=svk.SVK_METHOD_DIRECT, out=Dd)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    dir_ms = d0.elapsed_time(d1) / n_dir
+
+    # max over ranks
+    times = torch.tensor([ms_total, e2e_ms, kern_ms, dir_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    ms_total, e2e_ms, kern_ms, dir_ms = times.tolist()
+    px = W * H
+    value = world * px * args.steps / (ms_total / 1e3) / 1e6
+    e2e_value = world * px * n_e2e / (e2e_ms / 1e3) / 1e6
+    if rank != 0:
+        return
+
+    peak_bf16, hbm, peak_src = _peaks()
+    algo = _algo_flops_per_px(N, L, d) * px
+    achieved = algo / (kern_ms / 1e3) / 1e12
+    # raw MMA work of the launch (3 split products, padded taps and rows), for context
+    ng = (L + 7) // 8
+    nks = (ng + 1) // 2
+    G = 5
+    raw = 0
+    for y0 in range(0, H, G):
+        rows = min(H - 1, y0 + G - 1 + L // 2) - max(0, y0 - L // 2) + 1
+        raw += rows
+    n_prod = {"bf16x3": 3, "fp16x3": 3, "bf16": 1}[args.precision]
+    raw_flops = raw * ((W + 127) // 128) * nks * n_prod * 2 * 128 * 256 * 16
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "tc_basis_kernel_traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as f:
+            tj = json.load(f)
+        if tj.get("workload") == WORKLOAD and tj.get("precision") == args.precision:
+            traffic = tj.get("dram_bytes_per_launch")
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": f"{args.precision}-f32acc", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "W": W, "H": H, "L": L, "N": N, "degree": d, "basis": "gauss 0.7/1.5/2.5 deg 6/4/2",
+                   "method": "basis (tcgen05)", "precision": args.precision,
+                   "l2": f"{NROT} rotating input frames ({NROT * 3 * px * 4 / 2**20:.0f} MB > L2)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * px * 4, "d2h_bytes_per_step": px * 4},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_bf16, "unit": "TFLOP/s",
+                     "frac": achieved / peak_bf16, "traffic": traffic,
+                     "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)",
+                     "kernel": "tc_basis_kernel (+ table prep) per CUDA-event bracket",
+                     "algorithmic_flop_per_px": _algo_flops_per_px(N, L, d),
+                     "raw_mma_tflops": raw_flops / (kern_ms / 1e3) / 1e12,
+                     "raw_mma_frac": raw_flops / (kern_ms / 1e3) / 1e12 / peak_bf16},
+        "direct": {"value": world * px / (dir_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_frame": dir_ms,
+                   "dtype": "f32"},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        ref, rows, dt, cores = _oracle_band(R, I, basis.cpu().numpy(), c, d)
+        y0, y1 = rows
+        Dtc = Ds[(args.steps - 1) % NROT][y0:y1].cpu().numpy().astype(np.float64) + I[y0:y1]
+        Ddir = Dd[y0:y1].cpu().numpy().astype(np.float64) + I[y0:y1]
+        scale = np.abs(ref).max()
+        out["cpu_baseline"] = {"value": (y1 - y0) * W / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"rows {y0}..{y1 - 1} ({(y1 - y0) * W} px) of the frame, FP64 C oracle"}
+        out["max_rel_err"] = {"basis": float(np.abs(Dtc - ref).max() / scale),
+                              "direct": float(np.abs(Ddir - ref).max() / scale),
+                              "measure": "max|D_gpu - D_oracle| / max|R (x) K| over the cpu_baseline band"}
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

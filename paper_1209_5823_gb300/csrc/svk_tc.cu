@@ -29,9 +29,26 @@
 // Split precision.  R = Rh + Rl and B = Bh + Bl (BF16 or FP16 pairs); three MMAs per
 // K step, Ah*Bh + Ah*Bl + Al*Bh, accumulate in the same FP32 TMEM columns.
 //
-// Roles (9 warps): warps 0-3 epilogue (TMEM lane quarters 0-3), warp 4 TMEM owner and
-// MMA issuer (one thread), warps 5-8 producers.  All waits are bounded; a wait that
-// runs out records a status word and the CTA unwinds (MMAs drained, TMEM freed).
+// K steps.  A reference row has nG = ceil(L/8) groups of 8 taps; one MMA takes two
+// groups (K = 16).  Rows are consumed in pairs (r, r+1) held in consecutive pipeline
+// stages.  When nG is odd the last group of r and the last group of r+1 form one MMA:
+// its second core-matrix column lies one stage further in the A operand (LBO = stage
+// size) and one basis slice further in the B operand (LBO = Nb * 16 bytes), so only
+// ceil(L/8)*8 taps per row are multiplied instead of a multiple of 16.  A block with
+// an odd row count pads its last row with an all-zero tap group.
+//
+// Handshake granularity.  Producers fill stages in groups of kRowsPerGroup rows: one
+// `full` barrier per group (one arrival per row) and one `empty` commit per group.  An
+// mbarrier wait costs the single MMA-issuing thread a few hundred cycles, so waiting
+// once per group (18 MMAs in the split modes) keeps the tensor pipe fed.  Each block's
+// row sequence is padded with empty slots to a multiple of kRowsPerGroup.
+//
+// Roles (16 warps): warps 0-7 epilogue (TMEM lane quarter w % 4, output rows of parity
+// w / 4), warp 8 TMEM owner and MMA issuer (one thread), warps 9-15 producers (each
+// prefetches its next reference row into registers while it converts the current one).  No role uses local memory:
+// with ~227 KB of shared memory the L1 left for it is small.  All waits are bounded; a
+// wait that runs out records a status word and the CTA unwinds (MMAs drained, TMEM
+// freed).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -42,25 +59,29 @@ namespace svk {
 namespace {
 
 constexpr int kMaxSmem = 232448;  // 227 KB opt-in shared memory per CTA on sm_100-class parts
-constexpr int kEpiWarps = 4, kMmaWarp = 4, kProdWarps = 4, kFirstProdWarp = 5;
+constexpr int kEpiWarps = 8, kMmaWarp = 8, kProdWarps = 7, kFirstProdWarp = 9;
+constexpr int kSegRegs = 5;  // staged row segment: <= 160 elements = 5 per lane
 constexpr int kThreads = (kEpiWarps + 1 + kProdWarps) * 32;
 constexpr int kTileM = 128;
 constexpr int kMaxStages = 8;  // Hankel stages (reference rows in flight), upper bound
+constexpr int kRowsPerGroup = 4;  // rows per full/empty handshake
 constexpr uint32_t kTmemCols = 512;
 constexpr int kAccStride = 256;  // TMEM columns per accumulator buffer
 
 // ----------------------------------------------------------------- plan (host+device)
 struct Plan {
   int N, L, h, G, nmma;    // stamps, kernel size, half size, output rows/block, MMA N
-  int nKG, nks;            // K groups of 8 taps per reference row, K steps of 16
+  int nG, nKG;             // tap groups of 8 per reference row; table groups (nG rounded
+                           // up to even: the extra group is all zero)
   int S;                   // Hankel blocks per reference row (= 16 + nKG - 1)
+  size_t stage_bytes;      // one pipeline stage (hi [+ lo] Hankel tiles)
   int seglen;              // staged row length (elements) = 8 S + 8
   int NP, nrows;           // table slices, table rows per K group
   int parts;               // 2 for split precision, 1 for plain BF16
   int NS;                  // Hankel pipeline stages
   int prec;
   size_t table_bytes;      // one table (hi or lo)
-  size_t off_tab_hi, off_tab_lo, off_stage, off_stg, off_coef, off_alpha, off_bar, smem;
+  size_t off_tab_hi, off_tab_lo, off_stage, off_stg, off_coef, off_alpha, off_alphaS, off_bar, smem;
 };
 
 __host__ __device__ inline int rup(int v, int m) { return (v + m - 1) / m * m; }
@@ -72,15 +93,17 @@ static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
   q.h = (L - 1) / 2;
   q.G = G;
   q.prec = prec;
+  if (NS < kRowsPerGroup || NS > kMaxStages || NS % kRowsPerGroup != 0) return false;
   q.NS = NS;
   q.parts = (prec == SVK_PREC_BF16) ? 1 : 2;
   q.nmma = rup(G * N, 16);
   if (q.nmma > 256 || q.nmma < 16) return false;
-  const int ng = (L + 7) / 8;
-  q.nks = (ng + 1) / 2;
-  q.nKG = 2 * q.nks;
+  q.nG = (L + 7) / 8;
+  q.nKG = q.nG + (q.nG & 1);
   q.S = kTileM / 8 + q.nKG - 1;
   q.seglen = 8 * q.S + 8;
+  if (q.seglen > 32 * kSegRegs) return false;
+  q.stage_bytes = (size_t)q.parts * q.S * 128;
   q.NP = L + 2 * (G - 1);
   q.nrows = rup(q.NP * N + 16, 8);
   q.table_bytes = (size_t)q.nKG * q.nrows * 16;
@@ -91,13 +114,15 @@ static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
   if (q.parts == 2) o += q.table_bytes;
   o = rup((int)o, 128);
   q.off_stage = o;
-  o += (size_t)NS * q.parts * q.S * 128;
+  o += (size_t)NS * q.stage_bytes;
   q.off_stg = o;  // per producer warp: parts x 2 copies x seglen bf16 (+16 B pad each)
   o += (size_t)kProdWarps * q.parts * 2 * rup(q.seglen * 2 + 16, 16);
   q.off_coef = o;
   o += (size_t)rup(N * 10 * 4, 16);
   q.off_alpha = o;
   o += (size_t)rup(G * N * 4 * 4, 16);
+  q.off_alphaS = o;  // G x 64 load slots x float4
+  o += (size_t)G * 64 * 16;
   q.off_bar = o;
   o += 8 * (2 * kMaxStages + 4 + 2) + 16;
   q.smem = o + 128;  // base alignment slack
@@ -109,8 +134,10 @@ static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
 }
 
 static bool choose_plan(int N, int L, int prec, Plan *p) {
-  for (int G = 5; G >= 1; --G)
-    for (int NS = kMaxStages; NS >= 4; NS -= 2)
+  // two handshake groups in flight first (producers fill one while the MMAs drain the
+  // other), then the widest MMA that fits
+  for (int NS = kMaxStages; NS >= kRowsPerGroup; NS -= kRowsPerGroup)
+    for (int G = 5; G >= 1; --G)
       if (make_plan(N, L, prec, G, NS, p)) return true;
   return false;
 }
@@ -164,6 +191,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld16p(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 __device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
   uint32_t r;
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
@@ -172,7 +207,7 @@ __device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void epi_bar_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // Split x into hi + lo 16-bit floats; returns the two bit patterns.
 template <int PREC>
@@ -197,6 +232,29 @@ struct Sched {
     x0 = (b % nbx) * kTileM;
     y0 = (b / nbx) * G;
   }
+};
+
+// The CTA's sequence of reference rows: for each of its blocks the rows
+// max(0, y0-h) .. min(H-1, y0+G-1+h), padded with empty slots to a multiple of
+// kRowsPerGroup.
+struct RowIt {
+  int b, i, n, nseq, r_lo, x0, y0;
+  __device__ void set_block(int bb, const Sched &sc, int G, int h, int H) {
+    b = bb;
+    i = 0;
+    if (b < sc.nblocks) {
+      sc.block(b, G, x0, y0);
+      r_lo = max(0, y0 - h);
+      n = min(H - 1, y0 + G - 1 + h) - r_lo + 1;
+      nseq = (n + kRowsPerGroup - 1) / kRowsPerGroup * kRowsPerGroup;
+    }
+  }
+  __device__ void next(const Sched &sc, int G, int h, int H) {
+    if (++i >= nseq) set_block(b + gridDim.x, sc, G, h, H);
+  }
+  __device__ bool valid(const Sched &sc) const { return b < sc.nblocks; }
+  __device__ bool real() const { return i < n; }
+  __device__ int row() const { return r_lo + i; }
 };
 
 // ----------------------------------------------------------------- table preparation
@@ -251,14 +309,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain_bar + 1);
   float *coef = reinterpret_cast<float *>(sm + pl.off_coef);
   float *alpha = reinterpret_cast<float *>(sm + pl.off_alpha);
+  float *alphaS = reinterpret_cast<float *>(sm + pl.off_alphaS);
+  const bool fast = (N >= 16 && N <= 64);
 
   // ---- set-up
   if (warp == kMmaWarp) {
     tmem_alloc(tmem_slot, kTmemCols);
     if (lane == 0) {
-      for (int s = 0; s < NS; ++s) {
-        mbar_init(&full[s], 1);
-        mbar_init(&empty[s], 1);
+      for (int q = 0; q < NS / kRowsPerGroup; ++q) {
+        mbar_init(&full[q], kRowsPerGroup);  // one arrival per row of the group
+        mbar_init(&empty[q], 1);             // one commit per group
       }
       for (int b = 0; b < 2; ++b) {
         mbar_init(&acc_full[b], 1);
@@ -293,97 +353,153 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp >= kFirstProdWarp) {
     // ================================================================ producers
-    const int pw = warp - kFirstProdWarp;
-    uint16_t *stg = reinterpret_cast<uint16_t *>(sm + pl.off_stg) +
-                    (size_t)pw * kParts * 2 * (rup(pl.seglen * 2 + 16, 16) / 2);
+    // P = min(kProdWarps, NS) warps take the rows in turn.  A warp about to fill group q
+    // waits for group q - NG (NG = NS / kRowsPerGroup groups) to drain; its previous row,
+    // P slots earlier, already waited for group q - ceil(P / kRowsPerGroup) - NG, so with
+    // ceil(P / kRowsPerGroup) <= NG group q - 2 NG is drained and the parity wait cannot
+    // alias a phase two uses ahead.
+    const int pw = warp - kFirstProdWarp, nprod = kProdWarps < NS ? kProdWarps : NS;
+    if (pw >= nprod) goto done;
     const int cstride = rup(pl.seglen * 2 + 16, 16) / 2;  // elements between staging copies
-    uint32_t row_seq = 0;
-    for (int b = blockIdx.x; b < sc.nblocks; b += gridDim.x) {
-      int x0, y0;
-      sc.block(b, G, x0, y0);
-      const int r_lo = max(0, y0 - h), r_hi = min(H - 1, y0 + G - 1 + h);
-      for (int r = r_lo; r <= r_hi; ++r, ++row_seq) {
-        if ((int)(row_seq % kProdWarps) != pw) continue;
-        const int stage = row_seq % NS;
-        const uint32_t use = row_seq / NS;
-        if (!mbar_wait_bounded(&empty[stage], (use & 1) ^ 1, status)) goto done;
-        // stage the row segment R(r, x0 - h + e), e < seglen, as hi/lo 16-bit copies;
-        // copy 1 is shifted by one element so every chunk start is 4-byte aligned
-        const float *rrow = R + (size_t)r * pitch_R;
-        const int xb = x0 - h;
-        for (int e = lane; e < pl.seglen; e += 32) {
-          const int gx = xb + e;
-          const float v = (gx >= 0 && gx < W) ? rrow[gx] * rscale : 0.0f;
-          uint16_t hv, lv;
-          split16<PREC>(v, hv, lv);
-          stg[e] = hv;
-          if (e > 0) stg[cstride + e - 1] = hv;
-          if (kParts == 2) {
-            stg[2 * cstride + e] = lv;
-            if (e > 0) stg[3 * cstride + e - 1] = lv;
+    uint16_t *stg = reinterpret_cast<uint16_t *>(sm + pl.off_stg) + (size_t)pw * kParts * 2 * cstride;
+    RowIt it;
+    it.set_block(blockIdx.x, sc, G, h, H);
+    for (int k = 0; k < pw && it.valid(sc); ++k) it.next(sc, G, h, H);
+    uint32_t seq = (uint32_t)pw;
+    float cur[kSegRegs], nxt[kSegRegs];
+    auto load_row = [&](const RowIt &ri, float (&v)[kSegRegs]) {
+      const float *rrow = R + (size_t)ri.row() * pitch_R;
+      const int xb = ri.x0 - h;
+#pragma unroll
+      for (int j = 0; j < kSegRegs; ++j) {
+        const int e = lane + 32 * j, gx = xb + e;
+        v[j] = (e < pl.seglen && gx >= 0 && gx < W) ? __ldg(rrow + gx) * rscale : 0.0f;
+      }
+    };
+    if (it.valid(sc) && it.real()) load_row(it, cur);
+    while (it.valid(sc)) {
+      RowIt nx = it;
+      for (int k = 0; k < nprod && nx.valid(sc); ++k) nx.next(sc, G, h, H);
+      if (nx.valid(sc) && nx.real()) load_row(nx, nxt);  // in flight while this row is built
+      const int stage = seq % NS, grp = stage / kRowsPerGroup;
+      if (!mbar_wait_bounded(&empty[grp], ((seq / NS) & 1) ^ 1, status)) goto done;
+      if (it.real()) {
+        // hi/lo 16-bit copies of the segment; copy 1 is shifted by one element so every
+        // 8-element chunk starts on a 4-byte boundary in one of the two copies
+#pragma unroll
+        for (int j = 0; j < kSegRegs; ++j) {
+          const int e = lane + 32 * j;
+          if (e < pl.seglen) {
+            uint16_t hv, lv;
+            split16<PREC>(cur[j], hv, lv);
+            stg[e] = hv;
+            if (e > 0) stg[cstride + e - 1] = hv;
+            if (kParts == 2) {
+              stg[2 * cstride + e] = lv;
+              if (e > 0) stg[3 * cstride + e - 1] = lv;
+            }
           }
         }
         __syncwarp();
-        unsigned char *hk = sm + pl.off_stage + (size_t)stage * kParts * pl.S * 128;
-        for (int e = lane; e < 8 * pl.S; e += 32) {
+        unsigned char *hk = sm + pl.off_stage + (size_t)stage * pl.stage_bytes;
+        // chunk e (e < 8 S <= 152): elements e .. e + 7; all loads issued before the stores
+        uint4 chunk[kSegRegs][kParts];
+#pragma unroll
+        for (int j = 0; j < kSegRegs; ++j) {
+          const int e = lane + 32 * j;
 #pragma unroll
           for (int part = 0; part < kParts; ++part) {
-            const uint16_t *src = stg + (size_t)(2 * part + (e & 1)) * cstride + (e & ~1);
-            const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
-            uint4 chunk;
-            chunk.x = s32[0];
-            chunk.y = s32[1];
-            chunk.z = s32[2];
-            chunk.w = s32[3];
-            *reinterpret_cast<uint4 *>(hk + (size_t)part * pl.S * 128 + (size_t)e * 16) = chunk;
+            if (e < 8 * pl.S) {
+              const uint32_t *s32 =
+                  reinterpret_cast<const uint32_t *>(stg + (size_t)(2 * part + (e & 1)) * cstride + (e & ~1));
+              chunk[j][part] = make_uint4(s32[0], s32[1], s32[2], s32[3]);
+            }
           }
         }
+#pragma unroll
+        for (int j = 0; j < kSegRegs; ++j) {
+          const int e = lane + 32 * j;
+#pragma unroll
+          for (int part = 0; part < kParts; ++part)
+            if (e < 8 * pl.S) *reinterpret_cast<uint4 *>(hk + (size_t)part * pl.S * 128 + (size_t)e * 16) = chunk[j][part];
+        }
         fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full[stage]);
-        __syncwarp();
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[grp]);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < kSegRegs; ++j) cur[j] = nxt[j];
+      it = nx;
+      seq += nprod;
     }
   } else if (warp == kMmaWarp) {
     // ================================================================ MMA issuer
+    // Descriptors are built once; the start-address field is linear (units of 16 bytes),
+    // so every MMA's descriptors are a base descriptor plus an offset: the issuing
+    // thread spends a few integer instructions per MMA instead of rebuilding them.
     if (lane == 0) {
       if (!mbar_wait_bounded(tab_bar, 0, status)) goto drain;
       {
         const uint32_t idesc = idesc_f16(kFmt, kTileM, pl.nmma);
-        const uint32_t tab_h = smem_u32(sm + pl.off_tab_hi), tab_l = smem_u32(sm + pl.off_tab_lo);
-        const uint32_t stage0 = smem_u32(sm + pl.off_stage);
-        const uint32_t lbo_b = (uint32_t)pl.nrows * 16u;
-        uint32_t row_seq = 0, blk_seq = 0;
+        const uint32_t lbo_b = (uint32_t)pl.nrows * 16u, sbytes = (uint32_t)pl.stage_bytes;
+        const uint64_t dA = sdesc(smem_u32(sm + pl.off_stage), 128u, 128u);
+        const uint64_t dB = sdesc(smem_u32(sm + pl.off_tab_hi), lbo_b, 128u);
+        const uint64_t dAx = sdesc(smem_u32(sm + pl.off_stage) + (uint32_t)(pl.nG - 1) * 128u, sbytes, 128u);
+        const uint64_t dBx = sdesc(smem_u32(sm + pl.off_tab_hi) + (uint32_t)(pl.nG - 1) * lbo_b, (uint32_t)N * 16u, 128u);
+        const uint64_t oBl = (uint64_t)((pl.off_tab_lo - pl.off_tab_hi) >> 4);  // hi -> lo table
+        const uint64_t oAl = (uint64_t)((pl.S * 128) >> 4);                     // hi -> lo Hankel
+        const uint64_t oKs_a = 256u >> 4, oKs_b = (uint64_t)(2u * lbo_b) >> 4;  // one K step
+        const uint64_t oStage = sbytes >> 4, oSlice = (uint64_t)N;              // N rows x 16 B
+        const int inrow = (pl.nG - (pl.nG & 1)) / 2;  // K steps a paired row takes on its own
+        uint32_t row_seq = 0, blk_seq = 0, acc = 0, d_tmem = 0;
+        // K steps [0, nsteps) of the row whose Hankel tile is at descriptor a and whose
+        // basis window starts at descriptor b
+        auto row_mmas = [&](uint64_t a, uint64_t b, int nsteps) {
+          for (int ks = 0; ks < nsteps; ++ks, a += oKs_a, b += oKs_b) {
+            umma_f16(d_tmem, a, b, idesc, acc);
+            acc = 1;
+            if (kParts == 2) {
+              umma_f16(d_tmem, a, b + oBl, idesc, 1);
+              umma_f16(d_tmem, a + oAl, b, idesc, 1);
+            }
+          }
+        };
         for (int b = blockIdx.x; b < sc.nblocks; b += gridDim.x, ++blk_seq) {
           int x0, y0;
           sc.block(b, G, x0, y0);
           const int buf = blk_seq & 1;
           if (!mbar_wait_bounded(&acc_empty[buf], ((blk_seq >> 1) & 1) ^ 1, status)) goto drain;
           tc_fence_after();
-          const uint32_t d_tmem = tmem_base + (uint32_t)(buf * kAccStride);
-          uint32_t acc = 0;
-          const int r_lo = max(0, y0 - h), r_hi = min(H - 1, y0 + G - 1 + h);
-          for (int r = r_lo; r <= r_hi; ++r, ++row_seq) {
-            const int stage = row_seq % NS;
-            if (!mbar_wait_bounded(&full[stage], (row_seq / NS) & 1, status)) goto drain;
-            tc_fence_after();
-            const uint32_t a_h = stage0 + (uint32_t)(stage * kParts * pl.S * 128);
-            const uint32_t a_l = a_h + (uint32_t)(pl.S * 128);
-            const uint32_t rho0 = (uint32_t)((r - y0 + h) * N);
-            for (int ks = 0; ks < pl.nks; ++ks) {
-              const uint32_t boff = (uint32_t)(2 * ks) * lbo_b + rho0 * 16u;
-              const uint64_t ah = sdesc(a_h + (uint32_t)ks * 256u, 128u, 128u);
-              const uint64_t bh = sdesc(tab_h + boff, lbo_b, 128u);
-              umma_f16(d_tmem, ah, bh, idesc, acc);
-              acc = 1;
-              if (kParts == 2) {
-                const uint64_t al = sdesc(a_l + (uint32_t)ks * 256u, 128u, 128u);
-                const uint64_t bl = sdesc(tab_l + boff, lbo_b, 128u);
-                umma_f16(d_tmem, ah, bl, idesc, 1);
-                umma_f16(d_tmem, al, bh, idesc, 1);
+          d_tmem = tmem_base + (uint32_t)(buf * kAccStride);
+          acc = 0;
+          const int r_lo = max(0, y0 - h), n = min(H - 1, y0 + G - 1 + h) - r_lo + 1;
+          const int nseq = (n + kRowsPerGroup - 1) / kRowsPerGroup * kRowsPerGroup;
+          for (int i = 0; i < nseq; i += 2, row_seq += 2) {
+            const int sa = row_seq % NS, grp = sa / kRowsPerGroup;  // stages sa, sa + 1
+            if (sa % kRowsPerGroup == 0)
+              if (!mbar_wait_bounded(&full[grp], (row_seq / NS) & 1, status)) goto drain;
+            // shared-memory operands: ordered by the producers' proxy fence + mbarrier
+            const uint64_t a = dA + (uint64_t)sa * oStage;
+            const uint64_t bw = dB + (uint64_t)(r_lo + i - y0 + h) * oSlice;  // window of row r_lo + i
+            if (i + 1 < n) {
+              row_mmas(a, bw, inrow);
+              row_mmas(a + oStage, bw + oSlice, inrow);
+              if (pl.nG & 1) {
+                // last tap group of rows r_lo + i and r_lo + i + 1 in one K step
+                const uint64_t ax = dAx + (uint64_t)sa * oStage;
+                const uint64_t bx = dBx + (uint64_t)(r_lo + i - y0 + h) * oSlice;
+                umma_f16(d_tmem, ax, bx, idesc, acc);
+                acc = 1;
+                if (kParts == 2) {
+                  umma_f16(d_tmem, ax, bx + oBl, idesc, 1);
+                  umma_f16(d_tmem, ax + oAl, bx, idesc, 1);
+                }
               }
+            } else if (i < n) {
+              row_mmas(a, bw, pl.nKG / 2);  // the odd last row, padded by the zero group
             }
-            umma_commit(&empty[stage]);  // stage reusable once these MMAs have read it
+            if ((sa + 2) % kRowsPerGroup == 0) umma_commit(&empty[grp]);
           }
           umma_commit(&acc_full[buf]);
         }
@@ -396,68 +512,145 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ================================================================ epilogue
-    const int m = threadIdx.x;  // TMEM lane == pixel offset in the tile
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    // Eight warps: warp w reads TMEM lane quarter w % 4 (pixels 32 (w % 4) ..) and the
+    // output rows g of parity w / 4, so two warps share each scheduler and one's TMEM
+    // wait overlaps the other's arithmetic.
+    const int et = threadIdx.x;                       // 0 .. 255
+    const int m = (warp & 3) * 32 + lane, par = warp >> 2;
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
     uint32_t blk_seq = 0;
+    float inext[3];
+    {
+      int xf = 0, yf = 0;
+      sc.block(blockIdx.x, G, xf, yf);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int g = par + 2 * j;
+        inext[j] = (I && g < G && yf + g < H && xf + m < W) ? __ldg(I + (size_t)(yf + g) * pitch_I + xf + m) : 0.0f;
+      }
+    }
     for (int b = blockIdx.x; b < sc.nblocks; b += gridDim.x, ++blk_seq) {
       int x0, y0;
       sc.block(b, G, x0, y0);
-      // alpha[g][k][i] = sum_j c[k][(i,j)] yt^j : a_k(x, y) = sum_i alpha[g][k][i] xt^i
+      // alpha[g][k][i] = sum_j c[k][(i,j)] yt^j, so a_k(x, y0+g) = sum_i alpha[g][k][i] xt^i
       epi_bar_sync();
-      for (int e = m; e < G * N; e += 128) {
+      if (fast)
+        for (int e = et; e < G * 64; e += kEpiWarps * 32)
+          *reinterpret_cast<float4 *>(alphaS + (size_t)e * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+      epi_bar_sync();
+      for (int e = et; e < G * N; e += kEpiWarps * 32) {
         const int g = e / N, k = e % N, y = y0 + g;
         const float yt = H > 1 ? (2.0f * (float)y - (float)(H - 1)) / (float)(H - 1) : 0.0f;
-        float al[4] = {0.f, 0.f, 0.f, 0.f};
-        int t = 0;
-        for (int i = 0; i <= degree; ++i) {
-          float yj = 1.0f, s = 0.0f;
-          for (int j = 0; j <= degree - i; ++j, ++t) {
-            s = fmaf(coef[k * 10 + t], yj, s);
-            yj *= yt;
-          }
-          al[i] = s;
+        const float *ck = coef + k * 10;  // packed (i outer, j inner) for i + j <= degree
+        const float y2 = yt * yt, y3 = y2 * yt;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (degree == 0) {
+          a0 = ck[0];
+        } else if (degree == 1) {
+          a0 = ck[0] + ck[1] * yt;
+          a1 = ck[2];
+        } else if (degree == 2) {
+          a0 = ck[0] + ck[1] * yt + ck[2] * y2;
+          a1 = ck[3] + ck[4] * yt;
+          a2 = ck[5];
+        } else {
+          a0 = ck[0] + ck[1] * yt + ck[2] * y2 + ck[3] * y3;
+          a1 = ck[4] + ck[5] * yt + ck[6] * y2;
+          a2 = ck[7] + ck[8] * yt;
+          a3 = ck[9];
         }
-        *reinterpret_cast<float4 *>(alpha + (size_t)e * 4) = make_float4(al[0], al[1], al[2], al[3]);
+        *reinterpret_cast<float4 *>(alpha + (size_t)e * 4) = make_float4(a0, a1, a2, a3);
+        if (fast) {
+          // the same coefficients at the TMEM-load slot that carries column k
+          // (load i covers columns min(16 i, N - 16) .. + 15; each column used once)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int st = min(16 * i, N - 16), slot = k - st;
+            if (16 * i < N && slot >= 0 && slot < 16 && k >= 16 * i)
+              *reinterpret_cast<float4 *>(alphaS + ((size_t)g * 64 + 16 * i + slot) * 4) = make_float4(a0, a1, a2, a3);
+          }
+        }
       }
       epi_bar_sync();
       const int buf = blk_seq & 1;
-      if (!mbar_wait_bounded(&acc_full[buf], (blk_seq >> 1) & 1, status)) break;
-      tc_fence_after();
       const int x = x0 + m;
       const float xt = W > 1 ? (2.0f * (float)x - (float)(W - 1)) / (float)(W - 1) : 0.0f;
-      for (int g = 0; g < G; ++g) {
-        const int y = y0 + g;
-        if (y >= H) break;
-        const uint32_t col0 = (uint32_t)(buf * kAccStride + (G - 1 - g) * N);
-        float s = 0.0f;
-        // columns [col0, col0 + N): 16-column loads; the last load is moved back so it
-        // never reads past column col0 + N - 1 (keeps every read inside the allocation)
-        for (int kc = 0; kc < N; kc += 16) {
-          const int start = (kc + 16 <= N || N < 16) ? kc : N - 16;
-          uint32_t v[16];
-          if (N >= 16) {
-            tmem_ld16(tmem_base + lane_off + col0 + (uint32_t)start, v);
-          } else {
+      // I of this block was loaded during the previous block; start the next block's loads
+      float ival[3];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] = 0u;
-            for (int e = 0; e < N; ++e) v[e] = tmem_ld1(tmem_base + lane_off + col0 + (uint32_t)e);
+      for (int j = 0; j < 3; ++j) ival[j] = inext[j];
+      {
+        const int bn = b + gridDim.x;
+        int xn = 0, yn = 0;
+        if (bn < sc.nblocks) sc.block(bn, G, xn, yn);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int g = par + 2 * j;
+          inext[j] = (I && bn < sc.nblocks && g < G && yn + g < H && xn + m < W)
+                         ? __ldg(I + (size_t)(yn + g) * pitch_I + xn + m) : 0.0f;
+        }
+      }
+      if (!mbar_wait_bounded(&acc_full[buf], (blk_seq >> 1) & 1, status)) break;
+      tc_fence_after();
+      const uint32_t tbase = tmem_base + lane_off + (uint32_t)(buf * kAccStride);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int g = par + 2 * j;
+        if (g >= G || y0 + g >= H) break;
+        const uint32_t c0 = tbase + (uint32_t)((G - 1 - g) * N);
+        // sum_k a_k C_k = sum_i xt^i (sum_k alpha[g][k][i] C_k): four independent dot
+        // products over the accumulator columns, then Horner in xt
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        if (fast) {
+          // 16 <= N <= 64: four 16-column loads (the last one moved back to end at column
+          // N - 1) and one wait; coefficients in load-slot order, zeros in repeated slots
+          uint32_t v[64];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int st = 16 * i < N ? min(16 * i, N - 16) : 0;  // unused slots re-read chunk 0
+            tmem_ld16p(c0 + (uint32_t)st, &v[16 * i]);
           }
           tmem_ld_wait();
+          const float4 *ap = reinterpret_cast<const float4 *>(alphaS) + (size_t)g * 64;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int k = start + e;
-            if (k >= kc && k < N) {
-              const float4 a4 = *reinterpret_cast<const float4 *>(alpha + (size_t)(g * N + k) * 4);
-              const float ak = fmaf(fmaf(fmaf(a4.w, xt, a4.z), xt, a4.y), xt, a4.x);
-              s = fmaf(ak, __uint_as_float(v[e]), s);
+          for (int q = 0; q < 64; ++q) {
+            const float4 a = ap[q];
+            const float cv = __uint_as_float(v[q]);
+            s0 = fmaf(a.x, cv, s0);
+            s1 = fmaf(a.y, cv, s1);
+            s2 = fmaf(a.z, cv, s2);
+            s3 = fmaf(a.w, cv, s3);
+          }
+        } else {
+          const float4 *a4 = reinterpret_cast<const float4 *>(alpha) + (size_t)g * N;
+          const int nfull = N >> 4, tail = N & 15;
+          for (int cc = 0; cc < nfull; ++cc) {
+            uint32_t v[16];
+            tmem_ld16(c0 + (uint32_t)(cc * 16), v);
+            tmem_ld_wait();
+            const float4 *ap = a4 + cc * 16;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const float4 a = ap[e];
+              const float cv = __uint_as_float(v[e]);
+              s0 = fmaf(a.x, cv, s0);
+              s1 = fmaf(a.y, cv, s1);
+              s2 = fmaf(a.z, cv, s2);
+              s3 = fmaf(a.w, cv, s3);
             }
           }
+          for (int e = 0; e < tail; ++e) {  // the last N mod 16 columns, one per load
+            const float cv = __uint_as_float(tmem_ld1(c0 + (uint32_t)(nfull * 16 + e)));
+            const float4 a = a4[nfull * 16 + e];
+            s0 = fmaf(a.x, cv, s0);
+            s1 = fmaf(a.y, cv, s1);
+            s2 = fmaf(a.z, cv, s2);
+            s3 = fmaf(a.w, cv, s3);
+          }
+          tmem_ld_wait();
         }
-        if (x < W) {
-          float o = s * out_scale;
-          if (I) o -= I[(size_t)y * pitch_I + x];
-          out[(size_t)y * pitch_out + x] = o;
-        }
+        const float sres = fmaf(fmaf(fmaf(s3, xt, s2), xt, s1), xt, s0);
+        if (x < W) out[(size_t)(y0 + g) * pitch_out + x] = sres * out_scale - ival[j];
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[buf]);

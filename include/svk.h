@@ -147,6 +147,23 @@ SVK_API int svk_difference(const float *R, int pitch_R, const float *I, int pitc
                    size_t ws_bytes, void *stream);
 
 /*
+ * D = (R (x) K_{x,y}) - I by the tensor-core basis form, allocating no device memory.
+ * The paper has no counterpart: this is an interface for callers that cannot allocate --
+ * a host application that owns the whole device heap, a pipeline that must not
+ * allocate (or risk a failed allocation) once it is running, or a caller with no way
+ * to pass a workspace.  Arguments as svk_difference with method SVK_METHOD_BASIS
+ * (precision SVK_PREC_BF16X3 / FP16X3 / BF16) and no workspace.
+ * Scratch: one 512 KiB __device__ array inside this library, held on every device that
+ * loads it until the process exits; requests needing more return SVK_ERR_WORKSPACE.
+ * The first call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents, so calls that overlap on the GPU race: serialise them.
+ */
+SVK_API int svk_difference_noalloc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
+                                   const float *basis, int N, int L, const float *coeffs, int degree,
+                                   int precision, int edge, float *D, int pitch_D, void *stream);
+
+/*
  * Bytes of device workspace svk_fit_coeffs needs.
  */
 SVK_API size_t svk_fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree,

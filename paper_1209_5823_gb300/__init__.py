@@ -35,7 +35,7 @@ SVK_EDGE_ZERO = 0
 # every symbol include/svk.h declares (checked by the tests)
 EXPORTS = (
     "svk_last_error", "svk_version", "svk_gauss_basis_count", "svk_build_basis", "svk_workspace_size",
-    "svk_convolve", "svk_difference", "svk_fit_workspace_size", "svk_fit_coeffs",
+    "svk_convolve", "svk_difference", "svk_fit_workspace_size", "svk_fit_coeffs", "svk_difference_noalloc",
 )
 
 
@@ -68,6 +68,7 @@ def load_library(path: str | None = None):
         "svk_difference": (i, [vp, i, vp, i, i, i, vp, i, i, vp, i, i, i, i, vp, i, vp, sz, vp]),
         "svk_fit_workspace_size": (sz, [i, i, i, i, i, i]),
         "svk_fit_coeffs": (i, [vp, vp, i, i, i, vp, i, i, vp, i, i, i, i, vp, vp, vp, vp, vp, sz, i, vp]),
+        "svk_difference_noalloc": (i, [vp, i, vp, i, i, i, vp, i, i, vp, i, i, i, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -171,6 +172,30 @@ def svk_difference(R, I, basis, coeffs, degree: int, method: int = SVK_METHOD_DI
     _check(load_library().svk_difference(_ptr(R), pR, _ptr(I), pI, W, H, _ptr(basis), N, L, _ptr(coeffs),
                                          int(degree), int(method), int(precision), int(edge), _ptr(out), pD,
                                          _ptr(workspace), ws_bytes, _stream(stream)))
+    return out
+
+
+def svk_difference_noalloc(R, I, basis, coeffs, degree: int, precision: int = SVK_PREC_BF16X3, out=None,
+                           stream=None, edge: int = SVK_EDGE_ZERO):
+    """D = (R (x) K_{x,y}) - I by the tensor-core basis form without any device allocation.
+
+    For callers that cannot allocate device memory while they run (their heap is owned by
+    a host application, or allocation is not allowed after start-up): the library uses
+    one built-in 512 KiB scratch array instead of a workspace.  Calls share that array,
+    so overlapping calls on the GPU must be serialised by the caller.
+    """
+    import torch
+    H, W, pR = _img(R, "R")
+    H2, W2, pI = _img(I, "I")
+    if (H2, W2) != (H, W):
+        raise ValueError("R and I differ in size")
+    N, L = basis.shape[0], basis.shape[1]
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=R.device)
+    _, _, pD = _img(out, "D")
+    _check(load_library().svk_difference_noalloc(_ptr(R), pR, _ptr(I), pI, W, H, _ptr(basis), N, L, _ptr(coeffs),
+                                                 int(degree), int(precision), int(edge), _ptr(out), pD,
+                                                 _stream(stream)))
     return out
 
 

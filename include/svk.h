@@ -164,6 +164,49 @@ SVK_API int svk_difference_noalloc(const float *R, int pitch_R, const float *I, 
                                    int precision, int edge, float *D, int pitch_D, void *stream);
 
 /*
+ * One frame of a batch: D = (R (x) K_{x,y}) - I (I may be NULL: D = R (x) K_{x,y}).
+ * Pointers are device memory; field meanings as in svk_difference.
+ */
+typedef struct svk_frame {
+  const float *R;
+  int pitch_R;
+  const float *I;
+  int pitch_I;
+  float *D;
+  int pitch_D;
+  int W, H;
+  const float *basis;
+  int N, L;
+  const float *coeffs;
+  int degree;
+} svk_frame;
+
+/* Bytes of device workspace svk_difference_batch needs for these frames (0 on error). */
+SVK_API size_t svk_batch_workspace_size(const svk_frame *frames, int n_frames, int precision);
+
+/*
+ * A night's batch of uneven frames (Sec. 3: a wide-field camera delivers many tiles per
+ * exposure) by the tensor-core basis form.  Frames are grouped by (N, L); each group
+ * runs as persistent launches over up to 64 frames whose blocks are split into
+ * contiguous ranges per CTA, every frame with its own size, degree, coefficients and
+ * basis (frames sharing one basis pointer share its tables).  `frames` is a HOST array
+ * of n_frames >= 1 descriptors, read during the call.  With a workspace the call issues
+ * only kernel launches and memsets on `stream`, so it can be captured in a CUDA graph
+ * and replayed.  Errors as svk_difference, checked for every frame before any launch.
+ */
+SVK_API int svk_difference_batch(const svk_frame *frames, int n_frames, int precision, void *workspace,
+                                 size_t ws_bytes, void *stream);
+
+/*
+ * Time every tensor-core plan (output rows per block G in 1..5, pipeline stages 4 or 8)
+ * on a synthetic W x H frame for (N, L, degree, precision), keep the fastest for later
+ * calls with that (N, L, precision) in this process, and report it through G_out /
+ * stages_out (nullable).  Allocates its test buffers on `stream` and synchronises it.
+ */
+SVK_API int svk_autotune(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out,
+                         void *stream);
+
+/*
  * Bytes of device workspace svk_fit_coeffs needs.
  */
 SVK_API size_t svk_fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree,

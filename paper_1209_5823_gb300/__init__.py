@@ -36,7 +36,16 @@ SVK_EDGE_ZERO = 0
 EXPORTS = (
     "svk_last_error", "svk_version", "svk_gauss_basis_count", "svk_build_basis", "svk_workspace_size",
     "svk_convolve", "svk_difference", "svk_fit_workspace_size", "svk_fit_coeffs", "svk_difference_noalloc",
+    "svk_batch_workspace_size", "svk_difference_batch", "svk_autotune",
 )
+
+
+class svk_frame(ctypes.Structure):
+    """struct svk_frame of include/svk.h (device pointers, pitches in elements)."""
+    _fields_ = [("R", ctypes.c_void_p), ("pitch_R", ctypes.c_int), ("I", ctypes.c_void_p), ("pitch_I", ctypes.c_int),
+                ("D", ctypes.c_void_p), ("pitch_D", ctypes.c_int), ("W", ctypes.c_int), ("H", ctypes.c_int),
+                ("basis", ctypes.c_void_p), ("N", ctypes.c_int), ("L", ctypes.c_int), ("coeffs", ctypes.c_void_p),
+                ("degree", ctypes.c_int)]
 
 
 class SvkError(RuntimeError):
@@ -69,6 +78,9 @@ def load_library(path: str | None = None):
         "svk_fit_workspace_size": (sz, [i, i, i, i, i, i]),
         "svk_fit_coeffs": (i, [vp, vp, i, i, i, vp, i, i, vp, i, i, i, i, vp, vp, vp, vp, vp, sz, i, vp]),
         "svk_difference_noalloc": (i, [vp, i, vp, i, i, i, vp, i, i, vp, i, i, i, vp, i, vp]),
+        "svk_batch_workspace_size": (sz, [vp, i, i]),
+        "svk_difference_batch": (i, [vp, i, i, vp, sz, vp]),
+        "svk_autotune": (i, [i, i, i, i, i, i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -197,6 +209,43 @@ def svk_difference_noalloc(R, I, basis, coeffs, degree: int, precision: int = SV
                                                  int(degree), int(precision), int(edge), _ptr(out), pD,
                                                  _stream(stream)))
     return out
+
+
+def _frames(items):
+    """items: sequence of dicts with R, I (or None), D, basis, coeffs, degree (torch tensors)."""
+    arr = (svk_frame * len(items))()
+    for k, it in enumerate(items):
+        H, W, pR = _img(it["R"], "R")
+        _, _, pD = _img(it["D"], "D")
+        pI = _img(it["I"], "I")[2] if it.get("I") is not None else W
+        b = it["basis"]
+        arr[k] = svk_frame(it["R"].data_ptr(), pR, it["I"].data_ptr() if it.get("I") is not None else None, pI,
+                           it["D"].data_ptr(), pD, W, H, b.data_ptr(), b.shape[0], b.shape[1],
+                           it["coeffs"].data_ptr(), int(it["degree"]))
+    return arr
+
+
+def svk_batch_workspace_size(items, precision: int = SVK_PREC_BF16X3) -> int:
+    arr = _frames(items)
+    return int(load_library().svk_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), len(items), int(precision)))
+
+
+def svk_difference_batch(items, precision: int = SVK_PREC_BF16X3, workspace=None, stream=None):
+    """D = (R (x) K) - I for every frame of `items` (dicts of CUDA tensors) in grouped
+    persistent launches; each item's "D" tensor receives its result."""
+    arr = _frames(items)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_difference_batch(ctypes.cast(arr, ctypes.c_void_p), len(items), int(precision),
+                                               _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def svk_autotune(N: int, L: int, degree: int, precision: int = SVK_PREC_BF16X3, W: int = 2048, H: int = 1024,
+                 stream=None):
+    """Time the tensor-core plans for (N, L, degree, precision); returns (G, stages) chosen."""
+    g, st = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load_library().svk_autotune(int(N), int(L), int(degree), int(precision), int(W), int(H),
+                                       ctypes.byref(g), ctypes.byref(st), _stream(stream)))
+    return g.value, st.value
 
 
 def svk_fit_workspace_size(n_stamps: int, stamp_size: int, N: int, L: int, degree: int, bg_degree: int) -> int:

@@ -187,6 +187,47 @@ int svk_difference(const float *R, int pitch_R, const float *I, int pitch_I, int
                   pitch_D, workspace, ws_bytes, stream, true);
 }
 
+static int check_batch(const svk_frame *frames, int n_frames, int precision) {
+  if (!frames || n_frames < 1) return set_error(SVK_ERR_ARG, "empty frame list");
+  for (int i = 0; i < n_frames; ++i) {
+    const svk_frame &f = frames[i];
+    const int st = check_conv_args(f.R, f.pitch_R, f.I, f.I ? f.pitch_I : f.W, f.W, f.H, f.basis, f.N, f.L, f.coeffs,
+                                   f.degree, SVK_METHOD_BASIS, precision, SVK_EDGE_ZERO, f.D, f.pitch_D, false);
+    if (st != SVK_OK) {
+      char msg[512];
+      snprintf(msg, sizeof(msg), "%s", svk::last_error());
+      return set_error(st, "frame %d: %s", i, msg);
+    }
+  }
+  return SVK_OK;
+}
+
+size_t svk_batch_workspace_size(const svk_frame *frames, int n_frames, int precision) {
+  if (check_batch(frames, n_frames, precision) != SVK_OK) return 0;
+  return batch_workspace_size(frames, n_frames, precision);
+}
+
+int svk_difference_batch(const svk_frame *frames, int n_frames, int precision, void *workspace, size_t ws_bytes,
+                         void *stream) {
+  int st = check_batch(frames, n_frames, precision);
+  if (st != SVK_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScopedWorkspace w;
+  const size_t need = batch_workspace_size(frames, n_frames, precision);
+  st = w.acquire(need, workspace, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  return launch_batch(frames, n_frames, precision, w.ptr, need, s);
+}
+
+int svk_autotune(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out, void *stream) {
+  if (precision != SVK_PREC_BF16X3 && precision != SVK_PREC_FP16X3 && precision != SVK_PREC_BF16)
+    return set_error(SVK_ERR_UNSUPPORTED, "autotune covers the tensor-core precisions only");
+  if (N < 1 || N > 256 || L < 1 || L > 31 || (L % 2) == 0 || degree < 0 || degree > 3 || W < 1 || H < 1 ||
+      W > 65535 || H > 65535)
+    return set_error(SVK_ERR_ARG, "bad autotune problem");
+  return autotune_tc(N, L, degree, precision, W, H, G_out, stages_out, static_cast<cudaStream_t>(stream));
+}
+
 size_t svk_fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree, int bg_degree) {
   return fit_workspace_size(n_stamps, stamp_size, N, L, degree, bg_degree);
 }

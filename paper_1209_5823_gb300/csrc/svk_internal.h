@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "svk.h"
+
 namespace svk {
 
 // Direct form (svk_direct.cu): kernel of Eq. 2 formed at every output pixel, FP32 FFMA.
@@ -21,6 +23,10 @@ size_t tc_workspace_size(int precision, int N, int L);
 int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
               const float *basis, int N, int L, const float *coeffs, int degree, int precision,
               float *out, int pitch_out, void *ws, size_t ws_bytes, cudaStream_t s);
+
+int launch_batch(const svk_frame *frames, int n, int precision, void *ws, size_t ws_bytes, cudaStream_t s);
+size_t batch_workspace_size(const svk_frame *frames, int n, int precision);
+int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out, cudaStream_t s);
 
 // Least-squares fit (svk_fit.cu).
 size_t fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree, int bg_degree);

@@ -52,6 +52,12 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "svk_common.cuh"
 #include "svk_internal.h"
 
@@ -134,10 +140,11 @@ static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
 }
 
 static bool choose_plan(int N, int L, int prec, Plan *p) {
-  // two handshake groups in flight first (producers fill one while the MMAs drain the
-  // other), then the widest MMA that fits
-  for (int NS = kMaxStages; NS >= kRowsPerGroup; NS -= kRowsPerGroup)
-    for (int G = 5; G >= 1; --G)
+  // the widest MMA (most output rows per block) that fits, with two handshake groups in
+  // flight when they fit (producers fill one while the MMAs drain the other); the
+  // autotuner replaces this default by measurement
+  for (int G = 5; G >= 1; --G)
+    for (int NS = kMaxStages; NS >= kRowsPerGroup; NS -= kRowsPerGroup)
       if (make_plan(N, L, prec, G, NS, p)) return true;
   return false;
 }
@@ -225,34 +232,64 @@ __device__ __forceinline__ void split16(float x, uint16_t &hi, uint16_t &lo) {
   }
 }
 
-// ----------------------------------------------------------------- block schedule
-struct Sched {
-  int nbx, nby, nblocks;
-  __device__ void block(int b, int G, int &x0, int &y0) const {
-    x0 = (b % nbx) * kTileM;
-    y0 = (b / nbx) * G;
-  }
+// ----------------------------------------------------------------- frames and blocks
+// A launch processes a set of frames that share one plan (same N, L, precision): every
+// frame's blocks are numbered consecutively from its block0, and each persistent CTA
+// takes a contiguous range of that block space.  The set travels as a __grid_constant__
+// kernel parameter, so a launch (or a CUDA graph of launches) needs no descriptor copy.
+constexpr int kMaxFrames = 64;
+
+struct FrameDesc {
+  const float *R, *I;
+  float *out;
+  const float *coeffs;
+  const uint4 *tab_hi, *tab_lo;  // this frame's basis tables (shared by frames with one basis)
+  int W, H, pitch_R, pitch_I, pitch_out, degree;
+  int nbx, block0;  // blocks per band of G rows; first block of the frame in the set
+  float rscale, out_scale;
 };
+
+struct FrameSet {
+  int n, nblocks;
+  FrameDesc fr[kMaxFrames];
+};
+
+__device__ __forceinline__ int advance_frame(const FrameSet &fs, int f, int b) {
+  while (f + 1 < fs.n && b >= fs.fr[f + 1].block0) ++f;
+  return f;
+}
+
+__device__ __forceinline__ void block_origin(const FrameDesc &fd, int b, int G, int &x0, int &y0) {
+  const int lb = b - fd.block0;
+  x0 = (lb % fd.nbx) * kTileM;
+  y0 = (lb / fd.nbx) * G;
+}
+
+__device__ __forceinline__ void cta_block_range(const FrameSet &fs, int &b0, int &b1) {
+  b0 = (int)((long long)blockIdx.x * fs.nblocks / gridDim.x);
+  b1 = (int)((long long)(blockIdx.x + 1) * fs.nblocks / gridDim.x);
+}
 
 // The CTA's sequence of reference rows: for each of its blocks the rows
 // max(0, y0-h) .. min(H-1, y0+G-1+h), padded with empty slots to a multiple of
 // kRowsPerGroup.
 struct RowIt {
-  int b, i, n, nseq, r_lo, x0, y0;
-  __device__ void set_block(int bb, const Sched &sc, int G, int h, int H) {
+  int b, b_end, f, i, n, nseq, r_lo, x0, y0;
+  __device__ void set_block(const FrameSet &fs, int bb, int G, int h) {
     b = bb;
     i = 0;
-    if (b < sc.nblocks) {
-      sc.block(b, G, x0, y0);
+    if (b < b_end) {
+      f = advance_frame(fs, f, b);
+      block_origin(fs.fr[f], b, G, x0, y0);
       r_lo = max(0, y0 - h);
-      n = min(H - 1, y0 + G - 1 + h) - r_lo + 1;
+      n = min(fs.fr[f].H - 1, y0 + G - 1 + h) - r_lo + 1;
       nseq = (n + kRowsPerGroup - 1) / kRowsPerGroup * kRowsPerGroup;
     }
   }
-  __device__ void next(const Sched &sc, int G, int h, int H) {
-    if (++i >= nseq) set_block(b + gridDim.x, sc, G, h, H);
+  __device__ void next(const FrameSet &fs, int G, int h) {
+    if (++i >= nseq) set_block(fs, b + 1, G, h);
   }
-  __device__ bool valid(const Sched &sc) const { return b < sc.nblocks; }
+  __device__ bool valid() const { return b < b_end; }
   __device__ bool real() const { return i < n; }
   __device__ int row() const { return r_lo + i; }
 };
@@ -291,19 +328,15 @@ __global__ void tc_prep_table(const float *__restrict__ basis, Plan pl, float bs
 // ----------------------------------------------------------------- main kernel
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_basis_kernel(const float *__restrict__ R, int pitch_R, const float *__restrict__ I, int pitch_I, int W,
-                    int H, const float *__restrict__ coeffs, int degree, float *__restrict__ out, int pitch_out,
-                    const uint4 *__restrict__ tab_hi, const uint4 *__restrict__ tab_lo, Plan pl, Sched sc,
-                    float rscale, float out_scale, uint32_t *status) {
+    tc_basis_kernel(const __grid_constant__ FrameSet fs, const Plan pl, uint32_t *status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   constexpr int kParts = (PREC == SVK_PREC_BF16) ? 1 : 2;
   constexpr int kFmt = (PREC == SVK_PREC_FP16X3) ? 0 : 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int N = pl.N, G = pl.G, h = pl.h, T = n_terms(degree);
+  const int N = pl.N, G = pl.G, h = pl.h, NS = pl.NS;
 
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + pl.off_bar);
-  const int NS = pl.NS;
   uint64_t *full = bars, *empty = bars + kMaxStages, *acc_full = bars + 2 * kMaxStages,
            *acc_empty = acc_full + 2, *tab_bar = acc_empty + 2, *drain_bar = tab_bar + 1;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain_bar + 1);
@@ -311,6 +344,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   float *alpha = reinterpret_cast<float *>(sm + pl.off_alpha);
   float *alphaS = reinterpret_cast<float *>(sm + pl.off_alphaS);
   const bool fast = (N >= 16 && N <= 64);
+  int b_begin, b_end;
+  cta_block_range(fs, b_begin, b_end);
 
   // ---- set-up
   if (warp == kMmaWarp) {
@@ -327,23 +362,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(tab_bar, 1);
       mbar_init(drain_bar, 1);
       fence_mbar_init();
-      // the basis tables, once per CTA (bulk copies of <= 32 KB)
-      const uint32_t total = (uint32_t)(pl.table_bytes * kParts);
-      mbar_arrive_expect_tx(tab_bar, total);
-      for (int part = 0; part < kParts; ++part) {
-        const unsigned char *src = reinterpret_cast<const unsigned char *>(part ? tab_lo : tab_hi);
-        unsigned char *dst = sm + (part ? pl.off_tab_lo : pl.off_tab_hi);
-        for (size_t o = 0; o < pl.table_bytes; o += 32768) {
-          const uint32_t n = (uint32_t)((pl.table_bytes - o) < 32768 ? (pl.table_bytes - o) : 32768);
-          bulk_load(dst + o, src + o, n, tab_bar);
-        }
-      }
-    }
-  }
-  if (warp < kEpiWarps) {
-    for (int i = threadIdx.x; i < N * 10; i += kEpiWarps * 32) {
-      const int k = i / 10, t = i % 10;
-      coef[i] = (t < T) ? coeffs[(size_t)k * T + t] : 0.0f;
     }
   }
   tc_fence_before();
@@ -363,24 +381,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int cstride = rup(pl.seglen * 2 + 16, 16) / 2;  // elements between staging copies
     uint16_t *stg = reinterpret_cast<uint16_t *>(sm + pl.off_stg) + (size_t)pw * kParts * 2 * cstride;
     RowIt it;
-    it.set_block(blockIdx.x, sc, G, h, H);
-    for (int k = 0; k < pw && it.valid(sc); ++k) it.next(sc, G, h, H);
+    it.b_end = b_end;
+    it.f = 0;
+    it.set_block(fs, b_begin, G, h);
+    for (int k = 0; k < pw && it.valid(); ++k) it.next(fs, G, h);
     uint32_t seq = (uint32_t)pw;
     float cur[kSegRegs], nxt[kSegRegs];
     auto load_row = [&](const RowIt &ri, float (&v)[kSegRegs]) {
-      const float *rrow = R + (size_t)ri.row() * pitch_R;
+      const FrameDesc &fd = fs.fr[ri.f];
+      const float *rrow = fd.R + (size_t)ri.row() * fd.pitch_R;
       const int xb = ri.x0 - h;
 #pragma unroll
       for (int j = 0; j < kSegRegs; ++j) {
         const int e = lane + 32 * j, gx = xb + e;
-        v[j] = (e < pl.seglen && gx >= 0 && gx < W) ? __ldg(rrow + gx) * rscale : 0.0f;
+        v[j] = (e < pl.seglen && gx >= 0 && gx < fd.W) ? __ldg(rrow + gx) * fd.rscale : 0.0f;
       }
     };
-    if (it.valid(sc) && it.real()) load_row(it, cur);
-    while (it.valid(sc)) {
+    if (it.valid() && it.real()) load_row(it, cur);
+    while (it.valid()) {
       RowIt nx = it;
-      for (int k = 0; k < nprod && nx.valid(sc); ++k) nx.next(sc, G, h, H);
-      if (nx.valid(sc) && nx.real()) load_row(nx, nxt);  // in flight while this row is built
+      for (int k = 0; k < nprod && nx.valid(); ++k) nx.next(fs, G, h);
+      if (nx.valid() && nx.real()) load_row(nx, nxt);  // in flight while this row is built
       const int stage = seq % NS, grp = stage / kRowsPerGroup;
       if (!mbar_wait_bounded(&empty[grp], ((seq / NS) & 1) ^ 1, status)) goto done;
       if (it.real()) {
@@ -438,8 +459,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Descriptors are built once; the start-address field is linear (units of 16 bytes),
     // so every MMA's descriptors are a base descriptor plus an offset: the issuing
     // thread spends a few integer instructions per MMA instead of rebuilding them.
+    uint32_t drain_phase = 0;
     if (lane == 0) {
-      if (!mbar_wait_bounded(tab_bar, 0, status)) goto drain;
       {
         const uint32_t idesc = idesc_f16(kFmt, kTileM, pl.nmma);
         const uint32_t lbo_b = (uint32_t)pl.nrows * 16u, sbytes = (uint32_t)pl.stage_bytes;
@@ -452,7 +473,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint64_t oKs_a = 256u >> 4, oKs_b = (uint64_t)(2u * lbo_b) >> 4;  // one K step
         const uint64_t oStage = sbytes >> 4, oSlice = (uint64_t)N;              // N rows x 16 B
         const int inrow = (pl.nG - (pl.nG & 1)) / 2;  // K steps a paired row takes on its own
-        uint32_t row_seq = 0, blk_seq = 0, acc = 0, d_tmem = 0;
+        uint32_t row_seq = 0, blk_seq = 0, acc = 0, d_tmem = 0, tab_phase = 0;
+        const uint4 *loaded = nullptr;
+        // the frame's basis tables into shared memory, once every MMA that reads the
+        // tables now there has completed (frames with one basis share their tables)
+        auto load_tables = [&](const FrameDesc &fd) -> bool {
+          if (fd.tab_hi == loaded) return true;
+          if (loaded) {
+            umma_commit(drain_bar);
+            if (!mbar_wait_bounded(drain_bar, drain_phase, status)) return false;
+            drain_phase ^= 1;
+          }
+          mbar_arrive_expect_tx(tab_bar, (uint32_t)(pl.table_bytes * kParts));
+          for (int part = 0; part < kParts; ++part) {
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(part ? fd.tab_lo : fd.tab_hi);
+            unsigned char *dst = sm + (part ? pl.off_tab_lo : pl.off_tab_hi);
+            for (size_t o = 0; o < pl.table_bytes; o += 32768) {
+              const uint32_t n = (uint32_t)((pl.table_bytes - o) < 32768 ? (pl.table_bytes - o) : 32768);
+              bulk_load(dst + o, src + o, n, tab_bar);
+            }
+          }
+          if (!mbar_wait_bounded(tab_bar, tab_phase, status)) return false;
+          tab_phase ^= 1;
+          loaded = fd.tab_hi;
+          return true;
+        };
         // K steps [0, nsteps) of the row whose Hankel tile is at descriptor a and whose
         // basis window starts at descriptor b
         auto row_mmas = [&](uint64_t a, uint64_t b, int nsteps) {
@@ -465,15 +510,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         };
-        for (int b = blockIdx.x; b < sc.nblocks; b += gridDim.x, ++blk_seq) {
+        int f = 0;
+        for (int b = b_begin; b < b_end; ++b, ++blk_seq) {
+          f = advance_frame(fs, f, b);
+          const FrameDesc &fd = fs.fr[f];
+          if (!load_tables(fd)) goto drain;
           int x0, y0;
-          sc.block(b, G, x0, y0);
+          block_origin(fd, b, G, x0, y0);
           const int buf = blk_seq & 1;
           if (!mbar_wait_bounded(&acc_empty[buf], ((blk_seq >> 1) & 1) ^ 1, status)) goto drain;
           tc_fence_after();
           d_tmem = tmem_base + (uint32_t)(buf * kAccStride);
           acc = 0;
-          const int r_lo = max(0, y0 - h), n = min(H - 1, y0 + G - 1 + h) - r_lo + 1;
+          const int r_lo = max(0, y0 - h), n = min(fd.H - 1, y0 + G - 1 + h) - r_lo + 1;
           const int nseq = (n + kRowsPerGroup - 1) / kRowsPerGroup * kRowsPerGroup;
           for (int i = 0; i < nseq; i += 2, row_seq += 2) {
             const int sa = row_seq % NS, grp = sa / kRowsPerGroup;  // stages sa, sa + 1
@@ -507,7 +556,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     drain:
       // every MMA issued by this thread has completed before TMEM is released
       umma_commit(drain_bar);
-      mbar_wait_bounded(drain_bar, 0, status);
+      mbar_wait_bounded(drain_bar, drain_phase, status);
     }
     __syncwarp();
   } else {
@@ -515,32 +564,48 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Eight warps: warp w reads TMEM lane quarter w % 4 (pixels 32 (w % 4) ..) and the
     // output rows g of parity w / 4, so two warps share each scheduler and one's TMEM
     // wait overlaps the other's arithmetic.
-    const int et = threadIdx.x;                       // 0 .. 255
+    const int et = threadIdx.x;  // 0 .. 255
     const int m = (warp & 3) * 32 + lane, par = warp >> 2;
     const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
     uint32_t blk_seq = 0;
+    int f = 0, coef_frame = -1;
     float inext[3];
-    {
-      int xf = 0, yf = 0;
-      sc.block(blockIdx.x, G, xf, yf);
+    auto load_I = [&](int b, int fi, float (&v)[3]) {
+      int xq = 0, yq = 0;
+      const bool ok = b < b_end;
+      const FrameDesc &fq = fs.fr[fi];
+      if (ok) block_origin(fq, b, G, xq, yq);
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int g = par + 2 * j;
-        inext[j] = (I && g < G && yf + g < H && xf + m < W) ? __ldg(I + (size_t)(yf + g) * pitch_I + xf + m) : 0.0f;
+        v[j] = (ok && fq.I && g < G && yq + g < fq.H && xq + m < fq.W)
+                   ? __ldg(fq.I + (size_t)(yq + g) * fq.pitch_I + xq + m) : 0.0f;
       }
-    }
-    for (int b = blockIdx.x; b < sc.nblocks; b += gridDim.x, ++blk_seq) {
+    };
+    if (b_begin < b_end) load_I(b_begin, advance_frame(fs, 0, b_begin), inext);
+    for (int b = b_begin; b < b_end; ++b, ++blk_seq) {
+      f = advance_frame(fs, f, b);
+      const FrameDesc &fd = fs.fr[f];
       int x0, y0;
-      sc.block(b, G, x0, y0);
-      // alpha[g][k][i] = sum_j c[k][(i,j)] yt^j, so a_k(x, y0+g) = sum_i alpha[g][k][i] xt^i
+      block_origin(fd, b, G, x0, y0);
+      const int degree = fd.degree;
       epi_bar_sync();
+      if (f != coef_frame) {  // this frame's coefficients c[k][t], packed per stamp
+        const int T = n_terms(degree);
+        for (int i = et; i < N * 10; i += kEpiWarps * 32) {
+          const int k = i / 10, t = i % 10;
+          coef[i] = (t < T) ? fd.coeffs[(size_t)k * T + t] : 0.0f;
+        }
+        coef_frame = f;
+      }
       if (fast)
         for (int e = et; e < G * 64; e += kEpiWarps * 32)
           *reinterpret_cast<float4 *>(alphaS + (size_t)e * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
       epi_bar_sync();
+      // alpha[g][k][i] = sum_j c[k][(i,j)] yt^j, so a_k(x, y0+g) = sum_i alpha[g][k][i] xt^i
       for (int e = et; e < G * N; e += kEpiWarps * 32) {
         const int g = e / N, k = e % N, y = y0 + g;
-        const float yt = H > 1 ? (2.0f * (float)y - (float)(H - 1)) / (float)(H - 1) : 0.0f;
+        const float yt = fd.H > 1 ? (2.0f * (float)y - (float)(fd.H - 1)) / (float)(fd.H - 1) : 0.0f;
         const float *ck = coef + k * 10;  // packed (i outer, j inner) for i + j <= degree
         const float y2 = yt * yt, y3 = y2 * yt;
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -574,29 +639,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       epi_bar_sync();
       const int buf = blk_seq & 1;
       const int x = x0 + m;
-      const float xt = W > 1 ? (2.0f * (float)x - (float)(W - 1)) / (float)(W - 1) : 0.0f;
+      const float xt = fd.W > 1 ? (2.0f * (float)x - (float)(fd.W - 1)) / (float)(fd.W - 1) : 0.0f;
       // I of this block was loaded during the previous block; start the next block's loads
       float ival[3];
 #pragma unroll
       for (int j = 0; j < 3; ++j) ival[j] = inext[j];
-      {
-        const int bn = b + gridDim.x;
-        int xn = 0, yn = 0;
-        if (bn < sc.nblocks) sc.block(bn, G, xn, yn);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const int g = par + 2 * j;
-          inext[j] = (I && bn < sc.nblocks && g < G && yn + g < H && xn + m < W)
-                         ? __ldg(I + (size_t)(yn + g) * pitch_I + xn + m) : 0.0f;
-        }
-      }
+      if (b + 1 < b_end) load_I(b + 1, advance_frame(fs, f, b + 1), inext);
       if (!mbar_wait_bounded(&acc_full[buf], (blk_seq >> 1) & 1, status)) break;
       tc_fence_after();
       const uint32_t tbase = tmem_base + lane_off + (uint32_t)(buf * kAccStride);
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int g = par + 2 * j;
-        if (g >= G || y0 + g >= H) break;
+        if (g >= G || y0 + g >= fd.H) break;
         const uint32_t c0 = tbase + (uint32_t)((G - 1 - g) * N);
         // sum_k a_k C_k = sum_i xt^i (sum_k alpha[g][k][i] C_k): four independent dot
         // products over the accumulator columns, then Horner in xt
@@ -650,7 +705,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld_wait();
         }
         const float sres = fmaf(fmaf(fmaf(s3, xt, s2), xt, s1), xt, s0);
-        if (x < W) out[(size_t)(y0 + g) * pitch_out + x] = sres * out_scale - ival[j];
+        if (x < fd.W) fd.out[(size_t)(y0 + g) * fd.pitch_out + x] = sres * fd.out_scale - ival[j];
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[buf]);
@@ -665,9 +720,154 @@ done:
 
 }  // namespace
 
+// ================================================================== host side
+namespace {
+
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;  // (N, L, prec) -> (G, stages)
+
+bool plan_for(int N, int L, int prec, Plan *pl) {
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(std::make_tuple(N, L, prec));
+    if (it != g_tuned.end() && make_plan(N, L, prec, it->second.first, it->second.second, pl)) return true;
+  }
+  return choose_plan(N, L, prec, pl);
+}
+
+void prec_scales(int prec, float &bscale, float &rscale) {
+  bscale = 1.0f;
+  rscale = 1.0f;
+  if (prec == SVK_PREC_FP16X3) {
+    bscale = 1024.0f;       // basis values are O(1e-3 .. 1)
+    rscale = 1.0f / 16.0f;  // counts up to ~1e6 stay below 65504
+  }
+}
+
+// Workspace of one launch over `n` frames that share a plan: one table pair per distinct
+// basis pointer, then a status word.
+size_t set_workspace(const svk_frame *fr, int n, const Plan &pl) {
+  int distinct = 0;
+  for (int i = 0; i < n; ++i) {
+    bool seen = false;
+    for (int j = 0; j < i; ++j) seen |= fr[j].basis == fr[i].basis;
+    distinct += seen ? 0 : 1;
+  }
+  return (size_t)distinct * pl.table_bytes * 2 + 256;
+}
+
+template <int P>
+int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *ws, cudaStream_t s) {
+  static FrameSet fs;  // built on the host, passed by value as the kernel parameter
+  static std::mutex fs_mutex;
+  std::lock_guard<std::mutex> lock(fs_mutex);
+  float bscale, rscale;
+  prec_scales(P, bscale, rscale);
+  fs.n = n;
+  int blocks = 0, ntab = 0;
+  const int nrow_items = pl.nKG * pl.nrows;
+  for (int i = 0; i < n; ++i) {
+    FrameDesc &d = fs.fr[i];
+    d.R = fr[i].R;
+    d.I = fr[i].I;
+    d.out = fr[i].D;
+    d.coeffs = fr[i].coeffs;
+    d.W = fr[i].W;
+    d.H = fr[i].H;
+    d.pitch_R = fr[i].pitch_R;
+    d.pitch_I = fr[i].pitch_I;
+    d.pitch_out = fr[i].pitch_D;
+    d.degree = fr[i].degree;
+    d.nbx = (fr[i].W + kTileM - 1) / kTileM;
+    d.block0 = blocks;
+    blocks += d.nbx * ((fr[i].H + pl.G - 1) / pl.G);
+    d.rscale = rscale;
+    d.out_scale = 1.0f / (bscale * rscale);
+    int same = -1;
+    for (int j = 0; j < i; ++j)
+      if (fr[j].basis == fr[i].basis) same = j;
+    if (same >= 0) {
+      d.tab_hi = fs.fr[same].tab_hi;
+      d.tab_lo = fs.fr[same].tab_lo;
+    } else {
+      uint4 *th = reinterpret_cast<uint4 *>(ws + (size_t)ntab * pl.table_bytes * 2);
+      uint4 *tl = reinterpret_cast<uint4 *>(ws + (size_t)ntab * pl.table_bytes * 2 + pl.table_bytes);
+      tc_prep_table<P><<<(nrow_items + 255) / 256, 256, 0, s>>>(fr[i].basis, pl, bscale, th, pl.parts == 2 ? tl : nullptr);
+      d.tab_hi = th;
+      d.tab_lo = tl;
+      ++ntab;
+    }
+  }
+  fs.nblocks = blocks;
+  uint32_t *status = reinterpret_cast<uint32_t *>(ws + (size_t)ntab * pl.table_bytes * 2);
+  cudaError_t e = cudaMemsetAsync(status, 0, 4, s);
+  if (e != cudaSuccess) return cuda_status(e, "status reset");
+  e = cudaFuncSetAttribute(tc_basis_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  if (e != cudaSuccess) return cuda_status(e, "tc_basis_kernel smem attribute");
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = blocks < nsm ? blocks : nsm;
+  if (grid > 0) tc_basis_kernel<P><<<grid, kThreads, pl.smem, s>>>(fs, pl, status);
+  return cuda_status(cudaGetLastError(), "tc_basis_kernel launch");
+}
+
+int launch_set(const svk_frame *fr, int n, int prec, const Plan &pl, void *ws, size_t ws_bytes, cudaStream_t s) {
+  if (n < 1 || n > kMaxFrames) return set_error(SVK_ERR_ARG, "frame set of %d (1..%d)", n, kMaxFrames);
+  if (!ws || ws_bytes < set_workspace(fr, n, pl)) return set_error(SVK_ERR_WORKSPACE, "tensor-core workspace too small");
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  if (prec == SVK_PREC_BF16X3) return launch_set_prec<SVK_PREC_BF16X3>(fr, n, pl, w, s);
+  if (prec == SVK_PREC_FP16X3) return launch_set_prec<SVK_PREC_FP16X3>(fr, n, pl, w, s);
+  return launch_set_prec<SVK_PREC_BF16>(fr, n, pl, w, s);
+}
+
+// Frames of a batch grouped by (N, L): launches of up to kMaxFrames frames each.
+struct BatchPlan {
+  std::vector<std::vector<int>> sets;
+  std::vector<Plan> plans;
+  size_t ws = 0;
+};
+
+int plan_batch(const svk_frame *fr, int n, int prec, BatchPlan *bp) {
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  std::vector<std::pair<int, int>> order;
+  for (int i = 0; i < n; ++i) {
+    const auto key = std::make_pair(fr[i].N, fr[i].L);
+    if (!groups.count(key)) order.push_back(key);
+    groups[key].push_back(i);
+  }
+  for (const auto &key : order) {
+    Plan pl;
+    if (!plan_for(key.first, key.second, prec, &pl))
+      return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan for N=%d L=%d", key.first, key.second);
+    const auto &idx = groups[key];
+    for (size_t o = 0; o < idx.size(); o += kMaxFrames) {
+      std::vector<int> set(idx.begin() + o, idx.begin() + std::min(idx.size(), o + kMaxFrames));
+      std::vector<svk_frame> tmp;
+      for (int i : set) tmp.push_back(fr[i]);
+      bp->ws += (set_workspace(tmp.data(), (int)tmp.size(), pl) + 255) & ~size_t(255);
+      bp->sets.push_back(set);
+      bp->plans.push_back(pl);
+    }
+  }
+  return SVK_OK;
+}
+
+__global__ void tune_fill_kernel(float *p, size_t n, float base, float amp, uint32_t seed) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t x = (uint32_t)i * 2654435761u + seed;
+    x ^= x >> 13;
+    x *= 0x5bd1e995u;
+    x ^= x >> 15;
+    p[i] = base + amp * ((float)(x & 0xFFFFFF) / 16777216.0f - 0.5f);
+  }
+}
+
+}  // namespace
+
 size_t tc_workspace_size(int precision, int N, int L) {
   Plan pl;
-  if (!choose_plan(N, L, precision, &pl)) return 0;
+  if (!plan_for(N, L, precision, &pl)) return 0;
   return pl.table_bytes * 2 + 256;
 }
 
@@ -675,47 +875,127 @@ int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, i
               int L, const float *coeffs, int degree, int precision, float *out, int pitch_out, void *ws,
               size_t ws_bytes, cudaStream_t s) {
   Plan pl;
-  if (!choose_plan(N, L, precision, &pl))
+  if (!plan_for(N, L, precision, &pl))
     return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan fits shared memory for N=%d L=%d", N, L);
-  if (!ws || ws_bytes < pl.table_bytes * 2 + 256) return set_error(SVK_ERR_WORKSPACE, "tensor-core workspace too small");
+  svk_frame f{};
+  f.R = R;
+  f.pitch_R = pitch_R;
+  f.I = I;
+  f.pitch_I = pitch_I;
+  f.D = out;
+  f.pitch_D = pitch_out;
+  f.W = W;
+  f.H = H;
+  f.basis = basis;
+  f.N = N;
+  f.L = L;
+  f.coeffs = coeffs;
+  f.degree = degree;
+  return launch_set(&f, 1, precision, pl, ws, ws_bytes, s);
+}
+
+size_t batch_workspace_size(const svk_frame *frames, int n, int precision) {
+  BatchPlan bp;
+  if (plan_batch(frames, n, precision, &bp) != SVK_OK) return 0;
+  return bp.ws;
+}
+
+int launch_batch(const svk_frame *frames, int n, int precision, void *ws, size_t ws_bytes, cudaStream_t s) {
+  BatchPlan bp;
+  int st = plan_batch(frames, n, precision, &bp);
+  if (st != SVK_OK) return st;
+  if (!ws || ws_bytes < bp.ws) return set_error(SVK_ERR_WORKSPACE, "batch workspace of %zu bytes needed", bp.ws);
   unsigned char *w = static_cast<unsigned char *>(ws);
-  uint4 *th = reinterpret_cast<uint4 *>(w);
-  uint4 *tl = reinterpret_cast<uint4 *>(w + pl.table_bytes);
-  uint32_t *status = reinterpret_cast<uint32_t *>(w + pl.table_bytes * 2);
-  cudaError_t e = cudaMemsetAsync(status, 0, 4, s);
-  if (e != cudaSuccess) return cuda_status(e, "status reset");
-  // FP16 operands: power-of-two scales keep R and B inside the FP16 range
-  float bscale = 1.0f, rscale = 1.0f;
-  if (precision == SVK_PREC_FP16X3) {
-    bscale = 1024.0f;       // basis values are O(1e-3 .. 1)
-    rscale = 1.0f / 16.0f;  // counts up to ~1e6 stay below 65504
+  size_t off = 0;
+  for (size_t k = 0; k < bp.sets.size(); ++k) {
+    std::vector<svk_frame> tmp;
+    for (int i : bp.sets[k]) tmp.push_back(frames[i]);
+    const size_t need = set_workspace(tmp.data(), (int)tmp.size(), bp.plans[k]);
+    st = launch_set(tmp.data(), (int)tmp.size(), precision, bp.plans[k], w + off, need, s);
+    if (st != SVK_OK) return st;
+    off += (need + 255) & ~size_t(255);
   }
-  const int nrow_items = pl.nKG * pl.nrows;
-  int dev = 0, nsm = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  Sched sc;
-  sc.nbx = (W + kTileM - 1) / kTileM;
-  sc.nby = (H + pl.G - 1) / pl.G;
-  sc.nblocks = sc.nbx * sc.nby;
-  const int grid = sc.nblocks < nsm ? sc.nblocks : nsm;
-  const float out_scale = 1.0f / (bscale * rscale);
-#define SVK_TC_LAUNCH(P)                                                                                       \
-  do {                                                                                                         \
-    tc_prep_table<P><<<(nrow_items + 255) / 256, 256, 0, s>>>(basis, pl, bscale, th, pl.parts == 2 ? tl : nullptr); \
-    e = cudaFuncSetAttribute(tc_basis_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);   \
-    if (e != cudaSuccess) return cuda_status(e, "tc_basis_kernel smem attribute");                             \
-    tc_basis_kernel<P><<<grid, kThreads, pl.smem, s>>>(R, pitch_R, I, pitch_I, W, H, coeffs, degree, out,      \
-                                                       pitch_out, th, tl, pl, sc, rscale, out_scale, status);   \
-  } while (0)
-  if (precision == SVK_PREC_BF16X3)
-    SVK_TC_LAUNCH(SVK_PREC_BF16X3);
-  else if (precision == SVK_PREC_FP16X3)
-    SVK_TC_LAUNCH(SVK_PREC_FP16X3);
-  else
-    SVK_TC_LAUNCH(SVK_PREC_BF16);
-#undef SVK_TC_LAUNCH
-  return cuda_status(cudaGetLastError(), "tc_basis_kernel launch");
+  return SVK_OK;
+}
+
+int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out, cudaStream_t s) {
+  const int T = n_terms(degree);
+  const size_t px = (size_t)W * H;
+  float *R = nullptr, *I = nullptr, *D = nullptr, *B = nullptr, *C = nullptr;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  for (int G = 1; G <= 5; ++G)
+    for (int NS = kRowsPerGroup; NS <= kMaxStages; NS += kRowsPerGroup) {
+      Plan pl;
+      if (make_plan(N, L, precision, G, NS, &pl) && pl.table_bytes * 2 + 256 > ws_bytes) ws_bytes = pl.table_bytes * 2 + 256;
+    }
+  if (ws_bytes == 0) return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan for N=%d L=%d", N, L);
+  cudaError_t e = cudaMallocAsync(&R, px * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&I, px * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&D, px * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&B, (size_t)N * L * L * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&C, (size_t)N * T * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&ws, ws_bytes, s);
+  int st = cuda_status(e, "autotune buffers");
+  float best = 1e30f;
+  int bestG = 0, bestNS = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == SVK_OK) {
+    tune_fill_kernel<<<256, 256, 0, s>>>(R, px, 1500.0f, 1000.0f, 1u);
+    tune_fill_kernel<<<256, 256, 0, s>>>(I, px, 1500.0f, 1000.0f, 2u);
+    tune_fill_kernel<<<64, 256, 0, s>>>(B, (size_t)N * L * L, 0.0f, 0.1f, 3u);
+    tune_fill_kernel<<<8, 256, 0, s>>>(C, (size_t)N * T, 0.0f, 0.2f, 4u);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    svk_frame f{};
+    f.R = R;
+    f.pitch_R = W;
+    f.I = I;
+    f.pitch_I = W;
+    f.D = D;
+    f.pitch_D = W;
+    f.W = W;
+    f.H = H;
+    f.basis = B;
+    f.N = N;
+    f.L = L;
+    f.coeffs = C;
+    f.degree = degree;
+    for (int G = 5; G >= 1 && st == SVK_OK; --G)
+      for (int NS = kMaxStages; NS >= kRowsPerGroup && st == SVK_OK; NS -= kRowsPerGroup) {
+        Plan pl;
+        if (!make_plan(N, L, precision, G, NS, &pl)) continue;
+        st = launch_set(&f, 1, precision, pl, ws, ws_bytes, s);  // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && st == SVK_OK; ++r) st = launch_set(&f, 1, precision, pl, ws, ws_bytes, s);
+        cudaEventRecord(e1, s);
+        if (st == SVK_OK) st = cuda_status(cudaEventSynchronize(e1), "autotune timing");
+        float ms = 0.0f;
+        if (st == SVK_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (st == SVK_OK && ms < best) {
+          best = ms;
+          bestG = G;
+          bestNS = NS;
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  cudaFreeAsync(R, s);
+  cudaFreeAsync(I, s);
+  cudaFreeAsync(D, s);
+  cudaFreeAsync(B, s);
+  cudaFreeAsync(C, s);
+  cudaFreeAsync(ws, s);
+  if (st != SVK_OK) return st;
+  if (bestG == 0) return set_error(SVK_ERR_UNSUPPORTED, "autotune found no plan");
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[std::make_tuple(N, L, precision)] = std::make_pair(bestG, bestNS);
+  }
+  if (G_out) *G_out = bestG;
+  if (stages_out) *stages_out = bestNS;
+  return SVK_OK;
 }
 
 }  // namespace svk

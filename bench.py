@@ -49,6 +49,40 @@ def _algo_flops_per_px(N, L, degree):
     return 2 * N * L * L + 2 * N * T + 2 * N + 1
 
 
+def _raw_mma_flops(W, H, L, G, nmma, n_prod):
+    """MMA FLOP one tensor-core launch issues: per block of G output rows the reference
+    rows are taken in pairs; a pair costs 2 * (nG // 2) + (nG % 2) K steps of 16 taps, an
+    odd last row (nG + nG % 2) / 2, with nG = ceil(L / 8) groups of 8 taps per row."""
+    h = L // 2
+    nG = (L + 7) // 8
+    k_steps = 0
+    for y0 in range(0, H, G):
+        n = min(H - 1, y0 + G - 1 + h) - max(0, y0 - h) + 1
+        k_steps += (n // 2) * (2 * (nG // 2) + (nG % 2)) + (n % 2) * ((nG + (nG % 2)) // 2)
+    return k_steps * ((W + 127) // 128) * n_prod * 2 * 128 * nmma * 16
+
+
+def _traffic(precision):
+    """DRAM bytes per launch of the tensor-core kernel from the committed ncu summary, or
+    None when that summary was taken on another workload or an older kernel source."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "tc_basis_kernel_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_1209_5823_gb300", "csrc", "svk_tc.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if kv.get("workload") != WORKLOAD or kv.get("precision") != precision or kv.get("source_sha256") != sha:
+        return None
+    return int(kv["dram_bytes_per_launch"])
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
@@ -131,6 +165,90 @@ def _oracle_band(R, I, basis32, c32, degree, budget_s=12.0):
     return ref, (y0, y0 + nrows), dt, oracle.get_threads()
 
 
+def _night_batch(svk, torch, dev, stream, reps=3):
+    """The night batch: 60 frames (20 x 2048^2, 20 x 2048x4096, 20 x 4096^2, seeded order),
+    L in {15..31}, degree 0..3.  One CUDA graph replaying svk_difference_batch against 60
+    per-frame svk_difference calls; plans autotuned per L first."""
+    import numpy as np
+    import starfield
+    specs = starfield.batch_specs()
+    base = {}
+    for sp in specs:  # one rendered field per size; frames are scaled copies (distinct buffers)
+        if (sp.W, sp.H) not in base:
+            R, I, _ = starfield.frame_pair(starfield.FrameSpec("b", sp.W, sp.H, sp.n_stars, sp.L, sp.degree, sp.seed))
+            base[(sp.W, sp.H)] = (torch.from_numpy(R.astype(np.float32)).to(dev),
+                                  torch.from_numpy(I.astype(np.float32)).to(dev))
+    bases, items = {}, []
+    for k, sp in enumerate(specs):
+        if sp.L not in bases:
+            bases[sp.L] = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, sp.L)
+        R0, I0 = base[(sp.W, sp.H)]
+        c = starfield.planted_coeffs(49, sp.degree, starfield.rng(sp.seed))
+        items.append(dict(R=R0 * (1.0 + 1e-3 * k), I=I0 * (1.0 + 1e-3 * k), D=torch.empty_like(R0),
+                          basis=bases[sp.L], coeffs=torch.from_numpy(c.astype(np.float32)).to(dev), degree=sp.degree))
+    del base
+    tuned = {}
+    for L in sorted(bases):
+        tuned[L] = svk.svk_autotune(49, L, 2, svk.SVK_PREC_BF16X3, W=2048, H=512)
+    px = sum(it["R"].numel() for it in items)
+    ws = torch.empty(svk.svk_batch_workspace_size(items), dtype=torch.uint8, device=dev)
+    wsf = torch.empty(max(svk.svk_workspace_size(1, svk.SVK_PREC_BF16X3, 0, 0, 49, L, 0) for L in bases),
+                      dtype=torch.uint8, device=dev)
+
+    def per_frame():
+        for it in items:
+            svk.svk_difference(it["R"], it["I"], it["basis"], it["coeffs"], it["degree"], method=svk.SVK_METHOD_BASIS,
+                               precision=svk.SVK_PREC_BF16X3, out=it["D"], workspace=wsf)
+
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        svk.svk_difference_batch(items, workspace=ws, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        svk.svk_difference_batch(items, workspace=ws, stream=s)
+    out = {}
+    for name, fn in (("graph_batch", g.replay), ("per_frame_launches", per_frame)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_night": ms, "value": px / (ms / 1e3) / 1e6, "unit": UNIT}
+    out["frames"] = len(items)
+    out["mpixels"] = px / 1e6
+    out["tuned_plans"] = {str(L): {"G": v[0], "stages": v[1]} for L, v in tuned.items()}
+    out["workload"] = "night_60_frames_2048sq_2048x4096_4096sq_L15-31_d0-3"
+    return out
+
+
+def _fit_timing(svk, torch, dev, R, I, reps=3):
+    """Device OIS fit at 500 stamps of 41 x 41, L = 25, 49 stamps, cubic coefficients and a
+    constant background (on the 2048 x 4096 frame)."""
+    import numpy as np
+    import starfield
+    H, W = R.shape
+    g = starfield.rng(starfield.BASE_SEED + 2)
+    st = torch.from_numpy(np.stack([g.integers(30, W - 30, 500), g.integers(30, H - 30, 500)], 1).astype(np.int32)).to(dev)
+    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, 25)
+    Rt, It = torch.from_numpy(R).to(dev), torch.from_numpy(I).to(dev)
+    ws = torch.empty(svk.svk_fit_workspace_size(500, 41, 49, 25, 3, 0), dtype=torch.uint8, device=dev)
+    svk.svk_fit_coeffs(Rt, It, st, 41, B, 3, bg_degree=0, workspace=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        co, chi2, info = svk.svk_fit_coeffs(Rt, It, st, 41, B, 3, bg_degree=0, workspace=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    return {"ms": e0.elapsed_time(e1) / reps, "unknowns": 49 * 10 + 1, "stamp_pixels": 500 * 41 * 41,
+            "info": int(info.item()), "workload": "fit_500x41x41_L25_N49_d3_bg0"}
+
+
 def run_reference(args, rank):
     """Reference arm: the FP64 oracle on the host cores, same metric and workload."""
     if rank != 0:
@@ -177,6 +295,7 @@ def main():
     ap.add_argument("--impl", default="svk", choices=["svk", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the night-batch and fit measurements")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -295,23 +414,10 @@ def main():
     peak_bf16, hbm, peak_src = _peaks()
     algo = _algo_flops_per_px(N, L, d) * px
     achieved = algo / (kern_ms / 1e3) / 1e12
-    # raw MMA work of the launch (3 split products, padded taps and rows), for context
-    ng = (L + 7) // 8
-    nks = (ng + 1) // 2
-    G = 5
-    raw = 0
-    for y0 in range(0, H, G):
-        rows = min(H - 1, y0 + G - 1 + L // 2) - max(0, y0 - L // 2) + 1
-        raw += rows
-    n_prod = {"bf16x3": 3, "fp16x3": 3, "bf16": 1}[args.precision]
-    raw_flops = raw * ((W + 127) // 128) * nks * n_prod * 2 * 128 * 256 * 16
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "tc_basis_kernel_traffic.json")
-    if os.path.exists(tp):
-        with open(tp) as f:
-            tj = json.load(f)
-        if tj.get("workload") == WORKLOAD and tj.get("precision") == args.precision:
-            traffic = tj.get("dram_bytes_per_launch")
+    # raw MMA work of the launch (split products, padded taps, window rows), for context:
+    # the default plan for N = 49, L = 19 stacks G = 5 output rows per block (MMA N = 256)
+    raw_flops = _raw_mma_flops(W, H, L, G=5, nmma=256, n_prod={"bf16x3": 3, "fp16x3": 3, "bf16": 1}[args.precision])
+    traffic = _traffic(args.precision)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -327,12 +433,16 @@ def main():
                      "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)",
                      "kernel": "tc_basis_kernel (+ table prep) per CUDA-event bracket",
                      "algorithmic_flop_per_px": _algo_flops_per_px(N, L, d),
+                     "plan": "G=5 output rows per block, 8 stages",
                      "raw_mma_tflops": raw_flops / (kern_ms / 1e3) / 1e12,
                      "raw_mma_frac": raw_flops / (kern_ms / 1e3) / 1e12 / peak_bf16},
         "direct": {"value": world * px / (dir_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_frame": dir_ms,
                    "dtype": "f32"},
         "clocks": clocks,
     }
+    if not args.no_extras:
+        out["night_batch"] = _night_batch(svk, torch, dev, stream)
+        out["fit"] = _fit_timing(svk, torch, dev, R, I)
     if not args.no_cpu_baseline:
         ref, rows, dt, cores = _oracle_band(R, I, basis.cpu().numpy(), c, d)
         y0, y1 = rows

@@ -207,6 +207,39 @@ SVK_API int svk_autotune(int N, int L, int degree, int precision, int W, int H, 
                          void *stream);
 
 /*
+ * Coefficient network.  A small CNN predicts, from a (R, I) star-stamp pair, the local
+ * kernel coefficients a_k (Eq. 3 evaluated at the stamp; Eq. 2 combines them with the
+ * basis), as a fast stand-in for the least-squares fit of Sec. 2 whose result then
+ * serves as its judge and fallback.  Input x: device float32 [batch][2][64][64] (channel 0
+ * R, channel 1 I, both already normalised by the caller); output float32 [batch][n_out].
+ * Architecture: four 3x3 convolutions (2->32 stride 2, 32->32 stride 2, 32->32 stride 2,
+ * 32->32 stride 1, zero padding 1, ReLU), global average pooling, linear 32 -> n_out.
+ * Parameters: one float32 vector of svk_cnn_param_count(n_out) values (FP32 master
+ * copy); every layer computes with the weights rounded to BF16 and accumulates in FP32.
+ * 1 <= n_out <= 256, 1 <= batch <= 4096.
+ */
+SVK_API int svk_cnn_param_count(int n_out);
+SVK_API size_t svk_cnn_workspace_size(int batch, int n_out);
+SVK_API int svk_cnn_forward(const float *params, const float *x, int batch, int n_out, float *out, void *workspace,
+                            size_t ws_bytes, void *stream);
+/* Mean squared error against target [batch][n_out] into *loss (device float) and its
+ * gradient with respect to every parameter into grad (device float [param_count]). */
+SVK_API int svk_cnn_gradient(const float *params, const float *x, const float *target, int batch, int n_out,
+                             float *grad, float *loss, void *workspace, size_t ws_bytes, void *stream);
+/* One Adam step (bias-corrected, step >= 1) on the FP32 parameters with moments m, v. */
+SVK_API int svk_cnn_adam(float *params, float *m, float *v, const float *grad, int n_params, int step, float lr,
+                         float beta1, float beta2, float eps, void *stream);
+/*
+ * Coefficient field from local predictions: for stamps s at (x_s, y_s) of a W x H frame
+ * with local coefficients local[s][k] (device float32 [S][N]) and optional weights
+ * (device float32 [S] or NULL), the FP64 least-squares c[k][t] of
+ * a_k(x, y) = sum_t c[k][t] m_t(xt, yt) (Eq. 3 with the coordinate reading of svk_convolve)
+ * into coeffs (device double [N][T]); *info = -1, or the failing pivot (coeffs zero).
+ */
+SVK_API int svk_cnn_field_fit(const float *local, const int *xy, const float *weights, int S, int N, int W, int H,
+                              int degree, double *coeffs, int *info, void *stream);
+
+/*
  * Bytes of device workspace svk_fit_coeffs needs.
  */
 SVK_API size_t svk_fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree,

@@ -36,7 +36,8 @@ SVK_EDGE_ZERO = 0
 EXPORTS = (
     "svk_last_error", "svk_version", "svk_gauss_basis_count", "svk_build_basis", "svk_workspace_size",
     "svk_convolve", "svk_difference", "svk_fit_workspace_size", "svk_fit_coeffs", "svk_difference_noalloc",
-    "svk_batch_workspace_size", "svk_difference_batch", "svk_autotune",
+    "svk_batch_workspace_size", "svk_difference_batch", "svk_autotune", "svk_cnn_param_count",
+    "svk_cnn_workspace_size", "svk_cnn_forward", "svk_cnn_gradient", "svk_cnn_adam", "svk_cnn_field_fit",
 )
 
 
@@ -81,6 +82,13 @@ def load_library(path: str | None = None):
         "svk_batch_workspace_size": (sz, [vp, i, i]),
         "svk_difference_batch": (i, [vp, i, i, vp, sz, vp]),
         "svk_autotune": (i, [i, i, i, i, i, i, vp, vp, vp]),
+        "svk_cnn_param_count": (i, [i]),
+        "svk_cnn_workspace_size": (sz, [i, i]),
+        "svk_cnn_forward": (i, [vp, vp, i, i, vp, vp, sz, vp]),
+        "svk_cnn_gradient": (i, [vp, vp, vp, i, i, vp, vp, vp, sz, vp]),
+        "svk_cnn_adam": (i, [vp, vp, vp, vp, i, i, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             vp]),
+        "svk_cnn_field_fit": (i, [vp, vp, vp, i, i, i, i, i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -272,3 +280,57 @@ def svk_fit_coeffs(R, I, stamp_xy, stamp_size: int, basis, degree: int, bg_degre
                                          _ptr(chi2), _ptr(info), _ptr(workspace), ws_bytes, int(bool(sync)),
                                          _stream(stream)))
     return coeffs, chi2, info
+
+
+# ---------------------------------------------------------------- coefficient network
+def svk_cnn_param_count(n_out: int) -> int:
+    return int(load_library().svk_cnn_param_count(int(n_out)))
+
+
+def svk_cnn_workspace_size(batch: int, n_out: int) -> int:
+    return int(load_library().svk_cnn_workspace_size(int(batch), int(n_out)))
+
+
+def svk_cnn_forward(params, x, n_out: int, out=None, workspace=None, stream=None):
+    """Local coefficients [batch][n_out] from normalised stamp pairs x [batch][2][64][64]."""
+    import torch
+    B = x.shape[0]
+    if out is None:
+        out = torch.empty((B, n_out), dtype=torch.float32, device=x.device)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_cnn_forward(_ptr(params), _ptr(x), B, int(n_out), _ptr(out), _ptr(workspace), ws_bytes,
+                                          _stream(stream)))
+    return out
+
+
+def svk_cnn_gradient(params, x, target, grad=None, loss=None, workspace=None, stream=None):
+    """(grad [param_count], loss [1]) of the mean squared error against target."""
+    import torch
+    B, n_out = target.shape
+    if grad is None:
+        grad = torch.empty_like(params)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_cnn_gradient(_ptr(params), _ptr(x), _ptr(target), B, int(n_out), _ptr(grad), _ptr(loss),
+                                           _ptr(workspace), ws_bytes, _stream(stream)))
+    return grad, loss
+
+
+def svk_cnn_adam(params, m, v, grad, step: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8, stream=None):
+    _check(load_library().svk_cnn_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), params.numel(), int(step), lr,
+                                       beta1, beta2, eps, _stream(stream)))
+
+
+def svk_cnn_field_fit(local, xy, W: int, H: int, degree: int, weights=None, stream=None):
+    """FP64 polynomial field c[k][t] from local predictions local [S][N] at stamp centres xy [S][2]."""
+    import torch
+    S, N = local.shape
+    T = n_terms(degree)
+    coeffs = torch.zeros((N, T), dtype=torch.float64, device=local.device)
+    info = torch.zeros(1, dtype=torch.int32, device=local.device)
+    xy32 = xy.to(torch.int32).contiguous()
+    _check(load_library().svk_cnn_field_fit(_ptr(local), _ptr(xy32), _ptr(weights), S, N, int(W), int(H), int(degree),
+                                            _ptr(coeffs), _ptr(info), _stream(stream)))
+    return coeffs, info

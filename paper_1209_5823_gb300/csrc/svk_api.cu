@@ -228,6 +228,60 @@ int svk_autotune(int N, int L, int degree, int precision, int W, int H, int *G_o
   return autotune_tc(N, L, degree, precision, W, H, G_out, stages_out, static_cast<cudaStream_t>(stream));
 }
 
+int svk_cnn_param_count(int n_out) { return (n_out < 1 || n_out > 256) ? -1 : cnn_param_count(n_out); }
+
+size_t svk_cnn_workspace_size(int batch, int n_out) {
+  if (batch < 1 || batch > 4096 || n_out < 1 || n_out > 256) return 0;
+  return cnn_workspace_size(batch, n_out);
+}
+
+static int check_cnn(const void *params, const void *x, int batch, int n_out) {
+  if (!params || !x) return set_error(SVK_ERR_ARG, "NULL network parameter or input pointer");
+  if (batch < 1 || batch > 4096 || n_out < 1 || n_out > 256)
+    return set_error(SVK_ERR_ARG, "batch %d / n_out %d out of range", batch, n_out);
+  return SVK_OK;
+}
+
+int svk_cnn_forward(const float *params, const float *x, int batch, int n_out, float *out, void *workspace,
+                    size_t ws_bytes, void *stream) {
+  int st = check_cnn(params, x, batch, n_out);
+  if (st != SVK_OK) return st;
+  if (!out) return set_error(SVK_ERR_ARG, "NULL output");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScopedWorkspace w;
+  const size_t need = cnn_workspace_size(batch, n_out);
+  st = w.acquire(need, workspace, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  return cnn_forward(params, x, batch, n_out, out, w.ptr, need, s);
+}
+
+int svk_cnn_gradient(const float *params, const float *x, const float *target, int batch, int n_out, float *grad,
+                     float *loss, void *workspace, size_t ws_bytes, void *stream) {
+  int st = check_cnn(params, x, batch, n_out);
+  if (st != SVK_OK) return st;
+  if (!target || !grad || !loss) return set_error(SVK_ERR_ARG, "NULL target, gradient or loss pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScopedWorkspace w;
+  const size_t need = cnn_workspace_size(batch, n_out);
+  st = w.acquire(need, workspace, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  return cnn_gradient(params, x, target, batch, n_out, grad, loss, w.ptr, need, s);
+}
+
+int svk_cnn_adam(float *params, float *m, float *v, const float *grad, int n_params, int step, float lr, float beta1,
+                 float beta2, float eps, void *stream) {
+  if (!params || !m || !v || !grad || n_params < 1 || step < 1)
+    return set_error(SVK_ERR_ARG, "bad optimiser arguments");
+  return cnn_adam(params, m, v, grad, n_params, step, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream));
+}
+
+int svk_cnn_field_fit(const float *local, const int *xy, const float *weights, int S, int N, int W, int H, int degree,
+                      double *coeffs, int *info, void *stream) {
+  if (!local || !xy || !coeffs || !info || S < 1 || N < 1 || W < 1 || H < 1 || degree < 0 || degree > 3)
+    return set_error(SVK_ERR_ARG, "bad field-fit arguments");
+  return cnn_field_fit(local, xy, weights, S, N, W, H, degree, coeffs, info, static_cast<cudaStream_t>(stream));
+}
+
 size_t svk_fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree, int bg_degree) {
   return fit_workspace_size(n_stamps, stamp_size, N, L, degree, bg_degree);
 }

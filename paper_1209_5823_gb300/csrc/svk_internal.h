@@ -35,4 +35,16 @@ int launch_fit(const float *R, const float *I, int W, int H, int pitch, const in
                int bg_degree, const float *weight, double *coeffs_out, double *chi2_out,
                int *info_out, void *ws, size_t ws_bytes, cudaStream_t s);
 
+// Coefficient network (svk_cnn.cu).
+int cnn_param_count(int n_out);
+size_t cnn_workspace_size(int B, int n_out);
+int cnn_forward(const float *params, const float *x, int B, int n_out, float *out, void *ws, size_t ws_bytes,
+                cudaStream_t s);
+int cnn_gradient(const float *params, const float *x, const float *target, int B, int n_out, float *grad, float *loss,
+                 void *ws, size_t ws_bytes, cudaStream_t s);
+int cnn_adam(float *params, float *m, float *v, const float *grad, int n, int step, float lr, float b1, float b2,
+             float eps, cudaStream_t s);
+int cnn_field_fit(const float *local, const int *xy, const float *wts, int S, int N, int W, int H, int degree,
+                  double *coeffs, int *info, cudaStream_t s);
+
 }  // namespace svk

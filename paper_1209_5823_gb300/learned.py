@@ -1,0 +1,149 @@
+"""Learned coefficients: the coefficient network as a fast stand-in for the OIS fit.
+
+Pipeline (every numerical step runs in the library's kernels; this module moves tensors):
+
+1. Training pairs come from the plain method: reference stamps R (cut around stars of a
+   rendered field, with an h-pixel margin), local coefficients a drawn per stamp, and
+   I = R (x) K(a) + noise computed by svk_difference_batch (each stamp a frame of degree
+   0), cropped to 64 x 64.
+2. The network (svk_cnn_*) is trained with its own gradient and Adam kernels to map the
+   normalised pair to a (standardised by the draw's mean and spread).
+3. On a frame: stamps at star positions -> local predictions -> svk_cnn_field_fit (FP64
+   polynomial field c[k][t]) -> svk_difference.  If the residual chi^2 per stamp pixel
+   exceeds `fallback_ratio` times the noise floor, the FP64 fit (svk_fit_coeffs) replaces
+   the prediction.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import (SVK_BASIS_GAUSS, SVK_METHOD_BASIS, SVK_PREC_BF16X3, svk_build_basis, svk_cnn_adam,
+               svk_cnn_field_fit, svk_cnn_forward, svk_cnn_gradient, svk_cnn_param_count, svk_cnn_workspace_size,
+               svk_difference, svk_difference_batch, svk_fit_coeffs)
+
+STAMP = 64
+SKY = 1000.0
+SCALE = 3000.0  # input normalisation: (counts - sky) / SCALE
+
+
+@dataclass
+class CoeffPrior:
+    """Distribution of the local coefficients the network is trained on."""
+    n_out: int
+    mean0: float = 1.0
+    sd0: float = 0.03
+    sd: float = 0.02
+
+    def mean(self, device):
+        m = torch.zeros(self.n_out, device=device)
+        m[0] = self.mean0
+        return m
+
+    def std(self, device):
+        s = torch.full((self.n_out,), self.sd, device=device)
+        s[0] = self.sd0
+        return s
+
+
+def normalise(R, I):
+    """[n][64][64] counts -> network input [n][2][64][64]."""
+    return torch.stack([(R - SKY) / SCALE, (I - SKY) / SCALE], dim=1).contiguous()
+
+
+def cut_stamps(img, cx, cy, size):
+    """size x size stamps of img (zero outside) centred on integer (cx, cy) (torch tensors)."""
+    H, W = img.shape
+    half = size // 2
+    off = torch.arange(size, device=img.device) - half
+    ys = cy[:, None] + off[None, :]
+    xs = cx[:, None] + off[None, :]
+    ok = (ys[:, :, None] >= 0) & (ys[:, :, None] < H) & (xs[:, None, :] >= 0) & (xs[:, None, :] < W)
+    v = img[ys.clamp(0, H - 1)[:, :, None], xs.clamp(0, W - 1)[:, None, :]]
+    return torch.where(ok, v, torch.zeros_like(v)).contiguous()
+
+
+def make_pairs(R_field, cx, cy, a, basis, noise_sigma, gen, chunk=64):
+    """(x [n][2][64][64], R stamps, I stamps): I = R (x) K(a) + noise by the basis form."""
+    L = basis.shape[1]
+    h = L // 2
+    big = cut_stamps(R_field, cx, cy, STAMP + 2 * h)
+    n = big.shape[0]
+    Ibig = torch.empty_like(big)
+    for s in range(0, n, chunk):
+        items = [dict(R=big[i], I=None, D=Ibig[i], basis=basis, coeffs=a[i:i + 1].T.contiguous(), degree=0)
+                 for i in range(s, min(n, s + chunk))]
+        svk_difference_batch(items, precision=SVK_PREC_BF16X3)
+    Rs = big[:, h:h + STAMP, h:h + STAMP]
+    Is = Ibig[:, h:h + STAMP, h:h + STAMP] + noise_sigma * torch.randn(Rs.shape, device=Rs.device, generator=gen)
+    return normalise(Rs, Is), Rs.contiguous(), Is.contiguous()
+
+
+class CoefficientNetwork:
+    def __init__(self, params: torch.Tensor, prior: CoeffPrior, batch: int = 256):
+        self.params = params.contiguous()
+        self.prior = prior
+        self.n_out = prior.n_out
+        assert params.numel() == svk_cnn_param_count(self.n_out)
+        self.batch = batch
+        self.ws = torch.empty(svk_cnn_workspace_size(batch, self.n_out), dtype=torch.uint8, device=params.device)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+
+    def train(self, x, a, steps: int, lr: float = 1e-3, gen=None):
+        """Adam on standardised targets; returns the per-step losses (device tensor)."""
+        dev = x.device
+        z = ((a - self.prior.mean(dev)) / self.prior.std(dev)).contiguous()
+        losses = torch.empty(steps, device=dev)
+        grad = torch.empty_like(self.params)
+        n = x.shape[0]
+        for s in range(steps):
+            idx = torch.randint(0, n, (self.batch,), device=dev, generator=gen)
+            xb, zb = x[idx].contiguous(), z[idx].contiguous()
+            svk_cnn_gradient(self.params, xb, zb, grad=grad, loss=losses[s:s + 1], workspace=self.ws)
+            self.step += 1
+            svk_cnn_adam(self.params, self.m, self.v, grad, self.step, lr=lr)
+        return losses
+
+    def predict(self, x):
+        dev = x.device
+        out = []
+        for s in range(0, x.shape[0], self.batch):
+            xb = x[s:s + self.batch].contiguous()
+            ws = self.ws if xb.shape[0] == self.batch else None
+            out.append(svk_cnn_forward(self.params, xb, self.n_out, workspace=ws))
+        z = torch.cat(out)
+        return self.prior.mean(dev) + self.prior.std(dev) * z
+
+
+def apply_to_frame(net, R, I, stamp_xy, basis, degree, noise_sigma, fit_stamp=41, fallback_ratio=2.0):
+    """Coefficients for a frame from the network, with the FP64 fit as fallback.
+
+    Returns dict(coeffs [N][T] float32, source "network"|"fit", chi2_per_px, floor)."""
+    cx = stamp_xy[:, 0].long()
+    cy = stamp_xy[:, 1].long()
+    x = normalise(cut_stamps(R, cx, cy, STAMP), cut_stamps(I, cx, cy, STAMP))
+    local = net.predict(x).contiguous()
+    H, W = R.shape
+    c64, info = svk_cnn_field_fit(local, stamp_xy, W, H, degree)
+    coeffs = c64.float().contiguous()
+    D = svk_difference(R, I, basis, coeffs, degree, method=SVK_METHOD_BASIS, precision=SVK_PREC_BF16X3)
+    half = fit_stamp // 2
+    Ds = cut_stamps(D, cx, cy, fit_stamp)
+    Ds = Ds - Ds.mean(dim=(1, 2), keepdim=True)  # the background is not part of the prediction
+    chi2 = float((Ds.double() ** 2).mean())
+    # noise floor of D = R (x) K - I with both frames at noise_sigma: sigma^2 (1 + sum K^2),
+    # K ~ the unit-sum first stamp
+    floor = noise_sigma ** 2 * (1.0 + float((basis[0].double() ** 2).sum()))
+    out = dict(coeffs=coeffs, source="network", chi2_per_px=chi2, floor=floor, info=int(info.item()))
+    if int(info.item()) >= 0 or chi2 > fallback_ratio * floor:
+        co, _, finfo = svk_fit_coeffs(R, I, stamp_xy, fit_stamp, basis, degree, bg_degree=0)
+        T = (degree + 1) * (degree + 2) // 2
+        out["coeffs"] = co[:basis.shape[0] * T].reshape(basis.shape[0], T).float().contiguous()
+        out["source"] = "fit"
+        out["fit_info"] = int(finfo.item())
+    return out

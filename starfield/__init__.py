@@ -185,3 +185,36 @@ def frame_pair(spec: FrameSpec, with_second_epoch: bool = True):
             return 1.02 - 0.04 * (y / max(H - 1, 1))
         I = add_noise(render(cat, W, H, extra_sigma=extra, flux_scale=fscale), 30.0, g)
     return R, I, cat
+
+
+# ---------------------------------------------------------------- coefficient network inputs
+CNN_IN = 64        # stamp side
+CNN_CH = 32        # channels of every hidden layer
+CNN_LAYERS = ((2, 2), (CNN_CH, 2), (CNN_CH, 2), (CNN_CH, 1))  # (input channels, stride) of the 4 convs
+
+
+def cnn_param_shapes(n_out: int):
+    """Parameter tensors of the coefficient network, in the flat order both the oracle
+    and the CUDA library use: per conv layer w[Cout][Cin][3][3] then b[Cout], then the
+    linear layer w[n_out][CNN_CH] and b[n_out]."""
+    shapes = []
+    for cin, _ in CNN_LAYERS:
+        shapes.append((CNN_CH, cin, 3, 3))
+        shapes.append((CNN_CH,))
+    shapes.append((n_out, CNN_CH))
+    shapes.append((n_out,))
+    return shapes
+
+
+def cnn_init_params(n_out: int, seed: int) -> np.ndarray:
+    """He-uniform weights, zero biases (float32 flat vector)."""
+    g = rng(seed)
+    out = []
+    for shp in cnn_param_shapes(n_out):
+        if len(shp) == 1:
+            out.append(np.zeros(shp))
+        else:
+            fan_in = int(np.prod(shp[1:]))
+            lim = math.sqrt(6.0 / fan_in)
+            out.append(g.uniform(-lim, lim, shp))
+    return np.concatenate([a.reshape(-1) for a in out]).astype(np.float32)

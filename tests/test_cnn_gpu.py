@@ -1,0 +1,131 @@
+"""The coefficient network on the device: forward and gradients against the FP64 oracle
+(same BF16-rounded weights), the optimiser step, the polynomial field fit, and training on
+pairs the plain method generates (loss falls, predictions beat the prior, the network path
+is faster than the FP64 fit, and the fallback hands bad predictions to the fit)."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1209_5823_gb300 as svk
+import starfield
+from oracle import cnn as ocnn
+from paper_1209_5823_gb300 import learned
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(a):
+    """Round float32 values to the nearest BF16 (ties to even), as float32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def _data(B, n_out, seed):
+    g = starfield.rng(seed)
+    x = g.normal(0, 1, (B, 2, 64, 64)).astype(np.float32)
+    t = g.normal(0, 1, (B, n_out)).astype(np.float32)
+    return x, t
+
+
+@pytest.mark.parametrize("n_out", [49, 7])
+def test_forward_and_gradient_match_oracle(n_out):
+    p = starfield.cnn_init_params(n_out, 11)
+    x, t = _data(3, n_out, 12)
+    dp, dx, dt = (torch.from_numpy(a).cuda() for a in (p, x, t))
+    out = svk.svk_cnn_forward(dp, dx, n_out).cpu().numpy()
+    grad, loss = svk.svk_cnn_gradient(dp, dx, dt)
+    pq = bf16_round(p).astype(np.float64)
+    ref_out, _ = ocnn.forward(pq, x.astype(np.float64), n_out)
+    ref_loss, ref_grad = ocnn.loss_and_grad(pq, x.astype(np.float64), t.astype(np.float64), n_out)
+    assert np.abs(out - ref_out).max() <= 1e-4 * np.abs(ref_out).max()
+    assert abs(float(loss.item()) - ref_loss) <= 1e-4 * ref_loss
+    g = grad.cpu().numpy().astype(np.float64)
+    # every parameter block separately (scales differ by orders of magnitude)
+    o = 0
+    for shp in starfield.cnn_param_shapes(n_out):
+        n = int(np.prod(shp))
+        a, b = g[o:o + n], ref_grad[o:o + n]
+        assert np.abs(a - b).max() <= 2e-3 * np.abs(b).max() + 1e-9, shp
+        o += n
+
+
+def test_adam_step():
+    n = 1000
+    g = starfield.rng(3)
+    p = g.normal(0, 1, n).astype(np.float32)
+    gr = g.normal(0, 1, n).astype(np.float32)
+    dp, dm, dv, dg = (torch.from_numpy(a).cuda() for a in (p.copy(), np.zeros(n, np.float32), np.zeros(n, np.float32), gr))
+    svk.svk_cnn_adam(dp, dm, dv, dg, 1, lr=0.01)
+    # first bias-corrected Adam step is lr * g / (|g| + eps)
+    exp = p - 0.01 * gr / (np.abs(gr) + 1e-8)
+    np.testing.assert_allclose(dp.cpu().numpy(), exp, rtol=0, atol=1e-6)
+
+
+def test_field_fit_recovers_polynomial():
+    W, H, d, N, S = 4096, 2048, 2, 5, 200
+    g = starfield.rng(4)
+    xy = np.stack([g.integers(0, W, S), g.integers(0, H, S)], 1).astype(np.int32)
+    c = g.normal(0, 1, (N, 6))
+    xt = (2 * xy[:, 0] - (W - 1)) / (W - 1)
+    yt = (2 * xy[:, 1] - (H - 1)) / (H - 1)
+    mono = np.stack([np.ones(S), yt, yt ** 2, xt, xt * yt, xt ** 2], 1)
+    local = (mono @ c.T).astype(np.float32)
+    co, info = svk.svk_cnn_field_fit(torch.from_numpy(local).cuda(), torch.from_numpy(xy).cuda(), W, H, d)
+    assert int(info.item()) == -1
+    np.testing.assert_allclose(co.cpu().numpy(), c, rtol=0, atol=2e-5)
+
+
+def _field(W, H, seed):
+    g = starfield.rng(seed)
+    cat = starfield.star_catalog(W, H, int(W * H * 0.0024), g)
+    R = starfield.add_noise(starfield.render(cat, W, H), 30.0, g).astype(np.float32)
+    return torch.from_numpy(R).cuda(), cat
+
+
+def test_training_learns_and_network_path_is_faster_with_fallback():
+    dev = torch.device("cuda")
+    L, N = 19, 49
+    basis = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, L)
+    prior = learned.CoeffPrior(N)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    Rf, cat = _field(1024, 1024, 6)
+    bright = np.argsort(cat.flux)[::-1][:3000]
+    cx = torch.from_numpy(np.clip(cat.x[bright].astype(np.int64), 48, 1024 - 48)).cuda()
+    cy = torch.from_numpy(np.clip(cat.y[bright].astype(np.int64), 48, 1024 - 48)).cuda()
+    n = cx.numel()
+    a = prior.mean(dev) + prior.std(dev) * torch.randn((n, N), device=dev, generator=gen)
+    x, _, _ = learned.make_pairs(Rf, cx, cy, a, basis, 30.0, gen)
+    ntr = n - 500
+    net = learned.CoefficientNetwork(torch.from_numpy(starfield.cnn_init_params(N, 7)).cuda(), prior, batch=128)
+    losses = net.train(x[:ntr], a[:ntr], 800, lr=3e-3, gen=gen).cpu().numpy()
+    assert losses[-50:].mean() < 0.92 * losses[:50].mean()
+    pred = net.predict(x[ntr:])
+    err_net = float(((pred - a[ntr:]) / prior.std(dev)).pow(2).mean())
+    # predicting the prior mean scores 1.0 (+- 0.01 over 500 x 49 held-out values)
+    assert err_net < 0.95
+
+    # a frame whose kernel has spatially varying coefficients: network path vs FP64 fit
+    W = H = 1024
+    c_true = torch.from_numpy(starfield.planted_coeffs(N, 1, starfield.rng(8)).astype(np.float32)).cuda()
+    I = svk.svk_convolve(Rf, basis, c_true, 1, method=svk.SVK_METHOD_BASIS, precision=svk.SVK_PREC_BF16X3)
+    I = I + 30.0 * torch.randn(I.shape, device=dev, generator=gen)
+    st = torch.stack([cx[:300], cy[:300]], 1).to(torch.int32)
+    learned.apply_to_frame(net, Rf, I, st, basis, 1, 30.0, fallback_ratio=1e9)  # warm both paths
+    svk.svk_fit_coeffs(Rf, I, st, 41, basis, 1, bg_degree=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = learned.apply_to_frame(net, Rf, I, st, basis, 1, 30.0, fallback_ratio=1e9)
+    torch.cuda.synchronize()
+    t_net = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    svk.svk_fit_coeffs(Rf, I, st, 41, basis, 1, bg_degree=0)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    assert res["source"] == "network" and t_net < t_fit
+    # garbage weights: the residual check hands the frame to the fit
+    bad = learned.CoefficientNetwork(torch.zeros_like(net.params), learned.CoeffPrior(N, mean0=0.0), batch=128)
+    res2 = learned.apply_to_frame(bad, Rf, I, st, basis, 1, 30.0, fallback_ratio=2.0)
+    assert res2["source"] == "fit"

@@ -249,6 +249,115 @@ def _fit_timing(svk, torch, dev, R, I, reps=3):
             "info": int(info.item()), "workload": "fit_500x41x41_L25_N49_d3_bg0"}
 
 
+def _precision_table(svk, torch, dev):
+    """4096 x 4096 frame, L = 25, 49 stamps, cubic coefficients: every arithmetic of the
+    contraction against the FP64 oracle on 2000 random pixels plus the 200 brightest
+    star centres (so the scale max|R (x) K| includes the star peaks), and its time."""
+    import numpy as np
+    import oracle
+    import starfield
+    spec = starfield.CONFIGS[2]
+    g = starfield.rng(spec.seed)
+    cat = starfield.star_catalog(spec.W, spec.H, spec.n_stars, g)
+    R = starfield.add_noise(starfield.render(cat, spec.W, spec.H), 30.0, g).astype(np.float32)
+    c = starfield.planted_coeffs(49, spec.degree, starfield.rng(spec.seed + 7)).astype(np.float32)
+    Rt = torch.from_numpy(R).to(dev)
+    ct = torch.from_numpy(c).to(dev)
+    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, spec.L)
+    gs = starfield.rng(spec.seed + 9)
+    top = np.argsort(cat.flux)[::-1][:200]
+    px = np.concatenate([gs.integers(0, spec.W, 2000), np.clip(np.round(cat.x[top]), 0, spec.W - 1)]).astype(np.int32)
+    py = np.concatenate([gs.integers(0, spec.H, 2000), np.clip(np.round(cat.y[top]), 0, spec.H - 1)]).astype(np.int32)
+    ref = oracle.convolve_points(R.astype(np.float64), B.cpu().numpy().astype(np.float64), c.astype(np.float64),
+                                 spec.degree, px, py)
+    scale = np.abs(ref).max()
+    out = {"workload": spec.name, "sample": "2000 random pixels + 200 brightest star centres", "paths": {}}
+    for name, method, prec in (("basis_bf16x3", svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3),
+                               ("basis_fp16x3", svk.SVK_METHOD_BASIS, svk.SVK_PREC_FP16X3),
+                               ("basis_bf16", svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16),
+                               ("direct_fp32", svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32)):
+        o = svk.svk_convolve(Rt, B, ct, spec.degree, method=method, precision=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record()
+        for _ in range(reps):
+            svk.svk_convolve(Rt, B, ct, spec.degree, method=method, precision=prec, out=o)
+        e1.record()
+        torch.cuda.synchronize()
+        got = o[torch.from_numpy(py).to(dev).long(), torch.from_numpy(px).to(dev).long()].double().cpu().numpy()
+        ms = e0.elapsed_time(e1) / reps
+        out["paths"][name] = {"max_rel_err": float(np.abs(got - ref).max() / scale),
+                              "rms_rel_err": float(np.sqrt(((got - ref) ** 2).mean()) / scale),
+                              "ms": ms, "mpixel_s": spec.W * spec.H / (ms / 1e3) / 1e6}
+    return out
+
+
+def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=3000):
+    """Coefficient network trained on n_pairs (R, I) stamp pairs the plain method makes,
+    then applied to the 2048 x 4096 frame against the FP64 fit."""
+    import time as _t
+    import numpy as np
+    import starfield
+    from paper_1209_5823_gb300 import learned
+    N, L, d = 49, 19, 2
+    basis = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, L)
+    prior = learned.CoeffPrior(N)
+    gen = torch.Generator(device=dev).manual_seed(starfield.BASE_SEED + 4)
+    H, W = R.shape
+    Rt = torch.from_numpy(R).to(dev)
+    g = starfield.rng(starfield.BASE_SEED + 4)
+    cat = starfield.star_catalog(W, H, 20000, starfield.rng(starfield.CONFIGS[1].seed))
+    bright = np.nonzero(cat.flux > 3000)[0]
+    pick = g.choice(bright, n_pairs)
+    cx = torch.from_numpy(np.clip(np.round(cat.x[pick]), 48, W - 49).astype(np.int64)).to(dev)
+    cy = torch.from_numpy(np.clip(np.round(cat.y[pick]), 48, H - 49).astype(np.int64)).to(dev)
+    a = prior.mean(dev) + prior.std(dev) * torch.randn((n_pairs, N), device=dev, generator=gen)
+    t0 = _t.perf_counter()
+    x, _, _ = learned.make_pairs(Rt, cx, cy, a, basis, 30.0, gen)
+    torch.cuda.synchronize()
+    t_pairs = _t.perf_counter() - t0
+    n_hold = 2000
+    net = learned.CoefficientNetwork(torch.from_numpy(starfield.cnn_init_params(N, starfield.BASE_SEED)).to(dev), prior)
+    t0 = _t.perf_counter()
+    losses = net.train(x[:-n_hold], a[:-n_hold], steps, lr=3e-3, gen=gen)
+    torch.cuda.synchronize()
+    t_train = _t.perf_counter() - t0
+    pred = net.predict(x[-n_hold:])
+    err = ((pred - a[-n_hold:]) / prior.std(dev)).pow(2).mean(dim=0).cpu().numpy()
+    # a frame with a spatially varying kernel: network + field fit vs the FP64 fit
+    c_true = torch.from_numpy(starfield.planted_coeffs(N, d, starfield.rng(starfield.BASE_SEED + 5))
+                              .astype(np.float32)).to(dev)
+    I = svk.svk_convolve(Rt, basis, c_true, d, method=svk.SVK_METHOD_BASIS, precision=svk.SVK_PREC_BF16X3)
+    I = I + 30.0 * torch.randn(I.shape, device=dev, generator=gen)
+    top = np.argsort(cat.flux)[::-1][:500]
+    st = torch.from_numpy(np.stack([np.clip(np.round(cat.x[top]), 30, W - 31), np.clip(np.round(cat.y[top]), 30, H - 31)],
+                                   1).astype(np.int32)).to(dev)
+    learned.apply_to_frame(net, Rt, I, st, basis, d, 30.0, fallback_ratio=1e9, reference_noise_sigma=0.0)
+    co_fit, chi2_fit, _ = svk.svk_fit_coeffs(Rt, I, st, 41, basis, d, bg_degree=0)
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    res = learned.apply_to_frame(net, Rt, I, st, basis, d, 30.0, fallback_ratio=1e9, reference_noise_sigma=0.0)
+    torch.cuda.synchronize()
+    t_net = _t.perf_counter() - t0
+    t0 = _t.perf_counter()
+    co_fit, chi2_fit, _ = svk.svk_fit_coeffs(Rt, I, st, 41, basis, d, bg_degree=0)
+    torch.cuda.synchronize()
+    t_fit = _t.perf_counter() - t0
+    T = (d + 1) * (d + 2) // 2
+    cf = co_fit[:N * T].reshape(N, T).float().contiguous()
+    Df = svk.svk_difference(Rt, I, basis, cf, d, method=svk.SVK_METHOD_BASIS, precision=svk.SVK_PREC_BF16X3)
+    Ds = learned.cut_stamps(Df, st[:, 0].long(), st[:, 1].long(), 41)
+    chi2_fit_px = float(((Ds - Ds.mean(dim=(1, 2), keepdim=True)).double() ** 2).mean())
+    return {"workload": "cnn_4conv32_64x64_pairs_to_49_local_coeffs",
+            "pairs": n_pairs, "steps": steps, "batch": net.batch, "pairs_s": t_pairs, "train_s": t_train,
+            "loss_first100": float(losses[:100].mean()), "loss_last100": float(losses[-100:].mean()),
+            "heldout_mse_std_units": float(err.mean()), "heldout_mse_a0": float(err[0]), "prior_mse_std_units": 1.0,
+            "frame": {"stamps": 500, "degree": d, "network_s": t_net, "fp64_fit_s": t_fit,
+                      "network_chi2_per_px": res["chi2_per_px"], "fit_chi2_per_px": chi2_fit_px,
+                      "noise_floor": res["floor"], "source": res["source"]}}
+
+
 def run_reference(args, rank):
     """Reference arm: the FP64 oracle on the host cores, same metric and workload."""
     if rank != 0:
@@ -443,6 +552,8 @@ def main():
     if not args.no_extras:
         out["night_batch"] = _night_batch(svk, torch, dev, stream)
         out["fit"] = _fit_timing(svk, torch, dev, R, I)
+        out["precision"] = _precision_table(svk, torch, dev)
+        out["learned"] = _learned(svk, torch, dev, R, I)
     if not args.no_cpu_baseline:
         ref, rows, dt, cores = _oracle_band(R, I, basis.cpu().numpy(), c, d)
         y0, y1 = rows

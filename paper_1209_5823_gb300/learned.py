@@ -120,9 +120,13 @@ class CoefficientNetwork:
         return self.prior.mean(dev) + self.prior.std(dev) * z
 
 
-def apply_to_frame(net, R, I, stamp_xy, basis, degree, noise_sigma, fit_stamp=41, fallback_ratio=2.0):
+def apply_to_frame(net, R, I, stamp_xy, basis, degree, noise_sigma, fit_stamp=41, fallback_ratio=2.0,
+                   reference_noise_sigma=None):
     """Coefficients for a frame from the network, with the FP64 fit as fallback.
 
+    noise_sigma is the noise of I, reference_noise_sigma that of R when it is independent
+    of I's (default: the same; 0 when I was made from the noisy R itself).  The noise floor
+    of the residual D is noise_sigma^2 + reference_noise_sigma^2 sum K^2.
     Returns dict(coeffs [N][T] float32, source "network"|"fit", chi2_per_px, floor)."""
     cx = stamp_xy[:, 0].long()
     cy = stamp_xy[:, 1].long()
@@ -136,9 +140,9 @@ def apply_to_frame(net, R, I, stamp_xy, basis, degree, noise_sigma, fit_stamp=41
     Ds = cut_stamps(D, cx, cy, fit_stamp)
     Ds = Ds - Ds.mean(dim=(1, 2), keepdim=True)  # the background is not part of the prediction
     chi2 = float((Ds.double() ** 2).mean())
-    # noise floor of D = R (x) K - I with both frames at noise_sigma: sigma^2 (1 + sum K^2),
-    # K ~ the unit-sum first stamp
-    floor = noise_sigma ** 2 * (1.0 + float((basis[0].double() ** 2).sum()))
+    # noise floor of D = R (x) K - I, with K ~ the unit-sum first stamp
+    rs = noise_sigma if reference_noise_sigma is None else reference_noise_sigma
+    floor = noise_sigma ** 2 + rs ** 2 * float((basis[0].double() ** 2).sum())
     out = dict(coeffs=coeffs, source="network", chi2_per_px=chi2, floor=floor, info=int(info.item()))
     if int(info.item()) >= 0 or chi2 > fallback_ratio * floor:
         co, _, finfo = svk_fit_coeffs(R, I, stamp_xy, fit_stamp, basis, degree, bg_degree=0)

@@ -358,6 +358,48 @@ def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=3000):
                       "noise_floor": res["floor"], "source": res["source"]}}
 
 
+def _time(torch, fn, reps=5):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _paper_sweep(svk, torch, dev):
+    """The paper's measured workload (Sec. 3, Fig. 1): delta basis, L = 7 (49 stamps),
+    second-order coefficients, images from 256^2 to one 4846 x 4868 camera tile; every
+    form's Mpixel/s and the rate in the paper's cost model (20 L^2 + 1 FLOP per pixel)."""
+    import numpy as np
+    import starfield
+    L, d = 7, 2
+    B = svk.svk_build_basis(svk.SVK_BASIS_DELTA, L)
+    c = torch.from_numpy(starfield.planted_coeffs(49, d, starfield.rng(starfield.BASE_SEED + 6), const_sd=0.01,
+                                                  spatial_sd=0.005).astype(np.float32)).to(dev)
+    rows = []
+    for (W, H) in ((256, 256), (512, 512), (1024, 1024), (2048, 2048), (4096, 4096), (4846, 4868)):
+        g = torch.Generator(device=dev).manual_seed(W)
+        R = 1000.0 + 30.0 * torch.randn((H, W), device=dev, generator=g)
+        I = 1000.0 + 30.0 * torch.randn((H, W), device=dev, generator=g)
+        D = torch.empty_like(R)
+        row = {"W": W, "H": H}
+        for name, method, prec in (("direct_fp32", svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32),
+                                   ("basis_bf16x3", svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3),
+                                   ("tform_bf16x3", svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3)):
+            ws = torch.empty(max(1, svk.svk_workspace_size(method, prec, W, H, 49, L, d)), dtype=torch.uint8, device=dev)
+            ms = _time(torch, lambda: svk.svk_difference(R, I, B, c, d, method=method, precision=prec, out=D,
+                                                         workspace=ws if method else None))
+            row[name] = {"ms": ms, "mpixel_s": W * H / (ms / 1e3) / 1e6,
+                         "paper_model_tflops": (20 * L * L + 1) * W * H / (ms / 1e3) / 1e12}
+        rows.append(row)
+    return {"workload": "paper_dfb_L7_d2_sizes_256sq_to_4846x4868", "rows": rows,
+            "paper_model": "20 L^2 + 1 FLOP per pixel (Sec. 3)"}
+
+
 def run_reference(args, rank):
     """Reference arm: the FP64 oracle on the host cores, same metric and workload."""
     if rank != 0:
@@ -509,6 +551,12 @@ def main():
     torch.cuda.synchronize()
     dir_ms = d0.elapsed_time(d1) / n_dir
 
+    # the T-factored form on the same frame (a different form of the same result)
+    Dt = torch.empty((H, W), dtype=torch.float32, device=dev)
+    wst = torch.empty(svk.svk_workspace_size(svk.SVK_METHOD_TFORM, prec, W, H, N, L, d), dtype=torch.uint8, device=dev)
+    tf_ms = _time(torch, lambda: svk.svk_difference(Rs[0], Is[0], basis, ct, d, method=svk.SVK_METHOD_TFORM,
+                                                    precision=prec, out=Dt, workspace=wst), reps=20)
+
     # max over ranks
     times = torch.tensor([ms_total, e2e_ms, kern_ms, dir_ms], dtype=torch.float64, device=dev)
     if dist:
@@ -548,11 +596,14 @@ def main():
         "direct": {"value": world * px / (dir_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_frame": dir_ms,
                    "dtype": "f32"},
         "clocks": clocks,
+        "tform": {"value": world * px / (tf_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_frame": tf_ms,
+                  "form": "sum_t m_t (R (x) K_t) - I, K_t = sum_k c[k][t] B_k (same result, T = 6 convolutions)"},
     }
     if not args.no_extras:
         out["night_batch"] = _night_batch(svk, torch, dev, stream)
         out["fit"] = _fit_timing(svk, torch, dev, R, I)
         out["precision"] = _precision_table(svk, torch, dev)
+        out["paper_sweep"] = _paper_sweep(svk, torch, dev)
         out["learned"] = _learned(svk, torch, dev, R, I)
     if not args.no_cpu_baseline:
         ref, rows, dt, cores = _oracle_band(R, I, basis.cpu().numpy(), c, d)
@@ -562,6 +613,8 @@ def main():
         scale = np.abs(ref).max()
         out["cpu_baseline"] = {"value": (y1 - y0) * W / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"rows {y0}..{y1 - 1} ({(y1 - y0) * W} px) of the frame, FP64 C oracle"}
+        Dtf = Dt[y0:y1].cpu().numpy().astype(np.float64) + I[y0:y1]
+        out["tform"]["max_rel_err"] = float(np.abs(Dtf - ref).max() / scale)
         out["max_rel_err"] = {"basis": float(np.abs(Dtc - ref).max() / scale),
                               "direct": float(np.abs(Ddir - ref).max() / scale),
                               "measure": "max|D_gpu - D_oracle| / max|R (x) K| over the cpu_baseline band"}

@@ -70,6 +70,11 @@ extern "C" {
 #define SVK_METHOD_BASIS 1  /* R (x) B_k for all k as an implicit-im2col GEMM on the       */
                             /* tensor cores (tcgen05, TMEM accumulators), then a fused     */
                             /* polynomial epilogue sum_k a_k(x,y) C_k(x,y) (- I)           */
+#define SVK_METHOD_TFORM 2  /* the same result by linearity of Eq. 2 and 3 as              */
+                            /* sum_t m_t(xt,yt) (R (x) K_t)(x,y) (- I), K_t = sum_k c[k][t] */
+                            /* B_k: T = (d+1)(d+2)/2 convolutions on the tensor cores       */
+                            /* instead of N; any N (delta bases included); precisions as   */
+                            /* SVK_METHOD_BASIS                                             */
 
 /* arithmetic of the contraction */
 #define SVK_PREC_FP32 0   /* DIRECT only: FP32 FFMA                                       */

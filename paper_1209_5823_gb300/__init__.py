@@ -26,6 +26,7 @@ SVK_NORM_NONE = 0
 SVK_NORM_ALARD = 1
 SVK_METHOD_DIRECT = 0
 SVK_METHOD_BASIS = 1
+SVK_METHOD_TFORM = 2
 SVK_PREC_FP32 = 0
 SVK_PREC_BF16X3 = 1
 SVK_PREC_FP16X3 = 2

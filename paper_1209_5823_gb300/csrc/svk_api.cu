@@ -98,10 +98,11 @@ static int check_conv_args(const float *R, int pitch_R, const float *I, int pitc
   if (method == SVK_METHOD_DIRECT) {
     if (precision != SVK_PREC_FP32)
       return set_error(SVK_ERR_UNSUPPORTED, "the direct method computes in FP32 only");
-  } else if (method == SVK_METHOD_BASIS) {
+  } else if (method == SVK_METHOD_BASIS || method == SVK_METHOD_TFORM) {
     if (precision != SVK_PREC_BF16X3 && precision != SVK_PREC_FP16X3 && precision != SVK_PREC_BF16)
-      return set_error(SVK_ERR_UNSUPPORTED, "basis method precision %d not built", precision);
-    if (N > 256) return set_error(SVK_ERR_UNSUPPORTED, "basis method supports N <= 256 (got %d)", N);
+      return set_error(SVK_ERR_UNSUPPORTED, "tensor-core precision %d not built", precision);
+    if (method == SVK_METHOD_BASIS && N > 256)
+      return set_error(SVK_ERR_UNSUPPORTED, "basis method supports N <= 256 (got %d)", N);
   } else {
     return set_error(SVK_ERR_ARG, "unknown method %d", method);
   }
@@ -120,6 +121,13 @@ static int run_conv(const float *R, int pitch_R, const float *I, int pitch_I, in
     return launch_direct(R, pitch_R, need_I ? I : nullptr, pitch_I, W, H, basis, N, L, coeffs, degree, out,
                          pitch_out, s);
   ScopedWorkspace w;
+  if (method == SVK_METHOD_TFORM) {
+    const size_t need = tform_workspace_size(precision, L, degree);
+    st = w.acquire(need, ws, ws_bytes, s);
+    if (st != SVK_OK) return st;
+    return launch_tform(R, pitch_R, need_I ? I : nullptr, pitch_I, W, H, basis, N, L, coeffs, degree, precision, out,
+                        pitch_out, w.ptr, need, s);
+  }
   st = w.acquire(tc_workspace_size(precision, N, L), ws, ws_bytes, s);
   if (st != SVK_OK) return st;
   return launch_tc(R, pitch_R, need_I ? I : nullptr, pitch_I, W, H, basis, N, L, coeffs, degree, precision,
@@ -169,6 +177,7 @@ size_t svk_workspace_size(int method, int precision, int W, int H, int N, int L,
   (void)H;
   (void)degree;
   if (method == SVK_METHOD_BASIS) return tc_workspace_size(precision, N, L);
+  if (method == SVK_METHOD_TFORM) return tform_workspace_size(precision, L, degree);
   return 0;
 }
 

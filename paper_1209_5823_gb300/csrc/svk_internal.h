@@ -24,6 +24,10 @@ int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, i
               const float *basis, int N, int L, const float *coeffs, int degree, int precision,
               float *out, int pitch_out, void *ws, size_t ws_bytes, cudaStream_t s);
 
+size_t tform_workspace_size(int precision, int L, int degree);
+int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis, int N,
+                 int L, const float *coeffs, int degree, int precision, float *out, int pitch_out, void *ws,
+                 size_t ws_bytes, cudaStream_t s);
 int launch_batch(const svk_frame *frames, int n, int precision, void *ws, size_t ws_bytes, cudaStream_t s);
 size_t batch_workspace_size(const svk_frame *frames, int n, int precision);
 int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out, cudaStream_t s);

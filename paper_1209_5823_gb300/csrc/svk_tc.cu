@@ -71,6 +71,7 @@ constexpr int kThreads = (kEpiWarps + 1 + kProdWarps) * 32;
 constexpr int kTileM = 128;
 constexpr int kMaxStages = 8;  // Hankel stages (reference rows in flight), upper bound
 constexpr int kRowsPerGroup = 4;  // rows per full/empty handshake
+constexpr int kMaxG = 40;          // output rows per block (few stamps: the T-factored form)
 constexpr uint32_t kTmemCols = 512;
 constexpr int kAccStride = 256;  // TMEM columns per accumulator buffer
 
@@ -127,8 +128,8 @@ static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
   o += (size_t)rup(N * 10 * 4, 16);
   q.off_alpha = o;
   o += (size_t)rup(G * N * 4 * 4, 16);
-  q.off_alphaS = o;  // G x 64 load slots x float4
-  o += (size_t)G * 64 * 16;
+  q.off_alphaS = o;  // G x 64 load slots x float4 (only the 16..64-stamp epilogue uses it)
+  if (N >= 16 && N <= 64) o += (size_t)G * 64 * 16;
   q.off_bar = o;
   o += 8 * (2 * kMaxStages + 4 + 2) + 16;
   q.smem = o + 128;  // base alignment slack
@@ -143,7 +144,7 @@ static bool choose_plan(int N, int L, int prec, Plan *p) {
   // the widest MMA (most output rows per block) that fits, with two handshake groups in
   // flight when they fit (producers fill one while the MMAs drain the other); the
   // autotuner replaces this default by measurement
-  for (int G = 5; G >= 1; --G)
+  for (int G = kMaxG; G >= 1; --G)
     for (int NS = kMaxStages; NS >= kRowsPerGroup; NS -= kRowsPerGroup)
       if (make_plan(N, L, prec, G, NS, p)) return true;
   return false;
@@ -648,10 +649,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait_bounded(&acc_full[buf], (blk_seq >> 1) & 1, status)) break;
       tc_fence_after();
       const uint32_t tbase = tmem_base + lane_off + (uint32_t)(buf * kAccStride);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
+#pragma unroll 1
+      for (int j = 0;; ++j) {
         const int g = par + 2 * j;
         if (g >= G || y0 + g >= fd.H) break;
+        // rows beyond the first three per warp (plans with G > 6) read I here
+        const float iv = j == 0 ? ival[0] : j == 1 ? ival[1] : j == 2 ? ival[2]
+                       : (fd.I && x < fd.W ? __ldg(fd.I + (size_t)(y0 + g) * fd.pitch_I + x) : 0.0f);
         const uint32_t c0 = tbase + (uint32_t)((G - 1 - g) * N);
         // sum_k a_k C_k = sum_i xt^i (sum_k alpha[g][k][i] C_k): four independent dot
         // products over the accumulator columns, then Horner in xt
@@ -705,7 +709,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld_wait();
         }
         const float sres = fmaf(fmaf(fmaf(s3, xt, s2), xt, s1), xt, s0);
-        if (x < fd.W) fd.out[(size_t)(y0 + g) * fd.pitch_out + x] = sres * fd.out_scale - ival[j];
+        if (x < fd.W) fd.out[(size_t)(y0 + g) * fd.pitch_out + x] = sres * fd.out_scale - iv;
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[buf]);
@@ -894,6 +898,62 @@ int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, i
   return launch_set(&f, 1, precision, pl, ws, ws_bytes, s);
 }
 
+namespace {
+// K_t = sum_k c[k][t] B_k (FP64 sums, stored FP32) and the T x T identity coefficients
+// that make the epilogue's polynomial sum_t m_t C_t.
+__global__ void tform_combine_kernel(const float *__restrict__ basis, const float *__restrict__ coeffs, int N, int T,
+                                     int LL, float *__restrict__ Kt, float *__restrict__ ident) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < T * LL) {
+    const int t = idx / LL, i = idx % LL;
+    double acc = 0.0;
+    for (int k = 0; k < N; ++k) acc += (double)coeffs[(size_t)k * T + t] * (double)basis[(size_t)k * LL + i];
+    Kt[idx] = (float)acc;
+  }
+  if (idx < T * T) ident[idx] = (idx / T == idx % T) ? 1.0f : 0.0f;
+}
+
+size_t tform_head_bytes(int T, int L) { return ((size_t)T * L * L * 4 + (size_t)T * T * 4 + 255) & ~size_t(255); }
+}  // namespace
+
+size_t tform_workspace_size(int precision, int L, int degree) {
+  const int T = n_terms(degree);
+  Plan pl;
+  if (!plan_for(T, L, precision, &pl)) return 0;
+  return tform_head_bytes(T, L) + pl.table_bytes * 2 + 256;
+}
+
+int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis, int N,
+                 int L, const float *coeffs, int degree, int precision, float *out, int pitch_out, void *ws,
+                 size_t ws_bytes, cudaStream_t s) {
+  const int T = n_terms(degree);
+  Plan pl;
+  if (!plan_for(T, L, precision, &pl))
+    return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan for T=%d L=%d", T, L);
+  const size_t head = tform_head_bytes(T, L);
+  if (!ws || ws_bytes < head + pl.table_bytes * 2 + 256) return set_error(SVK_ERR_WORKSPACE, "T-form workspace too small");
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  float *Kt = reinterpret_cast<float *>(w);
+  float *ident = Kt + (size_t)T * L * L;
+  const int n = T * L * L > T * T ? T * L * L : T * T;
+  tform_combine_kernel<<<(n + 255) / 256, 256, 0, s>>>(basis, coeffs, N, T, L * L, Kt, ident);
+  svk_frame f{};
+  f.R = R;
+  f.pitch_R = pitch_R;
+  f.I = I;
+  f.pitch_I = pitch_I;
+  f.D = out;
+  f.pitch_D = pitch_out;
+  f.W = W;
+  f.H = H;
+  f.basis = Kt;
+  f.N = T;
+  f.L = L;
+  f.coeffs = ident;
+  f.degree = degree;
+  return launch_set(&f, 1, precision, pl, w + head, ws_bytes - head, s);
+}
+
 size_t batch_workspace_size(const svk_frame *frames, int n, int precision) {
   BatchPlan bp;
   if (plan_batch(frames, n, precision, &bp) != SVK_OK) return 0;
@@ -924,7 +984,7 @@ int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_ou
   float *R = nullptr, *I = nullptr, *D = nullptr, *B = nullptr, *C = nullptr;
   void *ws = nullptr;
   size_t ws_bytes = 0;
-  for (int G = 1; G <= 5; ++G)
+  for (int G = 1; G <= kMaxG; ++G)
     for (int NS = kRowsPerGroup; NS <= kMaxStages; NS += kRowsPerGroup) {
       Plan pl;
       if (make_plan(N, L, precision, G, NS, &pl) && pl.table_bytes * 2 + 256 > ws_bytes) ws_bytes = pl.table_bytes * 2 + 256;
@@ -961,7 +1021,7 @@ int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_ou
     f.L = L;
     f.coeffs = C;
     f.degree = degree;
-    for (int G = 5; G >= 1 && st == SVK_OK; --G)
+    for (int G = kMaxG; G >= 1 && st == SVK_OK; --G)
       for (int NS = kMaxStages; NS >= kRowsPerGroup && st == SVK_OK; NS -= kRowsPerGroup) {
         Plan pl;
         if (!make_plan(N, L, precision, G, NS, &pl)) continue;

@@ -355,7 +355,8 @@ def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=3000):
             "heldout_mse_std_units": float(err.mean()), "heldout_mse_a0": float(err[0]), "prior_mse_std_units": 1.0,
             "frame": {"stamps": 500, "degree": d, "network_s": t_net, "fp64_fit_s": t_fit,
                       "network_chi2_per_px": res["chi2_per_px"], "fit_chi2_per_px": chi2_fit_px,
-                      "noise_floor": res["floor"], "source": res["source"]}}
+                      "noise_floor": res["floor"],
+                      "default_rule_source": "fit" if res["chi2_per_px"] > 2.0 * res["floor"] else "network"}}
 
 
 def _time(torch, fn, reps=5):

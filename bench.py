@@ -84,13 +84,31 @@ def _traffic(precision):
 
 
 def _dist():
+    """(dist module or None, rank, world size, local rank) from the torchrun environment.
+
+    NCCL between GPUs; gloo when CUDA is absent (the host logic's CPU tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend=backend)
         return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
     return None, 0, 1, 0
+
+
+def _max_over_ranks(dist, values, device):
+    """Element-wise maximum of a list of floats over all ranks (the job's slowest rank)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def _job_rate(world, px_per_rank_step, steps, ms):
+    """Whole-job Mpixel/s: every rank's pixels over the slowest rank's time."""
+    return world * px_per_rank_step * steps / (ms / 1e3) / 1e6
 
 
 class ClockSampler:
@@ -139,10 +157,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _frame():
-    import numpy as np
+def _frame_spec(rank=0):
+    """Rank r of a multi-GPU run times its own frame: same shape, seed offset by r."""
+    import dataclasses
     import starfield
     spec = starfield.CONFIGS[1]
+    return spec if rank == 0 else dataclasses.replace(spec, seed=spec.seed + 1000 * rank)
+
+
+def _frame(rank=0):
+    import numpy as np
+    import starfield
+    spec = _frame_spec(rank)
     R, I, _ = starfield.frame_pair(spec)
     c = starfield.planted_coeffs(49, spec.degree, starfield.rng(spec.seed + 7))
     return spec, R.astype(np.float32), I.astype(np.float32), c.astype(np.float32)
@@ -469,7 +495,7 @@ def main():
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     prec = {"bf16x3": svk.SVK_PREC_BF16X3, "fp16x3": svk.SVK_PREC_FP16X3, "bf16": svk.SVK_PREC_BF16}[args.precision]
-    spec, R, I, c = _frame()
+    spec, R, I, c = _frame(rank)
     H, W, L, d = spec.H, spec.W, spec.L, spec.degree
     N = 49
     stream = torch.cuda.current_stream()
@@ -559,13 +585,10 @@ def main():
                                                     precision=prec, out=Dt, workspace=wst), reps=20)
 
     # max over ranks
-    times = torch.tensor([ms_total, e2e_ms, kern_ms, dir_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    ms_total, e2e_ms, kern_ms, dir_ms = times.tolist()
+    ms_total, e2e_ms, kern_ms, dir_ms = _max_over_ranks(dist, [ms_total, e2e_ms, kern_ms, dir_ms], dev)
     px = W * H
-    value = world * px * args.steps / (ms_total / 1e3) / 1e6
-    e2e_value = world * px * n_e2e / (e2e_ms / 1e3) / 1e6
+    value = _job_rate(world, px, args.steps, ms_total)
+    e2e_value = _job_rate(world, px, n_e2e, e2e_ms)
     if rank != 0:
         return
 

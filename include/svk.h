@@ -277,6 +277,49 @@ SVK_API int svk_fit_coeffs(const float *R, const float *I, int W, int H, int pit
                    int bg_degree, const float *weight, double *coeffs_out, double *chi2_out,
                    int *info_out, void *workspace, size_t ws_bytes, int sync, void *stream);
 
+/*
+ * Measured multiply-add throughput of the current device, in FLOP/s (2 per FMA): FP32
+ * FFMA (fp64 == 0) or FP64 DFMA (fp64 != 0).  These are the denominators of the direct
+ * form's roofline (FP32 ALU bound) and of the fit's normal-equation accumulation (FP64).
+ * Tooling with no counterpart in the paper.  Synchronous: launches one warm-up and one
+ * timed kernel (~30 ms) on `stream` and waits for them; allocates a small scratch buffer.
+ *   flops_per_s  host double [1] (output).
+ */
+SVK_API int svk_measure_fma_peak(int fp64, double *flops_per_s, void *stream);
+
+/*
+ * Bytes of device workspace svk_select_stamps needs for a W x H frame (about 4 bytes
+ * per pixel: a peak map and buffers for the largest possible number of peaks).
+ */
+SVK_API size_t svk_select_workspace_size(int W, int H);
+
+/*
+ * Stamp centres for svk_fit_coeffs (Sec. 2: the fit runs over isolated stars; the
+ * paper leaves the selection rule open, this is the library's rule):
+ *   peak        R(p) - sky >= threshold and R(p) > R(q) for every in-frame 8-neighbour q
+ *               (a flat top has no peak);
+ *   selectable  margin <= x <= W-1-margin and margin <= y <= H-1-margin, R(p) <
+ *               saturation, and no other peak q with max(|dx|, |dy|) <= iso_radius has
+ *               R(q) - sky >= iso_frac * (R(p) - sky);
+ *   order       R(p) descending, equal values by y*W + x ascending.
+ * Differences and products are rounded to float32 one at a time.
+ *   R             device float32 [H][pitch]; W * H < 2^31, W, H <= 65535
+ *   sky, threshold, saturation   counts (threshold above sky; saturation is a level of R)
+ *   margin >= 0, 0 <= iso_radius <= 1024, iso_frac >= 0 (finite)
+ *   stamp_xy_out  device int32 [max_stamps][2]: (x, y) of the first selectable peaks in
+ *                 the order above (may be NULL when max_stamps == 0); entries past the
+ *                 selected count are left untouched
+ *   counts_out    device int32 [2]: {number written = min(selectable, max_stamps),
+ *                 number of peaks}
+ *   workspace     device scratch of svk_select_workspace_size(W, H) bytes, or NULL / 0
+ *                 (then allocated on the stream and released after the call).
+ * Asynchronous: the counts are known on the device only; the stamp list can be passed to
+ * svk_fit_coeffs once the caller has read counts_out[0].
+ */
+SVK_API int svk_select_stamps(const float *R, int W, int H, int pitch, float sky, float threshold, float saturation,
+                              int margin, int iso_radius, float iso_frac, int max_stamps, int *stamp_xy_out,
+                              int *counts_out, void *workspace, size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,7 @@ EXPORTS = (
     "svk_convolve", "svk_difference", "svk_fit_workspace_size", "svk_fit_coeffs", "svk_difference_noalloc",
     "svk_batch_workspace_size", "svk_difference_batch", "svk_autotune", "svk_cnn_param_count",
     "svk_cnn_workspace_size", "svk_cnn_forward", "svk_cnn_gradient", "svk_cnn_adam", "svk_cnn_field_fit",
+    "svk_select_workspace_size", "svk_select_stamps", "svk_measure_fma_peak",
 )
 
 
@@ -68,7 +69,7 @@ def load_library(path: str | None = None):
     if not os.path.exists(p):
         raise RuntimeError(f"CUDA library {p} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
     lib = ctypes.CDLL(p)
-    vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    vp, i, sz, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float
     sig = {
         "svk_last_error": (ctypes.c_char_p, []),
         "svk_version": (i, []),
@@ -90,6 +91,9 @@ def load_library(path: str | None = None):
         "svk_cnn_adam": (i, [vp, vp, vp, vp, i, i, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              vp]),
         "svk_cnn_field_fit": (i, [vp, vp, vp, i, i, i, i, i, vp, vp, vp]),
+        "svk_measure_fma_peak": (i, [i, vp, vp]),
+        "svk_select_workspace_size": (sz, [i, i]),
+        "svk_select_stamps": (i, [vp, i, i, i, f, f, f, i, i, f, i, vp, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -281,6 +285,35 @@ def svk_fit_coeffs(R, I, stamp_xy, stamp_size: int, basis, degree: int, bg_degre
                                          _ptr(chi2), _ptr(info), _ptr(workspace), ws_bytes, int(bool(sync)),
                                          _stream(stream)))
     return coeffs, chi2, info
+
+
+def svk_measure_fma_peak(fp64: bool = False, stream=None) -> float:
+    """Measured FP32 (or FP64) multiply-add throughput of the current device, FLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(load_library().svk_measure_fma_peak(int(bool(fp64)), ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
+def svk_select_workspace_size(W: int, H: int) -> int:
+    return int(load_library().svk_select_workspace_size(int(W), int(H)))
+
+
+def svk_select_stamps(R, sky: float, threshold: float, saturation: float, margin: int, iso_radius: int,
+                      iso_frac: float, max_stamps: int, workspace=None, stream=None):
+    """Stamp centres of isolated, unsaturated peaks of R, brightest first.
+
+    Returns (xy int32 [max_stamps][2], counts int32 [2] = {written, peaks}) on the device;
+    rows of xy past counts[0] are zero."""
+    import torch
+    H, W, p = _img(R, "R")
+    xy = torch.zeros((max(int(max_stamps), 0), 2), dtype=torch.int32, device=R.device)
+    counts = torch.zeros(2, dtype=torch.int32, device=R.device)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_select_stamps(_ptr(R), W, H, p, float(sky), float(threshold), float(saturation),
+                                            int(margin), int(iso_radius), float(iso_frac), int(max_stamps),
+                                            _ptr(xy) if max_stamps > 0 else _ptr(None), _ptr(counts),
+                                            _ptr(workspace), ws_bytes, _stream(stream)))
+    return xy, counts
 
 
 # ---------------------------------------------------------------- coefficient network

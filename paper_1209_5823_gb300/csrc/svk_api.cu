@@ -1,6 +1,7 @@
 // svk_api.cu -- the C ABI entry points declared in include/svk.h: argument checks on the
 // host, workspace handling and dispatch to the kernels of the other translation units.
 #include <cudaTypedefs.h>
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -324,6 +325,37 @@ int svk_fit_coeffs(const float *R, const float *I, int W, int H, int pitch, cons
   if (st != SVK_OK) return st;
   if (info >= 0) return set_error(SVK_ERR_NOT_SPD, "normal matrix not positive definite at pivot %d", info);
   return SVK_OK;
+}
+
+int svk_measure_fma_peak(int fp64, double *flops_per_s, void *stream) {
+  if (!flops_per_s) return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  return measure_fma_peak(fp64 ? 1 : 0, flops_per_s, static_cast<cudaStream_t>(stream));
+}
+
+size_t svk_select_workspace_size(int W, int H) {
+  if (W < 1 || H < 1 || W > 65535 || H > 65535 || (long long)W * H >= (1ll << 31)) return 0;
+  return select_workspace_size(W, H);
+}
+
+int svk_select_stamps(const float *R, int W, int H, int pitch, float sky, float threshold, float saturation,
+                      int margin, int iso_radius, float iso_frac, int max_stamps, int *stamp_xy_out, int *counts_out,
+                      void *workspace, size_t ws_bytes, void *stream) {
+  if (!R || !counts_out || (max_stamps > 0 && !stamp_xy_out)) return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  if (W < 1 || H < 1 || W > 65535 || H > 65535 || (long long)W * H >= (1ll << 31) || pitch < W)
+    return set_error(SVK_ERR_ARG, "bad frame size/pitch");
+  if (margin < 0 || iso_radius < 0 || iso_radius > 1024 || max_stamps < 0)
+    return set_error(SVK_ERR_ARG, "margin %d / iso_radius %d / max_stamps %d out of range", margin, iso_radius,
+                     max_stamps);
+  if (!(iso_frac >= 0.0f) || !std::isfinite(iso_frac) || !std::isfinite(sky) || std::isnan(threshold) ||
+      std::isnan(saturation))
+    return set_error(SVK_ERR_ARG, "sky, threshold, saturation and iso_frac must be numbers (iso_frac >= 0)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScopedWorkspace w;
+  const size_t need = select_workspace_size(W, H);
+  int st = w.acquire(need, workspace, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  return launch_select(R, W, H, pitch, sky, threshold, saturation, margin, iso_radius, iso_frac, max_stamps,
+                       stamp_xy_out, counts_out, w.ptr, need, s);
 }
 
 }  // extern "C"

@@ -39,6 +39,15 @@ int launch_fit(const float *R, const float *I, int W, int H, int pitch, const in
                int bg_degree, const float *weight, double *coeffs_out, double *chi2_out,
                int *info_out, void *ws, size_t ws_bytes, cudaStream_t s);
 
+// Stamp selection (svk_stamps.cu).
+size_t select_workspace_size(int W, int H);
+int launch_select(const float *R, int W, int H, int pitch, float sky, float threshold, float saturation, int margin,
+                  int iso_radius, float iso_frac, int max_stamps, int *xy, int *counts, void *ws, size_t ws_bytes,
+                  cudaStream_t s);
+
+// Measured FMA throughput (svk_peaks.cu).
+int measure_fma_peak(int fp64, double *flops_per_s, cudaStream_t s);
+
 // Coefficient network (svk_cnn.cu).
 int cnn_param_count(int n_out);
 size_t cnn_workspace_size(int B, int n_out);

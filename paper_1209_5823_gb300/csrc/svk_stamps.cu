@@ -1,0 +1,211 @@
+// svk_stamps.cu -- choice of the star stamps the least-squares fit runs over.
+//
+// Sec. 2 fits the coefficients over stamps around isolated stars and leaves the rule
+// open.  The rule implemented here:
+//   peak        R(p) - sky >= threshold and R(p) > R(q) for every in-frame 8-neighbour q
+//   selectable  margin <= x <= W-1-margin (likewise y), R(p) < saturation, and no other
+//               peak q with max(|dx|,|dy|) <= iso_radius has
+//               R(q) - sky >= iso_frac * (R(p) - sky)
+//   order       R(p) descending, then the row-major index y*W + x ascending.
+// Differences and products are rounded to float32 one operation at a time (no
+// contraction), so each decision is reproducible.
+//
+// Four steps on the stream, none of which needs the host to know a count:
+//   1. peak_kernel     one thread per pixel: peak map (1 byte/pixel), selectable-position
+//                      candidates appended to a list (order of arrival is irrelevant);
+//   2. isolate_kernel  one thread per candidate: scans its window of the peak map and
+//                      appends a 64-bit sort key (inverted order-preserving bits of R(p),
+//                      then the index) for each isolated one;
+//   3. bitonic sort of the keys, padded to the next power of two of their count read on
+//      the device; the host launches the passes for the largest possible count and the
+//      passes beyond the actual count return at once;
+//   4. output_kernel   the first max_stamps keys -> (x, y), and the counts.
+// Capacity: two peaks are never 8-neighbours, so a frame holds at most
+// ceil(W/2) * ceil(H/2) peaks; every buffer is sized for that.
+#include "svk_common.cuh"
+#include "svk_internal.h"
+
+namespace svk {
+namespace {
+
+constexpr int kLocalSort = 2048;  // keys sorted in shared memory by one block
+constexpr int kGridStride = 152 * 8;
+
+enum Counter { kSel = 0, kCand = 1, kPeaks = 2 };
+
+struct SelectLayout {
+  size_t off_pk, off_cnt, off_cand, off_keys, total;
+  long long cap, cap_p2;
+};
+
+long long next_pow2(long long v) {
+  long long p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+SelectLayout select_layout(int W, int H) {
+  SelectLayout l{};
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  l.cap = (long long)((W + 1) / 2) * ((H + 1) / 2);
+  l.cap_p2 = next_pow2(l.cap < 2 ? 2 : l.cap);
+  if (l.cap_p2 < kLocalSort) l.cap_p2 = kLocalSort;
+  size_t o = 0;
+  l.off_pk = o;
+  o += up((size_t)W * H);
+  l.off_cnt = o;
+  o += 256;
+  l.off_cand = o;
+  o += up((size_t)l.cap * 4);
+  l.off_keys = o;
+  o += (size_t)l.cap_p2 * 8;
+  l.total = o;
+  return l;
+}
+
+__device__ __forceinline__ uint32_t dev_next_pow2(uint32_t v) {
+  uint32_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+__global__ void peak_kernel(const float *__restrict__ R, int W, int H, int pitch, float sky, float thr, float sat,
+                            int margin, unsigned char *__restrict__ pk, int *__restrict__ cand, int *cnt) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W) return;
+  const float v = R[(size_t)y * pitch + x];
+  bool peak = __fsub_rn(v, sky) >= thr;
+  for (int dy = -1; dy <= 1 && peak; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int yy = y + dy, xx = x + dx;
+      if ((dy || dx) && yy >= 0 && yy < H && xx >= 0 && xx < W && !(v > R[(size_t)yy * pitch + xx])) peak = false;
+    }
+  pk[(size_t)y * W + x] = peak ? 1 : 0;
+  if (!peak) return;
+  atomicAdd(&cnt[kPeaks], 1);
+  if (x >= margin && x <= W - 1 - margin && y >= margin && y <= H - 1 - margin && v < sat)
+    cand[atomicAdd(&cnt[kCand], 1)] = y * W + x;
+}
+
+__device__ __forceinline__ unsigned long long sort_key(float v, uint32_t idx) {
+  uint32_t u = __float_as_uint(v);
+  if (u == 0x80000000u) u = 0;                      // -0 ranks with +0
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);   // ascending in v
+  return ((unsigned long long)(~u) << 32) | idx;    // descending v, then ascending index
+}
+
+__global__ void isolate_kernel(const float *__restrict__ R, int W, int H, int pitch, float sky, float frac, int rad,
+                               const unsigned char *__restrict__ pk, const int *__restrict__ cand, int *cnt,
+                               unsigned long long *__restrict__ keys) {
+  const int n = cnt[kCand];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int idx = cand[i], y = idx / W, x = idx % W;
+    const float v = R[(size_t)y * pitch + x];
+    const float bar = __fmul_rn(frac, __fsub_rn(v, sky));
+    bool iso = true;
+    const int y0 = max(0, y - rad), y1 = min(H - 1, y + rad), x0 = max(0, x - rad), x1 = min(W - 1, x + rad);
+    for (int yy = y0; yy <= y1 && iso; ++yy)
+      for (int xx = x0; xx <= x1; ++xx)
+        if (pk[(size_t)yy * W + xx] && (yy != y || xx != x) && __fsub_rn(R[(size_t)yy * pitch + xx], sky) >= bar) {
+          iso = false;
+          break;
+        }
+    if (iso) keys[atomicAdd(&cnt[kSel], 1)] = sort_key(v, (uint32_t)idx);
+  }
+}
+
+__global__ void pad_kernel(unsigned long long *keys, const int *cnt) {
+  const uint32_t n = (uint32_t)cnt[kSel], np2 = dev_next_pow2(n);
+  for (uint32_t i = n + blockIdx.x * blockDim.x + threadIdx.x; i < np2; i += gridDim.x * blockDim.x) keys[i] = ~0ull;
+}
+
+// One compare-exchange stage (k, j) of the bitonic network over the padded keys.
+__global__ void bitonic_global(unsigned long long *keys, const int *cnt, uint32_t k, uint32_t j) {
+  const uint32_t np2 = dev_next_pow2((uint32_t)cnt[kSel]);
+  if (k > np2) return;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np2; i += gridDim.x * blockDim.x) {
+    const uint32_t l = i ^ j;
+    if (l <= i) continue;
+    const unsigned long long a = keys[i], b = keys[l];
+    const bool up = (i & k) == 0;
+    if ((a > b) == up) {
+      keys[i] = b;
+      keys[l] = a;
+    }
+  }
+}
+
+// Stages k = k_lo .. k_hi (doubling) with j < kLocalSort, in shared memory: each block
+// holds one kLocalSort-key segment (pairs (i, i ^ j) never leave it for j < kLocalSort).
+__global__ void __launch_bounds__(kLocalSort / 2) bitonic_local(unsigned long long *keys, const int *cnt,
+                                                                uint32_t k_lo, uint32_t k_hi) {
+  __shared__ unsigned long long s[kLocalSort];
+  const uint32_t np2 = dev_next_pow2((uint32_t)cnt[kSel]);
+  const uint32_t base = blockIdx.x * kLocalSort;
+  if (k_lo > np2 || base >= np2) return;
+  const uint32_t len = np2 - base < (uint32_t)kLocalSort ? np2 - base : (uint32_t)kLocalSort;
+  for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) s[t] = keys[base + t];
+  __syncthreads();
+  for (uint32_t k = k_lo; k <= k_hi && k <= np2; k <<= 1)
+    for (uint32_t j = (k >> 1) < (uint32_t)(kLocalSort / 2) ? (k >> 1) : (uint32_t)(kLocalSort / 2); j > 0; j >>= 1) {
+      for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) {
+        const uint32_t l = t ^ j;
+        if (l > t && l < len) {
+          const unsigned long long a = s[t], b = s[l];
+          const bool up = ((base + t) & k) == 0;
+          if ((a > b) == up) {
+            s[t] = b;
+            s[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) keys[base + t] = s[t];
+}
+
+__global__ void output_kernel(const unsigned long long *keys, const int *cnt, int W, int max_stamps, int *xy,
+                              int *counts) {
+  const int n = min(cnt[kSel], max_stamps);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t idx = (uint32_t)(keys[i] & 0xFFFFFFFFull);
+    xy[2 * i] = (int)(idx % (uint32_t)W);
+    xy[2 * i + 1] = (int)(idx / (uint32_t)W);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    counts[0] = n;
+    counts[1] = cnt[kPeaks];
+  }
+}
+
+}  // namespace
+
+size_t select_workspace_size(int W, int H) { return select_layout(W, H).total; }
+
+int launch_select(const float *R, int W, int H, int pitch, float sky, float threshold, float saturation, int margin,
+                  int iso_radius, float iso_frac, int max_stamps, int *xy, int *counts, void *ws, size_t ws_bytes,
+                  cudaStream_t s) {
+  const SelectLayout l = select_layout(W, H);
+  if (ws_bytes < l.total) return set_error(SVK_ERR_WORKSPACE, "stamp-selection workspace too small");
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  unsigned char *pk = w + l.off_pk;
+  int *cnt = reinterpret_cast<int *>(w + l.off_cnt);
+  int *cand = reinterpret_cast<int *>(w + l.off_cand);
+  unsigned long long *keys = reinterpret_cast<unsigned long long *>(w + l.off_keys);
+  int st = cuda_status(cudaMemsetAsync(cnt, 0, 16, s), "clear counters");
+  if (st != SVK_OK) return st;
+  peak_kernel<<<dim3((W + 255) / 256, H), 256, 0, s>>>(R, W, H, pitch, sky, threshold, saturation, margin, pk, cand,
+                                                       cnt);
+  isolate_kernel<<<kGridStride, 256, 0, s>>>(R, W, H, pitch, sky, iso_frac, iso_radius, pk, cand, cnt, keys);
+  pad_kernel<<<kGridStride, 256, 0, s>>>(keys, cnt);
+  const uint32_t P = (uint32_t)l.cap_p2, nloc = P / kLocalSort;
+  bitonic_local<<<nloc, kLocalSort / 2, 0, s>>>(keys, cnt, 2u, (uint32_t)kLocalSort);
+  for (uint32_t k = 2 * kLocalSort; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j >= (uint32_t)kLocalSort; j >>= 1) bitonic_global<<<kGridStride, 256, 0, s>>>(keys, cnt, k, j);
+    bitonic_local<<<nloc, kLocalSort / 2, 0, s>>>(keys, cnt, k, k);
+  }
+  output_kernel<<<kGridStride / 8, 256, 0, s>>>(keys, cnt, W, max_stamps, xy, counts);
+  return cuda_status(cudaGetLastError(), "stamp selection launch");
+}
+
+}  // namespace svk

@@ -49,6 +49,12 @@ def _algo_flops_per_px(N, L, degree):
     return 2 * N * L * L + 2 * N * T + 2 * N + 1
 
 
+def _direct_flops_per_px(N, L, degree):
+    """Direct form per pixel: a_k (2NT), K = sum_k a_k B_k (2NL^2), sum K R (2L^2), - I."""
+    T = (degree + 1) * (degree + 2) // 2
+    return 2 * N * T + 2 * N * L * L + 2 * L * L + 1
+
+
 def _raw_mma_flops(W, H, L, G, nmma, n_prod):
     """MMA FLOP one tensor-core launch issues: per block of G output rows the reference
     rows are taken in pairs; a pair costs 2 * (nG // 2) + (nG % 2) K steps of 16 taps, an
@@ -252,27 +258,50 @@ def _night_batch(svk, torch, dev, stream, reps=3):
     return out
 
 
-def _fit_timing(svk, torch, dev, R, I, reps=3):
-    """Device OIS fit at 500 stamps of 41 x 41, L = 25, 49 stamps, cubic coefficients and a
-    constant background (on the 2048 x 4096 frame)."""
-    import numpy as np
-    import starfield
+def _fit_timing(svk, torch, dev, R, I, fp64_peak, reps=3):
+    """Stamp selection and the device OIS fit at 500 stamps of 41 x 41, L = 25, 49 stamps,
+    cubic coefficients and a constant background (on the 2048 x 4096 frame)."""
     H, W = R.shape
-    g = starfield.rng(starfield.BASE_SEED + 2)
-    st = torch.from_numpy(np.stack([g.integers(30, W - 30, 500), g.integers(30, H - 30, 500)], 1).astype(np.int32)).to(dev)
-    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, 25)
     Rt, It = torch.from_numpy(R).to(dev), torch.from_numpy(I).to(dev)
-    ws = torch.empty(svk.svk_fit_workspace_size(500, 41, 49, 25, 3, 0), dtype=torch.uint8, device=dev)
-    svk.svk_fit_coeffs(Rt, It, st, 41, B, 3, bg_degree=0, workspace=ws)
+    # the 500 brightest isolated, unsaturated peaks at least 30 px from the edges with no
+    # other peak above 5 % of their height within their stamp
+    sel = dict(sky=1000.0, threshold=150.0, saturation=20000.0, margin=30, iso_radius=20, iso_frac=0.05,
+               max_stamps=500)
+    wsel = torch.empty(svk.svk_select_workspace_size(W, H), dtype=torch.uint8, device=dev)
+    xy, counts = svk.svk_select_stamps(Rt, workspace=wsel, **sel)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        xy, counts = svk.svk_select_stamps(Rt, workspace=wsel, **sel)
+    e1.record()
+    torch.cuda.synchronize()
+    sel_ms = e0.elapsed_time(e1) / reps
+    n_sel, n_peaks = counts.tolist()
+    if n_sel < 1:
+        raise RuntimeError("no stamp selected on the bench frame")
+    st = xy[:n_sel].contiguous()
+    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, 25)
+    ws = torch.empty(svk.svk_fit_workspace_size(n_sel, 41, 49, 25, 3, 0), dtype=torch.uint8, device=dev)
+    svk.svk_fit_coeffs(Rt, It, st, 41, B, 3, bg_degree=0, workspace=ws)
+    torch.cuda.synchronize()
     e0.record()
     for _ in range(reps):
         co, chi2, info = svk.svk_fit_coeffs(Rt, It, st, 41, B, 3, bg_degree=0, workspace=ws)
     e1.record()
     torch.cuda.synchronize()
-    return {"ms": e0.elapsed_time(e1) / reps, "unknowns": 49 * 10 + 1, "stamp_pixels": 500 * 41 * 41,
-            "info": int(info.item()), "workload": "fit_500x41x41_L25_N49_d3_bg0"}
+    ms = e0.elapsed_time(e1) / reps
+    # FP64 moment accumulation: (N+2)(N+3)/2 column pairs x (1 product + 28 monomial FMAs)
+    # per stamp pixel (N = 49, monomials of degree <= 6)
+    px = n_sel * 41 * 41
+    flop64 = px * (51 * 52 // 2) * (1 + 2 * 28)
+    return {"ms": ms, "unknowns": 49 * 10 + 1, "stamp_pixels": px, "info": int(info.item()),
+            "workload": "fit_500x41x41_L25_N49_d3_bg0",
+            "stamps": {"selected": n_sel, "peaks": n_peaks, "select_ms": sel_ms, "rule": sel},
+            "roofline": {"bound": "fp64", "achieved": flop64 / (ms / 1e3) / 1e12, "peak": fp64_peak / 1e12,
+                         "unit": "TFLOP/s", "frac": flop64 / (ms / 1e3) / fp64_peak,
+                         "note": "FP64 moment FLOP over the whole fit time (selection excluded); peak = "
+                                 "measured DFMA throughput"}}
 
 
 def _precision_table(svk, torch, dev):
@@ -593,6 +622,9 @@ def main():
         return
 
     peak_bf16, hbm, peak_src = _peaks()
+    fp32_peak = svk.svk_measure_fma_peak(False)
+    fp64_peak = svk.svk_measure_fma_peak(True)
+    dir_flop = _direct_flops_per_px(N, L, d) * px
     algo = _algo_flops_per_px(N, L, d) * px
     achieved = algo / (kern_ms / 1e3) / 1e12
     # raw MMA work of the launch (split products, padded taps, window rows), for context:
@@ -618,14 +650,20 @@ def main():
                      "raw_mma_tflops": raw_flops / (kern_ms / 1e3) / 1e12,
                      "raw_mma_frac": raw_flops / (kern_ms / 1e3) / 1e12 / peak_bf16},
         "direct": {"value": world * px / (dir_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_frame": dir_ms,
-                   "dtype": "f32"},
+                   "dtype": "f32",
+                   "roofline": {"bound": "alu", "achieved": dir_flop / (dir_ms / 1e3) / 1e12,
+                                "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                                "frac": dir_flop / (dir_ms / 1e3) / fp32_peak,
+                                "algorithmic_flop_per_px": _direct_flops_per_px(N, L, d),
+                                "peak_source": "measured FP32 FFMA throughput (svk_measure_fma_peak)"}},
+        "measured_fma": {"fp32_tflops": fp32_peak / 1e12, "fp64_tflops": fp64_peak / 1e12},
         "clocks": clocks,
         "tform": {"value": world * px / (tf_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_frame": tf_ms,
                   "form": "sum_t m_t (R (x) K_t) - I, K_t = sum_k c[k][t] B_k (same result, T = 6 convolutions)"},
     }
     if not args.no_extras:
         out["night_batch"] = _night_batch(svk, torch, dev, stream)
-        out["fit"] = _fit_timing(svk, torch, dev, R, I)
+        out["fit"] = _fit_timing(svk, torch, dev, R, I, fp64_peak)
         out["precision"] = _precision_table(svk, torch, dev)
         out["paper_sweep"] = _paper_sweep(svk, torch, dev)
         out["learned"] = _learned(svk, torch, dev, R, I)

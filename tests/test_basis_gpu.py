@@ -44,6 +44,9 @@ def _run(W, H, L, d, N, prec, seed=0, pitch=None, kind=svk.SVK_BASIS_GAUSS, diff
     (300, 77, 19, 2, 49),    # ragged tiles, L = 19 (2-row blocks)
     (260, 40, 25, 3, 49),
     (130, 23, 31, 2, 49),    # largest kernel: 1-row blocks
+    (140, 33, 9, 1, 20),     # packed tails of 1 tap, one full tap group per row
+    (200, 41, 17, 2, 49),    # packed tails of 1 tap, two full groups
+    (150, 61, 25, 2, 10),    # packed tails of 1 tap, three full groups (cross-row K step)
     (47, 38, 7, 3, 5),       # odd pitch, few stamps, 3+ rows per block
     (1, 1, 5, 2, 49),        # 1x1 frame
     (5, 300, 15, 1, 49),     # L > W

@@ -278,6 +278,35 @@ SVK_API int svk_fit_coeffs(const float *R, const float *I, int W, int H, int pit
                    int *info_out, void *workspace, size_t ws_bytes, int sync, void *stream);
 
 /*
+ * Bytes of device workspace svk_difference_host needs: device copies of R, I and D
+ * (W * H * 4 bytes each, rounded up to 256) plus svk_workspace_size() of the method.
+ */
+SVK_API size_t svk_host_workspace_size(int method, int precision, int W, int H, int N, int L, int degree);
+
+/*
+ * D = (R (x) K_{x,y}) - I (Eq. 1) for images in HOST memory: the end-to-end call of a
+ * pipeline whose frames live on the host.  The frame is cut into n_bands row bands
+ * (at most 16; boundaries are rounded to the method's block of output rows); band b's
+ * rows of I and the rows of R it reads are copied in on an internal stream, the band is
+ * computed on `stream` by `method` / `precision` (as svk_difference), and its rows of D
+ * are copied out on a second internal stream, so copies overlap computation.
+ *   R, I       HOST float32 [H][pitch] (page-locked memory lets the copies overlap the
+ *              computation; pageable memory works but serialises them)
+ *   D          HOST float32 [H][pitch] (output; written when the stream reaches the end
+ *              of this call)
+ *   basis, coeffs   DEVICE, as for svk_difference
+ *   workspace  device scratch of svk_host_workspace_size() bytes, or NULL / 0 (then
+ *              allocated on the stream and released after the call).
+ * Asynchronous on `stream`: the call returns once the work is queued; `stream` waits for
+ * the last copy, so synchronising it (or an event recorded on it after the call) makes D
+ * valid.  Calls from several host threads are serialised while they queue work (the two
+ * internal copy streams of a device are shared).
+ */
+SVK_API int svk_difference_host(const float *R, const float *I, float *D, int W, int H, int pitch,
+                                const float *basis, int N, int L, const float *coeffs, int degree, int method,
+                                int precision, int n_bands, void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * Measured multiply-add throughput of the current device, in FLOP/s (2 per FMA): FP32
  * FFMA (fp64 == 0) or FP64 DFMA (fp64 != 0).  These are the denominators of the direct
  * form's roofline (FP32 ALU bound) and of the fit's normal-equation accumulation (FP64).

@@ -39,7 +39,8 @@ EXPORTS = (
     "svk_convolve", "svk_difference", "svk_fit_workspace_size", "svk_fit_coeffs", "svk_difference_noalloc",
     "svk_batch_workspace_size", "svk_difference_batch", "svk_autotune", "svk_cnn_param_count",
     "svk_cnn_workspace_size", "svk_cnn_forward", "svk_cnn_gradient", "svk_cnn_adam", "svk_cnn_field_fit",
-    "svk_select_workspace_size", "svk_select_stamps", "svk_measure_fma_peak",
+    "svk_select_workspace_size", "svk_select_stamps", "svk_measure_fma_peak", "svk_host_workspace_size",
+    "svk_difference_host",
 )
 
 
@@ -92,6 +93,8 @@ def load_library(path: str | None = None):
                              vp]),
         "svk_cnn_field_fit": (i, [vp, vp, vp, i, i, i, i, i, vp, vp, vp]),
         "svk_measure_fma_peak": (i, [i, vp, vp]),
+        "svk_host_workspace_size": (sz, [i, i, i, i, i, i, i]),
+        "svk_difference_host": (i, [vp, vp, vp, i, i, i, vp, i, i, vp, i, i, i, i, vp, sz, vp]),
         "svk_select_workspace_size": (sz, [i, i]),
         "svk_select_stamps": (i, [vp, i, i, i, f, f, f, i, i, f, i, vp, vp, vp, sz, vp]),
     }
@@ -285,6 +288,34 @@ def svk_fit_coeffs(R, I, stamp_xy, stamp_size: int, basis, degree: int, bg_degre
                                          _ptr(chi2), _ptr(info), _ptr(workspace), ws_bytes, int(bool(sync)),
                                          _stream(stream)))
     return coeffs, chi2, info
+
+
+def svk_host_workspace_size(method: int, precision: int, W: int, H: int, N: int, L: int, degree: int) -> int:
+    return int(load_library().svk_host_workspace_size(method, precision, W, H, N, L, degree))
+
+
+def svk_difference_host(R, I, basis, coeffs, degree: int, method: int = SVK_METHOD_BASIS,
+                        precision: int = SVK_PREC_BF16X3, out=None, n_bands: int = 8, workspace=None, stream=None):
+    """D = (R (x) K_{x,y}) - I with R, I and D in host memory (CPU float32 [H][pitch]
+    tensors; pin them for copy/compute overlap).  Asynchronous on the stream: D is valid
+    after the stream is synchronised."""
+    import torch
+    for name, t in (("R", R), ("I", I)):
+        if t.dtype != torch.float32 or t.is_cuda or t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError(f"{name} must be a host float32 [H][pitch] tensor with unit column stride")
+    if R.shape != I.shape or R.stride(0) != I.stride(0):
+        raise ValueError("R and I must have one shape and pitch")
+    H, W = R.shape
+    if out is None:
+        out = torch.empty_strided((H, W), (R.stride(0), 1), dtype=torch.float32, pin_memory=R.is_pinned())
+    if out.shape != R.shape or out.stride(0) != R.stride(0) or out.is_cuda:
+        raise ValueError("out must be a host tensor with the shape and pitch of R")
+    N, L = basis.shape[0], basis.shape[1]
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_difference_host(_ptr(R), _ptr(I), _ptr(out), W, H, R.stride(0), _ptr(basis), N, L,
+                                              _ptr(coeffs), int(degree), int(method), int(precision), int(n_bands),
+                                              _ptr(workspace), ws_bytes, _stream(stream)))
+    return out
 
 
 def svk_measure_fma_peak(fp64: bool = False, stream=None) -> float:

@@ -327,6 +327,26 @@ int svk_fit_coeffs(const float *R, const float *I, int W, int H, int pitch, cons
   return SVK_OK;
 }
 
+size_t svk_host_workspace_size(int method, int precision, int W, int H, int N, int L, int degree) {
+  if (W < 1 || H < 1 || W > 65535 || H > 65535) return 0;
+  return host_workspace_size(method, precision, W, H, N, L, degree);
+}
+
+int svk_difference_host(const float *R, const float *I, float *D, int W, int H, int pitch, const float *basis, int N,
+                        int L, const float *coeffs, int degree, int method, int precision, int n_bands,
+                        void *workspace, size_t ws_bytes, void *stream) {
+  int st = check_conv_args(R, pitch, I, pitch, W, H, basis, N, L, coeffs, degree, method, precision, SVK_EDGE_ZERO,
+                           D, pitch, true);
+  if (st != SVK_OK) return st;
+  if (n_bands < 1) return set_error(SVK_ERR_ARG, "n_bands=%d must be >= 1", n_bands);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScopedWorkspace w;
+  const size_t need = host_workspace_size(method, precision, W, H, N, L, degree);
+  st = w.acquire(need, workspace, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  return launch_host(R, I, D, W, H, pitch, basis, N, L, coeffs, degree, method, precision, n_bands, w.ptr, need, s);
+}
+
 int svk_measure_fma_peak(int fp64, double *flops_per_s, void *stream) {
   if (!flops_per_s) return set_error(SVK_ERR_ARG, "NULL pointer argument");
   return measure_fma_peak(fp64 ? 1 : 0, flops_per_s, static_cast<cudaStream_t>(stream));

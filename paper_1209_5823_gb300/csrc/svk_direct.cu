@@ -20,6 +20,7 @@ namespace svk {
 namespace {
 
 constexpr int kTX = 32, kTY = 8, kP = 4, kTileW = kTX * kP;
+static_assert(kTY == kDirectRows, "row bands of the direct form follow its block height");
 constexpr int kThreads = kTX * kTY;
 
 __host__ __device__ inline int round_up4(int v) { return (v + 3) & ~3; }
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     direct_kernel(const __grid_constant__ CUtensorMap tmR, int use_tma, const float *__restrict__ R,
                   int pitch_R, const float *__restrict__ I, int pitch_I, int W, int H,
                   const float *__restrict__ basis, int N, int L, const float *__restrict__ coeffs,
-                  int degree, float *__restrict__ out, int pitch_out, uint32_t *status) {
+                  int degree, float *__restrict__ out, int pitch_out, int y_begin, int y_end, uint32_t *status) {
   constexpr int NCP = Cfg<NC>::NCP;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uintptr_t>(Cs + NC * 10 + 1) & ~uintptr_t(7));
 
   const int tid = threadIdx.y * kTX + threadIdx.x;
-  const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTY;
+  const int x0 = blockIdx.x * kTileW, y0 = y_begin + blockIdx.y * kTY;
   const int xs = ((x0 - h) >> 2) << 2;  // floor to a multiple of 4 (16-byte TMA origin)
   const int xoff = (x0 - h) - xs;
 
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
 
-  if (y < H) {
+  if (y < y_end) {
 #pragma unroll
     for (int p = 0; p < kP; ++p) {
       const int x = x0 + tx + 32 * p;
@@ -188,7 +189,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int NC>
 int launch_nc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis,
-              int N, int L, const float *coeffs, int degree, float *out, int pitch_out, cudaStream_t s) {
+              int N, int L, const float *coeffs, int degree, float *out, int pitch_out, int y_begin, int y_end,
+              cudaStream_t s) {
   const int h = (L - 1) / 2;
   const size_t smem = direct_smem_bytes<NC>(L);
   cudaError_t e = cudaFuncSetAttribute(direct_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -196,20 +198,26 @@ int launch_nc(const float *R, int pitch_R, const float *I, int pitch_I, int W, i
   CUtensorMap tm;
   memset(&tm, 0, sizeof(tm));
   const int use_tma = encode_tmap_2d_f32(&tm, R, W, H, pitch_R, box_w(h), box_h(h)) ? 1 : 0;
-  dim3 grid((W + kTileW - 1) / kTileW, (H + kTY - 1) / kTY), block(kTX, kTY);
+  dim3 grid((W + kTileW - 1) / kTileW, (y_end - y_begin + kTY - 1) / kTY), block(kTX, kTY);
+  if (grid.y == 0) return SVK_OK;
   direct_kernel<NC><<<grid, block, smem, s>>>(tm, use_tma, R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs,
-                                             degree, out, pitch_out, nullptr);
+                                             degree, out, pitch_out, y_begin, y_end, nullptr);
   return cuda_status(cudaGetLastError(), "direct_kernel launch");
 }
 
 }  // namespace
 
 int launch_direct(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis,
-                  int N, int L, const float *coeffs, int degree, float *out, int pitch_out, cudaStream_t s) {
-  if (N <= 4) return launch_nc<4>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, s);
-  if (N <= 8) return launch_nc<8>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, s);
-  if (N <= 16) return launch_nc<16>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, s);
-  return launch_nc<25>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, s);
+                  int N, int L, const float *coeffs, int degree, float *out, int pitch_out, cudaStream_t s,
+                  int y_begin, int y_end) {
+  if (y_end < 0) y_end = H;
+  if (N <= 4)
+    return launch_nc<4>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  if (N <= 8)
+    return launch_nc<8>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  if (N <= 16)
+    return launch_nc<16>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  return launch_nc<25>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
 }
 
 }  // namespace svk

@@ -1,0 +1,149 @@
+// svk_host.cu -- the difference image of Eq. 1 from host buffers.
+//
+// The frame is cut into row bands.  Band b's rows of I and the rows of R it reads (its
+// rows plus h halo rows below; the rows above arrived with the earlier bands) are copied
+// in on one stream, the band is computed, and its rows of D are copied out on another
+// stream, so the copies of one band overlap the computation of its neighbours.  Bands are
+// computed alternately on the caller's stream and on a second compute stream, so one
+// band's last blocks overlap the next band's first ones instead of idling SMs.  The
+// basis tables are prepared once, before the bands.  Events order the streams; the
+// caller's stream waits for the last copy, so the whole call is one asynchronous
+// operation on it.  Band boundaries are multiples of the kernel's output-row block, so a
+// band's blocks never straddle two bands.
+#include <mutex>
+
+#include "svk_common.cuh"
+#include "svk_internal.h"
+
+namespace svk {
+namespace {
+
+constexpr int kMaxBands = 16;
+constexpr int kMaxDevices = 64;
+
+struct HostStreams {
+  bool ready = false;
+  cudaStream_t h2d = nullptr, d2h = nullptr, comp = nullptr;
+  cudaEvent_t start = nullptr, end = nullptr, in[kMaxBands] = {}, out[kMaxBands] = {};
+};
+
+std::mutex g_host_mutex;  // held while a call enqueues its work (streams and events are shared)
+HostStreams g_host[kMaxDevices];
+
+int host_streams(int dev, HostStreams **hs) {
+  if (dev < 0 || dev >= kMaxDevices) return set_error(SVK_ERR_UNSUPPORTED, "device %d out of range", dev);
+  HostStreams &h = g_host[dev];
+  if (!h.ready) {
+    int st = cuda_status(cudaStreamCreateWithFlags(&h.h2d, cudaStreamNonBlocking), "copy-in stream");
+    if (st == SVK_OK) st = cuda_status(cudaStreamCreateWithFlags(&h.d2h, cudaStreamNonBlocking), "copy-out stream");
+    if (st == SVK_OK) st = cuda_status(cudaStreamCreateWithFlags(&h.comp, cudaStreamNonBlocking), "compute stream");
+    if (st == SVK_OK) st = cuda_status(cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming), "event");
+    if (st == SVK_OK) st = cuda_status(cudaEventCreateWithFlags(&h.end, cudaEventDisableTiming), "event");
+    for (int b = 0; b < kMaxBands && st == SVK_OK; ++b) {
+      st = cuda_status(cudaEventCreateWithFlags(&h.in[b], cudaEventDisableTiming), "event");
+      if (st == SVK_OK) st = cuda_status(cudaEventCreateWithFlags(&h.out[b], cudaEventDisableTiming), "event");
+    }
+    if (st != SVK_OK) return st;
+    h.ready = true;
+  }
+  *hs = &h;
+  return SVK_OK;
+}
+
+size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
+
+size_t method_ws(int method, int precision, int N, int L, int degree) {
+  if (method == SVK_METHOD_BASIS) return tc_workspace_size(precision, N, L);
+  if (method == SVK_METHOD_TFORM) return tform_workspace_size(precision, L, degree);
+  return 0;
+}
+
+}  // namespace
+
+size_t host_workspace_size(int method, int precision, int W, int H, int N, int L, int degree) {
+  return 3 * up256((size_t)W * H * sizeof(float)) + method_ws(method, precision, N, L, degree);
+}
+
+int launch_host(const float *R, const float *I, float *D, int W, int H, int pitch, const float *basis, int N, int L,
+                const float *coeffs, int degree, int method, int precision, int n_bands, void *ws, size_t ws_bytes,
+                cudaStream_t s) {
+  const int h = (L - 1) / 2;
+  int gran = kDirectRows;
+  if (method != SVK_METHOD_DIRECT) {
+    gran = tc_rows_per_block(method == SVK_METHOD_TFORM ? n_terms(degree) : N, L, precision);
+    if (gran < 1) return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan for N=%d L=%d", N, L);
+  }
+  // band boundaries: multiples of gran, at most kMaxBands bands, none empty
+  int yb[kMaxBands + 1], nb = 0;
+  const int want = n_bands < 1 ? 1 : (n_bands > kMaxBands ? kMaxBands : n_bands);
+  yb[0] = 0;
+  for (int b = 1; b < want; ++b) {
+    const int y = (int)((long long)b * H / want) / gran * gran;
+    if (y > yb[nb] && y < H) yb[++nb] = y;
+  }
+  yb[++nb] = H;
+
+  const size_t frame = up256((size_t)W * H * sizeof(float));
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  float *Rd = reinterpret_cast<float *>(w), *Id = reinterpret_cast<float *>(w + frame);
+  float *Dd = reinterpret_cast<float *>(w + 2 * frame);
+  void *mws = w + 3 * frame;
+  const size_t mws_bytes = ws_bytes - 3 * frame;
+  const size_t row = (size_t)W * sizeof(float), hrow = (size_t)pitch * sizeof(float);
+
+  int dev = 0;
+  int st = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+  if (st != SVK_OK) return st;
+  std::lock_guard<std::mutex> lock(g_host_mutex);
+  HostStreams *hs = nullptr;
+  if ((st = host_streams(dev, &hs)) != SVK_OK) return st;
+  // the copies start after the caller's earlier work on its stream (the workspace may be
+  // in use there); the tables are prepared there first (a launch over no rows)
+  if (method == SVK_METHOD_TFORM)
+    st = launch_tform(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, precision, Dd, W, mws, mws_bytes, s, 0, 0, true);
+  else if (method == SVK_METHOD_BASIS)
+    st = launch_tc(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, precision, Dd, W, mws, mws_bytes, s, 0, 0, true);
+  if (st != SVK_OK) return st;
+  if ((st = cuda_status(cudaEventRecord(hs->start, s), "event record")) != SVK_OK) return st;
+  if ((st = cuda_status(cudaStreamWaitEvent(hs->h2d, hs->start, 0), "stream wait")) != SVK_OK) return st;
+  if ((st = cuda_status(cudaStreamWaitEvent(hs->d2h, hs->start, 0), "stream wait")) != SVK_OK) return st;
+  if ((st = cuda_status(cudaStreamWaitEvent(hs->comp, hs->start, 0), "stream wait")) != SVK_OK) return st;
+  int r_done = 0;  // rows of R already on their way
+  for (int b = 0; b < nb; ++b) {
+    const int y0 = yb[b], y1 = yb[b + 1];
+    const int r_need = y1 + h < H ? y1 + h : H;
+    if (r_need > r_done) {
+      st = cuda_status(cudaMemcpy2DAsync(Rd + (size_t)r_done * W, row, R + (size_t)r_done * pitch, hrow, row,
+                                         (size_t)(r_need - r_done), cudaMemcpyHostToDevice, hs->h2d),
+                       "copy R in");
+      if (st != SVK_OK) return st;
+      r_done = r_need;
+    }
+    st = cuda_status(cudaMemcpy2DAsync(Id + (size_t)y0 * W, row, I + (size_t)y0 * pitch, hrow, row,
+                                       (size_t)(y1 - y0), cudaMemcpyHostToDevice, hs->h2d),
+                     "copy I in");
+    if (st != SVK_OK) return st;
+    if ((st = cuda_status(cudaEventRecord(hs->in[b], hs->h2d), "event record")) != SVK_OK) return st;
+    cudaStream_t cs = (b & 1) ? hs->comp : s;
+    if ((st = cuda_status(cudaStreamWaitEvent(cs, hs->in[b], 0), "stream wait")) != SVK_OK) return st;
+    if (method == SVK_METHOD_DIRECT)
+      st = launch_direct(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, Dd, W, cs, y0, y1);
+    else if (method == SVK_METHOD_TFORM)
+      st = launch_tform(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, precision, Dd, W, mws, mws_bytes, cs, y0,
+                        y1, false);
+    else
+      st = launch_tc(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, precision, Dd, W, mws, mws_bytes, cs, y0, y1,
+                     false);
+    if (st != SVK_OK) return st;
+    if ((st = cuda_status(cudaEventRecord(hs->out[b], cs), "event record")) != SVK_OK) return st;
+    if ((st = cuda_status(cudaStreamWaitEvent(hs->d2h, hs->out[b], 0), "stream wait")) != SVK_OK) return st;
+    st = cuda_status(cudaMemcpy2DAsync(D + (size_t)y0 * pitch, hrow, Dd + (size_t)y0 * W, row, row,
+                                       (size_t)(y1 - y0), cudaMemcpyDeviceToHost, hs->d2h),
+                     "copy D out");
+    if (st != SVK_OK) return st;
+  }
+  if ((st = cuda_status(cudaEventRecord(hs->end, hs->d2h), "event record")) != SVK_OK) return st;
+  return cuda_status(cudaStreamWaitEvent(s, hs->end, 0), "stream wait");
+}
+
+}  // namespace svk

@@ -10,9 +10,12 @@ namespace svk {
 
 // Direct form (svk_direct.cu): kernel of Eq. 2 formed at every output pixel, FP32 FFMA.
 // I may be NULL (plain convolution).  Arguments already validated.
+// y_begin / y_end: the output rows to compute (-1 = to the last row); band starts must
+// be multiples of kDirectRows.
+constexpr int kDirectRows = 8;
 int launch_direct(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
                   const float *basis, int N, int L, const float *coeffs, int degree, float *out,
-                  int pitch_out, cudaStream_t s);
+                  int pitch_out, cudaStream_t s, int y_begin = 0, int y_end = -1);
 
 // Basis tabulation (svk_basis.cu).
 int launch_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg,
@@ -20,14 +23,20 @@ int launch_build_basis(int kind, int L, int n_gauss, const double *sigma, const 
 
 // Tensor-core basis form (svk_tc.cu).
 size_t tc_workspace_size(int precision, int N, int L);
+// y_begin / y_end: the output rows to compute (a band of the frame; -1 = to the last
+// row); prep = false reuses the tables an earlier call with the same arguments and
+// workspace prepared.  Band starts other than 0 must be multiples of
+// tc_rows_per_block(N or T, L, precision).
 int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
               const float *basis, int N, int L, const float *coeffs, int degree, int precision,
-              float *out, int pitch_out, void *ws, size_t ws_bytes, cudaStream_t s);
+              float *out, int pitch_out, void *ws, size_t ws_bytes, cudaStream_t s,
+              int y_begin = 0, int y_end = -1, bool prep = true);
+int tc_rows_per_block(int N, int L, int precision);  // 0 when no plan fits
 
 size_t tform_workspace_size(int precision, int L, int degree);
 int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis, int N,
                  int L, const float *coeffs, int degree, int precision, float *out, int pitch_out, void *ws,
-                 size_t ws_bytes, cudaStream_t s);
+                 size_t ws_bytes, cudaStream_t s, int y_begin = 0, int y_end = -1, bool prep = true);
 int launch_batch(const svk_frame *frames, int n, int precision, void *ws, size_t ws_bytes, cudaStream_t s);
 size_t batch_workspace_size(const svk_frame *frames, int n, int precision);
 int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out, cudaStream_t s);
@@ -38,6 +47,12 @@ int launch_fit(const float *R, const float *I, int W, int H, int pitch, const in
                int n_stamps, int stamp_size, const float *basis, int N, int L, int degree,
                int bg_degree, const float *weight, double *coeffs_out, double *chi2_out,
                int *info_out, void *ws, size_t ws_bytes, cudaStream_t s);
+
+// The difference image from host buffers, pipelined over row bands (svk_host.cu).
+size_t host_workspace_size(int method, int precision, int W, int H, int N, int L, int degree);
+int launch_host(const float *R, const float *I, float *D, int W, int H, int pitch, const float *basis, int N, int L,
+                const float *coeffs, int degree, int method, int precision, int n_bands, void *ws, size_t ws_bytes,
+                cudaStream_t s);
 
 // Stamp selection (svk_stamps.cu).
 size_t select_workspace_size(int W, int H);

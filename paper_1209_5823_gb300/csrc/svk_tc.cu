@@ -246,6 +246,7 @@ struct FrameDesc {
   const float *coeffs;
   const uint4 *tab_hi, *tab_lo;  // this frame's basis tables (shared by frames with one basis)
   int W, H, pitch_R, pitch_I, pitch_out, degree;
+  int y_begin, y_end;  // output rows of this launch (a band of the frame, or all of it)
   int nbx, block0;  // blocks per band of G rows; first block of the frame in the set
   float rscale, out_scale;
 };
@@ -263,7 +264,7 @@ __device__ __forceinline__ int advance_frame(const FrameSet &fs, int f, int b) {
 __device__ __forceinline__ void block_origin(const FrameDesc &fd, int b, int G, int &x0, int &y0) {
   const int lb = b - fd.block0;
   x0 = (lb % fd.nbx) * kTileM;
-  y0 = (lb / fd.nbx) * G;
+  y0 = fd.y_begin + (lb / fd.nbx) * G;
 }
 
 __device__ __forceinline__ void cta_block_range(const FrameSet &fs, int &b0, int &b1) {
@@ -579,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int g = par + 2 * j;
-        v[j] = (ok && fq.I && g < G && yq + g < fq.H && xq + m < fq.W)
+        v[j] = (ok && fq.I && g < G && yq + g < fq.y_end && xq + m < fq.W)
                    ? __ldg(fq.I + (size_t)(yq + g) * fq.pitch_I + xq + m) : 0.0f;
       }
     };
@@ -652,7 +653,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
       for (int j = 0;; ++j) {
         const int g = par + 2 * j;
-        if (g >= G || y0 + g >= fd.H) break;
+        if (g >= G || y0 + g >= fd.y_end) break;
         // rows beyond the first three per warp (plans with G > 6) read I here
         const float iv = j == 0 ? ival[0] : j == 1 ? ival[1] : j == 2 ? ival[2]
                        : (fd.I && x < fd.W ? __ldg(fd.I + (size_t)(y0 + g) * fd.pitch_I + x) : 0.0f);
@@ -761,7 +762,8 @@ size_t set_workspace(const svk_frame *fr, int n, const Plan &pl) {
 }
 
 template <int P>
-int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *ws, cudaStream_t s) {
+int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *ws, const int *rows, bool prep,
+                    cudaStream_t s) {
   static FrameSet fs;  // built on the host, passed by value as the kernel parameter
   static std::mutex fs_mutex;
   std::lock_guard<std::mutex> lock(fs_mutex);
@@ -782,9 +784,11 @@ int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *w
     d.pitch_I = fr[i].pitch_I;
     d.pitch_out = fr[i].pitch_D;
     d.degree = fr[i].degree;
+    d.y_begin = rows ? rows[2 * i] : 0;
+    d.y_end = rows ? rows[2 * i + 1] : fr[i].H;
     d.nbx = (fr[i].W + kTileM - 1) / kTileM;
     d.block0 = blocks;
-    blocks += d.nbx * ((fr[i].H + pl.G - 1) / pl.G);
+    blocks += d.nbx * ((d.y_end - d.y_begin + pl.G - 1) / pl.G);
     d.rscale = rscale;
     d.out_scale = 1.0f / (bscale * rscale);
     int same = -1;
@@ -796,7 +800,8 @@ int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *w
     } else {
       uint4 *th = reinterpret_cast<uint4 *>(ws + (size_t)ntab * pl.table_bytes * 2);
       uint4 *tl = reinterpret_cast<uint4 *>(ws + (size_t)ntab * pl.table_bytes * 2 + pl.table_bytes);
-      tc_prep_table<P><<<(nrow_items + 255) / 256, 256, 0, s>>>(fr[i].basis, pl, bscale, th, pl.parts == 2 ? tl : nullptr);
+      if (prep)
+        tc_prep_table<P><<<(nrow_items + 255) / 256, 256, 0, s>>>(fr[i].basis, pl, bscale, th, pl.parts == 2 ? tl : nullptr);
       d.tab_hi = th;
       d.tab_lo = tl;
       ++ntab;
@@ -816,13 +821,17 @@ int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *w
   return cuda_status(cudaGetLastError(), "tc_basis_kernel launch");
 }
 
-int launch_set(const svk_frame *fr, int n, int prec, const Plan &pl, void *ws, size_t ws_bytes, cudaStream_t s) {
+// rows: per frame the output rows [rows[2i], rows[2i+1]) (multiples of G apart from the
+// frame's last row), or NULL for whole frames; prep = false reuses the basis tables an
+// earlier launch with the same plan, basis and workspace prepared.
+int launch_set(const svk_frame *fr, int n, int prec, const Plan &pl, void *ws, size_t ws_bytes, cudaStream_t s,
+               const int *rows = nullptr, bool prep = true) {
   if (n < 1 || n > kMaxFrames) return set_error(SVK_ERR_ARG, "frame set of %d (1..%d)", n, kMaxFrames);
   if (!ws || ws_bytes < set_workspace(fr, n, pl)) return set_error(SVK_ERR_WORKSPACE, "tensor-core workspace too small");
   unsigned char *w = static_cast<unsigned char *>(ws);
-  if (prec == SVK_PREC_BF16X3) return launch_set_prec<SVK_PREC_BF16X3>(fr, n, pl, w, s);
-  if (prec == SVK_PREC_FP16X3) return launch_set_prec<SVK_PREC_FP16X3>(fr, n, pl, w, s);
-  return launch_set_prec<SVK_PREC_BF16>(fr, n, pl, w, s);
+  if (prec == SVK_PREC_BF16X3) return launch_set_prec<SVK_PREC_BF16X3>(fr, n, pl, w, rows, prep, s);
+  if (prec == SVK_PREC_FP16X3) return launch_set_prec<SVK_PREC_FP16X3>(fr, n, pl, w, rows, prep, s);
+  return launch_set_prec<SVK_PREC_BF16>(fr, n, pl, w, rows, prep, s);
 }
 
 // Frames of a batch grouped by (N, L): launches of up to kMaxFrames frames each.
@@ -877,7 +886,7 @@ size_t tc_workspace_size(int precision, int N, int L) {
 
 int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis, int N,
               int L, const float *coeffs, int degree, int precision, float *out, int pitch_out, void *ws,
-              size_t ws_bytes, cudaStream_t s) {
+              size_t ws_bytes, cudaStream_t s, int y_begin, int y_end, bool prep) {
   Plan pl;
   if (!plan_for(N, L, precision, &pl))
     return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan fits shared memory for N=%d L=%d", N, L);
@@ -895,7 +904,13 @@ int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, i
   f.L = L;
   f.coeffs = coeffs;
   f.degree = degree;
-  return launch_set(&f, 1, precision, pl, ws, ws_bytes, s);
+  const int rows[2] = {y_begin, y_end < 0 ? H : y_end};
+  return launch_set(&f, 1, precision, pl, ws, ws_bytes, s, rows, prep);
+}
+
+int tc_rows_per_block(int N, int L, int precision) {
+  Plan pl;
+  return plan_for(N, L, precision, &pl) ? pl.G : 0;
 }
 
 namespace {
@@ -925,7 +940,7 @@ size_t tform_workspace_size(int precision, int L, int degree) {
 
 int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis, int N,
                  int L, const float *coeffs, int degree, int precision, float *out, int pitch_out, void *ws,
-                 size_t ws_bytes, cudaStream_t s) {
+                 size_t ws_bytes, cudaStream_t s, int y_begin, int y_end, bool prep) {
   const int T = n_terms(degree);
   Plan pl;
   if (!plan_for(T, L, precision, &pl))
@@ -936,7 +951,7 @@ int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W
   float *Kt = reinterpret_cast<float *>(w);
   float *ident = Kt + (size_t)T * L * L;
   const int n = T * L * L > T * T ? T * L * L : T * T;
-  tform_combine_kernel<<<(n + 255) / 256, 256, 0, s>>>(basis, coeffs, N, T, L * L, Kt, ident);
+  if (prep) tform_combine_kernel<<<(n + 255) / 256, 256, 0, s>>>(basis, coeffs, N, T, L * L, Kt, ident);
   svk_frame f{};
   f.R = R;
   f.pitch_R = pitch_R;
@@ -951,7 +966,8 @@ int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W
   f.L = L;
   f.coeffs = ident;
   f.degree = degree;
-  return launch_set(&f, 1, precision, pl, w + head, ws_bytes - head, s);
+  const int rows[2] = {y_begin, y_end < 0 ? H : y_end};
+  return launch_set(&f, 1, precision, pl, w + head, ws_bytes - head, s, rows, prep);
 }
 
 size_t batch_workspace_size(const svk_frame *frames, int n, int precision) {

@@ -5,7 +5,8 @@
 // Model at a stamp pixel p:  sum_k sum_t c[k][t] m_t(p) C_k(p) + sum_j g_j m_j(p),
 // C_k = R (x) B_k.  Normal equations A c = b with A = sum w v v^T, b = sum w v I.
 //
-// 1. fit_ck_kernel     C_k at every stamp pixel, FP32 (one thread per pixel).
+// 1. fit_ck_kernel     C_k at every stamp pixel, FP32 (R patch and basis chunks staged in
+//                      shared memory; 4 pixels x 7 stamps per thread).
 // 2. fit_gram_kernel   FP64 weighted moments over the extended columns
 //                      E = [C_0 .. C_{N-1}, I, 1]:
 //                        S[e1][e2][mu] = sum_p w E_e1 E_e2 mu(p)
@@ -13,9 +14,9 @@
 //                      A and b is one of these moments (m_t m_t' = mu_{t+t'}), so the
 //                      per-pixel work is (N+2)(N+3)/2 products x n_mu FMAs instead of M^2.
 // 3. fit_assemble      A, b from S.
-// 4. fit_cholesky      FP64 Cholesky (left-looking, one CTA); the first non-positive pivot
-//                      is reported in info and the solve is skipped.
-// 5. fit_solve         forward / backward substitution.
+// 4. chol_*            FP64 blocked Cholesky over the whole GPU; the first non-positive
+//                      pivot is reported in info and the solve is skipped.
+// 5. fit_solve         forward / backward substitution (one CTA).
 // 6. fit_chi2_kernel   chi^2 = sum w (model - I)^2 at the solution, a direct second pass.
 #include "svk_common.cuh"
 #include "svk_internal.h"
@@ -44,30 +45,80 @@ __device__ inline void stamp_pixel(const FitDims &f, const int *stamp_xy, int p,
   y = stamp_xy[2 * s + 1] - hs + q / f.S;
 }
 
-// C[p][k] = sum_{u,v} B_k(u,v) R(x - u, y - v), zero outside the frame (FP32)
-__global__ void fit_ck_kernel(const float *__restrict__ R, const float *__restrict__ basis, const int *stamp_xy,
-                              FitDims f, float *__restrict__ C) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= f.P) return;
-  int x, y;
-  stamp_pixel(f, stamp_xy, p, x, y);
-  const int h = (f.L - 1) / 2, LL = f.L * f.L;
-  const bool inside = x >= 0 && x < f.W && y >= 0 && y < f.H;
-  for (int k = 0; k < f.N; ++k) {
-    float acc = 0.0f;
-    if (inside) {
-      const float *bk = basis + (size_t)k * LL;
-      for (int vi = 0; vi < f.L; ++vi) {
-        const int yy = y - (vi - h);
-        if (yy < 0 || yy >= f.H) continue;
-        const float *rrow = R + (size_t)yy * f.pitch;
-        for (int ui = 0; ui < f.L; ++ui) {
-          const int xx = x - (ui - h);
-          if (xx >= 0 && xx < f.W) acc = fmaf(bk[vi * f.L + ui], __ldg(rrow + xx), acc);
+// C[p][k] = sum_{u,v} B_k(u,v) R(x - u, y - v), zero outside the frame (FP32).  CTA =
+// one tile of `ty` rows of one stamp: the R patch the tile reads (its pixels plus the
+// kernel halo, zero outside the frame) is staged in shared memory, the basis kCkStamps
+// stamps at a time ([tap][8] rows, read as two float4 broadcasts).  Thread = 4 pixels
+// (linear tile indices t, t + 256, ...), each with kCkStamps accumulators.
+constexpr int kCkThreads = 256, kCkPix = 4, kCkStamps = 7;
+
+int ck_tile_rows(int S) { return S >= kCkThreads * kCkPix ? 1 : (kCkThreads * kCkPix) / S; }
+
+size_t ck_smem_bytes(int S, int L, int ty) {
+  return ((size_t)(S + L - 1) * (ty + L - 1) + 3) / 4 * 16 + (size_t)L * L * 8 * sizeof(float);
+}
+
+__global__ void __launch_bounds__(kCkThreads) fit_ck_kernel(const float *__restrict__ R, const float *__restrict__ basis,
+                                                            const int *stamp_xy, FitDims f, int ty, float *__restrict__ C) {
+  extern __shared__ float4 ck_smem[];
+  const int st = blockIdx.x, ty0 = blockIdx.y * ty, S = f.S, L = f.L, h = (L - 1) / 2, hs = (S - 1) / 2;
+  const int rows = min(ty, S - ty0);
+  if (rows <= 0) return;
+  const int PW = S + L - 1, PH = rows + L - 1, LL = L * L;
+  float *Rp = reinterpret_cast<float *>(ck_smem);
+  float4 *Bs = ck_smem + (PW * PH + 3) / 4;  // [tap][2] float4 = 8 stamps (7 used)
+  const int xs = stamp_xy[2 * st], ys = stamp_xy[2 * st + 1];
+  const int ox = xs - hs - h, oy = ys - hs + ty0 - h;  // frame position of Rp[0][0]
+  for (int e = threadIdx.x; e < PW * PH; e += blockDim.x) {
+    const int gx = ox + e % PW, gy = oy + e / PW;
+    Rp[e] = (gx >= 0 && gx < f.W && gy >= 0 && gy < f.H) ? __ldg(R + (size_t)gy * f.pitch + gx) : 0.0f;
+  }
+  int off[kCkPix];      // Rp index of tap (0, 0) for the pixel: (qy + 2h) * PW + qx + 2h
+  int pglob[kCkPix];    // global stamp-pixel index, or -1
+  bool inside[kCkPix];
+#pragma unroll
+  for (int m = 0; m < kCkPix; ++m) {
+    const int q = threadIdx.x + kCkThreads * m;
+    const int qy = q / S, qx = q % S;
+    const bool valid = q < rows * S;
+    off[m] = valid ? (qy + 2 * h) * PW + qx + 2 * h : 2 * h * PW + 2 * h;
+    pglob[m] = valid ? st * S * S + (ty0 + qy) * S + qx : -1;
+    const int x = xs - hs + qx, y = ys - hs + ty0 + qy;
+    inside[m] = valid && x >= 0 && x < f.W && y >= 0 && y < f.H;
+  }
+  for (int k0 = 0; k0 < f.N; k0 += kCkStamps) {
+    __syncthreads();  // the previous chunk is consumed (first time: the patch is staged)
+    for (int e = threadIdx.x; e < LL * 8; e += blockDim.x) {
+      const int tap = e >> 3, j = e & 7;
+      reinterpret_cast<float *>(Bs)[e] = (j < kCkStamps && k0 + j < f.N) ? basis[(size_t)(k0 + j) * LL + tap] : 0.0f;
+    }
+    __syncthreads();
+    float acc[kCkPix][kCkStamps];
+#pragma unroll
+    for (int m = 0; m < kCkPix; ++m)
+#pragma unroll
+      for (int j = 0; j < kCkStamps; ++j) acc[m][j] = 0.0f;
+    for (int vi = 0; vi < L; ++vi) {
+      const float4 *brow = Bs + vi * L * 2;
+      const int rbase = -vi * PW;
+#pragma unroll 2
+      for (int ui = 0; ui < L; ++ui) {
+        const float4 b0 = brow[2 * ui], b1 = brow[2 * ui + 1];
+        const float bv[kCkStamps] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z};
+#pragma unroll
+        for (int m = 0; m < kCkPix; ++m) {
+          const float r = Rp[off[m] + rbase - ui];
+#pragma unroll
+          for (int j = 0; j < kCkStamps; ++j) acc[m][j] = fmaf(bv[j], r, acc[m][j]);
         }
       }
     }
-    C[(size_t)p * f.N + k] = acc;
+#pragma unroll
+    for (int m = 0; m < kCkPix; ++m)
+      if (pglob[m] >= 0)
+#pragma unroll
+        for (int j = 0; j < kCkStamps; ++j)
+          if (k0 + j < f.N) C[(size_t)pglob[m] * f.N + k0 + j] = inside[m] ? acc[m][j] : 0.0f;
   }
 }
 
@@ -209,60 +260,152 @@ __device__ double block_sum_d(double v, double *red) {
   return s;
 }
 
-// Left-looking Cholesky in place (lower triangle of row-major A), one CTA; *info = -1 on
-// success, else the first column whose pivot is not positive.
-__global__ void __launch_bounds__(1024) fit_cholesky_kernel(double *A, int M, int *info) {
-  __shared__ double red[32];
-  __shared__ double piv;
+// Blocked right-looking Cholesky in place (lower triangle of row-major A, M x M), panels
+// of kPanel columns.  FP64 runs at a small fraction of the FP32 rate on this part, so the
+// O(M^3) work is spread over the whole GPU: per panel p,
+//   chol_diag_kernel    factors the kPanel x kPanel diagonal block in shared memory (one
+//                       CTA) and reports the first non-positive pivot in *info;
+//   chol_trsm_kernel    A[i][panel] <- A[i][panel] L_pp^-T for the rows below (one row per
+//                       thread);
+//   chol_update_kernel  A[i][j] -= sum_{k in panel} A[i][k] A[j][k] for the trailing lower
+//                       triangle (32 x 32 tiles).
+// Every kernel returns at once when *info >= 0 (an earlier pivot failed).
+constexpr int kPanel = 64;
+
+__global__ void __launch_bounds__(256) chol_diag_kernel(double *A, int M, int p, int *info) {
+  __shared__ double Ls[kPanel][kPanel + 1];
   __shared__ int fail;
+  if (*info >= 0) return;
+  const int b = min(kPanel, M - p);
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int r = e / b, c = e % b;
+    Ls[r][c] = c <= r ? A[(size_t)(p + r) * M + p + c] : 0.0;
+  }
   if (threadIdx.x == 0) fail = -1;
-  for (int j = 0; j < M; ++j) {
-    double part = 0.0;
-    const double *rj = A + (size_t)j * M;
-    for (int k = threadIdx.x; k < j; k += blockDim.x) part = fma(rj[k], rj[k], part);
-    const double s = block_sum_d(part, red);
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
     if (threadIdx.x == 0) {
-      const double dd = rj[j] - s;
-      if (!(dd > 0.0)) fail = j;
-      else piv = sqrt(dd);
+      const double d = Ls[j][j];
+      if (!(d > 0.0)) fail = p + j;
+      else Ls[j][j] = sqrt(d);
     }
     __syncthreads();
     if (fail >= 0) break;
-    const double gjj = piv;
-    if (threadIdx.x == 0) A[(size_t)j * M + j] = gjj;
-    for (int i = j + 1 + threadIdx.x; i < M; i += blockDim.x) {
-      const double *ri = A + (size_t)i * M;
-      double acc = ri[j];
-      for (int k = 0; k < j; ++k) acc = fma(-ri[k], rj[k], acc);
-      A[(size_t)i * M + j] = acc / gjj;
+    const double inv = 1.0 / Ls[j][j];
+    for (int i = j + 1 + threadIdx.x; i < b; i += blockDim.x) Ls[i][j] *= inv;
+    __syncthreads();
+    const int n = b - j - 1;  // trailing triangle of the block
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int r = j + 1 + e / n, c = j + 1 + e % n;
+      if (c <= r) Ls[r][c] = fma(-Ls[r][j], Ls[c][j], Ls[r][c]);
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *info = fail;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int r = e / b, c = e % b;
+    if (c <= r) A[(size_t)(p + r) * M + p + c] = Ls[r][c];
+  }
+  if (threadIdx.x == 0 && fail >= 0) *info = fail;
 }
 
-// G G^T x = b (G from fit_cholesky_kernel); skipped, leaving x = 0, when info >= 0.
-__global__ void __launch_bounds__(1024) fit_solve_kernel(const double *G, const double *b, int M, const int *info,
-                                                         double *x) {
-  __shared__ double red[32];
+__global__ void __launch_bounds__(64) chol_trsm_kernel(double *A, int M, int p, const int *info) {
+  __shared__ double Ls[kPanel][kPanel + 1];
+  if (*info >= 0) return;
+  const int b = min(kPanel, M - p);
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int r = e / b, c = e % b;
+    Ls[r][c] = c <= r ? A[(size_t)(p + r) * M + p + c] : 0.0;
+  }
+  __syncthreads();
+  const int i = p + b + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double x[kPanel];
+  double *row = A + (size_t)i * M + p;
+#pragma unroll
+  for (int c = 0; c < kPanel; ++c) x[c] = c < b ? row[c] : 0.0;
+#pragma unroll
+  for (int c = 0; c < kPanel; ++c) {
+    if (c < b) {
+      double s = x[c];
+#pragma unroll
+      for (int k = 0; k < c; ++k) s = fma(-x[k], Ls[c][k], s);
+      x[c] = s / Ls[c][c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kPanel; ++c)
+    if (c < b) row[c] = x[c];
+}
+
+__global__ void __launch_bounds__(256) chol_update_kernel(double *A, int M, int p, const int *info) {
+  __shared__ double Pi[32][kPanel + 1], Pj[32][kPanel + 1];
+  if (*info >= 0) return;
+  const int b = min(kPanel, M - p), q = p + b;
+  // lower-triangular tile (ti >= tj) of the trailing matrix from the linear block index
+  int t = blockIdx.x, ti = 0;
+  while (t > ti) {
+    t -= ti + 1;
+    ++ti;
+  }
+  const int tj = t, i0 = q + 32 * ti, j0 = q + 32 * tj;
+  for (int e = threadIdx.x; e < 32 * b; e += blockDim.x) {
+    const int r = e / b, c = e % b;
+    Pi[r][c] = i0 + r < M ? A[(size_t)(i0 + r) * M + p + c] : 0.0;
+    Pj[r][c] = j0 + r < M ? A[(size_t)(j0 + r) * M + p + c] : 0.0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x & 31, r0 = threadIdx.x >> 5;  // column j0 + c, rows i0 + r0 + 8 m
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < b; ++k) {
+    const double pj = Pj[c][k];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[m] = fma(Pi[r0 + 8 * m][k], pj, acc[m]);
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int i = i0 + r0 + 8 * m, j = j0 + c;
+    if (i < M && j <= i) A[(size_t)i * M + j] -= acc[m];
+  }
+}
+
+// G G^T x = b (G from the Cholesky kernels); skipped, leaving x = 0, when info >= 0.  One
+// CTA: row i's dot product is split over the threads, reduced per warp and across warps.
+__global__ void __launch_bounds__(256) fit_solve_kernel(const double *G, const double *b, int M, const int *info,
+                                                        double *x) {
+  __shared__ double y[1024];
+  __shared__ double part[8];
   if (*info >= 0) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) x[i] = 0.0;
     return;
   }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   for (int i = 0; i < M; ++i) {  // forward: G y = b
-    double part = 0.0;
-    for (int k = threadIdx.x; k < i; k += blockDim.x) part = fma(G[(size_t)i * M + k], x[k], part);
-    const double s = block_sum_d(part, red);
-    if (threadIdx.x == 0) x[i] = (b[i] - s) / G[(size_t)i * M + i];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < i; k += blockDim.x) s = fma(G[(size_t)i * M + k], y[k], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) part[w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int v = 0; v < 8; ++v) t += part[v];
+      y[i] = (b[i] - t) / G[(size_t)i * M + i];
+    }
     __syncthreads();
   }
-  for (int i = M - 1; i >= 0; --i) {  // backward: G^T x = y
-    double part = 0.0;
-    for (int k = i + 1 + threadIdx.x; k < M; k += blockDim.x) part = fma(G[(size_t)k * M + i], x[k], part);
-    const double s = block_sum_d(part, red);
-    if (threadIdx.x == 0) x[i] = (x[i] - s) / G[(size_t)i * M + i];
+  for (int i = M - 1; i >= 0; --i) {  // backward: G^T x = y (column i of G below the diagonal)
+    double s = 0.0;
+    for (int k = i + 1 + threadIdx.x; k < M; k += blockDim.x) s = fma(G[(size_t)k * M + i], y[k], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) part[w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int v = 0; v < 8; ++v) t += part[v];
+      y[i] = (y[i] - t) / G[(size_t)i * M + i];
+    }
     __syncthreads();
   }
+  for (int i = threadIdx.x; i < M; i += blockDim.x) x[i] = y[i];
 }
 
 __global__ void fit_chi2_kernel(const float *__restrict__ C, const float *__restrict__ I, const float *__restrict__ weight,
@@ -370,14 +513,27 @@ int launch_fit(const float *R, const float *I, int W, int H, int pitch, const in
   cudaError_t e = cudaMemsetAsync(S, 0, (size_t)f.NE * f.NE * f.n_mu * sizeof(double), s);
   if (e == cudaSuccess && chi2_out) e = cudaMemsetAsync(chi2_out, 0, sizeof(double), s);
   if (e != cudaSuccess) return cuda_status(e, "fit memset");
-  fit_ck_kernel<<<(f.P + 127) / 128, 128, 0, s>>>(R, basis, stamp_xy, f, C);
+  const int ty = ck_tile_rows(f.S);
+  const size_t ck_smem = ck_smem_bytes(f.S, f.L, ty);
+  if ((e = cudaFuncSetAttribute(fit_ck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ck_smem)) != cudaSuccess)
+    return cuda_status(e, "fit_ck_kernel smem attribute");
+  fit_ck_kernel<<<dim3(f.n_stamps, (f.S + ty - 1) / ty), kCkThreads, ck_smem, s>>>(R, basis, stamp_xy, f, ty, C);
   const int npairs = f.NE * (f.NE + 1) / 2;
   const int px_per_cta = 4096;
   dim3 ggrid((f.P + px_per_cta - 1) / px_per_cta, (npairs + 255) / 256);
   fit_gram_kernel<<<ggrid, 256, 0, s>>>(C, I, weight, stamp_xy, f, px_per_cta, S);
   fit_assemble_kernel<<<(f.M * f.M + 255) / 256, 256, 0, s>>>(S, f, A, b);
-  fit_cholesky_kernel<<<1, 1024, 0, s>>>(A, f.M, info_out);
-  fit_solve_kernel<<<1, 1024, 0, s>>>(A, b, f.M, info_out, coeffs_out);
+  if ((e = cudaMemsetAsync(info_out, 0xFF, sizeof(int), s)) != cudaSuccess) return cuda_status(e, "info reset");
+  for (int p = 0; p < f.M; p += kPanel) {
+    chol_diag_kernel<<<1, 256, 0, s>>>(A, f.M, p, info_out);
+    const int rest = f.M - p - kPanel;
+    if (rest > 0) {
+      chol_trsm_kernel<<<(rest + 63) / 64, 64, 0, s>>>(A, f.M, p, info_out);
+      const int nt = (rest + 31) / 32;
+      chol_update_kernel<<<nt * (nt + 1) / 2, 256, 0, s>>>(A, f.M, p, info_out);
+    }
+  }
+  fit_solve_kernel<<<1, 256, 0, s>>>(A, b, f.M, info_out, coeffs_out);
   if (chi2_out) fit_chi2_kernel<<<(f.P + 255) / 256, 256, 0, s>>>(C, I, weight, stamp_xy, f, coeffs_out, info_out, chi2_out);
   return cuda_status(cudaGetLastError(), "fit kernels launch");
 }

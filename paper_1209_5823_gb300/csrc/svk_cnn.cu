@@ -23,7 +23,7 @@ namespace {
 constexpr int kIn = 64, kCh = 32, kLayers = 4;
 constexpr int kCin[kLayers] = {2, kCh, kCh, kCh};
 constexpr int kStride[kLayers] = {2, 2, 2, 1};
-constexpr int kHin[kLayers] = {64, 32, 16, 8};
+constexpr int kHin[kLayers] = {kIn, kIn / 2, kIn / 4, kIn / 8};
 constexpr int kHout[kLayers] = {32, 16, 8, 8};
 
 struct Layout {

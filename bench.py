@@ -198,6 +198,23 @@ def _oracle_band(R, I, basis32, c32, degree, budget_s=12.0):
     return ref, (y0, y0 + nrows), dt, oracle.get_threads()
 
 
+def _oracle_one_core(R, basis32, c32, degree, cores, rows=4):
+    """The same oracle on one host thread, a few rows of the frame's middle."""
+    import numpy as np
+    import oracle
+    H, W = R.shape
+    y0 = H // 2
+    oracle.set_threads(1)
+    try:
+        t = time.perf_counter()
+        oracle.convolve(R.astype(np.float64), basis32.astype(np.float64), c32.astype(np.float64), degree,
+                        rows=(y0, y0 + rows))
+        dt = time.perf_counter() - t
+    finally:
+        oracle.set_threads(cores)
+    return {"value": rows * W / dt / 1e6, "unit": UNIT, "cores": 1, "sample": f"rows {y0}..{y0 + rows - 1}"}
+
+
 def _night_batch(svk, torch, dev, stream, reps=3):
     """The night batch: 60 frames (20 x 2048^2, 20 x 2048x4096, 20 x 4096^2, seeded order),
     L in {15..31}, degree 0..3.  One CUDA graph replaying svk_difference_batch against 60
@@ -680,6 +697,7 @@ def main():
         scale = np.abs(ref).max()
         out["cpu_baseline"] = {"value": (y1 - y0) * W / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"rows {y0}..{y1 - 1} ({(y1 - y0) * W} px) of the frame, FP64 C oracle"}
+        out["cpu_baseline"]["single_core"] = _oracle_one_core(R, basis.cpu().numpy(), c, d, cores)
         Dtf = Dt[y0:y1].cpu().numpy().astype(np.float64) + I[y0:y1]
         out["tform"]["max_rel_err"] = float(np.abs(Dtf - ref).max() / scale)
         out["max_rel_err"] = {"basis": float(np.abs(Dtc - ref).max() / scale),

@@ -1,0 +1,102 @@
+"""Parity at the full workload sizes, in the launch configuration the bench times: the
+2048 x 4096 frame (L = 19, quadratic coefficients) and the 4096 x 4096 frame (L = 25,
+cubic), every GPU path against the FP64 oracle on sampled pixels the oracle computes one
+by one: the frame's corners and edges, the ragged last block rows, the brightest star
+centres and random pixels."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1209_5823_gb300 as svk
+import starfield
+from _helpers import TOL_FP32
+
+pytestmark = pytest.mark.gpu
+
+TOL_BF16 = 3e-3  # plain BF16 operands: measured 2.2e-3 at 4096^2, L = 25
+
+
+def _samples(W, H, cat, seed, n_random=2000, n_bright=200):
+    g = starfield.rng(seed)
+    xs, ys = [], []
+    for y in (0, 1, 2, H // 2, H - 3, H - 2, H - 1):          # edges and corners
+        for x in (0, 1, 2, 127, 128, W // 2, W - 3, W - 2, W - 1):
+            xs.append(x)
+            ys.append(y)
+    for y in range(H - 5, H):                                 # the (ragged) last block rows
+        for x in g.integers(0, W, 20):
+            xs.append(int(x))
+            ys.append(y)
+    top = np.argsort(cat.flux)[::-1][:n_bright]
+    xs += [int(v) for v in np.clip(np.round(cat.x[top]), 0, W - 1)]
+    ys += [int(v) for v in np.clip(np.round(cat.y[top]), 0, H - 1)]
+    xs += [int(v) for v in g.integers(0, W, n_random)]
+    ys += [int(v) for v in g.integers(0, H, n_random)]
+    return np.array(xs, dtype=np.int64), np.array(ys, dtype=np.int64)
+
+
+@pytest.fixture(scope="module", params=[1, 2], ids=["ccd_2048x4096_L19_d2", "ccd_4096x4096_L25_d3"])
+def frame(request):
+    spec = starfield.CONFIGS[request.param]
+    R, I, cat = starfield.frame_pair(spec)
+    R, I = R.astype(np.float32), I.astype(np.float32)
+    c = starfield.planted_coeffs(49, spec.degree, starfield.rng(spec.seed + 7)).astype(np.float32)
+    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, spec.L)
+    px, py = _samples(spec.W, spec.H, cat, spec.seed + 11)
+    ref = oracle.convolve_points(R.astype(np.float64), B.cpu().numpy().astype(np.float64), c.astype(np.float64),
+                                 spec.degree, px, py)
+    return dict(spec=spec, R=R, I=I, c=c, B=B, px=px, py=py, ref=ref)
+
+
+def _err(D, fr):
+    got = D.cpu().numpy()[fr["py"], fr["px"]].astype(np.float64) + fr["I"][fr["py"], fr["px"]]
+    return float(np.abs(got - fr["ref"]).max() / np.abs(fr["ref"]).max())
+
+
+@pytest.mark.parametrize("method,prec,tol", [
+    (svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3, TOL_FP32),
+    (svk.SVK_METHOD_BASIS, svk.SVK_PREC_FP16X3, TOL_FP32),
+    (svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16, TOL_BF16),
+    (svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3, TOL_FP32),
+    (svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32, TOL_FP32),
+], ids=["basis_bf16x3", "basis_fp16x3", "basis_bf16", "tform_bf16x3", "direct_fp32"])
+def test_full_size_device_call(frame, method, prec, tol):
+    fr = frame
+    D = svk.svk_difference(torch.from_numpy(fr["R"]).cuda(), torch.from_numpy(fr["I"]).cuda(), fr["B"],
+                           torch.from_numpy(fr["c"]).cuda(), fr["spec"].degree, method=method, precision=prec)
+    torch.cuda.synchronize()
+    assert _err(D, fr) <= tol
+
+
+def test_full_size_host_call(frame):
+    fr = frame
+    Rh = torch.from_numpy(fr["R"]).pin_memory()
+    Ih = torch.from_numpy(fr["I"]).pin_memory()
+    D = svk.svk_difference_host(Rh, Ih, fr["B"], torch.from_numpy(fr["c"]).cuda(), fr["spec"].degree, n_bands=8)
+    torch.cuda.synchronize()
+    assert _err(D, fr) <= TOL_FP32
+
+
+def test_full_size_night_batch_frames():
+    # the first four frames of the 60-frame night, full size, in one batch call
+    specs = starfield.batch_specs(60)[:4]
+    items, checks = [], []
+    for k, spec in enumerate(specs):
+        R, I, cat = starfield.frame_pair(spec)
+        R, I = R.astype(np.float32), I.astype(np.float32)
+        c = starfield.planted_coeffs(49, spec.degree, starfield.rng(spec.seed + 7)).astype(np.float32)
+        B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, spec.L)
+        px, py = _samples(spec.W, spec.H, cat, spec.seed + 11, n_random=500, n_bright=50)
+        ref = oracle.convolve_points(R.astype(np.float64), B.cpu().numpy().astype(np.float64),
+                                     c.astype(np.float64), spec.degree, px, py)
+        Rt, It = torch.from_numpy(R).cuda(), torch.from_numpy(I).cuda()
+        D = torch.empty_like(Rt)
+        items.append(dict(R=Rt, I=It, D=D, basis=B, coeffs=torch.from_numpy(c).cuda(), degree=spec.degree))
+        checks.append((D, I, px, py, ref))
+    svk.svk_difference_batch(items, precision=svk.SVK_PREC_BF16X3)
+    torch.cuda.synchronize()
+    assert len({s.L for s in specs}) > 1
+    for D, I, px, py, ref in checks:
+        got = D.cpu().numpy()[py, px].astype(np.float64) + I[py, px]
+        assert float(np.abs(got - ref).max() / np.abs(ref).max()) <= TOL_FP32

@@ -183,6 +183,25 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
+// The same MMA with the A-operand collector: ::fill keeps A (read from shared memory) in
+// the collector for the next MMA, ::lastuse takes A from the collector and releases it.
+__device__ __forceinline__ void umma_f16_fill(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_f16_lastuse(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                                 uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -504,12 +523,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         // basis window starts at descriptor b
         auto row_mmas = [&](uint64_t a, uint64_t b, int nsteps) {
           for (int ks = 0; ks < nsteps; ++ks, a += oKs_a, b += oKs_b) {
-            umma_f16(d_tmem, a, b, idesc, acc);
-            acc = 1;
-            if (kParts == 2) {
-              umma_f16(d_tmem, a, b + oBl, idesc, 1);
+            if (kParts == 2) {  // A hi read once for its two products
+              umma_f16_fill(d_tmem, a, b, idesc, acc);
+              umma_f16_lastuse(d_tmem, a, b + oBl, idesc, 1);
               umma_f16(d_tmem, a + oAl, b, idesc, 1);
+            } else {
+              umma_f16(d_tmem, a, b, idesc, acc);
             }
+            acc = 1;
           }
         };
         int f = 0;
@@ -540,12 +561,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // last tap group of rows r_lo + i and r_lo + i + 1 in one K step
                 const uint64_t ax = dAx + (uint64_t)sa * oStage;
                 const uint64_t bx = dBx + (uint64_t)(r_lo + i - y0 + h) * oSlice;
-                umma_f16(d_tmem, ax, bx, idesc, acc);
-                acc = 1;
                 if (kParts == 2) {
-                  umma_f16(d_tmem, ax, bx + oBl, idesc, 1);
+                  umma_f16_fill(d_tmem, ax, bx, idesc, acc);
+                  umma_f16_lastuse(d_tmem, ax, bx + oBl, idesc, 1);
                   umma_f16(d_tmem, ax + oAl, bx, idesc, 1);
+                } else {
+                  umma_f16(d_tmem, ax, bx, idesc, acc);
                 }
+                acc = 1;
               }
             } else if (i < n) {
               row_mmas(a, bw, pl.nKG / 2);  // the odd last row, padded by the zero group

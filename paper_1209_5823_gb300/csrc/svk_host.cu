@@ -105,45 +105,60 @@ int launch_host(const float *R, const float *I, float *D, int W, int H, int pitc
     st = launch_tc(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, precision, Dd, W, mws, mws_bytes, s, 0, 0, true);
   if (st != SVK_OK) return st;
   if ((st = cuda_status(cudaEventRecord(hs->start, s), "event record")) != SVK_OK) return st;
-  if ((st = cuda_status(cudaStreamWaitEvent(hs->h2d, hs->start, 0), "stream wait")) != SVK_OK) return st;
-  if ((st = cuda_status(cudaStreamWaitEvent(hs->d2h, hs->start, 0), "stream wait")) != SVK_OK) return st;
-  if ((st = cuda_status(cudaStreamWaitEvent(hs->comp, hs->start, 0), "stream wait")) != SVK_OK) return st;
-  int r_done = 0;  // rows of R already on their way
-  for (int b = 0; b < nb; ++b) {
-    const int y0 = yb[b], y1 = yb[b + 1];
-    const int r_need = y1 + h < H ? y1 + h : H;
-    if (r_need > r_done) {
-      st = cuda_status(cudaMemcpy2DAsync(Rd + (size_t)r_done * W, row, R + (size_t)r_done * pitch, hrow, row,
-                                         (size_t)(r_need - r_done), cudaMemcpyHostToDevice, hs->h2d),
-                       "copy R in");
-      if (st != SVK_OK) return st;
-      r_done = r_need;
+  // Queue the bands; whatever happens, the caller's stream then waits for all three
+  // internal streams, so nothing queued on them outlives the call's stream order (the
+  // workspace may be released on `s` right after it).
+  auto bands = [&]() -> int {
+    int e;
+    if ((e = cuda_status(cudaStreamWaitEvent(hs->h2d, hs->start, 0), "stream wait")) != SVK_OK) return e;
+    if ((e = cuda_status(cudaStreamWaitEvent(hs->d2h, hs->start, 0), "stream wait")) != SVK_OK) return e;
+    if ((e = cuda_status(cudaStreamWaitEvent(hs->comp, hs->start, 0), "stream wait")) != SVK_OK) return e;
+    int r_done = 0;  // rows of R already on their way
+    for (int b = 0; b < nb; ++b) {
+      const int y0 = yb[b], y1 = yb[b + 1];
+      const int r_need = y1 + h < H ? y1 + h : H;
+      if (r_need > r_done) {
+        e = cuda_status(cudaMemcpy2DAsync(Rd + (size_t)r_done * W, row, R + (size_t)r_done * pitch, hrow, row,
+                                          (size_t)(r_need - r_done), cudaMemcpyHostToDevice, hs->h2d),
+                        "copy R in");
+        if (e != SVK_OK) return e;
+        r_done = r_need;
+      }
+      e = cuda_status(cudaMemcpy2DAsync(Id + (size_t)y0 * W, row, I + (size_t)y0 * pitch, hrow, row,
+                                        (size_t)(y1 - y0), cudaMemcpyHostToDevice, hs->h2d),
+                      "copy I in");
+      if (e != SVK_OK) return e;
+      if ((e = cuda_status(cudaEventRecord(hs->in[b], hs->h2d), "event record")) != SVK_OK) return e;
+      cudaStream_t cs = (b & 1) ? hs->comp : s;
+      if ((e = cuda_status(cudaStreamWaitEvent(cs, hs->in[b], 0), "stream wait")) != SVK_OK) return e;
+      if (method == SVK_METHOD_DIRECT)
+        e = launch_direct(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, Dd, W, cs, y0, y1);
+      else if (method == SVK_METHOD_TFORM)
+        e = launch_tform(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, precision, Dd, W, mws, mws_bytes, cs, y0,
+                         y1, false);
+      else
+        e = launch_tc(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, precision, Dd, W, mws, mws_bytes, cs, y0, y1,
+                      false);
+      if (e != SVK_OK) return e;
+      if ((e = cuda_status(cudaEventRecord(hs->out[b], cs), "event record")) != SVK_OK) return e;
+      if ((e = cuda_status(cudaStreamWaitEvent(hs->d2h, hs->out[b], 0), "stream wait")) != SVK_OK) return e;
+      e = cuda_status(cudaMemcpy2DAsync(D + (size_t)y0 * pitch, hrow, Dd + (size_t)y0 * W, row, row,
+                                        (size_t)(y1 - y0), cudaMemcpyDeviceToHost, hs->d2h),
+                      "copy D out");
+      if (e != SVK_OK) return e;
     }
-    st = cuda_status(cudaMemcpy2DAsync(Id + (size_t)y0 * W, row, I + (size_t)y0 * pitch, hrow, row,
-                                       (size_t)(y1 - y0), cudaMemcpyHostToDevice, hs->h2d),
-                     "copy I in");
-    if (st != SVK_OK) return st;
-    if ((st = cuda_status(cudaEventRecord(hs->in[b], hs->h2d), "event record")) != SVK_OK) return st;
-    cudaStream_t cs = (b & 1) ? hs->comp : s;
-    if ((st = cuda_status(cudaStreamWaitEvent(cs, hs->in[b], 0), "stream wait")) != SVK_OK) return st;
-    if (method == SVK_METHOD_DIRECT)
-      st = launch_direct(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, Dd, W, cs, y0, y1);
-    else if (method == SVK_METHOD_TFORM)
-      st = launch_tform(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, precision, Dd, W, mws, mws_bytes, cs, y0,
-                        y1, false);
-    else
-      st = launch_tc(Rd, W, Id, W, W, H, basis, N, L, coeffs, degree, precision, Dd, W, mws, mws_bytes, cs, y0, y1,
-                     false);
-    if (st != SVK_OK) return st;
-    if ((st = cuda_status(cudaEventRecord(hs->out[b], cs), "event record")) != SVK_OK) return st;
-    if ((st = cuda_status(cudaStreamWaitEvent(hs->d2h, hs->out[b], 0), "stream wait")) != SVK_OK) return st;
-    st = cuda_status(cudaMemcpy2DAsync(D + (size_t)y0 * pitch, hrow, Dd + (size_t)y0 * W, row, row,
-                                       (size_t)(y1 - y0), cudaMemcpyDeviceToHost, hs->d2h),
-                     "copy D out");
-    if (st != SVK_OK) return st;
-  }
-  if ((st = cuda_status(cudaEventRecord(hs->end, hs->d2h), "event record")) != SVK_OK) return st;
-  return cuda_status(cudaStreamWaitEvent(s, hs->end, 0), "stream wait");
+    return SVK_OK;
+  };
+  st = bands();
+  // join (the events' earlier waits were captured when they were queued, so re-recording
+  // them here is safe)
+  cudaEventRecord(hs->in[0], hs->h2d);
+  cudaEventRecord(hs->out[0], hs->comp);
+  cudaEventRecord(hs->end, hs->d2h);
+  cudaStreamWaitEvent(s, hs->in[0], 0);
+  cudaStreamWaitEvent(s, hs->out[0], 0);
+  const int jst = cuda_status(cudaStreamWaitEvent(s, hs->end, 0), "stream join");
+  return st != SVK_OK ? st : jst;
 }
 
 }  // namespace svk

@@ -307,6 +307,17 @@ SVK_API int svk_difference_host(const float *R, const float *I, float *D, int W,
                                 int precision, int n_bands, void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * Self-test of the bounded waits of the library's pipelined kernels (failure detection
+ * without a fault): one device thread waits on an mbarrier that nothing ever arrives at,
+ * with the same bounded wait the kernels use (sleep-hinted try_wait, limit `limit_ns`,
+ * 1 us .. 10 s).  The wait gives up, records the timeout in a status word and returns;
+ * the call synchronises `stream`, stores the measured wait in *waited_ns (nullable) and
+ * returns SVK_ERR_TIMEOUT -- the expected result.  Any other status means the mechanism
+ * is broken.  The context stays usable.  Tooling with no counterpart in the paper.
+ */
+SVK_API int svk_selftest_bounded_wait(unsigned long long limit_ns, unsigned long long *waited_ns, void *stream);
+
+/*
  * Measured multiply-add throughput of the current device, in FLOP/s (2 per FMA): FP32
  * FFMA (fp64 == 0) or FP64 DFMA (fp64 != 0).  These are the denominators of the direct
  * form's roofline (FP32 ALU bound) and of the fit's normal-equation accumulation (FP64).

@@ -6,6 +6,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "svk_common.cuh"
 #include "svk_internal.h"
 
@@ -83,6 +85,15 @@ ScopedWorkspace::~ScopedWorkspace() {
 
 using namespace svk;
 
+// An NVTX range named after the entry point around each call that queues GPU work, so a
+// timeline tool shows the library's calls (the calls cost nothing without a tool).
+namespace {
+struct CallRange {
+  explicit CallRange(const char *name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 static int check_conv_args(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
                            const float *basis, int N, int L, const float *coeffs, int degree,
                            int method, int precision, int edge, const float *out, int pitch_out,
@@ -153,6 +164,7 @@ int svk_gauss_basis_count(int n_gauss, const int *deg) {
 
 int svk_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg, int normalize,
                     float *basis_out, int *n_basis_out, void *stream) {
+  CallRange range("svk_build_basis");
   if (!basis_out) return set_error(SVK_ERR_ARG, "NULL basis_out");
   if (L < 1 || L > 63 || (L % 2) == 0) return set_error(SVK_ERR_ARG, "L=%d must be odd in [1,63]", L);
   if (normalize != SVK_NORM_NONE && normalize != SVK_NORM_ALARD)
@@ -185,6 +197,7 @@ size_t svk_workspace_size(int method, int precision, int W, int H, int N, int L,
 int svk_convolve(const float *R, int W, int H, int pitch_R, const float *basis, int N, int L,
                  const float *coeffs, int degree, int method, int precision, int edge, float *out,
                  int pitch_out, void *workspace, size_t ws_bytes, void *stream) {
+  CallRange range("svk_convolve");
   return run_conv(R, pitch_R, nullptr, 0, W, H, basis, N, L, coeffs, degree, method, precision, edge, out,
                   pitch_out, workspace, ws_bytes, stream, false);
 }
@@ -193,6 +206,7 @@ int svk_difference(const float *R, int pitch_R, const float *I, int pitch_I, int
                    const float *basis, int N, int L, const float *coeffs, int degree, int method,
                    int precision, int edge, float *D, int pitch_D, void *workspace, size_t ws_bytes,
                    void *stream) {
+  CallRange range("svk_difference");
   return run_conv(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, method, precision, edge, D,
                   pitch_D, workspace, ws_bytes, stream, true);
 }
@@ -219,6 +233,7 @@ size_t svk_batch_workspace_size(const svk_frame *frames, int n_frames, int preci
 
 int svk_difference_batch(const svk_frame *frames, int n_frames, int precision, void *workspace, size_t ws_bytes,
                          void *stream) {
+  CallRange range("svk_difference_batch");
   int st = check_batch(frames, n_frames, precision);
   if (st != SVK_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -230,6 +245,7 @@ int svk_difference_batch(const svk_frame *frames, int n_frames, int precision, v
 }
 
 int svk_autotune(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out, void *stream) {
+  CallRange range("svk_autotune");
   if (precision != SVK_PREC_BF16X3 && precision != SVK_PREC_FP16X3 && precision != SVK_PREC_BF16)
     return set_error(SVK_ERR_UNSUPPORTED, "autotune covers the tensor-core precisions only");
   if (N < 1 || N > 256 || L < 1 || L > 31 || (L % 2) == 0 || degree < 0 || degree > 3 || W < 1 || H < 1 ||
@@ -254,6 +270,7 @@ static int check_cnn(const void *params, const void *x, int batch, int n_out) {
 
 int svk_cnn_forward(const float *params, const float *x, int batch, int n_out, float *out, void *workspace,
                     size_t ws_bytes, void *stream) {
+  CallRange range("svk_cnn_forward");
   int st = check_cnn(params, x, batch, n_out);
   if (st != SVK_OK) return st;
   if (!out) return set_error(SVK_ERR_ARG, "NULL output");
@@ -267,6 +284,7 @@ int svk_cnn_forward(const float *params, const float *x, int batch, int n_out, f
 
 int svk_cnn_gradient(const float *params, const float *x, const float *target, int batch, int n_out, float *grad,
                      float *loss, void *workspace, size_t ws_bytes, void *stream) {
+  CallRange range("svk_cnn_gradient");
   int st = check_cnn(params, x, batch, n_out);
   if (st != SVK_OK) return st;
   if (!target || !grad || !loss) return set_error(SVK_ERR_ARG, "NULL target, gradient or loss pointer");
@@ -280,6 +298,7 @@ int svk_cnn_gradient(const float *params, const float *x, const float *target, i
 
 int svk_cnn_adam(float *params, float *m, float *v, const float *grad, int n_params, int step, float lr, float beta1,
                  float beta2, float eps, void *stream) {
+  CallRange range("svk_cnn_adam");
   if (!params || !m || !v || !grad || n_params < 1 || step < 1)
     return set_error(SVK_ERR_ARG, "bad optimiser arguments");
   return cnn_adam(params, m, v, grad, n_params, step, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream));
@@ -287,6 +306,7 @@ int svk_cnn_adam(float *params, float *m, float *v, const float *grad, int n_par
 
 int svk_cnn_field_fit(const float *local, const int *xy, const float *weights, int S, int N, int W, int H, int degree,
                       double *coeffs, int *info, void *stream) {
+  CallRange range("svk_cnn_field_fit");
   if (!local || !xy || !coeffs || !info || S < 1 || N < 1 || W < 1 || H < 1 || degree < 0 || degree > 3)
     return set_error(SVK_ERR_ARG, "bad field-fit arguments");
   return cnn_field_fit(local, xy, weights, S, N, W, H, degree, coeffs, info, static_cast<cudaStream_t>(stream));
@@ -300,6 +320,7 @@ int svk_fit_coeffs(const float *R, const float *I, int W, int H, int pitch, cons
                    int n_stamps, int stamp_size, const float *basis, int N, int L, int degree,
                    int bg_degree, const float *weight, double *coeffs_out, double *chi2_out,
                    int *info_out, void *workspace, size_t ws_bytes, int sync, void *stream) {
+  CallRange range("svk_fit_coeffs");
   if (!R || !I || !stamp_xy || !basis || !coeffs_out || !info_out)
     return set_error(SVK_ERR_ARG, "NULL pointer argument");
   if (W < 1 || H < 1 || W > 65535 || H > 65535 || pitch < W) return set_error(SVK_ERR_ARG, "bad frame size/pitch");
@@ -335,6 +356,7 @@ size_t svk_host_workspace_size(int method, int precision, int W, int H, int N, i
 int svk_difference_host(const float *R, const float *I, float *D, int W, int H, int pitch, const float *basis, int N,
                         int L, const float *coeffs, int degree, int method, int precision, int n_bands,
                         void *workspace, size_t ws_bytes, void *stream) {
+  CallRange range("svk_difference_host");
   int st = check_conv_args(R, pitch, I, pitch, W, H, basis, N, L, coeffs, degree, method, precision, SVK_EDGE_ZERO,
                            D, pitch, true);
   if (st != SVK_OK) return st;
@@ -345,6 +367,12 @@ int svk_difference_host(const float *R, const float *I, float *D, int W, int H, 
   st = w.acquire(need, workspace, ws_bytes, s);
   if (st != SVK_OK) return st;
   return launch_host(R, I, D, W, H, pitch, basis, N, L, coeffs, degree, method, precision, n_bands, w.ptr, need, s);
+}
+
+int svk_selftest_bounded_wait(unsigned long long limit_ns, unsigned long long *waited_ns, void *stream) {
+  if (limit_ns < 1000ull || limit_ns > 10000000000ull)
+    return set_error(SVK_ERR_ARG, "limit %llu ns out of range [1 us, 10 s]", limit_ns);
+  return selftest_bounded_wait(limit_ns, waited_ns, static_cast<cudaStream_t>(stream));
 }
 
 int svk_measure_fma_peak(int fp64, double *flops_per_s, void *stream) {
@@ -360,6 +388,7 @@ size_t svk_select_workspace_size(int W, int H) {
 int svk_select_stamps(const float *R, int W, int H, int pitch, float sky, float threshold, float saturation,
                       int margin, int iso_radius, float iso_frac, int max_stamps, int *stamp_xy_out, int *counts_out,
                       void *workspace, size_t ws_bytes, void *stream) {
+  CallRange range("svk_select_stamps");
   if (!R || !counts_out || (max_stamps > 0 && !stamp_xy_out)) return set_error(SVK_ERR_ARG, "NULL pointer argument");
   if (W < 1 || H < 1 || W > 65535 || H > 65535 || (long long)W * H >= (1ll << 31) || pitch < W)
     return set_error(SVK_ERR_ARG, "bad frame size/pitch");

@@ -60,6 +60,10 @@ int launch_select(const float *R, int W, int H, int pitch, float sky, float thre
                   int iso_radius, float iso_frac, int max_stamps, int *xy, int *counts, void *ws, size_t ws_bytes,
                   cudaStream_t s);
 
+// Self-test of the bounded device waits (svk_selftest.cu); returns SVK_ERR_TIMEOUT when
+// the wait gave up as designed.
+int selftest_bounded_wait(unsigned long long limit_ns, unsigned long long *waited_ns, cudaStream_t s);
+
 // Measured FMA throughput (svk_peaks.cu).
 int measure_fma_peak(int fp64, double *flops_per_s, cudaStream_t s);
 

@@ -109,6 +109,22 @@ class CoefficientNetwork:
             svk_cnn_adam(self.params, self.m, self.v, grad, self.step, lr=lr)
         return losses
 
+    def state_dict(self):
+        """Everything training depends on: weights, Adam moments and step (device tensors,
+        cloned), the prior and the batch size.  Save it with torch.save; with the state of
+        the generator that draws the batches, training resumes bit for bit."""
+        return {"params": self.params.clone(), "m": self.m.clone(), "v": self.v.clone(), "step": self.step,
+                "prior": (self.prior.n_out, self.prior.mean0, self.prior.sd0, self.prior.sd), "batch": self.batch}
+
+    @classmethod
+    def from_state_dict(cls, sd, device=None):
+        params = sd["params"] if device is None else sd["params"].to(device)
+        net = cls(params.clone(), CoeffPrior(*sd["prior"]), batch=sd["batch"])
+        net.m.copy_(sd["m"])
+        net.v.copy_(sd["v"])
+        net.step = int(sd["step"])
+        return net
+
     def predict(self, x):
         dev = x.device
         out = []

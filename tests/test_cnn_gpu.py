@@ -129,3 +129,32 @@ def test_training_learns_and_network_path_is_faster_with_fallback():
     bad = learned.CoefficientNetwork(torch.zeros_like(net.params), learned.CoeffPrior(N, mean0=0.0), batch=128)
     res2 = learned.apply_to_frame(bad, Rf, I, st, basis, 1, 30.0, fallback_ratio=2.0, reference_noise_sigma=0.0)
     assert res2["source"] == "fit"
+
+
+def test_training_checkpoint_resumes_bit_exactly(tmp_path):
+    # weights, Adam moments, step and the batch generator's state saved mid-run: the
+    # resumed run ends with the same weights, bit for bit, as an uninterrupted one
+    N = 49
+    g0 = torch.Generator(device="cuda").manual_seed(11)
+    x = torch.randn((600, 2, 64, 64), device="cuda", generator=g0) * 0.3
+    a = torch.randn((600, N), device="cuda", generator=g0) * 0.02 + learned.CoeffPrior(N).mean(torch.device("cuda"))
+    init = torch.from_numpy(starfield.cnn_init_params(N, 3)).cuda()
+
+    full = learned.CoefficientNetwork(init.clone(), learned.CoeffPrior(N), batch=64)
+    gen = torch.Generator(device="cuda").manual_seed(12)
+    full.train(x, a, 20, lr=2e-3, gen=gen)
+
+    part = learned.CoefficientNetwork(init.clone(), learned.CoeffPrior(N), batch=64)
+    gen = torch.Generator(device="cuda").manual_seed(12)
+    part.train(x, a, 8, lr=2e-3, gen=gen)
+    torch.save({"net": part.state_dict(), "gen": gen.get_state()}, tmp_path / "ckpt.pt")
+    del part
+
+    ck = torch.load(tmp_path / "ckpt.pt")
+    resumed = learned.CoefficientNetwork.from_state_dict(ck["net"], device="cuda")
+    gen2 = torch.Generator(device="cuda")
+    gen2.set_state(ck["gen"])
+    resumed.train(x, a, 12, lr=2e-3, gen=gen2)
+    assert resumed.step == full.step == 20
+    assert torch.equal(resumed.params, full.params)
+    assert torch.equal(resumed.m, full.m) and torch.equal(resumed.v, full.v)

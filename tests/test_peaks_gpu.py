@@ -13,3 +13,18 @@ def test_fma_peaks_are_plausible():
     # fraction of that on this part
     assert 20e12 < fp32 < 90e12
     assert 0.1e12 < fp64 < fp32
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    import torch
+    for limit in (2_000_000, 20_000_000):  # 2 ms and 20 ms
+        st, waited = svk.svk_selftest_bounded_wait(limit)
+        assert st == svk.SVK_ERR_TIMEOUT
+        assert limit <= waited < limit + 250_000_000  # sleep-hinted polls: coarse but bounded
+    # the context still runs work afterwards
+    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, 7)
+    assert torch.isfinite(B).all()
+
+
+def test_bounded_wait_rejects_bad_limits():
+    assert svk.svk_selftest_bounded_wait(10)[0] == svk.SVK_ERR_ARG

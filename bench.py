@@ -12,7 +12,7 @@ the direct form's throughput beside it; the FP64 oracle timed on the host cores 
 band of rows (cpu_baseline), whose output also gives the measured max relative error
 of both GPU forms on that band.
 
-`--impl reference` times the FP64 oracle alone (the reference arm of this build).
+`--impl reference` times the FP64 oracle alone (the reference arm).
 """
 from __future__ import annotations
 
@@ -168,7 +168,7 @@ def _frame_spec(rank=0):
     """Rank r of a multi-GPU run times its own frame: same shape, seed offset by r."""
     import dataclasses
     import starfield
-    spec = starfield.CONFIGS[1]
+    spec = starfield.WORKLOADS["ccd_2048x4096_L19_d2"]
     return spec if rank == 0 else dataclasses.replace(spec, seed=spec.seed + 1000 * rank)
 
 
@@ -329,7 +329,7 @@ def _precision_table(svk, torch, dev):
     import numpy as np
     import oracle
     import starfield
-    spec = starfield.CONFIGS[2]
+    spec = starfield.WORKLOADS["ccd_4096x4096_L25_d3"]
     g = starfield.rng(spec.seed)
     cat = starfield.star_catalog(spec.W, spec.H, spec.n_stars, g)
     R = starfield.add_noise(starfield.render(cat, spec.W, spec.H), 30.0, g).astype(np.float32)
@@ -380,7 +380,7 @@ def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=3000):
     H, W = R.shape
     Rt = torch.from_numpy(R).to(dev)
     g = starfield.rng(starfield.BASE_SEED + 4)
-    cat = starfield.star_catalog(W, H, 20000, starfield.rng(starfield.CONFIGS[1].seed))
+    cat = starfield.star_catalog(W, H, 20000, starfield.rng(starfield.WORKLOADS["ccd_2048x4096_L19_d2"].seed))
     bright = np.nonzero(cat.flux > 3000)[0]
     pick = g.choice(bright, n_pairs)
     cx = torch.from_numpy(np.clip(np.round(cat.x[pick]), 48, W - 49).astype(np.int64)).to(dev)

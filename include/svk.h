@@ -51,7 +51,7 @@ extern "C" {
 #define SVK_ERR_CUDA 2        /* a CUDA runtime/driver call failed                        */
 #define SVK_ERR_NOT_SPD 3     /* normal matrix not positive definite (info = pivot)       */
 #define SVK_ERR_TIMEOUT 4     /* a bounded device-side wait ran out                       */
-#define SVK_ERR_UNSUPPORTED 5 /* valid request this build does not implement              */
+#define SVK_ERR_UNSUPPORTED 5 /* valid request the library does not implement              */
 #define SVK_ERR_WORKSPACE 6   /* caller workspace too small                               */
 
 /* basis kinds (Sec. 2: Gaussian function basis and Dirac delta function basis) */

@@ -11,8 +11,7 @@
  *   Eq. 1   D = (R (x) K) - I
  *   Eq. 2   K_{x,y} = sum_i a_i(x,y) B_i          (a different kernel at every pixel)
  *   Eq. 3   a(x,y) = bivariate polynomial of order n (n = 2 written out in the paper)
- * and the cost models of Sec. 3.  Readings of what the paper leaves open (all stated
- * again in the design doc):
+ * and the cost models of Sec. 3.  Readings of what the paper leaves open:
  *   - (x) is a true convolution: out(x,y) = sum_{u,v} K(u,v) R(x-u, y-v);
  *   - the kernel is evaluated at the OUTPUT pixel (x,y) (gather form, Sec. 4: one
  *     thread and one kernel per output pixel);

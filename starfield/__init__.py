@@ -136,12 +136,15 @@ def _density_stars(W, H):
     return int(round(20000 * (W * H) / (2048 * 4096)))
 
 
-CONFIGS = {
-    0: FrameSpec("starfield_256x256_L11_d1", 256, 256, 200, 11, 1, BASE_SEED + 0),
-    1: FrameSpec("ccd_2048x4096_L19_d2", 4096, 2048, 20000, 19, 2, BASE_SEED + 1),
-    2: FrameSpec("ccd_4096x4096_L25_d3", 4096, 4096, _density_stars(4096, 4096), 25, 3,
-                 BASE_SEED + 2, extra=dict(n_stamps=500, stamp_size=41)),
-}
+# the workloads by name: a 256^2 star field (L = 11, linear coefficients), the 2048-row x
+# 4096-column CCD frame (L = 19, quadratic) and the 4096^2 frame (L = 25, cubic, with the
+# fit's 500 stamps of 41 x 41)
+WORKLOADS = {spec.name: spec for spec in (
+    FrameSpec("starfield_256x256_L11_d1", 256, 256, 200, 11, 1, BASE_SEED + 0),
+    FrameSpec("ccd_2048x4096_L19_d2", 4096, 2048, 20000, 19, 2, BASE_SEED + 1),
+    FrameSpec("ccd_4096x4096_L25_d3", 4096, 4096, _density_stars(4096, 4096), 25, 3,
+              BASE_SEED + 2, extra=dict(n_stamps=500, stamp_size=41)),
+)}
 
 
 def batch_specs(n_frames: int = 60, seed: int = BASE_SEED + 3, scale: float = 1.0):

@@ -36,9 +36,9 @@ def _samples(W, H, cat, seed, n_random=2000, n_bright=200):
     return np.array(xs, dtype=np.int64), np.array(ys, dtype=np.int64)
 
 
-@pytest.fixture(scope="module", params=[1, 2], ids=["ccd_2048x4096_L19_d2", "ccd_4096x4096_L25_d3"])
+@pytest.fixture(scope="module", params=["ccd_2048x4096_L19_d2", "ccd_4096x4096_L25_d3"])
 def frame(request):
-    spec = starfield.CONFIGS[request.param]
+    spec = starfield.WORKLOADS[request.param]
     R, I, cat = starfield.frame_pair(spec)
     R, I = R.astype(np.float32), I.astype(np.float32)
     c = starfield.planted_coeffs(49, spec.degree, starfield.rng(spec.seed + 7)).astype(np.float32)

@@ -49,7 +49,7 @@ def test_parity_random_fields(W, H, n_stars, seed):
 def test_parity_full_size_frame():
     # 4096 x 4096 at the survey density: 500 stamps of 41 x 41, 30 px from the edges,
     # isolated within their stamp
-    spec = starfield.CONFIGS[2]
+    spec = starfield.WORKLOADS["ccd_4096x4096_L25_d3"]
     R = _field(spec.W, spec.H, spec.n_stars, spec.seed)
     want = _check(R, SKY, 150.0, 20000.0, 30, 20, 0.05, 500)
     assert len(want) == 500

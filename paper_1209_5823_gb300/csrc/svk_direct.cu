@@ -3,8 +3,8 @@
 // (Sec. 3: the best kernel at every pixel; Sec. 4: one kernel per output pixel) and
 // applied to the reference image, FP32 FFMA.
 //
-// Layout of one CTA (256 threads, 32 x 8):
-//   * output tile 128 x 8 pixels; thread (tx, ty) owns pixels x0 + tx + 32 p (p < 4) of
+// Layout of one CTA (384 threads, 32 x 12; three warps per scheduler, 168 registers):
+//   * output tile 128 x 12 pixels; thread (tx, ty) owns pixels x0 + tx + 32 p (p < 4) of
 //     row y0 + ty, so every shared-memory read of R is conflict-free and every global
 //     store is coalesced;
 //   * the R tile plus an h-pixel halo is staged in shared memory by one 2-D TMA load
@@ -19,7 +19,7 @@
 namespace svk {
 namespace {
 
-constexpr int kTX = 32, kTY = 8, kP = 4, kTileW = kTX * kP;
+constexpr int kTX = 32, kTY = 12, kP = 4, kTileW = kTX * kP;
 static_assert(kTY == kDirectRows, "row bands of the direct form follow its block height");
 constexpr int kThreads = kTX * kTY;
 

@@ -3,8 +3,9 @@
 // (Sec. 3: the best kernel at every pixel; Sec. 4: one kernel per output pixel) and
 // applied to the reference image, FP32 FFMA.
 //
-// Layout of one CTA (384 threads, 32 x 12; three warps per scheduler, 168 registers):
-//   * output tile 128 x 12 pixels; thread (tx, ty) owns pixels x0 + tx + 32 p (p < 4) of
+// Layout of one CTA (32 x TY threads, TY = 12 rows for L >= 13 -- three warps per
+// scheduler at 168 registers -- and 8 rows for smaller kernels):
+//   * output tile 128 x TY pixels; thread (tx, ty) owns pixels x0 + tx + 32 p (p < 4) of
 //     row y0 + ty, so every shared-memory read of R is conflict-free and every global
 //     store is coalesced;
 //   * the R tile plus an h-pixel halo is staged in shared memory by one 2-D TMA load
@@ -19,31 +20,29 @@
 namespace svk {
 namespace {
 
-constexpr int kTX = 32, kTY = 12, kP = 4, kTileW = kTX * kP;
-static_assert(kTY == kDirectRows, "row bands of the direct form follow its block height");
-constexpr int kThreads = kTX * kTY;
+constexpr int kTX = 32, kP = 4, kTileW = kTX * kP;
 
 __host__ __device__ inline int round_up4(int v) { return (v + 3) & ~3; }
 __host__ __device__ inline int box_w(int h) { return round_up4(kTileW + 2 * h + 3); }
-__host__ __device__ inline int box_h(int h) { return kTY + 2 * h; }
+__host__ __device__ inline int box_h(int h, int ty) { return ty + 2 * h; }
 
 template <int NC>
 struct Cfg {
   static constexpr int NCP = (NC + 3) & ~3;  // table row stride (16-byte rows)
 };
 
-template <int NC>
+template <int NC, int TY>
 size_t direct_smem_bytes(int L) {
   const int h = (L - 1) / 2;
-  size_t b = (size_t)box_w(h) * box_h(h) * 4;                 // R tile
+  size_t b = (size_t)box_w(h) * box_h(h, TY) * 4;             // R tile
   b += (size_t)L * L * Cfg<NC>::NCP * 4;                      // basis chunk [tap][NCP]
   b += (size_t)NC * 10 * 4;                                   // coefficient chunk
   b += 16;                                                    // mbarrier
   return b + 128;                                             // alignment slack
 }
 
-template <int NC>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int NC, int TY>
+__global__ void __launch_bounds__(kTX * TY, 1)
     direct_kernel(const __grid_constant__ CUtensorMap tmR, int use_tma, const float *__restrict__ R,
                   int pitch_R, const float *__restrict__ I, int pitch_I, int W, int H,
                   const float *__restrict__ basis, int N, int L, const float *__restrict__ coeffs,
@@ -52,14 +51,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const int h = (L - 1) / 2, LL = L * L, T = (degree + 1) * (degree + 2) / 2;
-  const int BW = box_w(h), BH = box_h(h);
+  const int BW = box_w(h), BH = box_h(h, TY);
   float *Rs = reinterpret_cast<float *>(smem);
   float *Bs = Rs + BW * BH;
   float *Cs = Bs + LL * NCP;
   uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uintptr_t>(Cs + NC * 10 + 1) & ~uintptr_t(7));
 
   const int tid = threadIdx.y * kTX + threadIdx.x;
-  const int x0 = blockIdx.x * kTileW, y0 = y_begin + blockIdx.y * kTY;
+  constexpr int kThreads = kTX * TY;
+  const int x0 = blockIdx.x * kTileW, y0 = y_begin + blockIdx.y * TY;
   const int xs = ((x0 - h) >> 2) << 2;  // floor to a multiple of 4 (16-byte TMA origin)
   const int xoff = (x0 - h) - xs;
 
@@ -187,37 +187,51 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int NC>
+template <int NC, int TY>
 int launch_nc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis,
               int N, int L, const float *coeffs, int degree, float *out, int pitch_out, int y_begin, int y_end,
               cudaStream_t s) {
   const int h = (L - 1) / 2;
-  const size_t smem = direct_smem_bytes<NC>(L);
-  cudaError_t e = cudaFuncSetAttribute(direct_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = direct_smem_bytes<NC, TY>(L);
+  cudaError_t e = cudaFuncSetAttribute(direct_kernel<NC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_status(e, "direct_kernel smem attribute");
   CUtensorMap tm;
   memset(&tm, 0, sizeof(tm));
-  const int use_tma = encode_tmap_2d_f32(&tm, R, W, H, pitch_R, box_w(h), box_h(h)) ? 1 : 0;
-  dim3 grid((W + kTileW - 1) / kTileW, (y_end - y_begin + kTY - 1) / kTY), block(kTX, kTY);
+  const int use_tma = encode_tmap_2d_f32(&tm, R, W, H, pitch_R, box_w(h), box_h(h, TY)) ? 1 : 0;
+  dim3 grid((W + kTileW - 1) / kTileW, (y_end - y_begin + TY - 1) / TY), block(kTX, TY);
   if (grid.y == 0) return SVK_OK;
-  direct_kernel<NC><<<grid, block, smem, s>>>(tm, use_tma, R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs,
+  direct_kernel<NC, TY><<<grid, block, smem, s>>>(tm, use_tma, R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs,
                                              degree, out, pitch_out, y_begin, y_end, nullptr);
   return cuda_status(cudaGetLastError(), "direct_kernel launch");
 }
 
 }  // namespace
 
+int direct_rows(int L) { return L >= 13 ? 12 : 8; }
+
+namespace {
+template <int TY>
+int launch_ty(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis, int N,
+              int L, const float *coeffs, int degree, float *out, int pitch_out, int y_begin, int y_end,
+              cudaStream_t s) {
+  if (N <= 4)
+    return launch_nc<4, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  if (N <= 8)
+    return launch_nc<8, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  if (N <= 16)
+    return launch_nc<16, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end,
+                             s);
+  return launch_nc<25, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+}
+}  // namespace
+
 int launch_direct(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis,
                   int N, int L, const float *coeffs, int degree, float *out, int pitch_out, cudaStream_t s,
                   int y_begin, int y_end) {
   if (y_end < 0) y_end = H;
-  if (N <= 4)
-    return launch_nc<4>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
-  if (N <= 8)
-    return launch_nc<8>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
-  if (N <= 16)
-    return launch_nc<16>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
-  return launch_nc<25>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  if (direct_rows(L) == 12)
+    return launch_ty<12>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  return launch_ty<8>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
 }
 
 }  // namespace svk

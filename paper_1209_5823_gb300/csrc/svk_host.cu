@@ -68,7 +68,7 @@ int launch_host(const float *R, const float *I, float *D, int W, int H, int pitc
                 const float *coeffs, int degree, int method, int precision, int n_bands, void *ws, size_t ws_bytes,
                 cudaStream_t s) {
   const int h = (L - 1) / 2;
-  int gran = kDirectRows;
+  int gran = direct_rows(L);
   if (method != SVK_METHOD_DIRECT) {
     gran = tc_rows_per_block(method == SVK_METHOD_TFORM ? n_terms(degree) : N, L, precision);
     if (gran < 1) return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan for N=%d L=%d", N, L);

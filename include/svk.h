@@ -307,6 +307,14 @@ SVK_API int svk_difference_host(const float *R, const float *I, float *D, int W,
                                 int precision, int n_bands, void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * The library's sticky device status: every bounded device wait that gives up (after
+ * ~2 s, e.g. a copy that never lands) records SVK_ERR_TIMEOUT there and its kernel
+ * unwinds, so results computed since the last check are invalid.  Synchronises `stream`,
+ * returns SVK_OK or SVK_ERR_TIMEOUT, and clears the word when `reset` is non-zero.
+ */
+SVK_API int svk_device_status(int reset, void *stream);
+
+/*
  * Self-test of the bounded waits of the library's pipelined kernels (failure detection
  * without a fault): one device thread waits on an mbarrier that nothing ever arrives at,
  * with the same bounded wait the kernels use (sleep-hinted try_wait, limit `limit_ns`,

@@ -40,7 +40,7 @@ EXPORTS = (
     "svk_batch_workspace_size", "svk_difference_batch", "svk_autotune", "svk_cnn_param_count",
     "svk_cnn_workspace_size", "svk_cnn_forward", "svk_cnn_gradient", "svk_cnn_adam", "svk_cnn_field_fit",
     "svk_select_workspace_size", "svk_select_stamps", "svk_measure_fma_peak", "svk_host_workspace_size",
-    "svk_difference_host", "svk_selftest_bounded_wait",
+    "svk_difference_host", "svk_selftest_bounded_wait", "svk_device_status",
 )
 
 
@@ -94,6 +94,7 @@ def load_library(path: str | None = None):
         "svk_cnn_field_fit": (i, [vp, vp, vp, i, i, i, i, i, vp, vp, vp]),
         "svk_measure_fma_peak": (i, [i, vp, vp]),
         "svk_selftest_bounded_wait": (i, [ctypes.c_ulonglong, vp, vp]),
+        "svk_device_status": (i, [i, vp]),
         "svk_host_workspace_size": (sz, [i, i, i, i, i, i, i]),
         "svk_difference_host": (i, [vp, vp, vp, i, i, i, vp, i, i, vp, i, i, i, i, vp, sz, vp]),
         "svk_select_workspace_size": (sz, [i, i]),
@@ -317,6 +318,12 @@ def svk_difference_host(R, I, basis, coeffs, degree: int, method: int = SVK_METH
                                               _ptr(coeffs), int(degree), int(method), int(precision), int(n_bands),
                                               _ptr(workspace), ws_bytes, _stream(stream)))
     return out
+
+
+def svk_device_status(reset: bool = False, stream=None) -> int:
+    """Synchronise the stream and return the library's sticky device status (SVK_OK, or
+    SVK_ERR_TIMEOUT after a bounded device wait gave up); clears it when `reset`."""
+    return int(load_library().svk_device_status(int(bool(reset)), _stream(stream)))
 
 
 def svk_selftest_bounded_wait(limit_ns: int, stream=None):

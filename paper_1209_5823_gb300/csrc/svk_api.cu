@@ -2,6 +2,7 @@
 // host, workspace handling and dispatch to the kernels of the other translation units.
 #include <cudaTypedefs.h>
 #include <cmath>
+#include <mutex>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -79,6 +80,24 @@ int ScopedWorkspace::acquire(size_t bytes, void *user_ws, size_t user_bytes, cud
 
 ScopedWorkspace::~ScopedWorkspace() {
   if (owned && ptr) cudaFreeAsync(ptr, stream);
+}
+
+// Sticky device status word: the library's bounded device waits record a timeout here
+// (kernels get its address as their status pointer); svk_device_status reads and clears it.
+__device__ uint32_t g_device_status;
+
+uint32_t *device_status_word() {
+  static std::mutex mu;
+  static uint32_t *addr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<uint32_t *>(p);
+  }
+  return addr[dev];
 }
 
 }  // namespace svk
@@ -367,6 +386,22 @@ int svk_difference_host(const float *R, const float *I, float *D, int W, int H, 
   st = w.acquire(need, workspace, ws_bytes, s);
   if (st != SVK_OK) return st;
   return launch_host(R, I, D, W, H, pitch, basis, N, L, coeffs, degree, method, precision, n_bands, w.ptr, need, s);
+}
+
+int svk_device_status(int reset, void *stream) {
+  uint32_t *w = device_status_word();
+  if (!w) return set_error(SVK_ERR_CUDA, "device status word not available");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  int st = cuda_status(cudaMemcpyAsync(&v, w, 4, cudaMemcpyDeviceToHost, s), "read device status");
+  if (st == SVK_OK) st = cuda_status(cudaStreamSynchronize(s), "device status sync");
+  if (st != SVK_OK) return st;
+  if (reset && v != 0) {
+    if ((st = cuda_status(cudaMemsetAsync(w, 0, 4, s), "clear device status")) != SVK_OK) return st;
+    if ((st = cuda_status(cudaStreamSynchronize(s), "device status sync")) != SVK_OK) return st;
+  }
+  if (v == kDevTimeout) return set_error(SVK_ERR_TIMEOUT, "a bounded device wait gave up (results since the last check are invalid)");
+  return v == 0 ? SVK_OK : set_error(SVK_ERR_CUDA, "device status 0x%x", v);
 }
 
 int svk_selftest_bounded_wait(unsigned long long limit_ns, unsigned long long *waited_ns, void *stream) {

@@ -35,6 +35,10 @@ __host__ __device__ inline int n_terms(int d) { return d < 0 ? 0 : (d + 1) * (d 
 // Device status word written by kernels with bounded waits (0 = fine).
 enum DeviceStatus : uint32_t { kDevOk = 0, kDevTimeout = 1 };
 
+// Address of the library's sticky device status word on the current device (the
+// kernels' status pointer), or NULL if it cannot be resolved.
+uint32_t *device_status_word();
+
 // ------------------------------------------------------------------ device side
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -201,7 +201,7 @@ int launch_nc(const float *R, int pitch_R, const float *I, int pitch_I, int W, i
   dim3 grid((W + kTileW - 1) / kTileW, (y_end - y_begin + TY - 1) / TY), block(kTX, TY);
   if (grid.y == 0) return SVK_OK;
   direct_kernel<NC, TY><<<grid, block, smem, s>>>(tm, use_tma, R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs,
-                                             degree, out, pitch_out, y_begin, y_end, nullptr);
+                                             degree, out, pitch_out, y_begin, y_end, device_status_word());
   return cuda_status(cudaGetLastError(), "direct_kernel launch");
 }
 

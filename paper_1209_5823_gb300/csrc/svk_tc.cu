@@ -831,10 +831,11 @@ int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *w
     }
   }
   fs.nblocks = blocks;
-  uint32_t *status = reinterpret_cast<uint32_t *>(ws + (size_t)ntab * pl.table_bytes * 2);
-  cudaError_t e = cudaMemsetAsync(status, 0, 4, s);
-  if (e != cudaSuccess) return cuda_status(e, "status reset");
-  e = cudaFuncSetAttribute(tc_basis_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  // the library's sticky status word (svk_device_status); the workspace word if it
+  // cannot be resolved
+  uint32_t *status = device_status_word();
+  if (!status) status = reinterpret_cast<uint32_t *>(ws + (size_t)ntab * pl.table_bytes * 2);
+  cudaError_t e = cudaFuncSetAttribute(tc_basis_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) return cuda_status(e, "tc_basis_kernel smem attribute");
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);

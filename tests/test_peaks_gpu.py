@@ -28,3 +28,20 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
 
 def test_bounded_wait_rejects_bad_limits():
     assert svk.svk_selftest_bounded_wait(10)[0] == svk.SVK_ERR_ARG
+
+
+def test_device_status_stays_clear_after_normal_work():
+    import numpy as np
+    import torch
+    assert svk.svk_device_status(reset=True) in (svk.SVK_OK, svk.SVK_ERR_TIMEOUT)
+    assert svk.svk_device_status() == svk.SVK_OK
+    R = torch.rand((70, 300), device="cuda") * 1000 + 1000
+    I = torch.rand((70, 300), device="cuda") * 1000 + 1000
+    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, 19)
+    c = torch.from_numpy(np.r_[np.ones((1, 6)), np.zeros((48, 6))].astype(np.float32)).cuda()
+    for method, prec in [(svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3), (svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32),
+                         (svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3)]:
+        svk.svk_difference(R, I, B, c, 2, method=method, precision=prec)
+    # the self-test's timeout is its own: the library's status stays clear
+    assert svk.svk_selftest_bounded_wait(1_000_000)[0] == svk.SVK_ERR_TIMEOUT
+    assert svk.svk_device_status() == svk.SVK_OK

@@ -108,36 +108,27 @@ __global__ void __launch_bounds__(kTX * TY, 1)
       if (!mbar_wait_bounded(bar, 0, status)) return;  // TMA never landed: give up cleanly
       tile_ready = true;
     }
-    // a_j(x_p, y) = sum_t c[k0+j][t] xt^i yt^j for the chunk (Eq. 3, order <= 3)
+    // a_j(x_p, y) = sum_t c[k0+j][t] xt^i yt^j for the chunk (Eq. 3, order <= 3): per stamp
+    // alpha_i = sum_jj c[(i, jj)] yt^jj (the same for the thread's pixels, which share a
+    // row), then Horner in xt.  Coefficient slots are packed (i outer, jj inner), skipping
+    // terms above `degree`.
     float a[NC][kP];
 #pragma unroll
-    for (int p = 0; p < kP; ++p) {
-      float mon[10];
-      int t = 0;
-      float xi = 1.0f;
+    for (int j = 0; j < NC; ++j) {
+      float al[4];
+      int tt = 0;
 #pragma unroll
       for (int i = 0; i <= 3; ++i) {
-        float yj = 1.0f;
+        float sacc = 0.0f, yj = 1.0f;
 #pragma unroll
         for (int jj = 0; jj <= 3 - i; ++jj) {
-          mon[t++] = (i + jj <= degree) ? xi * yj : 0.0f;
+          if (i + jj <= degree) sacc = fmaf(Cs[j * 10 + tt++], yj, sacc);
           yj *= yt;
         }
-        xi *= xt[p];
+        al[i] = sacc;
       }
 #pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        // coefficient slots are packed in the same (i outer, j inner) order, skipping
-        // terms above `degree`
-        float s = 0.0f;
-        int tt = 0, q = 0;
-#pragma unroll
-        for (int i = 0; i <= 3; ++i)
-#pragma unroll
-          for (int jj = 0; jj <= 3 - i; ++jj, ++q)
-            if (i + jj <= degree) s = fmaf(Cs[j * 10 + tt++], mon[q], s);
-        a[j][p] = s;
-      }
+      for (int p = 0; p < kP; ++p) a[j][p] = fmaf(fmaf(fmaf(al[3], xt[p], al[2]), xt[p], al[1]), xt[p], al[0]);
     }
     for (int vi = 0; vi < L; ++vi) {
       // smem row of image row y - v with v = vi - h; smem column of x - u with u = ui - h

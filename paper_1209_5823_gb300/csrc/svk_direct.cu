@@ -3,8 +3,8 @@
 // (Sec. 3: the best kernel at every pixel; Sec. 4: one kernel per output pixel) and
 // applied to the reference image, FP32 FFMA.
 //
-// Layout of one CTA (32 x TY threads, TY = 12 rows for L >= 13 -- three warps per
-// scheduler at 168 registers -- and 8 rows for smaller kernels):
+// Layout of one CTA (32 x TY threads, TY = 12 rows: three warps per scheduler at 168
+// registers, measured faster than 8 or 16 rows for L = 7 .. 31):
 //   * output tile 128 x TY pixels; thread (tx, ty) owns pixels x0 + tx + 32 p (p < 4) of
 //     row y0 + ty, so every shared-memory read of R is conflict-free and every global
 //     store is coalesced;
@@ -198,7 +198,7 @@ int launch_nc(const float *R, int pitch_R, const float *I, int pitch_I, int W, i
 
 }  // namespace
 
-int direct_rows(int L) { return L >= 13 ? 12 : 8; }
+int direct_rows(int) { return 12; }
 
 namespace {
 template <int TY>
@@ -220,9 +220,7 @@ int launch_direct(const float *R, int pitch_R, const float *I, int pitch_I, int 
                   int N, int L, const float *coeffs, int degree, float *out, int pitch_out, cudaStream_t s,
                   int y_begin, int y_end) {
   if (y_end < 0) y_end = H;
-  if (direct_rows(L) == 12)
-    return launch_ty<12>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
-  return launch_ty<8>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  return launch_ty<12>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
 }
 
 }  // namespace svk

@@ -11,7 +11,7 @@ namespace svk {
 // Direct form (svk_direct.cu): kernel of Eq. 2 formed at every output pixel, FP32 FFMA.
 // I may be NULL (plain convolution).  Arguments already validated.
 // y_begin / y_end: the output rows to compute (-1 = to the last row); band starts must
-// be multiples of direct_rows(L), the kernel's block height for kernel size L.
+// be multiples of direct_rows(L), the kernel's block height (12 rows).
 int direct_rows(int L);
 int launch_direct(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
                   const float *basis, int N, int L, const float *coeffs, int degree, float *out,

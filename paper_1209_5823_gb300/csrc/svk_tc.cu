@@ -723,14 +723,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           for (int e = 0; e < tail; ++e) {  // the last N mod 16 columns, one per load
-            const float cv = __uint_as_float(tmem_ld1(c0 + (uint32_t)(nfull * 16 + e)));
+            const uint32_t u = tmem_ld1(c0 + (uint32_t)(nfull * 16 + e));
             const float4 a = a4[nfull * 16 + e];
+            tmem_ld_wait();  // the loaded value is used only after the wait
+            const float cv = __uint_as_float(u);
             s0 = fmaf(a.x, cv, s0);
             s1 = fmaf(a.y, cv, s1);
             s2 = fmaf(a.z, cv, s2);
             s3 = fmaf(a.w, cv, s3);
           }
-          tmem_ld_wait();
         }
         const float sres = fmaf(fmaf(fmaf(s3, xt, s2), xt, s1), xt, s0);
         if (x < fd.W) fd.out[(size_t)(y0 + g) * fd.pitch_out + x] = sres * fd.out_scale - iv;

@@ -100,3 +100,36 @@ def test_full_size_night_batch_frames():
     for D, I, px, py, ref in checks:
         got = D.cpu().numpy()[py, px].astype(np.float64) + I[py, px]
         assert float(np.abs(got - ref).max() / np.abs(ref).max()) <= TOL_FP32
+
+
+@pytest.mark.parametrize("W,H,pitch", [(65535, 7, 65535), (65535, 6, 65536), (9, 65535, 9), (5, 30001, 8)])
+def test_maximum_frame_extents(W, H, pitch):
+    # the largest width and height the C ABI accepts (65535), unaligned and aligned pitches
+    g = starfield.rng(W + H)
+    R = (1000.0 + 200.0 * g.standard_normal((H, W))).astype(np.float32)
+    R[g.integers(0, H, 40), g.integers(0, W, 40)] += 20000.0
+    I = (R + 30.0 * g.standard_normal((H, W))).astype(np.float32)
+    L, d = 19, 2
+    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, L)
+    c = starfield.planted_coeffs(49, d, starfield.rng(5)).astype(np.float32)
+    xs = np.r_[[0, W - 1, W // 2, min(W - 1, 127), min(W - 1, 128)] * 4, g.integers(0, W, 300)]
+    ys = np.r_[[0] * 5 + [H - 1] * 5 + [H // 2] * 5 + [max(0, H - 3)] * 5, g.integers(0, H, 300)]
+    ref = oracle.convolve_points(R.astype(np.float64), B.cpu().numpy().astype(np.float64), c.astype(np.float64), d,
+                                 xs, ys)
+    Rt = torch.zeros((H, pitch), dtype=torch.float32, device="cuda")
+    It = torch.zeros((H, pitch), dtype=torch.float32, device="cuda")
+    Rt[:, :W] = torch.from_numpy(R)
+    It[:, :W] = torch.from_numpy(I)
+    ct = torch.from_numpy(c).cuda()
+    for method, prec in [(svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3), (svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32),
+                         (svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3)]:
+        D = svk.svk_difference(Rt[:, :W], It[:, :W], B, ct, d, method=method, precision=prec)
+        torch.cuda.synchronize()
+        got = D.cpu().numpy()[ys, xs].astype(np.float64) + I[ys, xs]
+        assert float(np.abs(got - ref).max() / np.abs(ref).max()) <= TOL_FP32, (method, prec)
+    Dh = svk.svk_difference_host(torch.from_numpy(R).pin_memory(), torch.from_numpy(I).pin_memory(), B, ct, d,
+                                 n_bands=5)
+    torch.cuda.synchronize()
+    got = Dh.numpy()[ys, xs].astype(np.float64) + I[ys, xs]
+    assert float(np.abs(got - ref).max() / np.abs(ref).max()) <= TOL_FP32
+    assert svk.svk_device_status() == svk.SVK_OK

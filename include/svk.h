@@ -78,10 +78,10 @@ extern "C" {
 
 /* arithmetic of the contraction */
 #define SVK_PREC_FP32 0   /* DIRECT only: FP32 FFMA                                       */
-#define SVK_PREC_BF16X3 1 /* BASIS: R and B split hi + lo in BF16, hi*hi + hi*lo + lo*hi, */
+#define SVK_PREC_BF16X3 1 /* BASIS, TFORM: R and B split hi + lo in BF16, hi*hi + hi*lo + lo*hi, */
                           /* FP32 accumulation                                            */
-#define SVK_PREC_FP16X3 2 /* BASIS: the same split in FP16 (power-of-two prescaled)       */
-#define SVK_PREC_BF16 3   /* BASIS: plain BF16 operands, FP32 accumulation (one MMA)       */
+#define SVK_PREC_FP16X3 2 /* BASIS, TFORM: the same split in FP16 (power-of-two prescaled) */
+#define SVK_PREC_BF16 3   /* BASIS, TFORM: plain BF16 operands, FP32 accumulation (one MMA) */
 
 #define SVK_EDGE_ZERO 0 /* R is zero outside the frame (the only mode)                    */
 
@@ -127,8 +127,9 @@ SVK_API size_t svk_workspace_size(int method, int precision, int W, int H, int N
  *   W, H     frame size (>= 1 each; W, H <= 65535)
  *   basis    device float32 [N][L][L] (1 <= N <= 4096, odd 1 <= L <= 31)
  *   coeffs   device float32 [N][T], T = (degree+1)(degree+2)/2, 0 <= degree <= 3
- *   method   SVK_METHOD_DIRECT (precision SVK_PREC_FP32) or SVK_METHOD_BASIS
- *            (precision SVK_PREC_BF16X3 / FP16X3 / BF16; N <= 256)
+ *   method   SVK_METHOD_DIRECT (precision SVK_PREC_FP32), SVK_METHOD_BASIS (precision
+ *            SVK_PREC_BF16X3 / FP16X3 / BF16; N <= 256) or SVK_METHOD_TFORM (the same
+ *            precisions; any N)
  *   edge     SVK_EDGE_ZERO
  *   out      device float32 [H][pitch_out]; must not overlap R
  *   workspace, ws_bytes   device scratch of at least svk_workspace_size() bytes, or

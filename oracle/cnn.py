@@ -13,7 +13,14 @@ Eq. 3's polynomials at the stamp, which Eq. 2 combines with the basis stamps):
 Convolution is cross-correlation, out[o][y][x] = b[o] + sum w[o][c][dy][dx]
 in[c][s y + dy - 1][s x + dx - 1] (zero outside).  Loss = mean over batch and outputs of
 (out - target)^2.  Forward and the hand-derived backward are written out per layer.
-Pins: finite differences of the loss (FP64), scipy correlate for the convolutions.
+
+BF16 storage (`rounding=round_bf16`): the network stores its input, every post-ReLU
+activation and every pre-activation gradient in BF16 and sums in FP32 or better; with
+the rounding hook the oracle rounds the same values at the same points (everything else
+stays FP64), so it computes what a BF16-storage network computes up to the summation
+precision.  Without the hook it is the plain FP64 network.
+Pins: finite differences of the loss (FP64), scipy correlate for the convolutions, torch
+autograd for the network with BF16 storage, torch's BF16 conversion for round_bf16.
 """
 from __future__ import annotations
 
@@ -67,21 +74,36 @@ def conv_bwd(x, w, dz, stride):
     return dxp[:, :, 1:-1, 1:-1], dw, dz.sum(axis=(0, 2, 3))
 
 
-def forward(params, x, n_out):
-    """x [B][2][64][64] -> (out [B][n_out], cache)."""
+def round_bf16(a):
+    """Nearest BF16 value (8 significant bits), ties to even, as float64.  Values are
+    taken to lie in BF16's normal range (no overflow or gradual underflow handling)."""
+    m, e = np.frexp(np.asarray(a, dtype=np.float64))  # a = m 2^e, 1/2 <= |m| < 1
+    return np.ldexp(np.rint(m * 256.0), e - 8)       # rint: round half to even
+
+
+def _identity(a):
+    return a
+
+
+def forward(params, x, n_out, rounding=None):
+    """x [B][2][64][64] -> (out [B][n_out], cache).  rounding: applied to the stored
+    input and activations (None: plain FP64)."""
+    r = rounding or _identity
     p = unflatten(params, n_out)
-    acts = [np.asarray(x, dtype=np.float64)]
+    acts = [r(np.asarray(x, dtype=np.float64))]
     for li, (_, stride) in enumerate(starfield.CNN_LAYERS):
         z = conv_fwd(acts[-1], p[2 * li], p[2 * li + 1], stride)
-        acts.append(np.maximum(z, 0.0))
+        acts.append(r(np.maximum(z, 0.0)))
     pooled = acts[-1].mean(axis=(2, 3))
     out = pooled @ p[-2].T + p[-1]
     return out, (p, acts, pooled)
 
 
-def loss_and_grad(params, x, target, n_out):
-    """(loss, flat gradient) of the mean squared error."""
-    out, (p, acts, pooled) = forward(params, x, n_out)
+def loss_and_grad(params, x, target, n_out, rounding=None):
+    """(loss, flat gradient) of the mean squared error.  rounding: also applied to the
+    stored pre-activation gradients dL/dz (None: plain FP64)."""
+    r = rounding or _identity
+    out, (p, acts, pooled) = forward(params, x, n_out, rounding)
     B = out.shape[0]
     diff = out - np.asarray(target, dtype=np.float64)
     loss = float((diff ** 2).mean())
@@ -94,6 +116,6 @@ def loss_and_grad(params, x, target, n_out):
     da = np.broadcast_to(dpool[:, :, None, None] / (a.shape[2] * a.shape[3]), a.shape).copy()
     for li in range(len(starfield.CNN_LAYERS) - 1, -1, -1):
         stride = starfield.CNN_LAYERS[li][1]
-        dz = da * (acts[li + 1] > 0.0)
+        dz = r(da * (acts[li + 1] > 0.0))
         da, grads[2 * li], grads[2 * li + 1] = conv_bwd(acts[li], p[2 * li], dz, stride)
     return loss, flatten(grads)

@@ -30,26 +30,58 @@ def _data(B, n_out, seed):
     return x, t
 
 
-@pytest.mark.parametrize("n_out", [49, 7])
-def test_forward_and_gradient_match_oracle(n_out):
-    p = starfield.cnn_init_params(n_out, 11)
-    x, t = _data(3, n_out, 12)
+# The network stores its input, activations and pre-activation gradients in BF16 and
+# sums in FP32; the oracle rounds the same values (FP64 otherwise).  What remains are
+# FP32 summation errors and rare rounding flips, where the two sides' unrounded values
+# straddle a BF16 rounding boundary (or a ReLU's zero) and a stored value differs by one
+# BF16 step.  Bars: outputs within 1e-3 of their largest value (measured <= 2.5e-4 up to
+# 256 stamps), each gradient block within one BF16 step, 2^-8, of its largest value
+# (measured <= 1.6e-3); against the plain FP64 network the gradients differ by up to 16 %.
+TOL_OUT = 1e-3
+TOL_GRAD = 2.0 ** -8
+
+
+def _check_against_oracle(B, n_out, seed):
+    p = starfield.cnn_init_params(n_out, seed)
+    x, t = _data(B, n_out, seed + 1)
     dp, dx, dt = (torch.from_numpy(a).cuda() for a in (p, x, t))
     out = svk.svk_cnn_forward(dp, dx, n_out).cpu().numpy()
     grad, loss = svk.svk_cnn_gradient(dp, dx, dt)
+    assert svk.svk_device_status() == svk.SVK_OK
     pq = bf16_round(p).astype(np.float64)
-    ref_out, _ = ocnn.forward(pq, x.astype(np.float64), n_out)
-    ref_loss, ref_grad = ocnn.loss_and_grad(pq, x.astype(np.float64), t.astype(np.float64), n_out)
-    assert np.abs(out - ref_out).max() <= 1e-4 * np.abs(ref_out).max()
-    assert abs(float(loss.item()) - ref_loss) <= 1e-4 * ref_loss
+    ref_out, _ = ocnn.forward(pq, x.astype(np.float64), n_out, rounding=ocnn.round_bf16)
+    ref_loss, ref_grad = ocnn.loss_and_grad(pq, x.astype(np.float64), t.astype(np.float64), n_out,
+                                            rounding=ocnn.round_bf16)
+    assert np.abs(out - ref_out).max() <= TOL_OUT * np.abs(ref_out).max()
+    assert abs(float(loss.item()) - ref_loss) <= TOL_OUT * ref_loss
     g = grad.cpu().numpy().astype(np.float64)
     # every parameter block separately (scales differ by orders of magnitude)
     o = 0
     for shp in starfield.cnn_param_shapes(n_out):
         n = int(np.prod(shp))
         a, b = g[o:o + n], ref_grad[o:o + n]
-        assert np.abs(a - b).max() <= 2e-3 * np.abs(b).max() + 1e-9, shp
+        assert np.abs(a - b).max() <= TOL_GRAD * np.abs(b).max() + 1e-9, shp
         o += n
+
+
+@pytest.mark.parametrize("n_out", [49, 7])
+def test_forward_and_gradient_match_oracle(n_out):
+    _check_against_oracle(3, n_out, 11)
+
+
+def test_ragged_batch_matches_oracle():
+    # 37 stamps: the 8x8 layers end in a partial 128-row tile, and the first layer's last
+    # weight-gradient chunk is shorter than the others
+    _check_against_oracle(37, 49, 21)
+
+
+def test_gradient_is_deterministic():
+    n_out = 49
+    p = torch.from_numpy(starfield.cnn_init_params(n_out, 3)).cuda()
+    x, t = (torch.from_numpy(a).cuda() for a in _data(300, n_out, 4))
+    g1, _ = svk.svk_cnn_gradient(p, x, t)
+    g2, _ = svk.svk_cnn_gradient(p, x, t)
+    assert torch.equal(g1, g2)
 
 
 def test_adam_step():

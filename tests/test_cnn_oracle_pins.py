@@ -64,3 +64,88 @@ def test_linear_output_layer_closed_form():
     x, _ = _batch(2, n_out, 3)
     out, _ = cnn.forward(params, x, n_out)
     np.testing.assert_allclose(out, np.tile(arrs[8] @ arrs[7] + arrs[9], (2, 1)), rtol=1e-13)
+
+
+def test_round_bf16_matches_torch_and_ties_to_even():
+    torch = __import__("pytest").importorskip("torch")
+    g = starfield.rng(21)
+    v = np.concatenate([g.normal(0, 1, 4000) * 10.0 ** g.integers(-6, 7, 4000), [0.0, -0.0, 1.0, -3.5]])
+    v32 = v.astype(np.float32)
+    ours = cnn.round_bf16(v32.astype(np.float64))
+    theirs = torch.from_numpy(v32).to(torch.bfloat16).double().numpy()
+    np.testing.assert_array_equal(ours, theirs)
+    # exact midpoints: BF16 spacing at 1 is 2^-7; ties go to the even significand
+    assert cnn.round_bf16(1 + 2.0 ** -8) == 1.0
+    assert cnn.round_bf16(1 + 3 * 2.0 ** -8) == 1 + 2.0 ** -6
+    assert cnn.round_bf16(-(1 + 3 * 2.0 ** -8)) == -(1 + 2.0 ** -6)
+    assert cnn.round_bf16(1 + 2.0 ** -8 + 2.0 ** -30) == 1 + 2.0 ** -7
+    assert cnn.round_bf16(3.0 * 2.0 ** -100) == 3.0 * 2.0 ** -100
+
+
+def test_bf16_storage_rounds_input_and_activations():
+    n_out = 4
+    params = starfield.cnn_init_params(n_out, 5).astype(np.float64)
+    x, _ = _batch(2, n_out, 6)
+    r = cnn.round_bf16
+    a, _ = cnn.forward(params, x, n_out, rounding=r)
+    b, _ = cnn.forward(params, r(x), n_out, rounding=r)
+    np.testing.assert_array_equal(a, b)  # the input is rounded first
+    assert np.abs(a - cnn.forward(params, x, n_out)[0]).max() > 0
+    # closed form: zero conv weights, positive biases -> every stored activation is the
+    # rounded bias chain, out = fc.w @ round(relu(b4)) + fc.b
+    shapes = starfield.cnn_param_shapes(n_out)
+    arrs = [np.zeros(s) for s in shapes]
+    arrs[7] = np.linspace(0.1, 3.2, 32)
+    arrs[8] = starfield.rng(2).normal(0, 1, (n_out, 32))
+    arrs[9] = np.linspace(-1, 1, n_out)
+    out, _ = cnn.forward(cnn.flatten(arrs), x, n_out, rounding=r)
+    np.testing.assert_allclose(out, np.tile(arrs[8] @ r(arrs[7]) + arrs[9], (2, 1)), rtol=1e-13)
+    assert np.abs(r(arrs[7]) - arrs[7]).max() > 1e-4
+
+
+def test_bf16_storage_gradient_matches_torch_autograd():
+    # the network with BF16 storage written with torch's conv2d and autograd: stored
+    # values rounded on the way forward (identity derivative), the gradient at each
+    # pre-activation rounded on the way back
+    torch = __import__("pytest").importorskip("torch")
+    F = torch.nn.functional
+    r = cnn.round_bf16
+
+    class StoreRound(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, a):
+            return torch.from_numpy(r(a.detach().numpy()))
+
+        @staticmethod
+        def backward(ctx, g):
+            return g
+
+    class GradRound(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, a):
+            return a.clone()
+
+        @staticmethod
+        def backward(ctx, g):
+            return torch.from_numpy(r(g.detach().numpy()))
+
+    n_out = 6
+    params = starfield.cnn_init_params(n_out, 13).astype(np.float64)
+    x, t = _batch(3, n_out, 14)
+    loss_o, grad_o = cnn.loss_and_grad(params, x, t, n_out, rounding=r)
+    ps = [torch.tensor(a, requires_grad=True) for a in cnn.unflatten(params, n_out)]
+    h = StoreRound.apply(torch.from_numpy(x))
+    for li, (_, stride) in enumerate(starfield.CNN_LAYERS):
+        z = F.conv2d(h, ps[2 * li], ps[2 * li + 1], stride=stride, padding=1)
+        h = StoreRound.apply(torch.relu(GradRound.apply(z)))
+    out = h.mean(dim=(2, 3)) @ ps[-2].T + ps[-1]
+    loss = ((out - torch.from_numpy(t)) ** 2).mean()
+    loss.backward()
+    grad_t = np.concatenate([p.grad.numpy().reshape(-1) for p in ps])
+    assert abs(loss.item() - loss_o) <= 1e-12 * loss_o
+    o = 0
+    for shp in starfield.cnn_param_shapes(n_out):
+        n = int(np.prod(shp))
+        a, b = grad_o[o:o + n], grad_t[o:o + n]
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max(), shp
+        o += n

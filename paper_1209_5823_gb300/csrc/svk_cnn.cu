@@ -46,6 +46,7 @@ constexpr int kK = kTaps * kCh;            // 288
 constexpr int kKChunks = kK / 8;           // 36
 constexpr int kPack = kK * kCh;            // 9216 BF16 per packed operand
 constexpr uint32_t kPackBytes = kPack * 2; // 18,432
+constexpr int kPack0 = 4 * kCh * 8;         // first layer: K = 18 padded to 32, 1024 BF16
 constexpr uint32_t kIdesc = idesc_f16(1, 128, 32);  // BF16 x BF16 -> FP32, M = 128, N = 32
 
 typedef __nv_bfloat16 bf16;
@@ -71,23 +72,25 @@ Layout param_layout(int n_out) {
   return l;
 }
 
-// Weight-gradient split: K (the output pixels of a layer) in chunks of a multiple of 64
-// pixels, about kWgChunks chunks per layer.  Depends on the batch only (deterministic).
-constexpr int kWgChunks = 128;
+// Weight-gradient split: K (the output pixels of a layer, a multiple of 64) in chunks of
+// a multiple of 64 pixels, about 304 chunks for a 32-channel layer (two CTAs on each of
+// 152 SMs) and 912 for the first layer (three per SM; its partial sums are small).
+// Depends on the batch only, so the gradient is deterministic.
 constexpr int kWgStage = 64;  // pixels per pipeline stage (4 MMAs of K = 16)
 
-int wg_per_chunk(int P) {
+int wg_target(int cin) { return cin == kCh ? 304 : 912; }
+int wg_per_chunk(int P, int cin) {
   const int stages = (P + kWgStage - 1) / kWgStage;
-  return kWgStage * ((stages + kWgChunks - 1) / kWgChunks);
+  return kWgStage * ((stages + wg_target(cin) - 1) / wg_target(cin));
 }
-int wg_nchunks(int P) { return (P + wg_per_chunk(P) - 1) / wg_per_chunk(P); }
+int wg_nchunks(int P, int cin) { return (P + wg_per_chunk(P, cin) - 1) / wg_per_chunk(P, cin); }
 int wg_rows(int cin) { return cin * kTaps + 1; }  // taps x channels, then the bias row
 
 struct Work {  // byte offsets into the workspace
   size_t wq;                     // float[param total]: parameters rounded to BF16
   size_t wf[kLayers], wd[kLayers];  // packed BF16 operands (forward, data grad), layers 1..3
   size_t act[kLayers], dz[kLayers];  // BF16 NHWC [B][H][H][32]: post-ReLU, pre-activation grad
-  size_t pooled, dpooled, out, dout, part, total;
+  size_t pooled, out, dout, part, total;
 };
 
 Work work_layout(int B, int n_out) {
@@ -99,6 +102,7 @@ Work work_layout(int B, int n_out) {
     return at;
   };
   w.wq = take(param_layout(n_out).total * sizeof(float));
+  w.wf[0] = take(kPack0 * sizeof(bf16));
   for (int i = 1; i < kLayers; ++i) {
     w.wf[i] = take(kPackBytes);
     w.wd[i] = take(kPackBytes);
@@ -109,11 +113,10 @@ Work work_layout(int B, int n_out) {
     w.act[i] = take(n * sizeof(bf16));
     w.dz[i] = take(n * sizeof(bf16));
     const int P = B * kHout[i] * kHout[i];
-    const size_t pb = (size_t)wg_nchunks(P) * wg_rows(kCin[i]) * kCh * sizeof(float);
+    const size_t pb = (size_t)wg_nchunks(P, kCin[i]) * wg_rows(kCin[i]) * kCh * sizeof(float);
     part = pb > part ? pb : part;
   }
   w.pooled = take((size_t)B * kCh * sizeof(float));
-  w.dpooled = take((size_t)B * kCh * sizeof(float));
   w.out = take((size_t)B * n_out * sizeof(float));
   w.dout = take((size_t)B * n_out * sizeof(float));
   w.part = take(part);
@@ -132,17 +135,24 @@ __device__ __forceinline__ float lo_f(uint32_t w) { return __uint_as_float(w << 
 __device__ __forceinline__ float hi_f(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
 // Rounded parameters (FP32 values of the BF16 weights) and the packed tensor-core
-// operands of layers 1..3:  wf[j][o][t] = W[o][c][tap],  wd[j][c][t] = W[o][c][tap]  with
-// k = 8 j + t = 32 tap + (c for wf, o for wd).
-__global__ void pack_kernel(const float *__restrict__ p, float *__restrict__ wq, int n_params, bf16 *wf1, bf16 *wd1,
-                            bf16 *wf2, bf16 *wd2, bf16 *wf3, bf16 *wd3, size_t w1, size_t w2, size_t w3) {
-  const int n = n_params + 3 * kPack;
+// operands.  Layers 1..3 (K = 8 j + t = 32 tap + channel):  wf[j][o][t] = W[o][c][tap]
+// with c the K channel, wd[j][c][t] = W[o][c][tap] with o the K channel.  Layer 0
+// (K = 2 tap + c < 18, zero above): wf0[j][o][t] = W0[o][c][tap].
+__global__ void pack_kernel(const float *__restrict__ p, float *__restrict__ wq, int n_params, bf16 *wf0, bf16 *wf1,
+                            bf16 *wd1, bf16 *wf2, bf16 *wd2, bf16 *wf3, bf16 *wd3, size_t w0, size_t w1, size_t w2,
+                            size_t w3) {
+  const int n = n_params + kPack0 + 3 * kPack;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (i < n_params) {
       wq[i] = bf16r(p[i]);
       continue;
     }
-    const int l = (i - n_params) / kPack, e = (i - n_params) % kPack;
+    if (i < n_params + kPack0) {
+      const int e = i - n_params, j = e >> 8, r = (e >> 3) & 31, k = 8 * j + (e & 7);
+      wf0[e] = __float2bfloat16_rn(k < 2 * kTaps ? p[w0 + (r * 2 + (k & 1)) * 9 + (k >> 1)] : 0.0f);
+      continue;
+    }
+    const int l = (i - n_params - kPack0) / kPack, e = (i - n_params - kPack0) % kPack;
     const int j = e >> 8, r = (e >> 3) & 31, t = e & 7;
     const int k = 8 * j + t, tap = k >> 5, ch = k & 31;
     const float *w = p + (l == 0 ? w1 : l == 1 ? w2 : w3);
@@ -153,71 +163,44 @@ __global__ void pack_kernel(const float *__restrict__ p, float *__restrict__ wq,
   }
 }
 
-// First layer, forward: out[b][y][x][o] = relu(b[o] + sum_{c,dy,dx} w[o][c][dy][dx]
-// x[b][c][2y+dy-1][2x+dx-1]) with x rounded to BF16; one thread per output pixel, all 32
-// channels, stored as BF16 NHWC.
-__global__ void __launch_bounds__(256) conv1_fwd_kernel(const float *__restrict__ x, const float *__restrict__ w,
-                                                        const float *__restrict__ bias, bf16 *__restrict__ out,
-                                                        int B) {
-  __shared__ float ws[kCh * 2 * 9], bs[kCh];
-  for (int i = threadIdx.x; i < kCh * 2 * 9; i += blockDim.x) ws[i] = w[i];
-  if (threadIdx.x < kCh) bs[threadIdx.x] = bias[threadIdx.x];
-  __syncthreads();
-  const int n = B * 32 * 32;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const int xo = idx & 31, yo = (idx >> 5) & 31, b = idx >> 10;
-    float v[2][9];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int yy = 2 * yo + t / 3 - 1, xx = 2 * xo + t % 3 - 1;
-        v[c][t] = (yy >= 0 && yy < kIn && xx >= 0 && xx < kIn)
-                      ? bf16r(__ldg(x + (((size_t)b * 2 + c) * kIn + yy) * kIn + xx))
-                      : 0.0f;
-      }
-    uint32_t o32[16];
-#pragma unroll
-    for (int o = 0; o < kCh; o += 2) {
-      float a0 = bs[o], a1 = bs[o + 1];
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-          a0 = fmaf(ws[(o * 2 + c) * 9 + t], v[c][t], a0);
-          a1 = fmaf(ws[((o + 1) * 2 + c) * 9 + t], v[c][t], a1);
-        }
-      o32[o >> 1] = pack2(fmaxf(a0, 0.0f), fmaxf(a1, 0.0f));
-    }
-    uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)idx * kCh);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(o32[4 * q], o32[4 * q + 1], o32[4 * q + 2], o32[4 * q + 3]);
-  }
-}
+// ----------------------------------------------------- convolutions on tcgen05
+// kFwd / kDgrad: the 32-channel layers (K = 9 taps x 32 channels, 36 chunks of 8).
+// kFwd1: the first layer (K = 9 taps x 2 channels = 18, zero-padded to 32: 4 chunks),
+// its A rows gathered from the float32 NCHW input and rounded to BF16.
+enum ConvMode { kFwd = 0, kDgrad = 1, kFwd1 = 2 };
 
-// ------------------------------------------------------ 32-channel layers on tcgen05
-enum ConvMode { kFwd = 0, kDgrad = 1 };
-constexpr int kConvThreads = 256;
-constexpr uint32_t kConvABytes = kKChunks * 128 * 16;  // 73,728: [36][128 rows][16 B]
-constexpr uint32_t kConvSmem = kConvABytes + kPackBytes + 64;
+template <int MODE>
+struct ConvShape {
+  static constexpr int KC = MODE == kFwd1 ? 4 : kKChunks;  // K chunks of 8 BF16
+  static constexpr int THREADS = MODE == kFwd1 ? 128 : 256;  // 1 or 2 threads per A row
+  static constexpr int MIN_CTAS = MODE == kFwd1 ? 6 : 2;
+  static constexpr uint32_t A_BYTES = KC * 128 * 16;  // [KC][128 rows][16 B]
+  static constexpr uint32_t B_BYTES = KC * kCh * 16;  // [KC][32 rows][16 B]
+  static constexpr uint32_t SMEM = A_BYTES + B_BYTES + 64;
+};
 
 // One 128-row tile per iteration of a persistent loop.  Rows are pixels of the grid G
-// (side 2^lg_g); source pixels lie on the grid S (side 2^lg_s), NHWC BF16 with 32
-// channels.  A row's K chunk (tap, 8 channels) is 16 contiguous bytes of the source:
+// (side 2^lg_g); source pixels lie on the grid S (side 2^lg_s).  For the 32-channel
+// modes a row's K chunk (tap, 8 channels) is 16 contiguous bytes of the NHWC BF16 source:
 //   forward  (grid G = output): source pixel (s y + dy - 1, s x + dx - 1);
 //   data grad (grid G = layer input): source pixel ((y + 1 - dy) / s, (x + 1 - dx) / s)
-//            where both divisions are exact, else zero.
+//            for the taps where both divisions are exact.  With s = 2 those taps depend
+//            only on the parities of (y, x): dy = 1 for even y, dy in {0, 2} for odd y
+//            (likewise dx), so the rows are split into the four parity classes (tiles
+//            never mix classes) and a tile's K holds only its class's 1, 2 or 4 taps.
 // Epilogue: forward adds the bias and applies the ReLU; data grad multiplies by the
-// ReLU mask of the layer below (act > 0).  Both store BF16 NHWC rows.
+// ReLU mask of the layer below (act > 0).  Both store BF16 NHWC rows of 32 channels.
 template <int MODE>
-__global__ void __launch_bounds__(kConvThreads, 2)
-    conv_mma_kernel(const bf16 *__restrict__ src, const bf16 *__restrict__ wpack, const float *__restrict__ bias,
+__global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN_CTAS)
+    conv_mma_kernel(const void *__restrict__ src_v, const bf16 *__restrict__ wpack, const float *__restrict__ bias,
                     const bf16 *__restrict__ mask, bf16 *__restrict__ out, int B, int lg_s, int lg_g, int stride,
                     uint32_t *status) {
+  using Sh = ConvShape<MODE>;
+  constexpr int NH = Sh::THREADS == 256 ? 1 : 2;  // 16-column halves per epilogue thread
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t *sA = smem;
-  uint8_t *sB = smem + kConvABytes;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kConvABytes + kPackBytes);
+  uint8_t *sB = smem + Sh::A_BYTES;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Sh::A_BYTES + Sh::B_BYTES);
   uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = 1 << lg_s, G = 1 << lg_g;
@@ -227,7 +210,7 @@ __global__ void __launch_bounds__(kConvThreads, 2)
   {  // the packed weights, once
     const uint4 *g = reinterpret_cast<const uint4 *>(wpack);
     uint4 *d = reinterpret_cast<uint4 *>(sB);
-    for (int i = tid; i < (int)(kPackBytes / 16); i += kConvThreads) d[i] = __ldg(g + i);
+    for (int i = tid; i < (int)(Sh::B_BYTES / 16); i += Sh::THREADS) d[i] = __ldg(g + i);
   }
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -241,73 +224,152 @@ __global__ void __launch_bounds__(kConvThreads, 2)
   const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
 
   const int m = tid & 127, half = tid >> 7;
+  const int q = warp & 3, h0 = NH == 1 ? warp >> 2 : 0;  // epilogue: TMEM lane quadrant, first half
+  float bv[16 * NH];
+#pragma unroll
+  for (int i = 0; i < 16 * NH; ++i) bv[i] = MODE != kDgrad ? __ldg(bias + 16 * h0 + i) : 0.0f;
+  // Data grad with stride 2: class c = 2 (y & 1) + (x & 1) over the half grid; every other
+  // mode: one class, the whole grid.
+  const bool split = MODE == kDgrad && stride == 2;
+  const int lg_c = split ? lg_g - 1 : lg_g;  // class grid side 2^lg_c
+  const int Pc = B << (2 * lg_c);
+  const int tiles_c = (Pc + 127) >> 7;
+  const int ntiles_all = split ? 4 * tiles_c : ntiles;
   uint32_t it = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    // ---- A tile: row m, chunks (tap, c8) with c8 in {2 half, 2 half + 1}
-    const int p = (tile << 7) + m;
-    const bool valid = p < P;
-    const int b = p >> (2 * lg_g), y = (p >> lg_g) & (G - 1), x = p & (G - 1);
-    uint4 v[kTaps][2];
+  for (int tile = blockIdx.x; tile < ntiles_all; tile += gridDim.x, ++it) {
+    const int cls = split ? tile / tiles_c : 0;
+    const int tcls = split ? tile - cls * tiles_c : tile;  // tile within the class
+    const int py = cls >> 1, px = cls & 1;
+    // the class's taps: dy in {ty0, ty0 + 2} (ndy of them: {1} for even y, {0, 2} for odd
+    // y); same for dx
+    const int ty0 = py ? 0 : 1, ndy = py ? 2 : 1;
+    const int tx0 = px ? 0 : 1, ndx = px ? 2 : 1;
+    // grid pixel of class row r, or -1 past the end
+    auto row_pixel = [&](int r) -> int {
+      if (r >= Pc) return -1;
+      if (!split) return r;
+      const int b = r >> (2 * lg_c), yc = (r >> lg_c) & ((1 << lg_c) - 1), xc = r & ((1 << lg_c) - 1);
+      return (((b << lg_g) + 2 * yc + py) << lg_g) + 2 * xc + px;
+    };
+    const int p = row_pixel((tcls << 7) + m);
+    const bool valid = p >= 0;
+    const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), x = p & (G - 1);
+    if (MODE == kFwd1) {  // ---- row m: k = 2 tap + c for k < 18, then zeros
+      const float *src = static_cast<const float *>(src_v);
+      float v[2 * kTaps];
 #pragma unroll
-    for (int t = 0; t < kTaps; ++t) {
-      const int dy = t / 3, dx = t % 3;
-      int yy, xx;
-      bool ok;
-      if (MODE == kFwd) {
-        yy = stride * y + dy - 1;
-        xx = stride * x + dx - 1;
-        ok = valid && yy >= 0 && yy < S && xx >= 0 && xx < S;
-      } else {
-        const int ty = y + 1 - dy, tx = x + 1 - dx;
-        ok = valid && ty >= 0 && tx >= 0 && (ty % stride) == 0 && (tx % stride) == 0;
-        yy = ty / stride;
-        xx = tx / stride;
-        ok = ok && yy < S && xx < S;
+      for (int t = 0; t < kTaps; ++t) {
+        const int yy = stride * y + t / 3 - 1, xx = stride * x + t % 3 - 1;
+        const bool ok = valid && yy >= 0 && yy < S && xx >= 0 && xx < S;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          v[2 * t + c] = ok ? __ldg(src + (((((size_t)b * 2 + c) << lg_s) + yy) << lg_s) + xx) : 0.0f;
       }
-      const size_t pix = ((((size_t)b << lg_s) + (ok ? yy : 0)) << lg_s) + (ok ? xx : 0);
-      const uint4 *s4 = reinterpret_cast<const uint4 *>(src + pix * kCh) + 2 * half;
-      v[t][0] = ok ? __ldg(s4) : make_uint4(0, 0, 0, 0);
-      v[t][1] = ok ? __ldg(s4 + 1) : make_uint4(0, 0, 0, 0);
-    }
+      uint8_t *row = sA + (uint32_t)m * 16u;
+      *reinterpret_cast<uint4 *>(row) =
+          make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+      *reinterpret_cast<uint4 *>(row + 2048) =
+          make_uint4(pack2(v[8], v[9]), pack2(v[10], v[11]), pack2(v[12], v[13]), pack2(v[14], v[15]));
+      *reinterpret_cast<uint4 *>(row + 4096) = make_uint4(pack2(v[16], v[17]), 0u, 0u, 0u);
+      *reinterpret_cast<uint4 *>(row + 6144) = make_uint4(0u, 0u, 0u, 0u);
+    } else if (MODE == kDgrad && split) {  // ---- class taps (iy, ix): at most 2 x 2
+      // y = 2 yc + py: tap dy = ty0 + 2 iy reads source row (y + 1 - dy) / 2, which is yc,
+      // or yc + 1 for (odd y, dy = 0); likewise for x.
+      const bf16 *src = static_cast<const bf16 *>(src_v);
+      const int yc = y >> 1, xc = x >> 1;
+      uint4 v[2][2][2];
 #pragma unroll
-    for (int t = 0; t < kTaps; ++t) {
-      const int j0 = t * 4 + 2 * half;
-      *reinterpret_cast<uint4 *>(sA + (uint32_t)j0 * 2048u + (uint32_t)m * 16u) = v[t][0];
-      *reinterpret_cast<uint4 *>(sA + (uint32_t)(j0 + 1) * 2048u + (uint32_t)m * 16u) = v[t][1];
+      for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < 2; ++ix) {
+          const int yy = yc + (py & (iy == 0)), xx = xc + (px & (ix == 0));
+          const bool ok = valid && iy < ndy && ix < ndx && yy < S && xx < S;
+          const size_t pix = ((((size_t)b << lg_s) + (ok ? yy : 0)) << lg_s) + (ok ? xx : 0);
+          const uint4 *s4 = reinterpret_cast<const uint4 *>(src + pix * kCh) + 2 * half;
+          v[iy][ix][0] = ok ? __ldg(s4) : make_uint4(0, 0, 0, 0);
+          v[iy][ix][1] = ok ? __ldg(s4 + 1) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+      for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < 2; ++ix)
+          if (iy < ndy && ix < ndx) {
+            const uint32_t j0 = (uint32_t)((iy * ndx + ix) * 4 + 2 * half);
+            *reinterpret_cast<uint4 *>(sA + j0 * 2048u + (uint32_t)m * 16u) = v[iy][ix][0];
+            *reinterpret_cast<uint4 *>(sA + (j0 + 1u) * 2048u + (uint32_t)m * 16u) = v[iy][ix][1];
+          }
+    } else {  // ---- row m: chunks (tap t, c8) with c8 in {2 half, 2 half + 1}
+      const bf16 *src = static_cast<const bf16 *>(src_v);
+      uint4 v[kTaps][2];
+#pragma unroll
+      for (int t = 0; t < kTaps; ++t) {
+        const int dy = t / 3, dx = t % 3;
+        // forward: source (s y + dy - 1, s x + dx - 1); data grad with s = 1: (y + 1 - dy, x + 1 - dx)
+        const int yy = MODE == kFwd ? stride * y + dy - 1 : y + 1 - dy;
+        const int xx = MODE == kFwd ? stride * x + dx - 1 : x + 1 - dx;
+        const bool ok = valid && yy >= 0 && yy < S && xx >= 0 && xx < S;
+        const size_t pix = ((((size_t)b << lg_s) + (ok ? yy : 0)) << lg_s) + (ok ? xx : 0);
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + pix * kCh) + 2 * half;
+        v[t][0] = ok ? __ldg(s4) : make_uint4(0, 0, 0, 0);
+        v[t][1] = ok ? __ldg(s4 + 1) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int t = 0; t < kTaps; ++t) {
+        const int j0 = t * 4 + 2 * half;
+        *reinterpret_cast<uint4 *>(sA + (uint32_t)j0 * 2048u + (uint32_t)m * 16u) = v[t][0];
+        *reinterpret_cast<uint4 *>(sA + (uint32_t)(j0 + 1) * 2048u + (uint32_t)m * 16u) = v[t][1];
+      }
     }
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
+      if (MODE == kDgrad && split) {  // the class's taps: A chunks 4 i + c8, B chunks 4 tap + c8
+        for (int i = 0; i < ndy * ndx; ++i) {
+          const int iy = ndx == 2 ? i >> 1 : i, ix = ndx == 2 ? i & 1 : 0;
+          const int tap = (ty0 + 2 * iy) * 3 + tx0 + 2 * ix;
 #pragma unroll
-      for (int k = 0; k < kKChunks / 2; ++k) {
-        const uint64_t a = sdesc(aBase + (uint32_t)k * 2u * 2048u, 2048u, 128u);
-        const uint64_t bd = sdesc(bBase + (uint32_t)k * 2u * 512u, 512u, 128u);
-        umma_f16(tmem, a, bd, kIdesc, k > 0 ? 1u : 0u);
+          for (int k = 0; k < 2; ++k) {
+            const uint64_t a = sdesc(aBase + (uint32_t)(4 * i + 2 * k) * 2048u, 2048u, 128u);
+            const uint64_t bd = sdesc(bBase + (uint32_t)(4 * tap + 2 * k) * 512u, 512u, 128u);
+            umma_f16(tmem, a, bd, kIdesc, (i > 0 || k > 0) ? 1u : 0u);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < Sh::KC / 2; ++k) {
+          const uint64_t a = sdesc(aBase + (uint32_t)k * 2u * 2048u, 2048u, 128u);
+          const uint64_t bd = sdesc(bBase + (uint32_t)k * 2u * 512u, 512u, 128u);
+          umma_f16(tmem, a, bd, kIdesc, k > 0 ? 1u : 0u);
+        }
       }
       umma_commit(bar);
+    }
+    // ---- epilogue: row 32 q + lane of the tile, output columns 16 h .. 16 h + 15
+    const int pr = row_pixel((tcls << 7) + 32 * q + lane);
+    uint4 m0 = make_uint4(0, 0, 0, 0), m1 = m0;
+    if (MODE == kDgrad && pr >= 0) {  // the ReLU mask, fetched while the MMAs run
+      const uint4 *mk = reinterpret_cast<const uint4 *>(mask + (size_t)pr * kCh + 16 * h0);
+      m0 = __ldg(mk);
+      m1 = __ldg(mk + 1);
     }
     const bool ok = mbar_wait_bounded(bar, it & 1u, status);
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    // ---- epilogue: warp -> TMEM lane quadrant (warp & 3), column half (warp >> 2)
-    {
-      const int q = warp & 3, h = warp >> 2;
-      const int row = 32 * q + lane;
-      const int pr = (tile << 7) + row;
+#pragma unroll
+    for (int hh = 0; hh < NH; ++hh) {
+      const int h = h0 + hh;
       uint32_t r[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h), r);
       tmem_ld_wait();
-      if (pr < P) {
+      if (pr >= 0) {
         uint32_t o32[8];
-        if (MODE == kFwd) {
+        if (MODE != kDgrad) {
 #pragma unroll
           for (int i = 0; i < 8; ++i)
-            o32[i] = pack2(fmaxf(__uint_as_float(r[2 * i]) + __ldg(bias + 16 * h + 2 * i), 0.0f),
-                           fmaxf(__uint_as_float(r[2 * i + 1]) + __ldg(bias + 16 * h + 2 * i + 1), 0.0f));
+            o32[i] = pack2(fmaxf(__uint_as_float(r[2 * i]) + bv[16 * hh + 2 * i], 0.0f),
+                           fmaxf(__uint_as_float(r[2 * i + 1]) + bv[16 * hh + 2 * i + 1], 0.0f));
         } else {
-          const uint4 *mk = reinterpret_cast<const uint4 *>(mask + (size_t)pr * kCh + 16 * h);
-          const uint4 m0 = __ldg(mk), m1 = __ldg(mk + 1);
           const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
           for (int i = 0; i < 8; ++i)
@@ -370,8 +432,10 @@ __device__ __forceinline__ void transpose8(const uint4 (&r)[8], uint4 (&t)[8]) {
 
 // Source of the weight gradient: CIN == 32, the layer input as BF16 NHWC [B][S][S][32];
 // CIN == 2, the network input as float32 NCHW [B][2][64][64], rounded to BF16 here.
+// A unit is 8 consecutive pixels of one K chunk: since the grid side is a multiple of 8
+// and chunks start at multiples of 64, they lie in one image row.
 template <int CIN>
-__global__ void __launch_bounds__(kWgThreads, 1)
+__global__ void __launch_bounds__(kWgThreads, CIN == kCh ? 2 : 3)
     wgrad_kernel(const void *__restrict__ src_v, const bf16 *__restrict__ dz, float *__restrict__ part, int B,
                  int lg_s, int lg_g, int stride, int per_chunk, uint32_t *status) {
   using Sh = WgShape<CIN>;
@@ -419,30 +483,31 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     constexpr int NG = CIN == kCh ? kTaps * 4 : Sh::NDATA;  // A units per K chunk
     for (int u = tid; u < (NG + 4) * 8; u += kWgThreads) {
       const int kc = u & 7, g = u >> 3;
+      const int pq = p0 + kc * 8;  // pixels pq .. pq + 7: image b, row y, columns x0 ..
+      const bool in = pq < p_end;
+      const int b = pq >> (2 * lg_g), y = (pq >> lg_g) & (G - 1), x0 = pq & (G - 1);
       if (g >= NG) {  // dz: 8 pixels x 8 output channels -> rows o, K = pixels
         const int o8 = g - NG;
+        const uint4 *d4 = reinterpret_cast<const uint4 *>(dz + (size_t)pq * kCh) + o8;
         uint4 r[8], t[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int p = p0 + kc * 8 + e;
-          r[e] = p < p_end ? __ldg(reinterpret_cast<const uint4 *>(dz + (size_t)p * kCh) + o8) : zero;
-        }
+        for (int e = 0; e < 8; ++e) r[e] = in ? __ldg(d4 + 4 * e) : zero;
         transpose8(r, t);
         uint8_t *dst = sB + kc * Sh::LBO_B + o8 * 128;
 #pragma unroll
         for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4 *>(dst + j * 16) = t[j];
       } else if (CIN == kCh) {  // 8 pixels x 8 input channels of one tap -> rows (tap, c)
         const int tap = g >> 2, c8 = g & 3, dy = tap / 3, dx = tap % 3;
-        const bf16 *src = static_cast<const bf16 *>(src_v);
+        const int yy = stride * y + dy - 1;
+        const bool row_ok = in && yy >= 0 && yy < S;
+        const uint4 *row = reinterpret_cast<const uint4 *>(static_cast<const bf16 *>(src_v) +
+                                                           ((((size_t)b << lg_s) + (row_ok ? yy : 0)) << lg_s) * kCh) +
+                           c8;
         uint4 r[8], t[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const int p = p0 + kc * 8 + e;
-          const int b = p >> (2 * lg_g), y = (p >> lg_g) & (G - 1), x = p & (G - 1);
-          const int yy = stride * y + dy - 1, xx = stride * x + dx - 1;
-          const bool ok = p < p_end && yy >= 0 && yy < S && xx >= 0 && xx < S;
-          const size_t pix = ((((size_t)b << lg_s) + (ok ? yy : 0)) << lg_s) + (ok ? xx : 0);
-          r[e] = ok ? __ldg(reinterpret_cast<const uint4 *>(src + pix * kCh) + c8) : zero;
+          const int xx = stride * (x0 + e) + dx - 1;
+          r[e] = (row_ok && xx >= 0 && xx < S) ? __ldg(row + 4 * xx) : zero;
         }
         transpose8(r, t);
         uint8_t *dst = sA + kc * Sh::LBO_A + (tap * kCh + c8 * 8) * 16;
@@ -450,15 +515,15 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4 *>(dst + j * 16) = t[j];
       } else {  // first layer: row (tap, c) of 8 pixels straight from the float input
         const int tap = g / CIN, c = g % CIN, dy = tap / 3, dx = tap % 3;
-        const float *src = static_cast<const float *>(src_v);
+        const int yy = stride * y + dy - 1;
+        const bool row_ok = in && yy >= 0 && yy < S;
+        const float *row = static_cast<const float *>(src_v) +
+                           ((((size_t)b * CIN + c) << lg_s) + (row_ok ? yy : 0)) * (size_t)S;
         float f[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const int p = p0 + kc * 8 + e;
-          const int b = p >> (2 * lg_g), y = (p >> lg_g) & (G - 1), x = p & (G - 1);
-          const int yy = stride * y + dy - 1, xx = stride * x + dx - 1;
-          const bool ok = p < p_end && yy >= 0 && yy < S && xx >= 0 && xx < S;
-          f[e] = ok ? __ldg(src + (((((size_t)b * CIN + c) << lg_s) + yy) << lg_s) + xx) : 0.0f;
+          const int xx = stride * (x0 + e) + dx - 1;
+          f[e] = (row_ok && xx >= 0 && xx < S) ? __ldg(row + xx) : 0.0f;
         }
         *reinterpret_cast<uint4 *>(sA + kc * Sh::LBO_A + g * 16) =
             make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
@@ -506,24 +571,38 @@ __global__ void __launch_bounds__(kWgThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, Sh::TMEM_COLS);
 }
 
-// Partial sums of the chunks, added in chunk order: dw[o][c][tap], db[o].
-__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int nchunks, int cin, float *__restrict__ gw,
-                                    float *__restrict__ gb) {
-  const int rows = cin * kTaps + 1;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows * kCh) return;
-  const int row = i / kCh, o = i % kCh;
+// Partial sums of the chunks: dw[o][c][tap], db[o].  One block of 1024 threads per row
+// (tap, c) or the bias row: 32 chunk slices, each summed in chunk order, then added in
+// slice order.
+constexpr int kRedSlices = 32;
+
+__global__ void __launch_bounds__(kRedSlices * kCh) wgrad_reduce_kernel(const float *__restrict__ part, int nchunks,
+                                                                        int cin, float *__restrict__ gw,
+                                                                        float *__restrict__ gb) {
+  __shared__ float red[kRedSlices][kCh];
+  const int rows = cin * kTaps + 1, row = blockIdx.x, o = threadIdx.x & 31, sl = threadIdx.x >> 5;
   float s = 0.0f;
-  for (int c = 0; c < nchunks; ++c) s += part[((size_t)c * rows + row) * kCh + o];
-  if (row < cin * kTaps) gw[((size_t)o * cin + row % cin) * 9 + row / cin] = s;
-  else gb[o] = s;
+#pragma unroll 4
+  for (int c = sl; c < nchunks; c += kRedSlices) s += part[((size_t)c * rows + row) * kCh + o];
+  red[sl][o] = s;
+  __syncthreads();
+  if (threadIdx.x < kCh) {
+    float t = 0.0f;
+    for (int i = 0; i < kRedSlices; ++i) t += red[i][o];
+    if (row < cin * kTaps) gw[((size_t)o * cin + row % cin) * 9 + row / cin] = t;
+    else gb[o] = t;
+  }
 }
 
-// pooled[b][c] = mean over the 8x8 positions; out[b][j] = fcb[j] + sum_c fcw[j][c] pooled[b][c]
+// pooled[b][c] = mean over the 8x8 positions; out[b][j] = fcb[j] + sum_c fcw[j][c] pooled[b][c].
+// With a target (training): dout = 2 (out - target) / (B n_out) and the block's share of
+// the mean squared error added to *loss.  One block of 64 threads per sample.
 __global__ void pool_fc_kernel(const bf16 *__restrict__ act, const float *__restrict__ fcw,
                                const float *__restrict__ fcb, float *__restrict__ pooled, float *__restrict__ out,
-                               int n_out) {
+                               int n_out, const float *__restrict__ target, float *__restrict__ dout, float *loss,
+                               int B) {
   __shared__ float pl[kCh];
+  __shared__ float red[2];
   const int b = blockIdx.x;
   if (threadIdx.x < kCh) {
     const bf16 *a = act + (size_t)b * 64 * kCh + threadIdx.x;
@@ -533,65 +612,65 @@ __global__ void pool_fc_kernel(const bf16 *__restrict__ act, const float *__rest
     pooled[b * kCh + threadIdx.x] = pl[threadIdx.x];
   }
   __syncthreads();
+  const float inv_n = 1.0f / (float)B / (float)n_out;
+  float sq = 0.0f;
   for (int j = threadIdx.x; j < n_out; j += blockDim.x) {
     float s = fcb[j];
     for (int c = 0; c < kCh; ++c) s = fmaf(fcw[j * kCh + c], pl[c], s);
     out[(size_t)b * n_out + j] = s;
+    if (target) {
+      const float d = s - target[(size_t)b * n_out + j];
+      dout[(size_t)b * n_out + j] = 2.0f * d * inv_n;
+      sq = fmaf(d, d, sq);
+    }
   }
-}
-
-// loss = mean (out - target)^2 (accumulated into *loss); dout = 2 (out - target) / (B n_out)
-__global__ void mse_kernel(const float *__restrict__ out, const float *__restrict__ target, float *__restrict__ dout,
-                           float *loss, int n) {
-  __shared__ float red[32];
-  float s = 0.0f;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float d = out[i] - target[i];
-    dout[i] = 2.0f * d / (float)n;
-    s = fmaf(d, d, s);
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  if (!target) return;
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) atomicAdd(loss, (red[0] + red[1]) * inv_n);
+}
+
+// Linear layer weight gradients: dfcw[j][c] = sum_b dout[b][j] pooled[b][c] and
+// dfcb[j] = sum_b dout[b][j]; one block per output j, 8 batch slices added in order.
+__global__ void fc_wgrad_kernel(const float *__restrict__ dout, const float *__restrict__ pooled,
+                                float *__restrict__ dfcw, float *__restrict__ dfcb, int B, int n_out) {
+  __shared__ float red[8][kCh + 1];
+  const int j = blockIdx.x, c = threadIdx.x & 31, part = threadIdx.x >> 5;
+  float s = 0.0f, sb = 0.0f;
+#pragma unroll 8
+  for (int b = part; b < B; b += 8) {
+    const float d = dout[(size_t)b * n_out + j];
+    s = fmaf(d, pooled[b * kCh + c], s);
+    sb += d;
+  }
+  red[part][c] = s;
+  if (c == 0) red[part][kCh] = sb;
+  __syncthreads();
+  if (threadIdx.x <= kCh) {
     float t = 0.0f;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    atomicAdd(loss, t / (float)n);
+    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
+    if (threadIdx.x < kCh) dfcw[j * kCh + threadIdx.x] = t;
+    else dfcb[j] = t;
   }
 }
 
-// linear layer gradients and dL/dpooled
-__global__ void fc_bwd_kernel(const float *__restrict__ dout, const float *__restrict__ pooled,
-                              const float *__restrict__ fcw, float *__restrict__ dfcw, float *__restrict__ dfcb,
-                              float *__restrict__ dpooled, int B, int n_out) {
+// Gradient at the last layer's pre-activation: dpooled[b][c] = sum_j dout[b][j] fcw[j][c],
+// spread as dpooled / 64 over the 8x8 positions, masked by the ReLU (act > 0), stored
+// BF16 NHWC.  One thread per (b, c).
+__global__ void fc_dgrad_unpool_kernel(const float *__restrict__ dout, const float *__restrict__ fcw,
+                                       const bf16 *__restrict__ act, bf16 *__restrict__ dz, int B, int n_out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n_out * kCh) {  // dfcw[j][c] = sum_b dout[b][j] pooled[b][c]
-    const int j = t / kCh, c = t % kCh;
-    float s = 0.0f;
-    for (int b = 0; b < B; ++b) s = fmaf(dout[(size_t)b * n_out + j], pooled[b * kCh + c], s);
-    dfcw[t] = s;
-  }
-  if (t < n_out) {
-    float s = 0.0f;
-    for (int b = 0; b < B; ++b) s += dout[(size_t)b * n_out + t];
-    dfcb[t] = s;
-  }
-  if (t < B * kCh) {  // dpooled[b][c] = sum_j dout[b][j] fcw[j][c]
-    const int b = t / kCh, c = t % kCh;
-    float s = 0.0f;
-    for (int j = 0; j < n_out; ++j) s = fmaf(dout[(size_t)b * n_out + j], fcw[j * kCh + c], s);
-    dpooled[t] = s;
-  }
-}
-
-// Gradient at the last layer's pre-activation: dpooled / 64 at every position, masked by
-// the ReLU (act > 0), stored BF16 NHWC.
-__global__ void unpool_mask_kernel(const float *__restrict__ dpooled, const bf16 *__restrict__ act,
-                                   bf16 *__restrict__ dz, int B) {
-  const int n = B * 64 * kCh;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float g = dpooled[(i >> 11) * kCh + (i & 31)] * (1.0f / 64.0f);
-    dz[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.0f ? g : 0.0f);
+  if (t >= B * kCh) return;
+  const int b = t / kCh, c = t % kCh;
+  float s = 0.0f;
+#pragma unroll 8
+  for (int j = 0; j < n_out; ++j) s = fmaf(dout[(size_t)b * n_out + j], fcw[j * kCh + c], s);
+  const bf16 g = __float2bfloat16_rn(s * (1.0f / 64.0f));
+  const bf16 z = __float2bfloat16_rn(0.0f);
+  for (int i = 0; i < 64; ++i) {
+    const size_t at = ((size_t)b * 64 + i) * kCh + c;
+    dz[at] = __bfloat162float(act[at]) > 0.0f ? g : z;
   }
 }
 
@@ -621,15 +700,16 @@ int sm_count() {
 }
 
 template <int MODE>
-int conv_mma(const bf16 *src, const bf16 *wpack, const float *bias, const bf16 *mask, bf16 *out, int B, int lg_s,
+int conv_mma(const void *src, const bf16 *wpack, const float *bias, const bf16 *mask, bf16 *out, int B, int lg_s,
              int lg_g, int stride, int nsm, cudaStream_t s) {
+  using Sh = ConvShape<MODE>;
   cudaError_t e = cudaFuncSetAttribute(conv_mma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kConvSmem);
+                                       (int)Sh::SMEM);
   if (e != cudaSuccess) return cuda_status(e, "network convolution attributes");
   const int ntiles = ((B << (2 * lg_g)) + 127) >> 7;
-  const int grid = ntiles < 2 * nsm ? ntiles : 2 * nsm;
-  conv_mma_kernel<MODE><<<grid, kConvThreads, kConvSmem, s>>>(src, wpack, bias, mask, out, B, lg_s, lg_g, stride,
-                                                              device_status_word());
+  const int grid = ntiles < Sh::MIN_CTAS * nsm ? ntiles : Sh::MIN_CTAS * nsm;
+  conv_mma_kernel<MODE><<<grid, Sh::THREADS, Sh::SMEM, s>>>(src, wpack, bias, mask, out, B, lg_s, lg_g, stride,
+                                                            device_status_word());
   return cuda_status(cudaGetLastError(), "network convolution");
 }
 
@@ -640,17 +720,17 @@ int wgrad(const void *src, const bf16 *dz, float *part, float *gw, float *gb, in
   cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
   if (e != cudaSuccess) return cuda_status(e, "network weight-gradient attributes");
   const int P = B << (2 * lg_g);
-  const int per = wg_per_chunk(P), nch = wg_nchunks(P);
+  const int per = wg_per_chunk(P, CIN), nch = wg_nchunks(P, CIN);
   wgrad_kernel<CIN><<<nch, kWgThreads, Sh::SMEM, s>>>(src, dz, part, B, lg_s, lg_g, stride, per, device_status_word());
   const int rows = wg_rows(CIN);
-  wgrad_reduce_kernel<<<(rows * kCh + 255) / 256, 256, 0, s>>>(part, nch, CIN, gw, gb);
+  wgrad_reduce_kernel<<<rows, kRedSlices * kCh, 0, s>>>(part, nch, CIN, gw, gb);
   return cuda_status(cudaGetLastError(), "network weight gradient");
 }
 
 struct Bufs {
   float *wq;
   bf16 *wf[kLayers], *wd[kLayers], *act[kLayers], *dz[kLayers];
-  float *pooled, *dpooled, *out, *dout, *part;
+  float *pooled, *out, *dout, *part;
 };
 
 Bufs bufs(void *ws_v, const Work &Wk) {
@@ -658,13 +738,12 @@ Bufs bufs(void *ws_v, const Work &Wk) {
   Bufs b{};
   b.wq = reinterpret_cast<float *>(ws + Wk.wq);
   for (int i = 0; i < kLayers; ++i) {
-    b.wf[i] = i > 0 ? reinterpret_cast<bf16 *>(ws + Wk.wf[i]) : nullptr;
+    b.wf[i] = reinterpret_cast<bf16 *>(ws + Wk.wf[i]);
     b.wd[i] = i > 0 ? reinterpret_cast<bf16 *>(ws + Wk.wd[i]) : nullptr;
     b.act[i] = reinterpret_cast<bf16 *>(ws + Wk.act[i]);
     b.dz[i] = reinterpret_cast<bf16 *>(ws + Wk.dz[i]);
   }
   b.pooled = reinterpret_cast<float *>(ws + Wk.pooled);
-  b.dpooled = reinterpret_cast<float *>(ws + Wk.dpooled);
   b.out = reinterpret_cast<float *>(ws + Wk.out);
   b.dout = reinterpret_cast<float *>(ws + Wk.dout);
   b.part = reinterpret_cast<float *>(ws + Wk.part);
@@ -672,20 +751,22 @@ Bufs bufs(void *ws_v, const Work &Wk) {
 }
 
 int pack(const float *params, const Layout &L, const Bufs &b, cudaStream_t s) {
-  pack_kernel<<<grid_for(L.total + 3 * kPack), 256, 0, s>>>(params, b.wq, (int)L.total, b.wf[1], b.wd[1], b.wf[2],
-                                                           b.wd[2], b.wf[3], b.wd[3], L.w[1], L.w[2], L.w[3]);
+  pack_kernel<<<grid_for(L.total + kPack0 + 3 * kPack), 256, 0, s>>>(params, b.wq, (int)L.total, b.wf[0], b.wf[1],
+                                                                    b.wd[1], b.wf[2], b.wd[2], b.wf[3], b.wd[3],
+                                                                    L.w[0], L.w[1], L.w[2], L.w[3]);
   return cuda_status(cudaGetLastError(), "network weight packing");
 }
 
 // x -> act[0..3] -> pooled -> out (parameters already packed)
-int forward(const float *x, const Layout &L, const Bufs &b, int B, int n_out, float *out, int nsm, cudaStream_t s) {
-  conv1_fwd_kernel<<<grid_for((size_t)B * 1024), 256, 0, s>>>(x, b.wq + L.w[0], b.wq + L.b[0], b.act[0], B);
-  int st = cuda_status(cudaGetLastError(), "network first layer");
+int forward(const float *x, const Layout &L, const Bufs &b, int B, int n_out, float *out, int nsm, cudaStream_t s,
+            const float *target = nullptr, float *loss = nullptr) {
+  int st = conv_mma<kFwd1>(x, b.wf[0], b.wq + L.b[0], nullptr, b.act[0], B, kLgIn[0], kLgOut[0], kStride[0], nsm, s);
   for (int li = 1; li < kLayers && st == SVK_OK; ++li)
     st = conv_mma<kFwd>(b.act[li - 1], b.wf[li], b.wq + L.b[li], nullptr, b.act[li], B, kLgIn[li], kLgOut[li],
                         kStride[li], nsm, s);
   if (st != SVK_OK) return st;
-  pool_fc_kernel<<<B, 64, 0, s>>>(b.act[kLayers - 1], b.wq + L.fcw, b.wq + L.fcb, b.pooled, out, n_out);
+  pool_fc_kernel<<<B, 64, 0, s>>>(b.act[kLayers - 1], b.wq + L.fcw, b.wq + L.fcb, b.pooled, out, n_out, target,
+                                  b.dout, loss, B);
   return cuda_status(cudaGetLastError(), "network pooling");
 }
 
@@ -804,15 +885,12 @@ int cnn_gradient(const float *params, const float *x, const float *target, int B
   const Bufs b = bufs(ws, work_layout(B, n_out));
   const int nsm = sm_count();
   if ((st = pack(params, L, b, s)) != SVK_OK) return st;
-  if ((st = forward(x, L, b, B, n_out, b.out, nsm, s)) != SVK_OK) return st;
   cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), s);
   if (e != cudaSuccess) return cuda_status(e, "loss reset");
-  const int n = B * n_out;
-  mse_kernel<<<grid_for(n), 256, 0, s>>>(b.out, target, b.dout, loss, n);
-  fc_bwd_kernel<<<grid_for((size_t)(n_out * kCh > B * kCh ? n_out * kCh : B * kCh)), 256, 0, s>>>(
-      b.dout, b.pooled, b.wq + L.fcw, grad + L.fcw, grad + L.fcb, b.dpooled, B, n_out);
-  unpool_mask_kernel<<<grid_for((size_t)B * 64 * kCh), 256, 0, s>>>(b.dpooled, b.act[kLayers - 1],
-                                                                    b.dz[kLayers - 1], B);
+  if ((st = forward(x, L, b, B, n_out, b.out, nsm, s, target, loss)) != SVK_OK) return st;
+  fc_wgrad_kernel<<<n_out, 256, 0, s>>>(b.dout, b.pooled, grad + L.fcw, grad + L.fcb, B, n_out);
+  fc_dgrad_unpool_kernel<<<(B * kCh + 255) / 256, 256, 0, s>>>(b.dout, b.wq + L.fcw, b.act[kLayers - 1],
+                                                               b.dz[kLayers - 1], B, n_out);
   if ((st = cuda_status(cudaGetLastError(), "network output gradient")) != SVK_OK) return st;
   for (int li = kLayers - 1; li >= 1; --li) {
     st = wgrad<kCh>(b.act[li - 1], b.dz[li], b.part, grad + L.w[li], grad + L.b[li], B, kLgIn[li], kLgOut[li],

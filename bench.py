@@ -82,9 +82,11 @@ def _traffic(precision):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_1209_5823_gb300", "csrc", "svk_tc.cu")
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("svk_tc.cu", "svk_umma.cuh"):  # the kernel and its tcgen05 wrappers
+        with open(os.path.join(ROOT, "paper_1209_5823_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    sha = h.hexdigest()
     if kv.get("workload") != WORKLOAD or kv.get("precision") != precision or kv.get("source_sha256") != sha:
         return None
     return int(kv["dram_bytes_per_launch"])
@@ -398,6 +400,20 @@ def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=3000):
     t_train = _t.perf_counter() - t0
     pred = net.predict(x[-n_hold:])
     err = ((pred - a[-n_hold:]) / prior.std(dev)).pow(2).mean(dim=0).cpu().numpy()
+    # device time of one gradient call (batch 256) and of a 4096-stamp forward pass
+    xb, zb = x[:net.batch].contiguous(), ((a[:net.batch] - prior.mean(dev)) / prior.std(dev)).contiguous()
+    gbuf, lbuf = torch.empty_like(net.params), torch.empty(1, device=dev)
+    grad_ms = _time(torch, lambda: svk.svk_cnn_gradient(net.params, xb, zb, grad=gbuf, loss=lbuf, workspace=net.ws),
+                    reps=50)
+    xf = x[:4096].contiguous()
+    fout = torch.empty((4096, N), device=dev)
+    fws = torch.empty(svk.svk_cnn_workspace_size(4096, N), dtype=torch.uint8, device=dev)
+    fwd_ms = _time(torch, lambda: svk.svk_cnn_forward(net.params, xf, N, out=fout, workspace=fws), reps=20)
+    # algorithmic FLOP per stamp: forward convolutions (2 x MACs), the same again for the
+    # weight gradients, and the data gradients of the three 32-channel layers
+    conv = [32 * 32 * 32 * 18, 16 * 16 * 32 * 288, 8 * 8 * 32 * 288, 8 * 8 * 32 * 288]
+    f_fwd = 2 * sum(conv)
+    f_train = 2 * f_fwd + 2 * sum(conv[1:])
     # a frame with a spatially varying kernel: network + field fit vs the FP64 fit
     c_true = torch.from_numpy(starfield.planted_coeffs(N, d, starfield.rng(starfield.BASE_SEED + 5))
                               .astype(np.float32)).to(dev)
@@ -424,6 +440,11 @@ def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=3000):
     chi2_fit_px = float(((Ds - Ds.mean(dim=(1, 2), keepdim=True)).double() ** 2).mean())
     return {"workload": "cnn_4conv32_64x64_pairs_to_49_local_coeffs",
             "pairs": n_pairs, "steps": steps, "batch": net.batch, "pairs_s": t_pairs, "train_s": t_train,
+            "train_step_ms": 1e3 * t_train / steps, "gradient_ms": grad_ms,
+            "train_stamps_per_s": net.batch / (1e-3 * grad_ms), "forward_4096_ms": fwd_ms,
+            "forward_stamps_per_s": 4096 / (1e-3 * fwd_ms), "flop_per_stamp_forward": f_fwd,
+            "flop_per_stamp_train": f_train, "gradient_tflops": f_train * net.batch / (1e-3 * grad_ms) / 1e12,
+            "forward_tflops": f_fwd * 4096 / (1e-3 * fwd_ms) / 1e12,
             "loss_first100": float(losses[:100].mean()), "loss_last100": float(losses[-100:].mean()),
             "heldout_mse_std_units": float(err.mean()), "heldout_mse_a0": float(err[0]), "prior_mse_std_units": 1.0,
             "frame": {"stamps": 500, "degree": d, "network_s": t_net, "fp64_fit_s": t_fit,
@@ -521,6 +542,9 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the night-batch and fit measurements")
+    ap.add_argument("--learned-only", action="store_true",
+                    help="only the coefficient-network measurement (its own JSON line; for profiling)")
+    ap.add_argument("--learned-steps", type=int, default=3000, help="training steps of that measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -543,6 +567,11 @@ def main():
     dev = torch.device("cuda", local_rank)
     prec = {"bf16x3": svk.SVK_PREC_BF16X3, "fp16x3": svk.SVK_PREC_FP16X3, "bf16": svk.SVK_PREC_BF16}[args.precision]
     spec, R, I, c = _frame(rank)
+    if args.learned_only:
+        res = _learned(svk, torch, dev, R, I, steps=args.learned_steps)
+        if rank == 0:
+            print(json.dumps({"learned": res}), flush=True)
+        return
     H, W, L, d = spec.H, spec.W, spec.L, spec.degree
     N = 49
     stream = torch.cuda.current_stream()
@@ -688,7 +717,7 @@ def main():
         out["fit"] = _fit_timing(svk, torch, dev, R, I, fp64_peak)
         out["precision"] = _precision_table(svk, torch, dev)
         out["paper_sweep"] = _paper_sweep(svk, torch, dev)
-        out["learned"] = _learned(svk, torch, dev, R, I)
+        out["learned"] = _learned(svk, torch, dev, R, I, steps=args.learned_steps)
     if not args.no_cpu_baseline:
         ref, rows, dt, cores = _oracle_band(R, I, basis.cpu().numpy(), c, d)
         y0, y1 = rows

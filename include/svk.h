@@ -221,8 +221,14 @@ SVK_API int svk_autotune(int N, int L, int degree, int precision, int W, int H, 
  * Architecture: four 3x3 convolutions (2->32 stride 2, 32->32 stride 2, 32->32 stride 2,
  * 32->32 stride 1, zero padding 1, ReLU), global average pooling, linear 32 -> n_out.
  * Parameters: one float32 vector of svk_cnn_param_count(n_out) values (FP32 master
- * copy); every layer computes with the weights rounded to BF16 and accumulates in FP32.
- * 1 <= n_out <= 256, 1 <= batch <= 4096.
+ * copy).  Precision: weights are used rounded to BF16; the input, every post-ReLU
+ * activation and every pre-activation gradient are stored in BF16; all sums accumulate
+ * in FP32 (the convolutions on the tensor cores, BF16 x BF16 -> FP32).  The gradient is
+ * deterministic (fixed-order reductions, no atomics); the loss is summed with atomics.
+ * 1 <= n_out <= 256, 1 <= batch <= 4096.  workspace: device memory of
+ * svk_cnn_workspace_size(batch, n_out) bytes, 256-byte aligned, owned by the caller
+ * (SVK_ERR_WORKSPACE when smaller, SVK_ERR_ARG when misaligned; NULL: the library
+ * allocates one on the stream).
  */
 SVK_API int svk_cnn_param_count(int n_out);
 SVK_API size_t svk_cnn_workspace_size(int batch, int n_out);

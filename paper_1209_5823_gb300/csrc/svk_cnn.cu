@@ -204,8 +204,6 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
   uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = 1 << lg_s, G = 1 << lg_g;
-  const int P = B << (2 * lg_g);
-  const int ntiles = (P + 127) >> 7;
 
   {  // the packed weights, once
     const uint4 *g = reinterpret_cast<const uint4 *>(wpack);
@@ -223,111 +221,141 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
   const uint32_t tmem = *slot;
   const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
 
-  const int m = tid & 127, half = tid >> 7;
+  // A build: kFwd1, one row per thread.  Otherwise lane l of warp w takes 16-byte chunk
+  // c8 = l / 8 of rows 8 w + l % 8 and that + 64: a warp's load covers 8 whole 64-byte
+  // source pixels, and each group of 8 lanes (one shared-memory wavefront for 16-byte
+  // stores) writes 8 different rows, i.e. 8 different bank groups.
+  const int m = tid & 127, c8 = lane >> 3, rr = 8 * warp + (lane & 7);
   const int q = warp & 3, h0 = NH == 1 ? warp >> 2 : 0;  // epilogue: TMEM lane quadrant, first half
   float bv[16 * NH];
 #pragma unroll
   for (int i = 0; i < 16 * NH; ++i) bv[i] = MODE != kDgrad ? __ldg(bias + 16 * h0 + i) : 0.0f;
-  // Data grad with stride 2: class c = 2 (y & 1) + (x & 1) over the half grid; every other
-  // mode: one class, the whole grid.
+
+  // Data grad with stride 2: class c = 2 (y & 1) + (x & 1) over the half grid, each
+  // class's rows in their own tiles; every other mode: one class, the whole grid.
   const bool split = MODE == kDgrad && stride == 2;
   const int lg_c = split ? lg_g - 1 : lg_g;  // class grid side 2^lg_c
   const int Pc = B << (2 * lg_c);
   const int tiles_c = (Pc + 127) >> 7;
-  const int ntiles_all = split ? 4 * tiles_c : ntiles;
-  uint32_t it = 0;
-  for (int tile = blockIdx.x; tile < ntiles_all; tile += gridDim.x, ++it) {
+  const int ntiles = split ? 4 * tiles_c : tiles_c;
+  struct Tile {
+    int t;             // tile within its class
+    int py, px;        // class parities
+    int ty0, ndy;      // class taps dy in {ty0, ty0 + 2}, ndy of them: {1} for even y, {0, 2} for odd
+    int tx0, ndx;      // likewise for dx
+  };
+  auto tile_info = [&](int tile) {
+    Tile ti;
     const int cls = split ? tile / tiles_c : 0;
-    const int tcls = split ? tile - cls * tiles_c : tile;  // tile within the class
-    const int py = cls >> 1, px = cls & 1;
-    // the class's taps: dy in {ty0, ty0 + 2} (ndy of them: {1} for even y, {0, 2} for odd
-    // y); same for dx
-    const int ty0 = py ? 0 : 1, ndy = py ? 2 : 1;
-    const int tx0 = px ? 0 : 1, ndx = px ? 2 : 1;
-    // grid pixel of class row r, or -1 past the end
-    auto row_pixel = [&](int r) -> int {
-      if (r >= Pc) return -1;
-      if (!split) return r;
-      const int b = r >> (2 * lg_c), yc = (r >> lg_c) & ((1 << lg_c) - 1), xc = r & ((1 << lg_c) - 1);
-      return (((b << lg_g) + 2 * yc + py) << lg_g) + 2 * xc + px;
-    };
-    const int p = row_pixel((tcls << 7) + m);
-    const bool valid = p >= 0;
-    const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), x = p & (G - 1);
-    if (MODE == kFwd1) {  // ---- row m: k = 2 tap + c for k < 18, then zeros
+    ti.t = tile - cls * tiles_c;
+    ti.py = cls >> 1;
+    ti.px = cls & 1;
+    ti.ty0 = ti.py ? 0 : 1;
+    ti.ndy = ti.py ? 2 : 1;
+    ti.tx0 = ti.px ? 0 : 1;
+    ti.ndx = ti.px ? 2 : 1;
+    return ti;
+  };
+  auto row_pixel = [&](const Tile &ti, int r) -> int {  // grid pixel of class row r, -1 past the end
+    r += ti.t << 7;
+    if (r >= Pc) return -1;
+    if (!split) return r;
+    const int b = r >> (2 * lg_c), yc = (r >> lg_c) & ((1 << lg_c) - 1), xc = r & ((1 << lg_c) - 1);
+    return (((b << lg_g) + 2 * yc + ti.py) << lg_g) + 2 * xc + ti.px;
+  };
+
+  // ---- the A operand of a tile, loaded into registers (issued early) and stored later
+  uint4 v[2][kTaps];   // 32-channel modes: [row j][tap slot]
+  float f[2 * kTaps];  // first layer: k = 2 tap + c of row m
+  auto load = [&](const Tile &ti) {
+    if (MODE == kFwd1) {
+      const int p = row_pixel(ti, m);
+      const bool valid = p >= 0;
+      const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), x = p & (G - 1);
       const float *src = static_cast<const float *>(src_v);
-      float v[2 * kTaps];
 #pragma unroll
       for (int t = 0; t < kTaps; ++t) {
         const int yy = stride * y + t / 3 - 1, xx = stride * x + t % 3 - 1;
         const bool ok = valid && yy >= 0 && yy < S && xx >= 0 && xx < S;
 #pragma unroll
         for (int c = 0; c < 2; ++c)
-          v[2 * t + c] = ok ? __ldg(src + (((((size_t)b * 2 + c) << lg_s) + yy) << lg_s) + xx) : 0.0f;
+          f[2 * t + c] = ok ? __ldg(src + (((((size_t)b * 2 + c) << lg_s) + yy) << lg_s) + xx) : 0.0f;
       }
-      uint8_t *row = sA + (uint32_t)m * 16u;
-      *reinterpret_cast<uint4 *>(row) =
-          make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
-      *reinterpret_cast<uint4 *>(row + 2048) =
-          make_uint4(pack2(v[8], v[9]), pack2(v[10], v[11]), pack2(v[12], v[13]), pack2(v[14], v[15]));
-      *reinterpret_cast<uint4 *>(row + 4096) = make_uint4(pack2(v[16], v[17]), 0u, 0u, 0u);
-      *reinterpret_cast<uint4 *>(row + 6144) = make_uint4(0u, 0u, 0u, 0u);
-    } else if (MODE == kDgrad && split) {  // ---- class taps (iy, ix): at most 2 x 2
-      // y = 2 yc + py: tap dy = ty0 + 2 iy reads source row (y + 1 - dy) / 2, which is yc,
-      // or yc + 1 for (odd y, dy = 0); likewise for x.
-      const bf16 *src = static_cast<const bf16 *>(src_v);
-      const int yc = y >> 1, xc = x >> 1;
-      uint4 v[2][2][2];
+      return;
+    }
+    const bf16 *src = static_cast<const bf16 *>(src_v);
 #pragma unroll
-      for (int iy = 0; iy < 2; ++iy)
-#pragma unroll
-        for (int ix = 0; ix < 2; ++ix) {
-          const int yy = yc + (py & (iy == 0)), xx = xc + (px & (ix == 0));
-          const bool ok = valid && iy < ndy && ix < ndx && yy < S && xx < S;
-          const size_t pix = ((((size_t)b << lg_s) + (ok ? yy : 0)) << lg_s) + (ok ? xx : 0);
-          const uint4 *s4 = reinterpret_cast<const uint4 *>(src + pix * kCh) + 2 * half;
-          v[iy][ix][0] = ok ? __ldg(s4) : make_uint4(0, 0, 0, 0);
-          v[iy][ix][1] = ok ? __ldg(s4 + 1) : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-      for (int iy = 0; iy < 2; ++iy)
-#pragma unroll
-        for (int ix = 0; ix < 2; ++ix)
-          if (iy < ndy && ix < ndx) {
-            const uint32_t j0 = (uint32_t)((iy * ndx + ix) * 4 + 2 * half);
-            *reinterpret_cast<uint4 *>(sA + j0 * 2048u + (uint32_t)m * 16u) = v[iy][ix][0];
-            *reinterpret_cast<uint4 *>(sA + (j0 + 1u) * 2048u + (uint32_t)m * 16u) = v[iy][ix][1];
-          }
-    } else {  // ---- row m: chunks (tap t, c8) with c8 in {2 half, 2 half + 1}
-      const bf16 *src = static_cast<const bf16 *>(src_v);
-      uint4 v[kTaps][2];
-#pragma unroll
-      for (int t = 0; t < kTaps; ++t) {
-        const int dy = t / 3, dx = t % 3;
-        // forward: source (s y + dy - 1, s x + dx - 1); data grad with s = 1: (y + 1 - dy, x + 1 - dx)
-        const int yy = MODE == kFwd ? stride * y + dy - 1 : y + 1 - dy;
-        const int xx = MODE == kFwd ? stride * x + dx - 1 : x + 1 - dx;
-        const bool ok = valid && yy >= 0 && yy < S && xx >= 0 && xx < S;
+    for (int j = 0; j < 2; ++j) {
+      const int p = row_pixel(ti, rr + 64 * j);
+      const bool valid = p >= 0;
+      const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), x = p & (G - 1);
+      auto chunk = [&](int yy, int xx, bool ok) -> uint4 {  // 16 bytes c8 of a source pixel
         const size_t pix = ((((size_t)b << lg_s) + (ok ? yy : 0)) << lg_s) + (ok ? xx : 0);
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + pix * kCh) + 2 * half;
-        v[t][0] = ok ? __ldg(s4) : make_uint4(0, 0, 0, 0);
-        v[t][1] = ok ? __ldg(s4 + 1) : make_uint4(0, 0, 0, 0);
-      }
+        return ok ? __ldg(reinterpret_cast<const uint4 *>(src + pix * kCh) + c8) : make_uint4(0, 0, 0, 0);
+      };
+      if (MODE == kDgrad && split) {
+        // y = 2 yc + py: tap dy = ty0 + 2 iy reads source row (y + 1 - dy) / 2, which is
+        // yc, or yc + 1 for (odd y, dy = 0); likewise for x.  Slot 2 iy + ix.
 #pragma unroll
-      for (int t = 0; t < kTaps; ++t) {
-        const int j0 = t * 4 + 2 * half;
-        *reinterpret_cast<uint4 *>(sA + (uint32_t)j0 * 2048u + (uint32_t)m * 16u) = v[t][0];
-        *reinterpret_cast<uint4 *>(sA + (uint32_t)(j0 + 1) * 2048u + (uint32_t)m * 16u) = v[t][1];
+        for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+          for (int ix = 0; ix < 2; ++ix) {
+            const int yy = (y >> 1) + (ti.py & (iy == 0)), xx = (x >> 1) + (ti.px & (ix == 0));
+            v[j][2 * iy + ix] = chunk(yy, xx, valid && iy < ti.ndy && ix < ti.ndx && yy < S && xx < S);
+          }
+      } else {
+#pragma unroll
+        for (int t = 0; t < kTaps; ++t) {
+          const int dy = t / 3, dx = t % 3;
+          // forward: source (s y + dy - 1, s x + dx - 1); data grad with s = 1: (y + 1 - dy, x + 1 - dx)
+          const int yy = MODE == kFwd ? stride * y + dy - 1 : y + 1 - dy;
+          const int xx = MODE == kFwd ? stride * x + dx - 1 : x + 1 - dx;
+          v[j][t] = chunk(yy, xx, valid && yy >= 0 && yy < S && xx >= 0 && xx < S);
+        }
       }
     }
+  };
+  auto store = [&](const Tile &ti) {
+    if (MODE == kFwd1) {  // row m: k = 2 tap + c for k < 18, then zeros
+      uint8_t *row = sA + (uint32_t)m * 16u;
+      *reinterpret_cast<uint4 *>(row) =
+          make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+      *reinterpret_cast<uint4 *>(row + 2048) =
+          make_uint4(pack2(f[8], f[9]), pack2(f[10], f[11]), pack2(f[12], f[13]), pack2(f[14], f[15]));
+      *reinterpret_cast<uint4 *>(row + 4096) = make_uint4(pack2(f[16], f[17]), 0u, 0u, 0u);
+      *reinterpret_cast<uint4 *>(row + 6144) = make_uint4(0u, 0u, 0u, 0u);
+      return;
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      uint8_t *row = sA + (uint32_t)(rr + 64 * j) * 16u + (uint32_t)c8 * 2048u;
+      if (MODE == kDgrad && split) {  // K chunk (class tap i = iy ndx + ix, c8)
+#pragma unroll
+        for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+          for (int ix = 0; ix < 2; ++ix)
+            if (iy < ti.ndy && ix < ti.ndx)
+              *reinterpret_cast<uint4 *>(row + (uint32_t)(4 * (iy * ti.ndx + ix)) * 2048u) = v[j][2 * iy + ix];
+      } else {
+#pragma unroll
+        for (int t = 0; t < kTaps; ++t) *reinterpret_cast<uint4 *>(row + (uint32_t)(4 * t) * 2048u) = v[j][t];
+      }
+    }
+  };
+
+  uint32_t it = 0;
+  if (blockIdx.x < ntiles) load(tile_info(blockIdx.x));
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const Tile ti = tile_info(tile);
+    store(ti);  // the MMAs of the previous tile have completed: A is free
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
       if (MODE == kDgrad && split) {  // the class's taps: A chunks 4 i + c8, B chunks 4 tap + c8
-        for (int i = 0; i < ndy * ndx; ++i) {
-          const int iy = ndx == 2 ? i >> 1 : i, ix = ndx == 2 ? i & 1 : 0;
-          const int tap = (ty0 + 2 * iy) * 3 + tx0 + 2 * ix;
+        for (int i = 0; i < ti.ndy * ti.ndx; ++i) {
+          const int iy = ti.ndx == 2 ? i >> 1 : i, ix = ti.ndx == 2 ? i & 1 : 0;
+          const int tap = (ti.ty0 + 2 * iy) * 3 + ti.tx0 + 2 * ix;
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
             const uint64_t a = sdesc(aBase + (uint32_t)(4 * i + 2 * k) * 2048u, 2048u, 128u);
@@ -345,10 +373,12 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
       }
       umma_commit(bar);
     }
+    // the next tile's loads are in flight while the MMAs and this tile's epilogue run
+    if (tile + (int)gridDim.x < ntiles) load(tile_info(tile + gridDim.x));
     // ---- epilogue: row 32 q + lane of the tile, output columns 16 h .. 16 h + 15
-    const int pr = row_pixel((tcls << 7) + 32 * q + lane);
+    const int pr = row_pixel(ti, 32 * q + lane);
     uint4 m0 = make_uint4(0, 0, 0, 0), m1 = m0;
-    if (MODE == kDgrad && pr >= 0) {  // the ReLU mask, fetched while the MMAs run
+    if (MODE == kDgrad && pr >= 0) {  // the ReLU mask
       const uint4 *mk = reinterpret_cast<const uint4 *>(mask + (size_t)pr * kCh + 16 * h0);
       m0 = __ldg(mk);
       m1 = __ldg(mk + 1);

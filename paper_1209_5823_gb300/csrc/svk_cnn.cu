@@ -33,7 +33,7 @@
 namespace svk {
 namespace {
 
-constexpr int kIn = 64, kCh = 32, kLayers = 4, kTaps = 9;
+constexpr int kCh = 32, kLayers = 4, kTaps = 9;
 constexpr int kCin[kLayers] = {2, kCh, kCh, kCh};
 constexpr int kStride[kLayers] = {2, 2, 2, 1};
 constexpr int kHout[kLayers] = {32, 16, 8, 8};
@@ -90,7 +90,7 @@ struct Work {  // byte offsets into the workspace
   size_t wq;                     // float[param total]: parameters rounded to BF16
   size_t wf[kLayers], wd[kLayers];  // packed BF16 operands (forward, data grad), layers 1..3
   size_t act[kLayers], dz[kLayers];  // BF16 NHWC [B][H][H][32]: post-ReLU, pre-activation grad
-  size_t pooled, out, dout, part, total;
+  size_t pooled, out, dout, part[kLayers], total;
 };
 
 Work work_layout(int B, int n_out) {
@@ -107,19 +107,16 @@ Work work_layout(int B, int n_out) {
     w.wf[i] = take(kPackBytes);
     w.wd[i] = take(kPackBytes);
   }
-  size_t part = 0;
   for (int i = 0; i < kLayers; ++i) {
     const size_t n = (size_t)B * kCh * kHout[i] * kHout[i];
     w.act[i] = take(n * sizeof(bf16));
     w.dz[i] = take(n * sizeof(bf16));
     const int P = B * kHout[i] * kHout[i];
-    const size_t pb = (size_t)wg_nchunks(P, kCin[i]) * wg_rows(kCin[i]) * kCh * sizeof(float);
-    part = pb > part ? pb : part;
+    w.part[i] = take((size_t)wg_nchunks(P, kCin[i]) * wg_rows(kCin[i]) * kCh * sizeof(float));
   }
   w.pooled = take((size_t)B * kCh * sizeof(float));
   w.out = take((size_t)B * n_out * sizeof(float));
   w.dout = take((size_t)B * n_out * sizeof(float));
-  w.part = take(part);
   w.total = o;
   return w;
 }
@@ -268,7 +265,7 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
   uint4 v[2][kTaps];   // 32-channel modes: [row j][tap slot]
   float f[2 * kTaps];  // first layer: k = 2 tap + c of row m
   auto load = [&](const Tile &ti) {
-    if (MODE == kFwd1) {
+    if constexpr (MODE == kFwd1) {
       const int p = row_pixel(ti, m);
       const bool valid = p >= 0;
       const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), x = p & (G - 1);
@@ -281,42 +278,42 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
         for (int c = 0; c < 2; ++c)
           f[2 * t + c] = ok ? __ldg(src + (((((size_t)b * 2 + c) << lg_s) + yy) << lg_s) + xx) : 0.0f;
       }
-      return;
-    }
-    const bf16 *src = static_cast<const bf16 *>(src_v);
+    } else {
+      const bf16 *src = static_cast<const bf16 *>(src_v);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int p = row_pixel(ti, rr + 64 * j);
-      const bool valid = p >= 0;
-      const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), x = p & (G - 1);
-      auto chunk = [&](int yy, int xx, bool ok) -> uint4 {  // 16 bytes c8 of a source pixel
-        const size_t pix = ((((size_t)b << lg_s) + (ok ? yy : 0)) << lg_s) + (ok ? xx : 0);
-        return ok ? __ldg(reinterpret_cast<const uint4 *>(src + pix * kCh) + c8) : make_uint4(0, 0, 0, 0);
-      };
-      if (MODE == kDgrad && split) {
-        // y = 2 yc + py: tap dy = ty0 + 2 iy reads source row (y + 1 - dy) / 2, which is
-        // yc, or yc + 1 for (odd y, dy = 0); likewise for x.  Slot 2 iy + ix.
+      for (int j = 0; j < 2; ++j) {
+        const int p = row_pixel(ti, rr + 64 * j);
+        const bool valid = p >= 0;
+        const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), x = p & (G - 1);
+        auto chunk = [&](int yy, int xx, bool ok) -> uint4 {  // 16 bytes c8 of a source pixel
+          const size_t pix = ((((size_t)b << lg_s) + (ok ? yy : 0)) << lg_s) + (ok ? xx : 0);
+          return ok ? __ldg(reinterpret_cast<const uint4 *>(src + pix * kCh) + c8) : make_uint4(0, 0, 0, 0);
+        };
+        if (MODE == kDgrad && split) {
+          // y = 2 yc + py: tap dy = ty0 + 2 iy reads source row (y + 1 - dy) / 2, which is
+          // yc, or yc + 1 for (odd y, dy = 0); likewise for x.  Slot 2 iy + ix.
 #pragma unroll
-        for (int iy = 0; iy < 2; ++iy)
+          for (int iy = 0; iy < 2; ++iy)
 #pragma unroll
-          for (int ix = 0; ix < 2; ++ix) {
-            const int yy = (y >> 1) + (ti.py & (iy == 0)), xx = (x >> 1) + (ti.px & (ix == 0));
-            v[j][2 * iy + ix] = chunk(yy, xx, valid && iy < ti.ndy && ix < ti.ndx && yy < S && xx < S);
+            for (int ix = 0; ix < 2; ++ix) {
+              const int yy = (y >> 1) + (ti.py & (iy == 0)), xx = (x >> 1) + (ti.px & (ix == 0));
+              v[j][2 * iy + ix] = chunk(yy, xx, valid && iy < ti.ndy && ix < ti.ndx && yy < S && xx < S);
+            }
+        } else {
+#pragma unroll
+          for (int t = 0; t < kTaps; ++t) {
+            const int dy = t / 3, dx = t % 3;
+            // forward: source (s y + dy - 1, s x + dx - 1); data grad with s = 1: (y + 1 - dy, x + 1 - dx)
+            const int yy = MODE == kFwd ? stride * y + dy - 1 : y + 1 - dy;
+            const int xx = MODE == kFwd ? stride * x + dx - 1 : x + 1 - dx;
+            v[j][t] = chunk(yy, xx, valid && yy >= 0 && yy < S && xx >= 0 && xx < S);
           }
-      } else {
-#pragma unroll
-        for (int t = 0; t < kTaps; ++t) {
-          const int dy = t / 3, dx = t % 3;
-          // forward: source (s y + dy - 1, s x + dx - 1); data grad with s = 1: (y + 1 - dy, x + 1 - dx)
-          const int yy = MODE == kFwd ? stride * y + dy - 1 : y + 1 - dy;
-          const int xx = MODE == kFwd ? stride * x + dx - 1 : x + 1 - dx;
-          v[j][t] = chunk(yy, xx, valid && yy >= 0 && yy < S && xx >= 0 && xx < S);
         }
       }
     }
   };
   auto store = [&](const Tile &ti) {
-    if (MODE == kFwd1) {  // row m: k = 2 tap + c for k < 18, then zeros
+    if constexpr (MODE == kFwd1) {  // row m: k = 2 tap + c for k < 18, then zeros
       uint8_t *row = sA + (uint32_t)m * 16u;
       *reinterpret_cast<uint4 *>(row) =
           make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
@@ -324,21 +321,21 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
           make_uint4(pack2(f[8], f[9]), pack2(f[10], f[11]), pack2(f[12], f[13]), pack2(f[14], f[15]));
       *reinterpret_cast<uint4 *>(row + 4096) = make_uint4(pack2(f[16], f[17]), 0u, 0u, 0u);
       *reinterpret_cast<uint4 *>(row + 6144) = make_uint4(0u, 0u, 0u, 0u);
-      return;
-    }
+    } else {
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      uint8_t *row = sA + (uint32_t)(rr + 64 * j) * 16u + (uint32_t)c8 * 2048u;
-      if (MODE == kDgrad && split) {  // K chunk (class tap i = iy ndx + ix, c8)
+      for (int j = 0; j < 2; ++j) {
+        uint8_t *row = sA + (uint32_t)(rr + 64 * j) * 16u + (uint32_t)c8 * 2048u;
+        if (MODE == kDgrad && split) {  // K chunk (class tap i = iy ndx + ix, c8)
 #pragma unroll
-        for (int iy = 0; iy < 2; ++iy)
+          for (int iy = 0; iy < 2; ++iy)
 #pragma unroll
-          for (int ix = 0; ix < 2; ++ix)
-            if (iy < ti.ndy && ix < ti.ndx)
-              *reinterpret_cast<uint4 *>(row + (uint32_t)(4 * (iy * ti.ndx + ix)) * 2048u) = v[j][2 * iy + ix];
-      } else {
+            for (int ix = 0; ix < 2; ++ix)
+              if (iy < ti.ndy && ix < ti.ndx)
+                *reinterpret_cast<uint4 *>(row + (uint32_t)(4 * (iy * ti.ndx + ix)) * 2048u) = v[j][2 * iy + ix];
+        } else {
 #pragma unroll
-        for (int t = 0; t < kTaps; ++t) *reinterpret_cast<uint4 *>(row + (uint32_t)(4 * t) * 2048u) = v[j][t];
+          for (int t = 0; t < kTaps; ++t) *reinterpret_cast<uint4 *>(row + (uint32_t)(4 * t) * 2048u) = v[j][t];
+        }
       }
     }
   };
@@ -423,7 +420,6 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
 // one chunk, N = 32 output channels.  Both operands are stored p-major in memory, so each
 // 8 x 8 block is transposed in registers on its way to shared memory (K-major UMMA
 // layout).  Two pipeline stages of 64 pixels; each CTA writes its chunk's partial sums.
-constexpr int kWgThreads = 256;
 
 template <int CIN>
 struct WgShape {
@@ -436,6 +432,9 @@ struct WgShape {
   static constexpr uint32_t B_STAGE = 8 * LBO_B;
   static constexpr uint32_t SMEM = 2 * (A_STAGE + B_STAGE) + 64;
   static constexpr uint32_t TMEM_COLS = MT == 3 ? 128 : 32;
+  // one build unit per thread per stage: (36 + 4) x 8 = 320 for 32 channels, (18 + 4) x 8
+  // = 176 for the first layer
+  static constexpr int THREADS = CIN == kCh ? 320 : 256;
 };
 
 // r[i] = row i (8 BF16); t[j] = column j (element i = r[i][j]).
@@ -465,7 +464,7 @@ __device__ __forceinline__ void transpose8(const uint4 (&r)[8], uint4 (&t)[8]) {
 // A unit is 8 consecutive pixels of one K chunk: since the grid side is a multiple of 8
 // and chunks start at multiples of 64, they lie in one image row.
 template <int CIN>
-__global__ void __launch_bounds__(kWgThreads, CIN == kCh ? 2 : 3)
+__global__ void __launch_bounds__(WgShape<CIN>::THREADS, CIN == kCh ? 2 : 3)
     wgrad_kernel(const void *__restrict__ src_v, const bf16 *__restrict__ dz, float *__restrict__ part, int B,
                  int lg_s, int lg_g, int stride, int per_chunk, uint32_t *status) {
   using Sh = WgShape<CIN>;
@@ -480,7 +479,7 @@ __global__ void __launch_bounds__(kWgThreads, CIN == kCh ? 2 : 3)
   const int nst = (p_end - p_begin + kWgStage - 1) / kWgStage;
   constexpr int NC = Sh::ROWS - Sh::NDATA;  // constant rows per K chunk
 
-  for (int i = tid; i < 2 * 8 * NC; i += kWgThreads) {  // the ones row and the zero rows
+  for (int i = tid; i < 2 * 8 * NC; i += Sh::THREADS) {  // the ones row and the zero rows
     const int st = i / (8 * NC), kc = (i / NC) % 8, row = Sh::NDATA + i % NC;
     const uint32_t v = row == Sh::NDATA ? 0x3F803F80u : 0u;  // BF16 1.0 pairs
     *reinterpret_cast<uint4 *>(smem + st * Sh::A_STAGE + kc * Sh::LBO_A + row * 16) = make_uint4(v, v, v, v);
@@ -511,7 +510,7 @@ __global__ void __launch_bounds__(kWgThreads, CIN == kCh ? 2 : 3)
     uint8_t *sB = smem + 2 * Sh::A_STAGE + buf * Sh::B_STAGE;
     const int p0 = p_begin + s * kWgStage;
     constexpr int NG = CIN == kCh ? kTaps * 4 : Sh::NDATA;  // A units per K chunk
-    for (int u = tid; u < (NG + 4) * 8; u += kWgThreads) {
+    for (int u = tid; u < (NG + 4) * 8; u += Sh::THREADS) {
       const int kc = u & 7, g = u >> 3;
       const int pq = p0 + kc * 8;  // pixels pq .. pq + 7: image b, row y, columns x0 ..
       const bool in = pq < p_end;
@@ -578,7 +577,7 @@ __global__ void __launch_bounds__(kWgThreads, CIN == kCh ? 2 : 3)
     const bool ok = mbar_wait_bounded(&bar[sl & 1], (uint32_t)((sl >> 1) & 1), status);
     failed = __syncthreads_or(!ok);
   }
-  if (!failed && nst > 0) {
+  if (!failed && nst > 0 && warp < 8) {  // warps 0-7: TMEM lane quadrant warp & 3, column half warp / 4
     tc_fence_after();
     const int q = warp & 3, h = warp >> 2;
 #pragma unroll
@@ -601,26 +600,34 @@ __global__ void __launch_bounds__(kWgThreads, CIN == kCh ? 2 : 3)
   if (warp == 0) tmem_dealloc(tmem, Sh::TMEM_COLS);
 }
 
-// Partial sums of the chunks: dw[o][c][tap], db[o].  One block of 1024 threads per row
-// (tap, c) or the bias row: 32 chunk slices, each summed in chunk order, then added in
-// slice order.
+// Partial sums of the chunks: dw[o][c][tap], db[o], every layer in one launch.  One
+// block of 1024 threads per row (tap, c) or bias row of a layer: 32 chunk slices, each
+// summed in chunk order, then added in slice order.
 constexpr int kRedSlices = 32;
 
-__global__ void __launch_bounds__(kRedSlices * kCh) wgrad_reduce_kernel(const float *__restrict__ part, int nchunks,
-                                                                        int cin, float *__restrict__ gw,
-                                                                        float *__restrict__ gb) {
+struct WgradSet {
+  const float *part[kLayers];
+  float *gw[kLayers], *gb[kLayers];
+  int cin[kLayers], nchunks[kLayers], row0[kLayers + 1];  // row0: first block of each layer
+};
+
+__global__ void __launch_bounds__(kRedSlices * kCh) wgrad_reduce_kernel(const __grid_constant__ WgradSet ws) {
   __shared__ float red[kRedSlices][kCh];
-  const int rows = cin * kTaps + 1, row = blockIdx.x, o = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  int l = 0;
+  while (l + 1 < kLayers && (int)blockIdx.x >= ws.row0[l + 1]) ++l;
+  const int cin = ws.cin[l], rows = cin * kTaps + 1, row = blockIdx.x - ws.row0[l];
+  const int o = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const float *part = ws.part[l];
   float s = 0.0f;
 #pragma unroll 4
-  for (int c = sl; c < nchunks; c += kRedSlices) s += part[((size_t)c * rows + row) * kCh + o];
+  for (int c = sl; c < ws.nchunks[l]; c += kRedSlices) s += part[((size_t)c * rows + row) * kCh + o];
   red[sl][o] = s;
   __syncthreads();
   if (threadIdx.x < kCh) {
     float t = 0.0f;
     for (int i = 0; i < kRedSlices; ++i) t += red[i][o];
-    if (row < cin * kTaps) gw[((size_t)o * cin + row % cin) * 9 + row / cin] = t;
-    else gb[o] = t;
+    if (row < cin * kTaps) ws.gw[l][((size_t)o * cin + row % cin) * 9 + row / cin] = t;
+    else ws.gb[l][o] = t;
   }
 }
 
@@ -661,36 +668,37 @@ __global__ void pool_fc_kernel(const bf16 *__restrict__ act, const float *__rest
   if (threadIdx.x == 0) atomicAdd(loss, (red[0] + red[1]) * inv_n);
 }
 
-// Linear layer weight gradients: dfcw[j][c] = sum_b dout[b][j] pooled[b][c] and
-// dfcb[j] = sum_b dout[b][j]; one block per output j, 8 batch slices added in order.
-__global__ void fc_wgrad_kernel(const float *__restrict__ dout, const float *__restrict__ pooled,
-                                float *__restrict__ dfcw, float *__restrict__ dfcb, int B, int n_out) {
-  __shared__ float red[8][kCh + 1];
-  const int j = blockIdx.x, c = threadIdx.x & 31, part = threadIdx.x >> 5;
-  float s = 0.0f, sb = 0.0f;
+// Output-layer gradients in one launch.  Blocks 0 .. n_out - 1: the linear layer's
+// weight gradients dfcw[j][c] = sum_b dout[b][j] pooled[b][c] and dfcb[j] = sum_b dout[b][j]
+// (8 batch slices added in order).  The other blocks, one thread per (b, c):
+// dpooled[b][c] = sum_j dout[b][j] fcw[j][c], spread as dpooled / 64 over the 8x8
+// positions, masked by the ReLU (act > 0), stored BF16 NHWC as the last layer's dz.
+__global__ void __launch_bounds__(256) fc_grad_kernel(const float *__restrict__ dout, const float *__restrict__ pooled,
+                                                      const float *__restrict__ fcw, const bf16 *__restrict__ act,
+                                                      float *__restrict__ dfcw, float *__restrict__ dfcb,
+                                                      bf16 *__restrict__ dz, int B, int n_out) {
+  if ((int)blockIdx.x < n_out) {
+    __shared__ float red[8][kCh + 1];
+    const int j = blockIdx.x, c = threadIdx.x & 31, part = threadIdx.x >> 5;
+    float s = 0.0f, sb = 0.0f;
 #pragma unroll 8
-  for (int b = part; b < B; b += 8) {
-    const float d = dout[(size_t)b * n_out + j];
-    s = fmaf(d, pooled[b * kCh + c], s);
-    sb += d;
+    for (int b = part; b < B; b += 8) {
+      const float d = dout[(size_t)b * n_out + j];
+      s = fmaf(d, pooled[b * kCh + c], s);
+      sb += d;
+    }
+    red[part][c] = s;
+    if (c == 0) red[part][kCh] = sb;
+    __syncthreads();
+    if (threadIdx.x <= kCh) {
+      float t = 0.0f;
+      for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
+      if (threadIdx.x < kCh) dfcw[j * kCh + threadIdx.x] = t;
+      else dfcb[j] = t;
+    }
+    return;
   }
-  red[part][c] = s;
-  if (c == 0) red[part][kCh] = sb;
-  __syncthreads();
-  if (threadIdx.x <= kCh) {
-    float t = 0.0f;
-    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
-    if (threadIdx.x < kCh) dfcw[j * kCh + threadIdx.x] = t;
-    else dfcb[j] = t;
-  }
-}
-
-// Gradient at the last layer's pre-activation: dpooled[b][c] = sum_j dout[b][j] fcw[j][c],
-// spread as dpooled / 64 over the 8x8 positions, masked by the ReLU (act > 0), stored
-// BF16 NHWC.  One thread per (b, c).
-__global__ void fc_dgrad_unpool_kernel(const float *__restrict__ dout, const float *__restrict__ fcw,
-                                       const bf16 *__restrict__ act, bf16 *__restrict__ dz, int B, int n_out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (blockIdx.x - n_out) * blockDim.x + threadIdx.x;
   if (t >= B * kCh) return;
   const int b = t / kCh, c = t % kCh;
   float s = 0.0f;
@@ -743,24 +751,23 @@ int conv_mma(const void *src, const bf16 *wpack, const float *bias, const bf16 *
   return cuda_status(cudaGetLastError(), "network convolution");
 }
 
+// A layer's partial weight-gradient sums (reduced for all layers by wgrad_reduce_kernel).
 template <int CIN>
-int wgrad(const void *src, const bf16 *dz, float *part, float *gw, float *gb, int B, int lg_s, int lg_g, int stride,
-          cudaStream_t s) {
+int wgrad(const void *src, const bf16 *dz, float *part, int B, int lg_s, int lg_g, int stride, cudaStream_t s) {
   using Sh = WgShape<CIN>;
   cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
   if (e != cudaSuccess) return cuda_status(e, "network weight-gradient attributes");
   const int P = B << (2 * lg_g);
   const int per = wg_per_chunk(P, CIN), nch = wg_nchunks(P, CIN);
-  wgrad_kernel<CIN><<<nch, kWgThreads, Sh::SMEM, s>>>(src, dz, part, B, lg_s, lg_g, stride, per, device_status_word());
-  const int rows = wg_rows(CIN);
-  wgrad_reduce_kernel<<<rows, kRedSlices * kCh, 0, s>>>(part, nch, CIN, gw, gb);
+  wgrad_kernel<CIN><<<nch, Sh::THREADS, Sh::SMEM, s>>>(src, dz, part, B, lg_s, lg_g, stride, per,
+                                                         device_status_word());
   return cuda_status(cudaGetLastError(), "network weight gradient");
 }
 
 struct Bufs {
   float *wq;
   bf16 *wf[kLayers], *wd[kLayers], *act[kLayers], *dz[kLayers];
-  float *pooled, *out, *dout, *part;
+  float *pooled, *out, *dout, *part[kLayers];
 };
 
 Bufs bufs(void *ws_v, const Work &Wk) {
@@ -772,11 +779,11 @@ Bufs bufs(void *ws_v, const Work &Wk) {
     b.wd[i] = i > 0 ? reinterpret_cast<bf16 *>(ws + Wk.wd[i]) : nullptr;
     b.act[i] = reinterpret_cast<bf16 *>(ws + Wk.act[i]);
     b.dz[i] = reinterpret_cast<bf16 *>(ws + Wk.dz[i]);
+    b.part[i] = reinterpret_cast<float *>(ws + Wk.part[i]);
   }
   b.pooled = reinterpret_cast<float *>(ws + Wk.pooled);
   b.out = reinterpret_cast<float *>(ws + Wk.out);
   b.dout = reinterpret_cast<float *>(ws + Wk.dout);
-  b.part = reinterpret_cast<float *>(ws + Wk.part);
   return b;
 }
 
@@ -918,19 +925,30 @@ int cnn_gradient(const float *params, const float *x, const float *target, int B
   cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), s);
   if (e != cudaSuccess) return cuda_status(e, "loss reset");
   if ((st = forward(x, L, b, B, n_out, b.out, nsm, s, target, loss)) != SVK_OK) return st;
-  fc_wgrad_kernel<<<n_out, 256, 0, s>>>(b.dout, b.pooled, grad + L.fcw, grad + L.fcb, B, n_out);
-  fc_dgrad_unpool_kernel<<<(B * kCh + 255) / 256, 256, 0, s>>>(b.dout, b.wq + L.fcw, b.act[kLayers - 1],
-                                                               b.dz[kLayers - 1], B, n_out);
+  fc_grad_kernel<<<n_out + (B * kCh + 255) / 256, 256, 0, s>>>(b.dout, b.pooled, b.wq + L.fcw, b.act[kLayers - 1],
+                                                                grad + L.fcw, grad + L.fcb, b.dz[kLayers - 1], B,
+                                                                n_out);
   if ((st = cuda_status(cudaGetLastError(), "network output gradient")) != SVK_OK) return st;
   for (int li = kLayers - 1; li >= 1; --li) {
-    st = wgrad<kCh>(b.act[li - 1], b.dz[li], b.part, grad + L.w[li], grad + L.b[li], B, kLgIn[li], kLgOut[li],
-                    kStride[li], s);
+    st = wgrad<kCh>(b.act[li - 1], b.dz[li], b.part[li], B, kLgIn[li], kLgOut[li], kStride[li], s);
     if (st == SVK_OK)
       st = conv_mma<kDgrad>(b.dz[li], b.wd[li], nullptr, b.act[li - 1], b.dz[li - 1], B, kLgOut[li], kLgIn[li],
                             kStride[li], nsm, s);
     if (st != SVK_OK) return st;
   }
-  return wgrad<2>(x, b.dz[0], b.part, grad + L.w[0], grad + L.b[0], B, kLgIn[0], kLgOut[0], kStride[0], s);
+  if ((st = wgrad<2>(x, b.dz[0], b.part[0], B, kLgIn[0], kLgOut[0], kStride[0], s)) != SVK_OK) return st;
+  WgradSet set{};
+  set.row0[0] = 0;
+  for (int li = 0; li < kLayers; ++li) {
+    set.part[li] = b.part[li];
+    set.cin[li] = kCin[li];
+    set.gw[li] = grad + L.w[li];
+    set.gb[li] = grad + L.b[li];
+    set.nchunks[li] = wg_nchunks(B * kHout[li] * kHout[li], kCin[li]);
+    set.row0[li + 1] = set.row0[li] + wg_rows(kCin[li]);
+  }
+  wgrad_reduce_kernel<<<set.row0[kLayers], kRedSlices * kCh, 0, s>>>(set);
+  return cuda_status(cudaGetLastError(), "network weight-gradient reduction");
 }
 
 int cnn_adam(float *params, float *m, float *v, const float *grad, int n, int step, float lr, float b1, float b2,

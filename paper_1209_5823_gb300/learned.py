@@ -93,18 +93,46 @@ class CoefficientNetwork:
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.step = 0
+        self._bufs = None   # fixed batch, gradient and loss buffers of the training step
+        self._graph = None  # the gradient call over those buffers, captured as a CUDA graph
+        self._graph_key = None
+
+    def _gradient(self, xb, zb, grad, loss):
+        """svk_cnn_gradient over the fixed training buffers, replayed as a CUDA graph
+        (captured on first use: the same kernels with the same arguments, minus the launch
+        gaps between them)."""
+        key = (xb.data_ptr(), zb.data_ptr(), grad.data_ptr(), loss.data_ptr(), self.params.data_ptr(),
+               self.ws.data_ptr())
+        if self._graph_key != key:
+            side = torch.cuda.Stream(device=xb.device)
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):  # first call outside the capture (lazy library setup)
+                svk_cnn_gradient(self.params, xb, zb, grad=grad, loss=loss, workspace=self.ws)
+            torch.cuda.current_stream().wait_stream(side)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                svk_cnn_gradient(self.params, xb, zb, grad=grad, loss=loss, workspace=self.ws)
+            self._graph, self._graph_key = graph, key
+        self._graph.replay()
 
     def train(self, x, a, steps: int, lr: float = 1e-3, gen=None):
         """Adam on standardised targets; returns the per-step losses (device tensor)."""
         dev = x.device
         z = ((a - self.prior.mean(dev)) / self.prior.std(dev)).contiguous()
         losses = torch.empty(steps, device=dev)
-        grad = torch.empty_like(self.params)
+        shape = (self.batch,) + tuple(x.shape[1:])
+        if self._bufs is None or self._bufs[0].shape != shape or self._bufs[0].device != dev:
+            self._bufs = (torch.empty(shape, dtype=torch.float32, device=dev),
+                          torch.empty((self.batch, self.n_out), dtype=torch.float32, device=dev),
+                          torch.empty_like(self.params), torch.empty(1, dtype=torch.float32, device=dev))
+        xb, zb, grad, loss = self._bufs
         n = x.shape[0]
         for s in range(steps):
             idx = torch.randint(0, n, (self.batch,), device=dev, generator=gen)
-            xb, zb = x[idx].contiguous(), z[idx].contiguous()
-            svk_cnn_gradient(self.params, xb, zb, grad=grad, loss=losses[s:s + 1], workspace=self.ws)
+            torch.index_select(x, 0, idx, out=xb)
+            torch.index_select(z, 0, idx, out=zb)
+            self._gradient(xb, zb, grad, loss)
+            losses[s:s + 1].copy_(loss)
             self.step += 1
             svk_cnn_adam(self.params, self.m, self.v, grad, self.step, lr=lr)
         return losses

@@ -73,15 +73,15 @@ Layout param_layout(int n_out) {
 }
 
 // Weight-gradient split: K (the output pixels of a layer, a multiple of 64) in chunks of
-// a multiple of 64 pixels, about 304 chunks for a 32-channel layer (two CTAs on each of
-// 152 SMs) and 912 for the first layer (three per SM; its partial sums are small).
-// Depends on the batch only, so the gradient is deterministic.
-constexpr int kWgStage = 64;  // pixels per pipeline stage (4 MMAs of K = 16)
-
-int wg_target(int cin) { return cin == kCh ? 304 : 912; }
+// whole pipeline stages (64 pixels for a 32-channel layer, 128 for the first layer),
+// about 304 chunks (two CTAs on each of 152 SMs), at least two stages each for a
+// 32-channel layer.  Depends on the batch only, so the gradient is deterministic.
+int wg_stage_px(int cin) { return cin == kCh ? 64 : 128; }
+int wg_target(int) { return 304; }
 int wg_per_chunk(int P, int cin) {
-  const int stages = (P + kWgStage - 1) / kWgStage;
-  return kWgStage * ((stages + wg_target(cin) - 1) / wg_target(cin));
+  const int px = wg_stage_px(cin), stages = (P + px - 1) / px;
+  const int per = (stages + wg_target(cin) - 1) / wg_target(cin);
+  return px * (cin == kCh && per < 2 ? 2 : per);
 }
 int wg_nchunks(int P, int cin) { return (P + wg_per_chunk(P, cin) - 1) / wg_per_chunk(P, cin); }
 int wg_rows(int cin) { return cin * kTaps + 1; }  // taps x channels, then the bias row
@@ -126,6 +126,19 @@ __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__floa
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+// 32-byte global accesses (one sector per lane and instruction); addresses 32-byte aligned.
+__device__ __forceinline__ void ld_nc_v8(const void *p, uint32_t (&r)[8]) {
+  asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "l"(p));
+}
+
+__device__ __forceinline__ void st_v8(void *p, const uint32_t (&r)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(r[0]), "r"(r[1]), "r"(r[2]),
+               "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
 }
 
 __device__ __forceinline__ float lo_f(uint32_t w) { return __uint_as_float(w << 16); }
@@ -374,12 +387,8 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
     if (tile + (int)gridDim.x < ntiles) load(tile_info(tile + gridDim.x));
     // ---- epilogue: row 32 q + lane of the tile, output columns 16 h .. 16 h + 15
     const int pr = row_pixel(ti, 32 * q + lane);
-    uint4 m0 = make_uint4(0, 0, 0, 0), m1 = m0;
-    if (MODE == kDgrad && pr >= 0) {  // the ReLU mask
-      const uint4 *mk = reinterpret_cast<const uint4 *>(mask + (size_t)pr * kCh + 16 * h0);
-      m0 = __ldg(mk);
-      m1 = __ldg(mk + 1);
-    }
+    uint32_t mw[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (MODE == kDgrad && pr >= 0) ld_nc_v8(mask + (size_t)pr * kCh + 16 * h0, mw);  // the ReLU mask
     const bool ok = mbar_wait_bounded(bar, it & 1u, status);
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
@@ -397,15 +406,12 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
             o32[i] = pack2(fmaxf(__uint_as_float(r[2 * i]) + bv[16 * hh + 2 * i], 0.0f),
                            fmaxf(__uint_as_float(r[2 * i + 1]) + bv[16 * hh + 2 * i + 1], 0.0f));
         } else {
-          const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
           for (int i = 0; i < 8; ++i)
             o32[i] = pack2(lo_f(mw[i]) > 0.0f ? __uint_as_float(r[2 * i]) : 0.0f,
                            hi_f(mw[i]) > 0.0f ? __uint_as_float(r[2 * i + 1]) : 0.0f);
         }
-        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)pr * kCh + 16 * h);
-        dst[0] = make_uint4(o32[0], o32[1], o32[2], o32[3]);
-        dst[1] = make_uint4(o32[4], o32[5], o32[6], o32[7]);
+        st_v8(out + (size_t)pr * kCh + 16 * h, o32);
       }
     }
     tc_fence_before();
@@ -426,15 +432,17 @@ struct WgShape {
   static constexpr int MT = CIN == kCh ? 3 : 1;  // 128-row M tiles
   static constexpr int ROWS = MT * 128;
   static constexpr int NDATA = CIN * kTaps;       // data rows; row NDATA holds ones
-  static constexpr uint32_t LBO_A = ROWS * 16 + 16;  // +16 B: the 8 K chunks on distinct banks
-  static constexpr uint32_t A_STAGE = 8 * LBO_A;
+  static constexpr int KCS = CIN == kCh ? 8 : 16;   // K chunks (8 pixels each) per stage
+  static constexpr int STAGE_PX = 8 * KCS;
+  static constexpr uint32_t LBO_A = ROWS * 16 + 16;  // +16 B: 8 consecutive K chunks on distinct banks
+  static constexpr uint32_t A_STAGE = KCS * LBO_A;
   static constexpr uint32_t LBO_B = kCh * 16 + 16;
-  static constexpr uint32_t B_STAGE = 8 * LBO_B;
+  static constexpr uint32_t B_STAGE = KCS * LBO_B;
   static constexpr uint32_t SMEM = 2 * (A_STAGE + B_STAGE) + 64;
   static constexpr uint32_t TMEM_COLS = MT == 3 ? 128 : 32;
-  // one build unit per thread per stage: (36 + 4) x 8 = 320 for 32 channels, (18 + 4) x 8
-  // = 176 for the first layer
-  static constexpr int THREADS = CIN == kCh ? 320 : 256;
+  // one build unit per thread per stage: (36 + 4) x 8 = 320 for 32 channels, (18 + 4) x 16
+  // = 352 for the first layer
+  static constexpr int THREADS = (CIN == kCh ? kTaps * 4 + 4 : CIN * kTaps + 4) * KCS;
 };
 
 // r[i] = row i (8 BF16); t[j] = column j (element i = r[i][j]).
@@ -464,7 +472,7 @@ __device__ __forceinline__ void transpose8(const uint4 (&r)[8], uint4 (&t)[8]) {
 // A unit is 8 consecutive pixels of one K chunk: since the grid side is a multiple of 8
 // and chunks start at multiples of 64, they lie in one image row.
 template <int CIN>
-__global__ void __launch_bounds__(WgShape<CIN>::THREADS, CIN == kCh ? 2 : 3)
+__global__ void __launch_bounds__(WgShape<CIN>::THREADS, 2)
     wgrad_kernel(const void *__restrict__ src_v, const bf16 *__restrict__ dz, float *__restrict__ part, int B,
                  int lg_s, int lg_g, int stride, int per_chunk, uint32_t *status) {
   using Sh = WgShape<CIN>;
@@ -476,11 +484,11 @@ __global__ void __launch_bounds__(WgShape<CIN>::THREADS, CIN == kCh ? 2 : 3)
   const int P = B << (2 * lg_g);
   const int p_begin = blockIdx.x * per_chunk;
   const int p_end = min(P, p_begin + per_chunk);
-  const int nst = (p_end - p_begin + kWgStage - 1) / kWgStage;
+  const int nst = (p_end - p_begin + Sh::STAGE_PX - 1) / Sh::STAGE_PX;
   constexpr int NC = Sh::ROWS - Sh::NDATA;  // constant rows per K chunk
 
-  for (int i = tid; i < 2 * 8 * NC; i += Sh::THREADS) {  // the ones row and the zero rows
-    const int st = i / (8 * NC), kc = (i / NC) % 8, row = Sh::NDATA + i % NC;
+  for (int i = tid; i < 2 * Sh::KCS * NC; i += Sh::THREADS) {  // the ones row and the zero rows
+    const int st = i / (Sh::KCS * NC), kc = (i / NC) % Sh::KCS, row = Sh::NDATA + i % NC;
     const uint32_t v = row == Sh::NDATA ? 0x3F803F80u : 0u;  // BF16 1.0 pairs
     *reinterpret_cast<uint4 *>(smem + st * Sh::A_STAGE + kc * Sh::LBO_A + row * 16) = make_uint4(v, v, v, v);
   }
@@ -508,10 +516,10 @@ __global__ void __launch_bounds__(WgShape<CIN>::THREADS, CIN == kCh ? 2 : 3)
     }
     uint8_t *sA = smem + buf * Sh::A_STAGE;
     uint8_t *sB = smem + 2 * Sh::A_STAGE + buf * Sh::B_STAGE;
-    const int p0 = p_begin + s * kWgStage;
+    const int p0 = p_begin + s * Sh::STAGE_PX;
     constexpr int NG = CIN == kCh ? kTaps * 4 : Sh::NDATA;  // A units per K chunk
-    for (int u = tid; u < (NG + 4) * 8; u += Sh::THREADS) {
-      const int kc = u & 7, g = u >> 3;
+    for (int u = tid; u < (NG + 4) * Sh::KCS; u += Sh::THREADS) {
+      const int kc = u % Sh::KCS, g = u / Sh::KCS;
       const int pq = p0 + kc * 8;  // pixels pq .. pq + 7: image b, row y, columns x0 ..
       const bool in = pq < p_end;
       const int b = pq >> (2 * lg_g), y = (pq >> lg_g) & (G - 1), x0 = pq & (G - 1);
@@ -564,7 +572,7 @@ __global__ void __launch_bounds__(WgShape<CIN>::THREADS, CIN == kCh ? 2 : 3)
       tc_fence_after();
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
 #pragma unroll
-      for (int k = 0; k < kWgStage / 16; ++k)
+      for (int k = 0; k < Sh::STAGE_PX / 16; ++k)
 #pragma unroll
         for (int i = 0; i < Sh::MT; ++i)
           umma_f16(tmem + 32u * i, sdesc(a0 + k * 2u * Sh::LBO_A + i * 2048u, Sh::LBO_A, 128u),
@@ -587,11 +595,11 @@ __global__ void __launch_bounds__(WgShape<CIN>::THREADS, CIN == kCh ? 2 : 3)
       tmem_ld_wait();
       const int row = 128 * i + 32 * q + lane;
       if (row <= Sh::NDATA) {
-        float4 *dst = reinterpret_cast<float4 *>(part + ((size_t)blockIdx.x * (Sh::NDATA + 1) + row) * kCh + 16 * h);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]), __uint_as_float(r[4 * j + 2]),
-                               __uint_as_float(r[4 * j + 3]));
+        float *dst = part + ((size_t)blockIdx.x * (Sh::NDATA + 1) + row) * kCh + 16 * h;
+        const uint32_t lo[8] = {r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7]};
+        const uint32_t hi[8] = {r[8], r[9], r[10], r[11], r[12], r[13], r[14], r[15]};
+        st_v8(dst, lo);
+        st_v8(dst + 8, hi);
       }
     }
   }

@@ -241,6 +241,12 @@ SVK_API int svk_cnn_gradient(const float *params, const float *x, const float *t
 /* One Adam step (bias-corrected, step >= 1) on the FP32 parameters with moments m, v. */
 SVK_API int svk_cnn_adam(float *params, float *m, float *v, const float *grad, int n_params, int step, float lr,
                          float beta1, float beta2, float eps, void *stream);
+/* The same step with the step count read from device memory (*step: device int32, >= 1
+ * when the kernel runs; the bias corrections 1 - beta^step are formed on the device), so
+ * that a training step can be captured once as a CUDA graph and replayed while the count
+ * advances.  Errors: SVK_ERR_ARG for NULL pointers or n_params < 1. */
+SVK_API int svk_cnn_adam_device_step(float *params, float *m, float *v, const float *grad, int n_params,
+                                     const int *step, float lr, float beta1, float beta2, float eps, void *stream);
 /*
  * Coefficient field from local predictions: for stamps s at (x_s, y_s) of a W x H frame
  * with local coefficients local[s][k] (device float32 [S][N]) and optional weights

@@ -38,7 +38,8 @@ EXPORTS = (
     "svk_last_error", "svk_version", "svk_gauss_basis_count", "svk_build_basis", "svk_workspace_size",
     "svk_convolve", "svk_difference", "svk_fit_workspace_size", "svk_fit_coeffs", "svk_difference_noalloc",
     "svk_batch_workspace_size", "svk_difference_batch", "svk_autotune", "svk_cnn_param_count",
-    "svk_cnn_workspace_size", "svk_cnn_forward", "svk_cnn_gradient", "svk_cnn_adam", "svk_cnn_field_fit",
+    "svk_cnn_workspace_size", "svk_cnn_forward", "svk_cnn_gradient", "svk_cnn_adam", "svk_cnn_adam_device_step",
+    "svk_cnn_field_fit",
     "svk_select_workspace_size", "svk_select_stamps", "svk_measure_fma_peak", "svk_host_workspace_size",
     "svk_difference_host", "svk_selftest_bounded_wait", "svk_device_status",
 )
@@ -91,6 +92,8 @@ def load_library(path: str | None = None):
         "svk_cnn_gradient": (i, [vp, vp, vp, i, i, vp, vp, vp, sz, vp]),
         "svk_cnn_adam": (i, [vp, vp, vp, vp, i, i, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              vp]),
+        "svk_cnn_adam_device_step": (i, [vp, vp, vp, vp, i, vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, vp]),
         "svk_cnn_field_fit": (i, [vp, vp, vp, i, i, i, i, i, vp, vp, vp]),
         "svk_measure_fma_peak": (i, [i, vp, vp]),
         "svk_selftest_bounded_wait": (i, [ctypes.c_ulonglong, vp, vp]),
@@ -402,6 +405,13 @@ def svk_cnn_adam(params, m, v, grad, step: int, lr: float = 1e-3, beta1: float =
                  eps: float = 1e-8, stream=None):
     _check(load_library().svk_cnn_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), params.numel(), int(step), lr,
                                        beta1, beta2, eps, _stream(stream)))
+
+
+def svk_cnn_adam_device_step(params, m, v, grad, step, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+                             eps: float = 1e-8, stream=None):
+    """svk_cnn_adam with the step count read from `step` (device int32 tensor of one element)."""
+    _check(load_library().svk_cnn_adam_device_step(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), params.numel(),
+                                                   _ptr(step), lr, beta1, beta2, eps, _stream(stream)))
 
 
 def svk_cnn_field_fit(local, xy, W: int, H: int, degree: int, weights=None, stream=None):

@@ -323,6 +323,14 @@ int svk_cnn_adam(float *params, float *m, float *v, const float *grad, int n_par
   return cnn_adam(params, m, v, grad, n_params, step, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream));
 }
 
+int svk_cnn_adam_device_step(float *params, float *m, float *v, const float *grad, int n_params, const int *step,
+                             float lr, float beta1, float beta2, float eps, void *stream) {
+  CallRange range("svk_cnn_adam_device_step");
+  if (!params || !m || !v || !grad || !step || n_params < 1) return set_error(SVK_ERR_ARG, "bad optimiser arguments");
+  return cnn_adam_device_step(params, m, v, grad, n_params, step, lr, beta1, beta2, eps,
+                              static_cast<cudaStream_t>(stream));
+}
+
 int svk_cnn_field_fit(const float *local, const int *xy, const float *weights, int S, int N, int W, int H, int degree,
                       double *coeffs, int *info, void *stream) {
   CallRange range("svk_cnn_field_fit");

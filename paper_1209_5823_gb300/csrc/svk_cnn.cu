@@ -733,6 +733,22 @@ __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float 
   }
 }
 
+// Adam with the step count in device memory (bias corrections formed here).
+__global__ void adam_dstep_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                                  const float *__restrict__ g, int n, const int *__restrict__ step, float lr, float b1,
+                                  float b2, float eps) {
+  const float t = (float)*step;
+  const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
 int grid_for(size_t n, int threads = 256) {
   const size_t g = (n + threads - 1) / threads;
   return (int)(g < 8192 ? (g > 0 ? g : 1) : 8192);
@@ -963,6 +979,12 @@ int cnn_adam(float *params, float *m, float *v, const float *grad, int n, int st
              float eps, cudaStream_t s) {
   const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
   adam_kernel<<<grid_for(n), 256, 0, s>>>(params, m, v, grad, n, lr, b1, b2, eps, c1, c2);
+  return cuda_status(cudaGetLastError(), "adam");
+}
+
+int cnn_adam_device_step(float *params, float *m, float *v, const float *grad, int n, const int *step, float lr,
+                         float b1, float b2, float eps, cudaStream_t s) {
+  adam_dstep_kernel<<<grid_for(n), 256, 0, s>>>(params, m, v, grad, n, step, lr, b1, b2, eps);
   return cuda_status(cudaGetLastError(), "adam");
 }
 

@@ -76,6 +76,8 @@ int cnn_gradient(const float *params, const float *x, const float *target, int B
                  void *ws, size_t ws_bytes, cudaStream_t s);
 int cnn_adam(float *params, float *m, float *v, const float *grad, int n, int step, float lr, float b1, float b2,
              float eps, cudaStream_t s);
+int cnn_adam_device_step(float *params, float *m, float *v, const float *grad, int n, const int *step, float lr,
+                         float b1, float b2, float eps, cudaStream_t s);
 int cnn_field_fit(const float *local, const int *xy, const float *wts, int S, int N, int W, int H, int degree,
                   double *coeffs, int *info, cudaStream_t s);
 

@@ -21,7 +21,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from . import (SVK_BASIS_GAUSS, SVK_METHOD_BASIS, SVK_PREC_BF16X3, svk_build_basis, svk_cnn_adam,
+from . import (SVK_BASIS_GAUSS, SVK_METHOD_BASIS, SVK_PREC_BF16X3, svk_build_basis, svk_cnn_adam_device_step,
                svk_cnn_field_fit, svk_cnn_forward, svk_cnn_gradient, svk_cnn_param_count, svk_cnn_workspace_size,
                svk_difference, svk_difference_batch, svk_fit_coeffs)
 
@@ -97,44 +97,52 @@ class CoefficientNetwork:
         self._graph = None  # the gradient call over those buffers, captured as a CUDA graph
         self._graph_key = None
 
-    def _gradient(self, xb, zb, grad, loss):
-        """svk_cnn_gradient over the fixed training buffers, replayed as a CUDA graph
-        (captured on first use: the same kernels with the same arguments, minus the launch
-        gaps between them)."""
-        key = (xb.data_ptr(), zb.data_ptr(), grad.data_ptr(), loss.data_ptr(), self.params.data_ptr(),
-               self.ws.data_ptr())
+    def _step_graph(self, x, z, lr):
+        """One training step over fixed buffers as a CUDA graph: gather the batch named by
+        the index buffer, svk_cnn_gradient, advance the device step count, Adam
+        (svk_cnn_adam_device_step).  Captured once per (inputs, learning rate); the kernels
+        and their arguments are those of the eager step."""
+        dev = x.device
+        shape = (self.batch,) + tuple(x.shape[1:])
+        if self._bufs is None or self._bufs["x"].shape != shape or self._bufs["x"].device != dev:
+            self._bufs = {"idx": torch.zeros(self.batch, dtype=torch.int64, device=dev),
+                          "x": torch.zeros(shape, dtype=torch.float32, device=dev),
+                          "z": torch.zeros((self.batch, self.n_out), dtype=torch.float32, device=dev),
+                          "grad": torch.zeros_like(self.params), "loss": torch.zeros(1, dtype=torch.float32, device=dev),
+                          "step": torch.zeros(1, dtype=torch.int32, device=dev)}
+            self._graph_key = None
+        b = self._bufs
+        key = (x.data_ptr(), z.data_ptr(), tuple(x.shape), float(lr), self.params.data_ptr(), self.ws.data_ptr())
         if self._graph_key != key:
-            side = torch.cuda.Stream(device=xb.device)
+            side = torch.cuda.Stream(device=dev)
             side.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(side):  # first call outside the capture (lazy library setup)
-                svk_cnn_gradient(self.params, xb, zb, grad=grad, loss=loss, workspace=self.ws)
+            with torch.cuda.stream(side):  # first library call outside the capture (lazy setup)
+                svk_cnn_gradient(self.params, b["x"], b["z"], grad=b["grad"], loss=b["loss"], workspace=self.ws)
             torch.cuda.current_stream().wait_stream(side)
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph):
-                svk_cnn_gradient(self.params, xb, zb, grad=grad, loss=loss, workspace=self.ws)
+                torch.index_select(x, 0, b["idx"], out=b["x"])
+                torch.index_select(z, 0, b["idx"], out=b["z"])
+                svk_cnn_gradient(self.params, b["x"], b["z"], grad=b["grad"], loss=b["loss"], workspace=self.ws)
+                b["step"].add_(1)
+                svk_cnn_adam_device_step(self.params, self.m, self.v, b["grad"], b["step"], lr=lr)
             self._graph, self._graph_key = graph, key
-        self._graph.replay()
+        return self._graph, b
 
     def train(self, x, a, steps: int, lr: float = 1e-3, gen=None):
         """Adam on standardised targets; returns the per-step losses (device tensor)."""
         dev = x.device
         z = ((a - self.prior.mean(dev)) / self.prior.std(dev)).contiguous()
+        x = x.contiguous()
         losses = torch.empty(steps, device=dev)
-        shape = (self.batch,) + tuple(x.shape[1:])
-        if self._bufs is None or self._bufs[0].shape != shape or self._bufs[0].device != dev:
-            self._bufs = (torch.empty(shape, dtype=torch.float32, device=dev),
-                          torch.empty((self.batch, self.n_out), dtype=torch.float32, device=dev),
-                          torch.empty_like(self.params), torch.empty(1, dtype=torch.float32, device=dev))
-        xb, zb, grad, loss = self._bufs
+        graph, b = self._step_graph(x, z, lr)
+        b["step"].fill_(self.step)
         n = x.shape[0]
         for s in range(steps):
-            idx = torch.randint(0, n, (self.batch,), device=dev, generator=gen)
-            torch.index_select(x, 0, idx, out=xb)
-            torch.index_select(z, 0, idx, out=zb)
-            self._gradient(xb, zb, grad, loss)
-            losses[s:s + 1].copy_(loss)
-            self.step += 1
-            svk_cnn_adam(self.params, self.m, self.v, grad, self.step, lr=lr)
+            torch.randint(0, n, (self.batch,), generator=gen, out=b["idx"])
+            graph.replay()
+            losses[s:s + 1].copy_(b["loss"])
+        self.step += steps
         return losses
 
     def state_dict(self):

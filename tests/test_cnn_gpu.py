@@ -190,3 +190,23 @@ def test_training_checkpoint_resumes_bit_exactly(tmp_path):
     assert resumed.step == full.step == 20
     assert torch.equal(resumed.params, full.params)
     assert torch.equal(resumed.m, full.m) and torch.equal(resumed.v, full.v)
+
+
+def test_adam_device_step_matches_host_step():
+    # the step count read from device memory: the same update as svk_cnn_adam over several
+    # steps (bias corrections formed on the device instead of the host: float32 rounding)
+    n = 5000
+    g = starfield.rng(31)
+    p0 = g.normal(0, 1, n).astype(np.float32)
+    grads = [g.normal(0, 1, n).astype(np.float32) for _ in range(5)]
+    a = [torch.from_numpy(v).cuda() for v in (p0.copy(), np.zeros(n, np.float32), np.zeros(n, np.float32))]
+    b = [torch.from_numpy(v).cuda() for v in (p0.copy(), np.zeros(n, np.float32), np.zeros(n, np.float32))]
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for k, gr in enumerate(grads, start=1):
+        dg = torch.from_numpy(gr).cuda()
+        svk.svk_cnn_adam(a[0], a[1], a[2], dg, k, lr=0.01)
+        step.fill_(k)
+        svk.svk_cnn_adam_device_step(b[0], b[1], b[2], dg, step, lr=0.01)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(y.cpu().numpy(), x.cpu().numpy(), rtol=1e-5, atol=1e-6)

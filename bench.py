@@ -6,8 +6,10 @@ variation): basis tabulation on the device, then D = (R (x) K_{x,y}) - I by the
 tensor-core basis form (BF16 hi+lo split, FP32 accumulation) through the C ABI.
 
 Printed JSON line (rank 0): value = Mpixel/s of D with inputs resident in HBM; e2e =
-the same through the host-buffer C-ABI call (svk_difference_host: copies in, compute and copies out of row bands overlapped, all timed); roofline of the
-dominant kernel (algorithmic FLOP / CUDA-event launch time vs the measured bf16 peak);
+the same from pinned host buffers through the C ABI (svk_difference_host_batch: every
+frame's R and I copied in and D copied out, the copies overlapped with the computation of
+the neighbouring frames, all timed; the single-frame svk_difference_host beside it);
+roofline of the dominant kernel (algorithmic FLOP / CUDA-event launch time vs the measured bf16 peak);
 the direct form's throughput beside it; the FP64 oracle timed on the host cores on a
 band of rows (cpu_baseline), whose output also gives the measured max relative error
 of both GPU forms on that band.
@@ -32,7 +34,9 @@ UNIT = "Mpixel/s"
 WORKLOAD = "ccd_2048x4096_L19_d2"
 L2_BYTES = 129 * 2 ** 20
 NROT = 4  # rotating input frames: 4 x (R, I, D) = 384 MB > L2
-E2E_BANDS = 8  # row bands of the host-buffer call (copies of one band overlap the others' work)
+E2E_BANDS = 2  # row bands per frame of the pipelined host-buffer call
+E2E_SINGLE_BANDS = 8  # row bands of the single-frame host-buffer call (reported beside it)
+NROT_HOST = 3  # distinct pinned host frames the end-to-end steps rotate through
 
 
 def _peaks():
@@ -615,32 +619,55 @@ def main():
     ms_total = t0.elapsed_time(t1)
     kern_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
 
-    # e2e through the C ABI with host buffers (svk_difference_host): every step copies R
-    # and I in and D out (pinned memory), in row bands that overlap the computation
-    Rh = torch.from_numpy(R).pin_memory()
-    Ih = torch.from_numpy(I).pin_memory()
-    Dh = torch.empty((H, W), dtype=torch.float32).pin_memory()
-    wsh = torch.empty(svk.svk_host_workspace_size(svk.SVK_METHOD_BASIS, prec, W, H, N, L, d), dtype=torch.uint8,
+    # e2e through the C ABI with host buffers: every step is one frame whose R and I are
+    # copied in from pinned host memory and whose D is copied out, its basis built and its
+    # tables prepared; svk_difference_host_batch pipelines the timed steps' frames (frame
+    # k + 1's copies in and frame k - 1's copies out overlap frame k's computation).
+    Rh = [torch.from_numpy(R).clone().pin_memory() for _ in range(NROT_HOST)]
+    Ih = [torch.from_numpy(I).clone().pin_memory() for _ in range(NROT_HOST)]
+    Dh = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(NROT_HOST)]
+    n_e2e = max(10, args.steps // 4)
+    bases = [torch.empty((N, L, L), dtype=torch.float32, device=dev) for _ in range(n_e2e)]
+    items = [dict(R=Rh[k % NROT_HOST], I=Ih[k % NROT_HOST], D=Dh[k % NROT_HOST], basis=bases[k], coeffs=ct, degree=d)
+             for k in range(n_e2e)]
+    wsh = torch.empty(svk.svk_host_batch_workspace_size(items, svk.SVK_METHOD_BASIS, prec), dtype=torch.uint8,
                       device=dev)
 
-    def e2e_step():
-        svk.svk_build_basis(svk.SVK_BASIS_GAUSS, L, out=basis)
-        svk.svk_difference_host(Rh, Ih, basis, ct, d, method=svk.SVK_METHOD_BASIS, precision=prec, out=Dh,
-                                n_bands=E2E_BANDS, workspace=wsh)
+    def e2e_run():
+        for b in bases:
+            svk.svk_build_basis(svk.SVK_BASIS_GAUSS, L, out=b)
+        svk.svk_difference_host_batch(items, method=svk.SVK_METHOD_BASIS, precision=prec, n_bands=E2E_BANDS,
+                                      workspace=wsh)
 
-    n_e2e = max(10, args.steps // 4)
-    for i in range(3):
-        e2e_step()
+    e2e_run()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for i in range(n_e2e):
-        e2e_step()
+    e2e_run()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
+
+    # the same frames one svk_difference_host call at a time (no overlap across frames)
+    ws1 = torch.empty(svk.svk_host_workspace_size(svk.SVK_METHOD_BASIS, prec, W, H, N, L, d), dtype=torch.uint8,
+                      device=dev)
+
+    def e2e_single(k):
+        svk.svk_build_basis(svk.SVK_BASIS_GAUSS, L, out=bases[k])
+        svk.svk_difference_host(Rh[k % NROT_HOST], Ih[k % NROT_HOST], bases[k], ct, d, method=svk.SVK_METHOD_BASIS,
+                                precision=prec, out=Dh[k % NROT_HOST], n_bands=E2E_SINGLE_BANDS, workspace=ws1)
+
+    for k in range(3):
+        e2e_single(k)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(n_e2e):
+        e2e_single(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e1_ms = e0.elapsed_time(e1)
     clocks = clk.stop()
 
     # the direct form on the same frame, for the "vs direct" half of the metric
@@ -664,10 +691,12 @@ def main():
                                                     precision=prec, out=Dt, workspace=wst), reps=20)
 
     # max over ranks
-    ms_total, e2e_ms, kern_ms, dir_ms = _max_over_ranks(dist, [ms_total, e2e_ms, kern_ms, dir_ms], dev)
+    ms_total, e2e_ms, e2e1_ms, kern_ms, dir_ms = _max_over_ranks(dist, [ms_total, e2e_ms, e2e1_ms, kern_ms, dir_ms],
+                                                                 dev)
     px = W * H
     value = _job_rate(world, px, args.steps, ms_total)
     e2e_value = _job_rate(world, px, n_e2e, e2e_ms)
+    e2e1_value = _job_rate(world, px, n_e2e, e2e1_ms)
     if rank != 0:
         return
 
@@ -691,7 +720,10 @@ def main():
                    "l2": f"{NROT} rotating input frames ({NROT * 3 * px * 4 / 2**20:.0f} MB > L2)"},
         "gpu_launches": launches_per_step * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * px * 4, "d2h_bytes_per_step": px * 4,
-                "call": f"svk_difference_host, pinned host buffers, {E2E_BANDS} row bands"},
+                "call": f"svk_difference_host_batch over the {n_e2e} timed frames (pinned host buffers rotating over "
+                        f"{NROT_HOST} frames, {E2E_BANDS} row bands each, basis built per frame)",
+                "single_frame_calls": {"value": e2e1_value, "unit": UNIT,
+                                       "call": f"svk_difference_host per frame, {E2E_SINGLE_BANDS} row bands"}},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_bf16, "unit": "TFLOP/s",
                      "frac": achieved / peak_bf16, "traffic": traffic,
                      "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)",

@@ -319,6 +319,29 @@ SVK_API int svk_difference_host(const float *R, const float *I, float *D, int W,
                                 const float *basis, int N, int L, const float *coeffs, int degree, int method,
                                 int precision, int n_bands, void *workspace, size_t ws_bytes, void *stream);
 
+/* Bytes of device workspace svk_difference_host_batch needs for these frames: two
+ * staging sets, each holding R, I and D of the largest frame and the method's tables
+ * (0 on error). */
+SVK_API size_t svk_host_batch_workspace_size(const svk_frame *frames, int n_frames, int method, int precision);
+
+/*
+ * A sequence of frames whose images live in HOST memory (a night streamed from the
+ * host): D_f = (R_f (x) K_f) - I_f (Eq. 1) for every frame, as svk_difference_host does
+ * for one, with the frames pipelined: frames alternate between two device staging sets,
+ * so frame f+1's copies in and frame f-1's copies out overlap frame f's computation, and
+ * within a frame the n_bands row bands are pipelined as in svk_difference_host.
+ *   frames     HOST array of n_frames >= 1 descriptors (read during the call): R, I and D
+ *              are HOST float32 [H][pitch_*] (page-locked for overlap), basis and coeffs
+ *              DEVICE, each frame with its own size, N, L and degree.
+ *   workspace  device scratch of svk_host_batch_workspace_size() bytes, or NULL / 0
+ *              (then allocated on the stream and released after the call).
+ * Asynchronous on `stream` like svk_difference_host: every D is written when the stream
+ * reaches the end of the call.  Errors as svk_difference_host, checked for every frame
+ * before any work is queued.
+ */
+SVK_API int svk_difference_host_batch(const svk_frame *frames, int n_frames, int method, int precision, int n_bands,
+                                      void *workspace, size_t ws_bytes, void *stream);
+
 /*
  * The library's sticky device status: every bounded device wait that gives up (after
  * ~2 s, e.g. a copy that never lands) records SVK_ERR_TIMEOUT there and its kernel

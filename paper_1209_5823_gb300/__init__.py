@@ -41,7 +41,8 @@ EXPORTS = (
     "svk_cnn_workspace_size", "svk_cnn_forward", "svk_cnn_gradient", "svk_cnn_adam", "svk_cnn_adam_device_step",
     "svk_cnn_field_fit",
     "svk_select_workspace_size", "svk_select_stamps", "svk_measure_fma_peak", "svk_host_workspace_size",
-    "svk_difference_host", "svk_selftest_bounded_wait", "svk_device_status",
+    "svk_difference_host", "svk_host_batch_workspace_size", "svk_difference_host_batch", "svk_selftest_bounded_wait",
+    "svk_device_status",
 )
 
 
@@ -100,6 +101,8 @@ def load_library(path: str | None = None):
         "svk_device_status": (i, [i, vp]),
         "svk_host_workspace_size": (sz, [i, i, i, i, i, i, i]),
         "svk_difference_host": (i, [vp, vp, vp, i, i, i, vp, i, i, vp, i, i, i, i, vp, sz, vp]),
+        "svk_host_batch_workspace_size": (sz, [vp, i, i, i]),
+        "svk_difference_host_batch": (i, [vp, i, i, i, i, vp, sz, vp]),
         "svk_select_workspace_size": (sz, [i, i]),
         "svk_select_stamps": (i, [vp, i, i, i, f, f, f, i, i, f, i, vp, vp, vp, sz, vp]),
     }
@@ -128,10 +131,11 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
-def _img(t, name):
+def _img(t, name, host=False):
     import torch
-    if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2 or t.stride(1) != 1:
-        raise ValueError(f"{name} must be a CUDA float32 [H][pitch] tensor with unit column stride")
+    where = "host" if host else "CUDA"
+    if t.dtype != torch.float32 or t.is_cuda == host or t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be a {where} float32 [H][pitch] tensor with unit column stride")
     return t.shape[0], t.shape[1], t.stride(0)
 
 
@@ -232,13 +236,14 @@ def svk_difference_noalloc(R, I, basis, coeffs, degree: int, precision: int = SV
     return out
 
 
-def _frames(items):
-    """items: sequence of dicts with R, I (or None), D, basis, coeffs, degree (torch tensors)."""
+def _frames(items, host=False):
+    """items: sequence of dicts with R, I (or None), D, basis, coeffs, degree (torch tensors;
+    R, I, D in host memory when `host`)."""
     arr = (svk_frame * len(items))()
     for k, it in enumerate(items):
-        H, W, pR = _img(it["R"], "R")
-        _, _, pD = _img(it["D"], "D")
-        pI = _img(it["I"], "I")[2] if it.get("I") is not None else W
+        H, W, pR = _img(it["R"], "R", host)
+        _, _, pD = _img(it["D"], "D", host)
+        pI = _img(it["I"], "I", host)[2] if it.get("I") is not None else W
         b = it["basis"]
         arr[k] = svk_frame(it["R"].data_ptr(), pR, it["I"].data_ptr() if it.get("I") is not None else None, pI,
                            it["D"].data_ptr(), pD, W, H, b.data_ptr(), b.shape[0], b.shape[1],
@@ -321,6 +326,25 @@ def svk_difference_host(R, I, basis, coeffs, degree: int, method: int = SVK_METH
                                               _ptr(coeffs), int(degree), int(method), int(precision), int(n_bands),
                                               _ptr(workspace), ws_bytes, _stream(stream)))
     return out
+
+
+def svk_host_batch_workspace_size(items, method: int = SVK_METHOD_BASIS, precision: int = SVK_PREC_BF16X3) -> int:
+    arr = _frames(items, host=True)
+    return int(load_library().svk_host_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), len(items), int(method),
+                                                            int(precision)))
+
+
+def svk_difference_host_batch(items, method: int = SVK_METHOD_BASIS, precision: int = SVK_PREC_BF16X3,
+                              n_bands: int = 2, workspace=None, stream=None):
+    """D = (R (x) K) - I for a sequence of frames in host memory: each item a dict with host
+    float32 [H][pitch] tensors R, I, D (pinned for overlap) and device basis, coeffs, degree.
+    Frames are pipelined (the next frame's copies in and the previous frame's copies out
+    overlap the current frame's computation).  Asynchronous on the stream."""
+    arr = _frames(items, host=True)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_difference_host_batch(ctypes.cast(arr, ctypes.c_void_p), len(items), int(method),
+                                                    int(precision), int(n_bands), _ptr(workspace), ws_bytes,
+                                                    _stream(stream)))
 
 
 def svk_device_status(reset: bool = False, stream=None) -> int:

@@ -396,6 +396,40 @@ int svk_difference_host(const float *R, const float *I, float *D, int W, int H, 
   return launch_host(R, I, D, W, H, pitch, basis, N, L, coeffs, degree, method, precision, n_bands, w.ptr, need, s);
 }
 
+static int check_host_frames(const svk_frame *frames, int n, int method, int precision) {
+  if (!frames || n < 1) return set_error(SVK_ERR_ARG, "no frames");
+  for (int f = 0; f < n; ++f) {
+    const svk_frame &F = frames[f];
+    int st = check_conv_args(F.R, F.pitch_R, F.I, F.pitch_I, F.W, F.H, F.basis, F.N, F.L, F.coeffs, F.degree, method,
+                             precision, SVK_EDGE_ZERO, F.D, F.pitch_D, true);
+    if (st != SVK_OK) {
+      char msg[256];
+      snprintf(msg, sizeof(msg), "%s", last_error());
+      return set_error(st, "frame %d: %s", f, msg);
+    }
+  }
+  return SVK_OK;
+}
+
+size_t svk_host_batch_workspace_size(const svk_frame *frames, int n_frames, int method, int precision) {
+  if (check_host_frames(frames, n_frames, method, precision) != SVK_OK) return 0;
+  return host_batch_workspace_size(frames, n_frames, method, precision);
+}
+
+int svk_difference_host_batch(const svk_frame *frames, int n_frames, int method, int precision, int n_bands,
+                              void *workspace, size_t ws_bytes, void *stream) {
+  CallRange range("svk_difference_host_batch");
+  int st = check_host_frames(frames, n_frames, method, precision);
+  if (st != SVK_OK) return st;
+  if (n_bands < 1) return set_error(SVK_ERR_ARG, "n_bands=%d must be >= 1", n_bands);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScopedWorkspace w;
+  const size_t need = host_batch_workspace_size(frames, n_frames, method, precision);
+  st = w.acquire(need, workspace, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  return launch_host_batch(frames, n_frames, method, precision, n_bands, w.ptr, need, s);
+}
+
 int svk_device_status(int reset, void *stream) {
   uint32_t *w = device_status_word();
   if (!w) return set_error(SVK_ERR_CUDA, "device status word not available");

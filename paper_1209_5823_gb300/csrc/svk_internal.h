@@ -53,6 +53,9 @@ size_t host_workspace_size(int method, int precision, int W, int H, int N, int L
 int launch_host(const float *R, const float *I, float *D, int W, int H, int pitch, const float *basis, int N, int L,
                 const float *coeffs, int degree, int method, int precision, int n_bands, void *ws, size_t ws_bytes,
                 cudaStream_t s);
+size_t host_batch_workspace_size(const svk_frame *frames, int n, int method, int precision);
+int launch_host_batch(const svk_frame *frames, int n, int method, int precision, int n_bands, void *ws,
+                      size_t ws_bytes, cudaStream_t s);
 
 // Stamp selection (svk_stamps.cu).
 size_t select_workspace_size(int W, int H);

@@ -76,3 +76,58 @@ def test_host_rejects_bad_arguments():
     with pytest.raises(svk.SvkError):
         svk.svk_difference_host(_host(R), _host(I), B, ct, 1, method=svk.SVK_METHOD_DIRECT,
                                 precision=svk.SVK_PREC_BF16X3)
+
+
+def _batch_items(specs, pitch_pad=0, seed=0):
+    """Host frames (pinned, row pitches padded by pitch_pad) of uneven sizes, kernel sizes
+    and degrees, with their device call results."""
+    items, expect = [], []
+    for k, (W, H, L, d, N) in enumerate(specs):
+        R, I, B, c = _inputs(W, H, L, d, N, seed=seed + 5 * k)
+        ct = torch.from_numpy(c).cuda()
+        Dh = torch.full((H, W + pitch_pad), float("nan"), dtype=torch.float32).pin_memory()
+        items.append(dict(R=_host(R, pitch=W + pitch_pad), I=_host(I, pitch=W + 2 * pitch_pad), D=Dh[:, :W], basis=B,
+                          coeffs=ct, degree=d))
+        expect.append((R, I, B, ct, d, Dh))
+    return items, expect
+
+
+BATCH_SPECS = [(300, 173, 19, 2, 49), (129, 37, 25, 3, 49), (200, 61, 15, 0, 49), (64, 200, 19, 1, 30),
+               (300, 173, 19, 2, 49)]
+
+
+@pytest.mark.parametrize("method,prec", METHODS)
+@pytest.mark.parametrize("n_bands", [1, 3])
+def test_host_batch_equals_device_calls(method, prec, n_bands):
+    # five frames through two staging sets (every set reused), uneven sizes, per-buffer
+    # pitches: each frame equals its device call bit for bit; pitch padding stays untouched
+    items, expect = _batch_items(BATCH_SPECS, pitch_pad=8 if n_bands == 3 else 0, seed=3)
+    svk.svk_difference_host_batch(items, method=method, precision=prec, n_bands=n_bands)
+    torch.cuda.synchronize()
+    for it, (R, I, B, ct, d, Dh) in zip(items, expect):
+        dev = svk.svk_difference(torch.from_numpy(R).cuda(), torch.from_numpy(I).cuda(), B, ct, d, method=method,
+                                 precision=prec)
+        assert torch.equal(it["D"], dev.cpu())
+        W = R.shape[1]
+        assert torch.isnan(Dh[:, W:]).all()
+
+
+def test_host_batch_matches_oracle_with_workspace():
+    specs = [(257, 61, 11, 1, 49), (130, 40, 15, 2, 49), (257, 61, 11, 1, 49)]
+    items, expect = _batch_items(specs, seed=7)
+    ws = torch.empty(svk.svk_host_batch_workspace_size(items), dtype=torch.uint8, device="cuda")
+    svk.svk_difference_host_batch(items, n_bands=4, workspace=ws)
+    torch.cuda.synchronize()
+    for it, (R, I, B, ct, d, Dh) in zip(items, expect):
+        ref = oracle_conv(R, B.cpu().numpy(), ct.cpu().numpy(), d)
+        assert rel_err(it["D"].numpy() + I, ref) <= TOL_FP32
+
+
+def test_host_batch_rejects_bad_frames():
+    items, _ = _batch_items([(64, 32, 7, 1, 20), (64, 32, 7, 1, 20)])
+    items[1]["degree"] = 5  # out of range in the second frame: nothing is queued
+    with pytest.raises(svk.SvkError):
+        svk.svk_difference_host_batch(items)
+    items, _ = _batch_items([(64, 32, 7, 1, 20)])
+    with pytest.raises(svk.SvkError):
+        svk.svk_difference_host_batch(items, n_bands=0)

@@ -229,11 +229,16 @@ def _night_batch(svk, torch, dev, stream, reps=3):
     import starfield
     specs = starfield.batch_specs()
     base = {}
+    host = {}
     for sp in specs:  # one rendered field per size; frames are scaled copies (distinct buffers)
         if (sp.W, sp.H) not in base:
             R, I, _ = starfield.frame_pair(starfield.FrameSpec("b", sp.W, sp.H, sp.n_stars, sp.L, sp.degree, sp.seed))
             base[(sp.W, sp.H)] = (torch.from_numpy(R.astype(np.float32)).to(dev),
                                   torch.from_numpy(I.astype(np.float32)).to(dev))
+            # pinned host copies for the night streamed from host memory (R, I read, D written)
+            host[(sp.W, sp.H)] = (torch.from_numpy(R.astype(np.float32)).pin_memory(),
+                                  torch.from_numpy(I.astype(np.float32)).pin_memory(),
+                                  torch.empty((sp.H, sp.W), dtype=torch.float32).pin_memory())
     bases, items = {}, []
     for k, sp in enumerate(specs):
         if sp.L not in bases:
@@ -263,8 +268,18 @@ def _night_batch(svk, torch, dev, stream, reps=3):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         svk.svk_difference_batch(items, workspace=ws, stream=s)
+    # the same night streamed from pinned host memory: every frame's R and I copied in and
+    # D copied out, overlapped with the neighbouring frames' computation
+    hitems = [dict(R=host[(it["R"].shape[1], it["R"].shape[0])][0], I=host[(it["R"].shape[1], it["R"].shape[0])][1],
+                   D=host[(it["R"].shape[1], it["R"].shape[0])][2], basis=it["basis"], coeffs=it["coeffs"],
+                   degree=it["degree"]) for it in items]
+    wsh = torch.empty(svk.svk_host_batch_workspace_size(hitems), dtype=torch.uint8, device=dev)
+
+    def host_stream():
+        svk.svk_difference_host_batch(hitems, n_bands=2, workspace=wsh)
+
     out = {}
-    for name, fn in (("graph_batch", g.replay), ("per_frame_launches", per_frame)):
+    for name, fn in (("graph_batch", g.replay), ("per_frame_launches", per_frame), ("host_stream", host_stream)):
         fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -275,6 +290,8 @@ def _night_batch(svk, torch, dev, stream, reps=3):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         out[name] = {"ms_per_night": ms, "value": px / (ms / 1e3) / 1e6, "unit": UNIT}
+    out["host_stream"]["call"] = ("svk_difference_host_batch from pinned host memory, 2 row bands per frame "
+                                  f"({3 * px * 4 / 2**30:.1f} GiB copied per night)")
     out["frames"] = len(items)
     out["mpixels"] = px / 1e6
     out["tuned_plans"] = {str(L): {"G": v[0], "stages": v[1]} for L, v in tuned.items()}

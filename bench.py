@@ -474,6 +474,10 @@ def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=3000):
                       "default_rule_source": "fit" if res["chi2_per_px"] > 2.0 * res["floor"] else "network"}}
 
 
+def n_terms_d(d):
+    return (d + 1) * (d + 2) // 2
+
+
 def _time(torch, fn, reps=5):
     fn()
     torch.cuda.synchronize()
@@ -706,6 +710,13 @@ def main():
     wst = torch.empty(svk.svk_workspace_size(svk.SVK_METHOD_TFORM, prec, W, H, N, L, d), dtype=torch.uint8, device=dev)
     tf_ms = _time(torch, lambda: svk.svk_difference(Rs[0], Is[0], basis, ct, d, method=svk.SVK_METHOD_TFORM,
                                                     precision=prec, out=Dt, workspace=wst), reps=20)
+    # the T-form on the CUDA cores (FP32 FFMA: the direct kernel over the T stamps K_t)
+    Dtf32 = torch.empty((H, W), dtype=torch.float32, device=dev)
+    wst32 = torch.empty(max(1, svk.svk_workspace_size(svk.SVK_METHOD_TFORM, svk.SVK_PREC_FP32, W, H, N, L, d)),
+                        dtype=torch.uint8, device=dev)
+    tf32_ms = _time(torch, lambda: svk.svk_difference(Rs[0], Is[0], basis, ct, d, method=svk.SVK_METHOD_TFORM,
+                                                      precision=svk.SVK_PREC_FP32, out=Dtf32, workspace=wst32),
+                    reps=20)
 
     # max over ranks
     ms_total, e2e_ms, e2e1_ms, kern_ms, dir_ms = _max_over_ranks(dist, [ms_total, e2e_ms, e2e1_ms, kern_ms, dir_ms],
@@ -759,7 +770,10 @@ def main():
         "measured_fma": {"fp32_tflops": fp32_peak / 1e12, "fp64_tflops": fp64_peak / 1e12},
         "clocks": clocks,
         "tform": {"value": world * px / (tf_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_frame": tf_ms,
-                  "form": "sum_t m_t (R (x) K_t) - I, K_t = sum_k c[k][t] B_k (same result, T = 6 convolutions)"},
+                  "form": "sum_t m_t (R (x) K_t) - I, K_t = sum_k c[k][t] B_k (same result, T = 6 convolutions)",
+                  "fp32_ffma": {"value": world * px / (tf32_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_frame": tf32_ms,
+                                "tflops": (2 * n_terms_d(d) * L * L + 2 * L * L) * px / (tf32_ms / 1e3) / 1e12,
+                                "flop_per_px": 2 * n_terms_d(d) * L * L + 2 * L * L}},
     }
     if not args.no_extras:
         out["night_batch"] = _night_batch(svk, torch, dev, stream)
@@ -778,6 +792,8 @@ def main():
         out["cpu_baseline"]["single_core"] = _oracle_one_core(R, basis.cpu().numpy(), c, d, cores)
         Dtf = Dt[y0:y1].cpu().numpy().astype(np.float64) + I[y0:y1]
         out["tform"]["max_rel_err"] = float(np.abs(Dtf - ref).max() / scale)
+        Dtf32h = Dtf32[y0:y1].cpu().numpy().astype(np.float64) + I[y0:y1]
+        out["tform"]["fp32_ffma"]["max_rel_err"] = float(np.abs(Dtf32h - ref).max() / scale)
         out["max_rel_err"] = {"basis": float(np.abs(Dtc - ref).max() / scale),
                               "direct": float(np.abs(Ddir - ref).max() / scale),
                               "measure": "max|D_gpu - D_oracle| / max|R (x) K| over the cpu_baseline band"}

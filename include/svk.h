@@ -72,12 +72,13 @@ extern "C" {
                             /* polynomial epilogue sum_k a_k(x,y) C_k(x,y) (- I)           */
 #define SVK_METHOD_TFORM 2  /* the same result by linearity of Eq. 2 and 3 as              */
                             /* sum_t m_t(xt,yt) (R (x) K_t)(x,y) (- I), K_t = sum_k c[k][t] */
-                            /* B_k: T = (d+1)(d+2)/2 convolutions on the tensor cores       */
-                            /* instead of N; any N (delta bases included); precisions as   */
-                            /* SVK_METHOD_BASIS                                             */
+                            /* B_k: T = (d+1)(d+2)/2 convolutions instead of N; any N       */
+                            /* (delta bases included); on the tensor cores with the         */
+                            /* precisions of SVK_METHOD_BASIS, or on the CUDA cores with    */
+                            /* SVK_PREC_FP32 (the direct kernel over the T stamps K_t)      */
 
 /* arithmetic of the contraction */
-#define SVK_PREC_FP32 0   /* DIRECT only: FP32 FFMA                                       */
+#define SVK_PREC_FP32 0   /* DIRECT, TFORM: FP32 FFMA on the CUDA cores                   */
 #define SVK_PREC_BF16X3 1 /* BASIS, TFORM: R and B split hi + lo in BF16, hi*hi + hi*lo + lo*hi, */
                           /* FP32 accumulation                                            */
 #define SVK_PREC_FP16X3 2 /* BASIS, TFORM: the same split in FP16 (power-of-two prescaled) */
@@ -129,7 +130,7 @@ SVK_API size_t svk_workspace_size(int method, int precision, int W, int H, int N
  *   coeffs   device float32 [N][T], T = (degree+1)(degree+2)/2, 0 <= degree <= 3
  *   method   SVK_METHOD_DIRECT (precision SVK_PREC_FP32), SVK_METHOD_BASIS (precision
  *            SVK_PREC_BF16X3 / FP16X3 / BF16; N <= 256) or SVK_METHOD_TFORM (the same
- *            precisions; any N)
+ *            precisions or SVK_PREC_FP32; any N)
  *   edge     SVK_EDGE_ZERO
  *   out      device float32 [H][pitch_out]; must not overlap R
  *   workspace, ws_bytes   device scratch of at least svk_workspace_size() bytes, or

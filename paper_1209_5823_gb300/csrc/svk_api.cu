@@ -130,8 +130,9 @@ static int check_conv_args(const float *R, int pitch_R, const float *I, int pitc
     if (precision != SVK_PREC_FP32)
       return set_error(SVK_ERR_UNSUPPORTED, "the direct method computes in FP32 only");
   } else if (method == SVK_METHOD_BASIS || method == SVK_METHOD_TFORM) {
-    if (precision != SVK_PREC_BF16X3 && precision != SVK_PREC_FP16X3 && precision != SVK_PREC_BF16)
-      return set_error(SVK_ERR_UNSUPPORTED, "tensor-core precision %d not built", precision);
+    const bool tc = precision == SVK_PREC_BF16X3 || precision == SVK_PREC_FP16X3 || precision == SVK_PREC_BF16;
+    if (!tc && !(method == SVK_METHOD_TFORM && precision == SVK_PREC_FP32))
+      return set_error(SVK_ERR_UNSUPPORTED, "precision %d not built for method %d", precision, method);
     if (method == SVK_METHOD_BASIS && N > 256)
       return set_error(SVK_ERR_UNSUPPORTED, "basis method supports N <= 256 (got %d)", N);
   } else {

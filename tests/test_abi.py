@@ -57,7 +57,7 @@ def _conv(lib, **kw):
     (dict(pR=63), svk.SVK_ERR_ARG), (dict(W=0), svk.SVK_ERR_ARG), (dict(d=4), svk.SVK_ERR_ARG),
     (dict(N=0), svk.SVK_ERR_ARG), (dict(edge=1), svk.SVK_ERR_ARG), (dict(method=7), svk.SVK_ERR_ARG),
     (dict(method=0, prec=1), svk.SVK_ERR_UNSUPPORTED), (dict(method=1, prec=0), svk.SVK_ERR_UNSUPPORTED),
-    (dict(method=1, prec=1, N=300), svk.SVK_ERR_UNSUPPORTED),
+    (dict(method=1, prec=1, N=300), svk.SVK_ERR_UNSUPPORTED), (dict(method=2, prec=7), svk.SVK_ERR_UNSUPPORTED),
 ])
 def test_host_argument_checks(lib, kw, status):
     assert _conv(lib, **kw) == status

@@ -40,6 +40,7 @@ def _inputs(W, H, L, N, d, seed):
     (svk.SVK_METHOD_BASIS, svk.SVK_PREC_FP16X3),
     (svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16),
     (svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3),
+    (svk.SVK_METHOD_TFORM, svk.SVK_PREC_FP32),
 ])
 @pytest.mark.parametrize("W,H,L", [(300, 173, 19), (129, 37, 25), (7, 5, 11), (1000, 3, 31)])
 def test_device_call_writes_every_pixel(method, prec, W, H, L):

@@ -59,8 +59,9 @@ def _err(D, fr):
     (svk.SVK_METHOD_BASIS, svk.SVK_PREC_FP16X3, TOL_FP32),
     (svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16, TOL_BF16),
     (svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3, TOL_FP32),
+    (svk.SVK_METHOD_TFORM, svk.SVK_PREC_FP32, TOL_FP32),
     (svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32, TOL_FP32),
-], ids=["basis_bf16x3", "basis_fp16x3", "basis_bf16", "tform_bf16x3", "direct_fp32"])
+], ids=["basis_bf16x3", "basis_fp16x3", "basis_bf16", "tform_bf16x3", "tform_fp32", "direct_fp32"])
 def test_full_size_device_call(frame, method, prec, tol):
     fr = frame
     D = svk.svk_difference(torch.from_numpy(fr["R"]).cuda(), torch.from_numpy(fr["I"]).cuda(), fr["B"],

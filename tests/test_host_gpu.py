@@ -27,7 +27,8 @@ def _host(a, pitch=None, pinned=True):
 
 
 METHODS = [(svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3), (svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3),
-           (svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32), (svk.SVK_METHOD_BASIS, svk.SVK_PREC_FP16X3)]
+           (svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32), (svk.SVK_METHOD_BASIS, svk.SVK_PREC_FP16X3),
+           (svk.SVK_METHOD_TFORM, svk.SVK_PREC_FP32)]
 
 
 @pytest.mark.parametrize("method,prec", METHODS)

@@ -14,7 +14,7 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("prec", [svk.SVK_PREC_BF16X3, svk.SVK_PREC_FP16X3])
+@pytest.mark.parametrize("prec", [svk.SVK_PREC_BF16X3, svk.SVK_PREC_FP16X3, svk.SVK_PREC_FP32])
 @pytest.mark.parametrize("W,H,L,d,kind", [
     (256, 256, 11, 1, svk.SVK_BASIS_GAUSS),
     (300, 177, 19, 2, svk.SVK_BASIS_GAUSS),   # many output rows per block, ragged

@@ -14,16 +14,16 @@
 // Parameter order (flat FP32): per conv layer w[Cout][Cin][3][3], b[Cout]; then the
 // linear layer w[n_out][32], b[n_out].
 //
-// The three 32-channel layers run on the tensor cores (tcgen05.mma, BF16 operands, FP32
-// accumulators in TMEM) as implicit GEMMs over NHWC activations:
-//   forward      rows = output pixels, K = 9 taps x 32 input channels, N = 32 outputs;
-//   data grad    rows = input pixels,  K = 9 taps x 32 output channels (the transposed
-//                convolution: a tap contributes where the strided position is hit);
-//   weight grad  rows = 9 taps x 32 input channels (+ a row of ones for the bias),
+// Every convolution runs on the tensor cores (tcgen05.mma, BF16 operands, FP32
+// accumulators in TMEM) as an implicit GEMM over NHWC activations:
+//   forward      rows = output pixels, K = 9 taps x input channels (18, padded to 32,
+//                for the 2-channel first layer), N = 32 outputs;
+//   data grad    rows = input pixels,  K = the taps that hit the strided grid x 32 output
+//                channels (the transposed convolution; for stride 2 the rows are split
+//                into the four parity classes, which have 1, 2 or 4 such taps);
+//   weight grad  rows = 9 taps x input channels (+ a row of ones for the bias),
 //                K = output pixels (split over CTAs, partial sums reduced in a fixed
 //                order, so the gradient is deterministic), N = 32 outputs.
-// The 2-channel first layer runs forward on the FP32 pipe (18 products per output) and
-// its weight gradient on the tensor cores like the others.
 #include <cuda_bf16.h>
 
 #include "svk_common.cuh"
@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
 // (tap, input channel) plus one row of ones (the bias), K runs over the output pixels of
 // one chunk, N = 32 output channels.  Both operands are stored p-major in memory, so each
 // 8 x 8 block is transposed in registers on its way to shared memory (K-major UMMA
-// layout).  Two pipeline stages of 64 pixels; each CTA writes its chunk's partial sums.
+// layout).  Two pipeline stages (64 pixels, 128 for the first layer); each CTA writes its
+// chunk's partial sums.
 
 template <int CIN>
 struct WgShape {
@@ -470,7 +471,7 @@ __device__ __forceinline__ void transpose8(const uint4 (&r)[8], uint4 (&t)[8]) {
 // Source of the weight gradient: CIN == 32, the layer input as BF16 NHWC [B][S][S][32];
 // CIN == 2, the network input as float32 NCHW [B][2][64][64], rounded to BF16 here.
 // A unit is 8 consecutive pixels of one K chunk: since the grid side is a multiple of 8
-// and chunks start at multiples of 64, they lie in one image row.
+// and chunks start at multiples of 64 pixels, they lie in one image row.
 template <int CIN>
 __global__ void __launch_bounds__(WgShape<CIN>::THREADS, 2)
     wgrad_kernel(const void *__restrict__ src_v, const bf16 *__restrict__ dz, float *__restrict__ part, int B,

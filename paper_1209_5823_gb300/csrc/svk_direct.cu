@@ -207,8 +207,13 @@ int launch_ty(const float *R, int pitch_R, const float *I, int pitch_I, int W, i
               cudaStream_t s) {
   if (N <= 4)
     return launch_nc<4, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  if (N <= 6)  // the T-form's six stamps at degree 2
+    return launch_nc<6, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
   if (N <= 8)
     return launch_nc<8, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  if (N <= 10)  // the T-form's ten stamps at degree 3
+    return launch_nc<10, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end,
+                             s);
   if (N <= 16)
     return launch_nc<16, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end,
                              s);

@@ -509,7 +509,8 @@ def _paper_sweep(svk, torch, dev):
         row = {"W": W, "H": H}
         for name, method, prec in (("direct_fp32", svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32),
                                    ("basis_bf16x3", svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3),
-                                   ("tform_bf16x3", svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3)):
+                                   ("tform_bf16x3", svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3),
+                                   ("tform_fp32", svk.SVK_METHOD_TFORM, svk.SVK_PREC_FP32)):
             ws = torch.empty(max(1, svk.svk_workspace_size(method, prec, W, H, 49, L, d)), dtype=torch.uint8, device=dev)
             ms = _time(torch, lambda: svk.svk_difference(R, I, B, c, d, method=method, precision=prec, out=D,
                                                          workspace=ws if method else None))

@@ -59,6 +59,21 @@ bool encode_tmap_2d_f32(CUtensorMap *map, const float *base, int W, int H, int p
   return r == CUDA_SUCCESS;
 }
 
+bool encode_tmap_nhwc32_bf16(CUtensorMap *map, const void *base, int S, int B, int box_x, int box_y, int box_b,
+                             int estride) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+  cuuint64_t dims[4] = {32, (cuuint64_t)S, (cuuint64_t)S, (cuuint64_t)B};
+  cuuint64_t strides[3] = {64, (cuuint64_t)S * 64, (cuuint64_t)S * S * 64};
+  cuuint32_t box[4] = {32, (cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_b};
+  cuuint32_t estr[4] = {1, (cuuint32_t)estride, (cuuint32_t)estride, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int ScopedWorkspace::acquire(size_t bytes, void *user_ws, size_t user_bytes, cudaStream_t s) {
   if (bytes == 0) return SVK_OK;
   if (user_ws) {

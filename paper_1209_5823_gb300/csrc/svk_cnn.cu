@@ -420,6 +420,230 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
   if (warp == 0) tmem_dealloc(tmem, 32);
 }
 
+// --------------------------------- 32-channel layers, TMA-fed: forward and data grad
+// A 128-row tile covers whole rows of one image (grid side 16: 8 rows) or two whole
+// images (side 8); for the stride-2 data gradient the grid is a parity class of the
+// layer input (side G / 2), rows in class order.  For each tap one 4-D TMA load brings
+// the tile's source pixels, 32 channels each, with zero fill outside the image, into an
+// 8 KB stage in the 64-byte-swizzled K-major UMMA layout (128 rows of 64 bytes, 8-row
+// groups 512 bytes apart); two MMAs of K = 16 take the tap's channels 0-15 and 16-31
+// (start address + 32 bytes).  Sources:
+//   forward      pixel (s x + dx - 1, s y + dy - 1): traversal stride s, 9 taps;
+//   data grad    stride 1: pixel (x + 1 - dx, y + 1 - dy), 9 taps; stride 2, class
+//                (py, px): pixel (xc + (px && ix == 0), yc + (py && iy == 0)) for the
+//                class's taps dy = ty0 + 2 iy, dx = tx0 + 2 ix (1, 2 or 4 of them).
+// Warp 0 issues the loads, warp 1 the MMAs into one of two TMEM accumulators, warps 2-5
+// drain the other: forward adds the bias and applies the ReLU, data grad multiplies by
+// the ReLU mask of the layer below; both store BF16 rows of 64 bytes.
+constexpr int kTfStages = 6;
+constexpr uint32_t kTfStageBytes = 128 * 64;  // one tap's A operand
+constexpr int kTfThreads = 192;
+constexpr uint32_t kTfSmem = kTfStages * kTfStageBytes + kPackBytes + 256 + 1024;  // + barriers, alignment
+
+// K-major, 64-byte swizzle: start >> 4 | (LBO 16 B, unused) | SBO 512 B >> 4 | version 1 |
+// layout 4 (SWIZZLE_64B) at bits 61-63.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(512u >> 4) << 32) | (1ull << 46) |
+         (4ull << 61);
+}
+
+struct TfGeom {
+  int lg_c;       // log2 of the row grid side (the class grid for the stride-2 data grad)
+  int lg_g;       // log2 of the output grid side
+  int TH, NB;     // rows per tile, images per tile
+  int tpi;        // tiles per image (NB == 1)
+  int tiles_c;    // tiles per class
+  int stride;     // the layer's stride
+  int split;      // data grad with stride 2: four parity classes
+};
+
+// Tap i of a tile (in registers: the producer and MMA threads call this per tap): the
+// source offsets (ox, oy) added to (f x0, f y0), f the forward stride (1 for the data
+// grad), and the weight tap it reads.  ntaps: 9, or the class's 1, 2 or 4.
+__device__ __forceinline__ int tf_ntaps(bool split, int cls) {
+  return split ? ((cls >> 1) ? 2 : 1) * ((cls & 1) ? 2 : 1) : kTaps;
+}
+
+template <int MODE>
+__device__ __forceinline__ void tf_tap(bool split, int cls, int i, int &ox, int &oy, int &wtap) {
+  if (MODE == kFwd || !split) {
+    const int dy = i / 3, dx = i - 3 * dy;
+    ox = MODE == kFwd ? dx - 1 : 1 - dx;
+    oy = MODE == kFwd ? dy - 1 : 1 - dy;
+    wtap = i;
+  } else {
+    const int py = cls >> 1, px = cls & 1;
+    const int iy = px ? i >> 1 : i, ix = px ? i & 1 : 0;  // ndx = 2 when px
+    ox = px & (ix == 0);
+    oy = py & (iy == 0);
+    wtap = ((py ? 0 : 1) + 2 * iy) * 3 + (px ? 0 : 1) + 2 * ix;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTfThreads, 2)
+    conv_tma_kernel(const __grid_constant__ CUtensorMap src, const bf16 *__restrict__ wpack,
+                    const float *__restrict__ bias, const bf16 *__restrict__ mask, bf16 *__restrict__ out, int B,
+                    const TfGeom geo, uint32_t *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA = sm;                                  // kTfStages x 8 KB, 1024-byte aligned
+  uint8_t *sB = sm + kTfStages * kTfStageBytes;      // packed weights [36][32][16 B]
+  uint64_t *full = reinterpret_cast<uint64_t *>(sB + kPackBytes);
+  uint64_t *empty = full + kTfStages, *tfull = empty + kTfStages, *tempty = tfull + 2, *drain = tempty + 2;
+  uint32_t *slot = reinterpret_cast<uint32_t *>(drain + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int Pc = B << (2 * geo.lg_c);  // rows of one class (of the grid when not split)
+  const int ntiles = geo.split ? 4 * geo.tiles_c : geo.tiles_c;
+  const int f = MODE == kFwd ? geo.stride : 1;
+  // tile -> class, first image and first row of the class grid
+  auto tile_origin = [&](int tile, int &cls, int &b0, int &y0) {
+    cls = geo.split ? tile / geo.tiles_c : 0;
+    const int t = tile - cls * geo.tiles_c;
+    b0 = geo.NB == 1 ? t / geo.tpi : t * geo.NB;
+    y0 = geo.NB == 1 ? (t % geo.tpi) * geo.TH : 0;
+  };
+
+  {  // the packed weights (generic-proxy stores, fenced for the tensor cores below)
+    const uint4 *g = reinterpret_cast<const uint4 *>(wpack);
+    uint4 *d = reinterpret_cast<uint4 *>(sB);
+    for (int i = tid; i < (int)(kPackBytes / 16); i += kTfThreads) d[i] = __ldg(g + i);
+  }
+  if (warp == 1) {
+    tmem_alloc(slot, 64);
+    if (lane == 0) {
+      for (int i = 0; i < kTfStages; ++i) {
+        mbar_init(&full[i], 1);
+        mbar_init(&empty[i], 1);
+      }
+      for (int i = 0; i < 2; ++i) {
+        mbar_init(&tfull[i], 1);
+        mbar_init(&tempty[i], 128);
+      }
+      mbar_init(drain, 1);
+      fence_mbar_init();
+    }
+  }
+  if (warp == 0 && lane == 0) prefetch_tmap(&src);
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+
+  if (warp == 0) {
+    // ============================================================= TMA producer
+    if (lane == 0) {
+      uint32_t seq = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int cls, b0, y0;
+        tile_origin(tile, cls, b0, y0);
+        const int n = tf_ntaps(geo.split, cls);
+        for (int i = 0; i < n; ++i, ++seq) {
+          int ox, oy, wt;
+          tf_tap<MODE>(geo.split, cls, i, ox, oy, wt);
+          const int stage = seq % kTfStages;
+          if (!mbar_wait_bounded(&empty[stage], ((seq / kTfStages) & 1) ^ 1, status)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[stage], kTfStageBytes);
+          tma_load_4d(sA + stage * kTfStageBytes, &src, &full[stage], 0, ox, f * y0 + oy, b0);
+        }
+      }
+      // on the normal path the MMAs consumed every load (they waited for each); after a
+      // timeout, wait (bounded) for the last load issued before leaving
+      if (!ok && seq > 0) mbar_wait_bounded(&full[(seq - 1) % kTfStages], ((seq - 1) / kTfStages) & 1, status);
+    }
+  } else if (warp == 1) {
+    // ============================================================= MMA issuer
+    if (lane == 0) {
+      uint32_t seq = 0, tcount = 0;
+      const uint32_t a0 = smem_u32(sA), b0s = smem_u32(sB);
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
+        int cls, b0, y0;
+        tile_origin(tile, cls, b0, y0);
+        const int n = tf_ntaps(geo.split, cls);
+        const int buf = tcount & 1;
+        if (!mbar_wait_bounded(&tempty[buf], ((tcount >> 1) & 1) ^ 1, status)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + 32u * buf;
+        bool ok = true;
+        for (int i = 0; i < n; ++i, ++seq) {
+          int ox, oy, wt;
+          tf_tap<MODE>(geo.split, cls, i, ox, oy, wt);
+          const int stage = seq % kTfStages;
+          if (!mbar_wait_bounded(&full[stage], (seq / kTfStages) & 1, status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+            umma_f16(d, sdesc_sw64(a0 + stage * kTfStageBytes + 32u * k),
+                     sdesc(b0s + (uint32_t)(4 * wt + 2 * k) * 512u, 512u, 128u), kIdesc, (i > 0 || k > 0) ? 1u : 0u);
+          umma_commit(&empty[stage]);
+        }
+        if (!ok) break;
+        umma_commit(&tfull[buf]);
+      }
+      umma_commit(drain);
+      mbar_wait_bounded(drain, 0, status);
+    }
+    __syncwarp();
+  } else {
+    // ============================================================= epilogue (warps 2-5)
+    const int q = warp & 3;  // TMEM lanes 32 q .. 32 q + 31 = tile rows
+    float bv[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) bv[i] = MODE == kFwd ? __ldg(bias + i) : 0.0f;
+    uint32_t tcount = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
+      int cls, b0, y0;
+      tile_origin(tile, cls, b0, y0);
+      // output pixel of this lane's row: tiles are contiguous 128-row ranges of their class
+      const int r = ((tile - cls * geo.tiles_c) << 7) + 32 * q + lane;
+      int p = r < Pc ? r : -1;
+      if (geo.split && p >= 0) {
+        const int gc = 1 << geo.lg_c, b = r >> (2 * geo.lg_c), yc = (r >> geo.lg_c) & (gc - 1), xc = r & (gc - 1);
+        p = (((b << geo.lg_g) + 2 * yc + (cls >> 1)) << geo.lg_g) + 2 * xc + (cls & 1);
+      }
+      uint32_t mw[2][8];
+      if (MODE == kDgrad && p >= 0) {  // the ReLU mask, read while the MMAs run
+        ld_nc_v8(mask + (size_t)p * kCh, mw[0]);
+        ld_nc_v8(mask + (size_t)p * kCh + 16, mw[1]);
+      }
+      const int buf = tcount & 1;
+      if (!mbar_wait_bounded(&tfull[buf], (tcount >> 1) & 1, status)) break;
+      tc_fence_after();
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        uint32_t rr[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 32u * buf + 16u * hh, rr);
+        tmem_ld_wait();
+        if (p >= 0) {
+          uint32_t o32[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (MODE == kFwd)
+              o32[i] = pack2(fmaxf(__uint_as_float(rr[2 * i]) + bv[16 * hh + 2 * i], 0.0f),
+                             fmaxf(__uint_as_float(rr[2 * i + 1]) + bv[16 * hh + 2 * i + 1], 0.0f));
+            else
+              o32[i] = pack2(lo_f(mw[hh][i]) > 0.0f ? __uint_as_float(rr[2 * i]) : 0.0f,
+                             hi_f(mw[hh][i]) > 0.0f ? __uint_as_float(rr[2 * i + 1]) : 0.0f);
+          }
+          st_v8(out + (size_t)p * kCh + 16 * hh, o32);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[buf]);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 64);
+}
+
 // ---------------------------------------------------- weight gradient on tcgen05
 // dW^T[(tap, c)][o] = sum_p col[p][(tap, c)] dz[p][o], db[o] = sum_p dz[p][o]: rows are
 // (tap, input channel) plus one row of ones (the bias), K runs over the output pixels of
@@ -776,6 +1000,41 @@ int conv_mma(const void *src, const bf16 *wpack, const float *bias, const bf16 *
   return cuda_status(cudaGetLastError(), "network convolution");
 }
 
+// A 32-channel layer through the TMA-fed kernel.  Forward: source NHWC [B][S][S][32]
+// (the layer input), output side 2^lg_g.  Data grad: source = the layer's dz (side S),
+// output = dz of the layer below (side 2^lg_g), mask = that layer's activations.
+template <int MODE>
+int conv_tma(const bf16 *src, int S, const bf16 *wpack, const float *bias, const bf16 *mask, bf16 *out, int B,
+             int lg_g, int stride, int nsm, cudaStream_t s) {
+  TfGeom geo;
+  geo.lg_g = lg_g;
+  geo.stride = stride;
+  geo.split = MODE == kDgrad && stride == 2;
+  geo.lg_c = geo.split ? lg_g - 1 : lg_g;
+  const int gc = 1 << geo.lg_c;
+  if (gc >= 16) {  // whole rows: 128 / gc of them per tile
+    geo.TH = 128 / gc;
+    geo.NB = 1;
+    geo.tpi = gc / geo.TH;
+  } else {  // whole images: 128 / gc^2 of them per tile
+    geo.TH = gc;
+    geo.NB = 128 / (gc * gc);
+    geo.tpi = 1;
+  }
+  geo.tiles_c = ((B << (2 * geo.lg_c)) + 127) >> 7;
+  const int f = MODE == kFwd ? stride : 1;  // traversal stride of the source
+  CUtensorMap tm;
+  if (!encode_tmap_nhwc32_bf16(&tm, src, S, B, f * gc, f * geo.TH, geo.NB, f))
+    return set_error(SVK_ERR_CUDA, "network tensor map refused");
+  cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kTfSmem);
+  if (e != cudaSuccess) return cuda_status(e, "network convolution attributes");
+  const int ntiles = geo.split ? 4 * geo.tiles_c : geo.tiles_c;
+  const int grid = ntiles < 2 * nsm ? ntiles : 2 * nsm;  // two CTAs per SM
+  conv_tma_kernel<MODE><<<grid, kTfThreads, kTfSmem, s>>>(tm, wpack, bias, mask, out, B, geo, device_status_word());
+  return cuda_status(cudaGetLastError(), "network convolution");
+}
+
 // A layer's partial weight-gradient sums (reduced for all layers by wgrad_reduce_kernel).
 template <int CIN>
 int wgrad(const void *src, const bf16 *dz, float *part, int B, int lg_s, int lg_g, int stride, cudaStream_t s) {
@@ -824,7 +1083,7 @@ int forward(const float *x, const Layout &L, const Bufs &b, int B, int n_out, fl
             const float *target = nullptr, float *loss = nullptr) {
   int st = conv_mma<kFwd1>(x, b.wf[0], b.wq + L.b[0], nullptr, b.act[0], B, kLgIn[0], kLgOut[0], kStride[0], nsm, s);
   for (int li = 1; li < kLayers && st == SVK_OK; ++li)
-    st = conv_mma<kFwd>(b.act[li - 1], b.wf[li], b.wq + L.b[li], nullptr, b.act[li], B, kLgIn[li], kLgOut[li],
+    st = conv_tma<kFwd>(b.act[li - 1], 1 << kLgIn[li], b.wf[li], b.wq + L.b[li], nullptr, b.act[li], B, kLgOut[li],
                         kStride[li], nsm, s);
   if (st != SVK_OK) return st;
   pool_fc_kernel<<<B, 64, 0, s>>>(b.act[kLayers - 1], b.wq + L.fcw, b.wq + L.fcb, b.pooled, out, n_out, target,
@@ -957,7 +1216,7 @@ int cnn_gradient(const float *params, const float *x, const float *target, int B
   for (int li = kLayers - 1; li >= 1; --li) {
     st = wgrad<kCh>(b.act[li - 1], b.dz[li], b.part[li], B, kLgIn[li], kLgOut[li], kStride[li], s);
     if (st == SVK_OK)
-      st = conv_mma<kDgrad>(b.dz[li], b.wd[li], nullptr, b.act[li - 1], b.dz[li - 1], B, kLgOut[li], kLgIn[li],
+      st = conv_tma<kDgrad>(b.dz[li], 1 << kLgOut[li], b.wd[li], nullptr, b.act[li - 1], b.dz[li - 1], B, kLgIn[li],
                             kStride[li], nsm, s);
     if (st != SVK_OK) return st;
   }

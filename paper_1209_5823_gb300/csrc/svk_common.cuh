@@ -21,6 +21,12 @@ const char *last_error();
 bool encode_tmap_2d_f32(CUtensorMap *map, const float *base, int W, int H, int pitch,
                         int box_w, int box_h);
 
+// 4-D BF16 tensor map over NHWC activations [B][S][S][32] (64-byte pixels), 64-byte
+// swizzle, zero fill out of bounds; the box is 32 channels x box_x x box_y x box_b with
+// traversal stride `estride` along x and y.  False when the driver refuses.
+bool encode_tmap_nhwc32_bf16(CUtensorMap *map, const void *base, int S, int B, int box_x, int box_y, int box_b,
+                             int estride);
+
 // Device-memory allocation on a stream for calls that received no workspace.
 struct ScopedWorkspace {
   void *ptr = nullptr;
@@ -121,6 +127,17 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
       "[%4];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 4-D tiled TMA load of one box into shared memory, completing on `bar` (coordinates
+// innermost first; the innermost one must be a multiple of 16 bytes).
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
 

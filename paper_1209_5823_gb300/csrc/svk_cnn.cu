@@ -43,7 +43,6 @@ constexpr int kLgOut[kLayers] = {5, 4, 3, 3};  // log2 kHout
 // Packed UMMA B operand of a 32-channel layer: K = tap * 32 + channel (288), 32 rows, in
 // the K-major no-swizzle layout: 36 core-matrix columns of [32 rows][8 BF16].
 constexpr int kK = kTaps * kCh;            // 288
-constexpr int kKChunks = kK / 8;           // 36
 constexpr int kPack = kK * kCh;            // 9216 BF16 per packed operand
 constexpr uint32_t kPackBytes = kPack * 2; // 18,432
 constexpr int kPack0 = 4 * kCh * 8;         // first layer: K = 18 padded to 32, 1024 BF16
@@ -173,52 +172,35 @@ __global__ void pack_kernel(const float *__restrict__ p, float *__restrict__ wq,
   }
 }
 
-// ----------------------------------------------------- convolutions on tcgen05
-// kFwd / kDgrad: the 32-channel layers (K = 9 taps x 32 channels, 36 chunks of 8).
-// kFwd1: the first layer (K = 9 taps x 2 channels = 18, zero-padded to 32: 4 chunks),
-// its A rows gathered from the float32 NCHW input and rounded to BF16.
-enum ConvMode { kFwd = 0, kDgrad = 1, kFwd1 = 2 };
+// ------------------------------------------------ first layer forward on tcgen05
+// K = 9 taps x 2 channels = 18 (k = 2 tap + c), zero-padded to 32 (4 chunks of 8): each
+// thread gathers one output pixel's 18 inputs from the float32 NCHW stamps, rounds them
+// to BF16 and writes its A row; the next tile's gather is in flight while the current
+// tile's MMAs and epilogue run.  128 threads: the epilogue warp q drains TMEM lanes
+// 32 q .. 32 q + 31 (bias, ReLU, BF16 NHWC rows of 64 bytes).
+constexpr int kC1Threads = 128;
+constexpr int kC1Chunks = 4;
+constexpr uint32_t kC1ABytes = kC1Chunks * 128 * 16;  // [4][128 rows][16 B]
+constexpr uint32_t kC1BBytes = kC1Chunks * kCh * 16;  // [4][32 rows][16 B]
+constexpr uint32_t kC1Smem = kC1ABytes + kC1BBytes + 64;
 
-template <int MODE>
-struct ConvShape {
-  static constexpr int KC = MODE == kFwd1 ? 4 : kKChunks;  // K chunks of 8 BF16
-  static constexpr int THREADS = MODE == kFwd1 ? 128 : 256;  // 1 or 2 threads per A row
-  static constexpr int MIN_CTAS = MODE == kFwd1 ? 6 : 2;
-  static constexpr uint32_t A_BYTES = KC * 128 * 16;  // [KC][128 rows][16 B]
-  static constexpr uint32_t B_BYTES = KC * kCh * 16;  // [KC][32 rows][16 B]
-  static constexpr uint32_t SMEM = A_BYTES + B_BYTES + 64;
-};
-
-// One 128-row tile per iteration of a persistent loop.  Rows are pixels of the grid G
-// (side 2^lg_g); source pixels lie on the grid S (side 2^lg_s).  For the 32-channel
-// modes a row's K chunk (tap, 8 channels) is 16 contiguous bytes of the NHWC BF16 source:
-//   forward  (grid G = output): source pixel (s y + dy - 1, s x + dx - 1);
-//   data grad (grid G = layer input): source pixel ((y + 1 - dy) / s, (x + 1 - dx) / s)
-//            for the taps where both divisions are exact.  With s = 2 those taps depend
-//            only on the parities of (y, x): dy = 1 for even y, dy in {0, 2} for odd y
-//            (likewise dx), so the rows are split into the four parity classes (tiles
-//            never mix classes) and a tile's K holds only its class's 1, 2 or 4 taps.
-// Epilogue: forward adds the bias and applies the ReLU; data grad multiplies by the
-// ReLU mask of the layer below (act > 0).  Both store BF16 NHWC rows of 32 channels.
-template <int MODE>
-__global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN_CTAS)
-    conv_mma_kernel(const void *__restrict__ src_v, const bf16 *__restrict__ wpack, const float *__restrict__ bias,
-                    const bf16 *__restrict__ mask, bf16 *__restrict__ out, int B, int lg_s, int lg_g, int stride,
-                    uint32_t *status) {
-  using Sh = ConvShape<MODE>;
-  constexpr int NH = Sh::THREADS == 256 ? 1 : 2;  // 16-column halves per epilogue thread
+__global__ void __launch_bounds__(kC1Threads, 6)
+    conv1_mma_kernel(const float *__restrict__ x, const bf16 *__restrict__ wpack, const float *__restrict__ bias,
+                     bf16 *__restrict__ out, int B, uint32_t *status) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t *sA = smem;
-  uint8_t *sB = smem + Sh::A_BYTES;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Sh::A_BYTES + Sh::B_BYTES);
+  uint8_t *sB = smem + kC1ABytes;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kC1ABytes + kC1BBytes);
   uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int S = 1 << lg_s, G = 1 << lg_g;
+  constexpr int S = 64, lg_g = 5, G = 32;  // 64 x 64 inputs, 32 x 32 outputs, stride 2
+  const int P = B << (2 * lg_g);
+  const int ntiles = (P + 127) >> 7;
 
   {  // the packed weights, once
     const uint4 *g = reinterpret_cast<const uint4 *>(wpack);
     uint4 *d = reinterpret_cast<uint4 *>(sB);
-    for (int i = tid; i < (int)(Sh::B_BYTES / 16); i += Sh::THREADS) d[i] = __ldg(g + i);
+    for (int i = tid; i < (int)(kC1BBytes / 16); i += kC1Threads) d[i] = __ldg(g + i);
   }
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -230,188 +212,60 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
   tc_fence_after();
   const uint32_t tmem = *slot;
   const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
+  float bv[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) bv[i] = __ldg(bias + i);
 
-  // A build: kFwd1, one row per thread.  Otherwise lane l of warp w takes 16-byte chunk
-  // c8 = l / 8 of rows 8 w + l % 8 and that + 64: a warp's load covers 8 whole 64-byte
-  // source pixels, and each group of 8 lanes (one shared-memory wavefront for 16-byte
-  // stores) writes 8 different rows, i.e. 8 different bank groups.
-  const int m = tid & 127, c8 = lane >> 3, rr = 8 * warp + (lane & 7);
-  const int q = warp & 3, h0 = NH == 1 ? warp >> 2 : 0;  // epilogue: TMEM lane quadrant, first half
-  float bv[16 * NH];
+  float f[2 * kTaps];  // row tid of a tile: k = 2 tap + c
+  auto load = [&](int tile) {
+    const int p = (tile << 7) + tid;
+    const bool valid = p < P;
+    const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), xo = p & (G - 1);
 #pragma unroll
-  for (int i = 0; i < 16 * NH; ++i) bv[i] = MODE != kDgrad ? __ldg(bias + 16 * h0 + i) : 0.0f;
-
-  // Data grad with stride 2: class c = 2 (y & 1) + (x & 1) over the half grid, each
-  // class's rows in their own tiles; every other mode: one class, the whole grid.
-  const bool split = MODE == kDgrad && stride == 2;
-  const int lg_c = split ? lg_g - 1 : lg_g;  // class grid side 2^lg_c
-  const int Pc = B << (2 * lg_c);
-  const int tiles_c = (Pc + 127) >> 7;
-  const int ntiles = split ? 4 * tiles_c : tiles_c;
-  struct Tile {
-    int t;             // tile within its class
-    int py, px;        // class parities
-    int ty0, ndy;      // class taps dy in {ty0, ty0 + 2}, ndy of them: {1} for even y, {0, 2} for odd
-    int tx0, ndx;      // likewise for dx
-  };
-  auto tile_info = [&](int tile) {
-    Tile ti;
-    const int cls = split ? tile / tiles_c : 0;
-    ti.t = tile - cls * tiles_c;
-    ti.py = cls >> 1;
-    ti.px = cls & 1;
-    ti.ty0 = ti.py ? 0 : 1;
-    ti.ndy = ti.py ? 2 : 1;
-    ti.tx0 = ti.px ? 0 : 1;
-    ti.ndx = ti.px ? 2 : 1;
-    return ti;
-  };
-  auto row_pixel = [&](const Tile &ti, int r) -> int {  // grid pixel of class row r, -1 past the end
-    r += ti.t << 7;
-    if (r >= Pc) return -1;
-    if (!split) return r;
-    const int b = r >> (2 * lg_c), yc = (r >> lg_c) & ((1 << lg_c) - 1), xc = r & ((1 << lg_c) - 1);
-    return (((b << lg_g) + 2 * yc + ti.py) << lg_g) + 2 * xc + ti.px;
-  };
-
-  // ---- the A operand of a tile, loaded into registers (issued early) and stored later
-  uint4 v[2][kTaps];   // 32-channel modes: [row j][tap slot]
-  float f[2 * kTaps];  // first layer: k = 2 tap + c of row m
-  auto load = [&](const Tile &ti) {
-    if constexpr (MODE == kFwd1) {
-      const int p = row_pixel(ti, m);
-      const bool valid = p >= 0;
-      const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), x = p & (G - 1);
-      const float *src = static_cast<const float *>(src_v);
+    for (int t = 0; t < kTaps; ++t) {
+      const int yy = 2 * y + t / 3 - 1, xx = 2 * xo + t % 3 - 1;
+      const bool ok = valid && yy >= 0 && yy < S && xx >= 0 && xx < S;
 #pragma unroll
-      for (int t = 0; t < kTaps; ++t) {
-        const int yy = stride * y + t / 3 - 1, xx = stride * x + t % 3 - 1;
-        const bool ok = valid && yy >= 0 && yy < S && xx >= 0 && xx < S;
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-          f[2 * t + c] = ok ? __ldg(src + (((((size_t)b * 2 + c) << lg_s) + yy) << lg_s) + xx) : 0.0f;
-      }
-    } else {
-      const bf16 *src = static_cast<const bf16 *>(src_v);
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int p = row_pixel(ti, rr + 64 * j);
-        const bool valid = p >= 0;
-        const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), x = p & (G - 1);
-        auto chunk = [&](int yy, int xx, bool ok) -> uint4 {  // 16 bytes c8 of a source pixel
-          const size_t pix = ((((size_t)b << lg_s) + (ok ? yy : 0)) << lg_s) + (ok ? xx : 0);
-          return ok ? __ldg(reinterpret_cast<const uint4 *>(src + pix * kCh) + c8) : make_uint4(0, 0, 0, 0);
-        };
-        if (MODE == kDgrad && split) {
-          // y = 2 yc + py: tap dy = ty0 + 2 iy reads source row (y + 1 - dy) / 2, which is
-          // yc, or yc + 1 for (odd y, dy = 0); likewise for x.  Slot 2 iy + ix.
-#pragma unroll
-          for (int iy = 0; iy < 2; ++iy)
-#pragma unroll
-            for (int ix = 0; ix < 2; ++ix) {
-              const int yy = (y >> 1) + (ti.py & (iy == 0)), xx = (x >> 1) + (ti.px & (ix == 0));
-              v[j][2 * iy + ix] = chunk(yy, xx, valid && iy < ti.ndy && ix < ti.ndx && yy < S && xx < S);
-            }
-        } else {
-#pragma unroll
-          for (int t = 0; t < kTaps; ++t) {
-            const int dy = t / 3, dx = t % 3;
-            // forward: source (s y + dy - 1, s x + dx - 1); data grad with s = 1: (y + 1 - dy, x + 1 - dx)
-            const int yy = MODE == kFwd ? stride * y + dy - 1 : y + 1 - dy;
-            const int xx = MODE == kFwd ? stride * x + dx - 1 : x + 1 - dx;
-            v[j][t] = chunk(yy, xx, valid && yy >= 0 && yy < S && xx >= 0 && xx < S);
-          }
-        }
-      }
+      for (int c = 0; c < 2; ++c) f[2 * t + c] = ok ? __ldg(x + ((((size_t)b * 2 + c) * S + yy) * S) + xx) : 0.0f;
     }
   };
-  auto store = [&](const Tile &ti) {
-    if constexpr (MODE == kFwd1) {  // row m: k = 2 tap + c for k < 18, then zeros
-      uint8_t *row = sA + (uint32_t)m * 16u;
-      *reinterpret_cast<uint4 *>(row) =
-          make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
-      *reinterpret_cast<uint4 *>(row + 2048) =
-          make_uint4(pack2(f[8], f[9]), pack2(f[10], f[11]), pack2(f[12], f[13]), pack2(f[14], f[15]));
-      *reinterpret_cast<uint4 *>(row + 4096) = make_uint4(pack2(f[16], f[17]), 0u, 0u, 0u);
-      *reinterpret_cast<uint4 *>(row + 6144) = make_uint4(0u, 0u, 0u, 0u);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        uint8_t *row = sA + (uint32_t)(rr + 64 * j) * 16u + (uint32_t)c8 * 2048u;
-        if (MODE == kDgrad && split) {  // K chunk (class tap i = iy ndx + ix, c8)
-#pragma unroll
-          for (int iy = 0; iy < 2; ++iy)
-#pragma unroll
-            for (int ix = 0; ix < 2; ++ix)
-              if (iy < ti.ndy && ix < ti.ndx)
-                *reinterpret_cast<uint4 *>(row + (uint32_t)(4 * (iy * ti.ndx + ix)) * 2048u) = v[j][2 * iy + ix];
-        } else {
-#pragma unroll
-          for (int t = 0; t < kTaps; ++t) *reinterpret_cast<uint4 *>(row + (uint32_t)(4 * t) * 2048u) = v[j][t];
-        }
-      }
-    }
-  };
-
   uint32_t it = 0;
-  if (blockIdx.x < ntiles) load(tile_info(blockIdx.x));
+  if (blockIdx.x < ntiles) load(blockIdx.x);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const Tile ti = tile_info(tile);
-    store(ti);  // the MMAs of the previous tile have completed: A is free
+    uint8_t *row = sA + (uint32_t)tid * 16u;  // the MMAs of the previous tile have completed
+    *reinterpret_cast<uint4 *>(row) =
+        make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+    *reinterpret_cast<uint4 *>(row + 2048) =
+        make_uint4(pack2(f[8], f[9]), pack2(f[10], f[11]), pack2(f[12], f[13]), pack2(f[14], f[15]));
+    *reinterpret_cast<uint4 *>(row + 4096) = make_uint4(pack2(f[16], f[17]), 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(row + 6144) = make_uint4(0u, 0u, 0u, 0u);
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      if (MODE == kDgrad && split) {  // the class's taps: A chunks 4 i + c8, B chunks 4 tap + c8
-        for (int i = 0; i < ti.ndy * ti.ndx; ++i) {
-          const int iy = ti.ndx == 2 ? i >> 1 : i, ix = ti.ndx == 2 ? i & 1 : 0;
-          const int tap = (ti.ty0 + 2 * iy) * 3 + ti.tx0 + 2 * ix;
 #pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const uint64_t a = sdesc(aBase + (uint32_t)(4 * i + 2 * k) * 2048u, 2048u, 128u);
-            const uint64_t bd = sdesc(bBase + (uint32_t)(4 * tap + 2 * k) * 512u, 512u, 128u);
-            umma_f16(tmem, a, bd, kIdesc, (i > 0 || k > 0) ? 1u : 0u);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < Sh::KC / 2; ++k) {
-          const uint64_t a = sdesc(aBase + (uint32_t)k * 2u * 2048u, 2048u, 128u);
-          const uint64_t bd = sdesc(bBase + (uint32_t)k * 2u * 512u, 512u, 128u);
-          umma_f16(tmem, a, bd, kIdesc, k > 0 ? 1u : 0u);
-        }
-      }
+      for (int k = 0; k < kC1Chunks / 2; ++k)
+        umma_f16(tmem, sdesc(aBase + (uint32_t)k * 2u * 2048u, 2048u, 128u),
+                 sdesc(bBase + (uint32_t)k * 2u * 512u, 512u, 128u), kIdesc, k > 0 ? 1u : 0u);
       umma_commit(bar);
     }
-    // the next tile's loads are in flight while the MMAs and this tile's epilogue run
-    if (tile + (int)gridDim.x < ntiles) load(tile_info(tile + gridDim.x));
-    // ---- epilogue: row 32 q + lane of the tile, output columns 16 h .. 16 h + 15
-    const int pr = row_pixel(ti, 32 * q + lane);
-    uint32_t mw[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    if (MODE == kDgrad && pr >= 0) ld_nc_v8(mask + (size_t)pr * kCh + 16 * h0, mw);  // the ReLU mask
+    if (tile + (int)gridDim.x < ntiles) load(tile + gridDim.x);  // in flight during the MMAs and epilogue
     const bool ok = mbar_wait_bounded(bar, it & 1u, status);
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
+    const int pr = (tile << 7) + 32 * warp + lane;
 #pragma unroll
-    for (int hh = 0; hh < NH; ++hh) {
-      const int h = h0 + hh;
+    for (int hh = 0; hh < 2; ++hh) {
       uint32_t r[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h), r);
+      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * hh), r);
       tmem_ld_wait();
-      if (pr >= 0) {
+      if (pr < P) {
         uint32_t o32[8];
-        if (MODE != kDgrad) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            o32[i] = pack2(fmaxf(__uint_as_float(r[2 * i]) + bv[16 * hh + 2 * i], 0.0f),
-                           fmaxf(__uint_as_float(r[2 * i + 1]) + bv[16 * hh + 2 * i + 1], 0.0f));
-        } else {
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            o32[i] = pack2(lo_f(mw[i]) > 0.0f ? __uint_as_float(r[2 * i]) : 0.0f,
-                           hi_f(mw[i]) > 0.0f ? __uint_as_float(r[2 * i + 1]) : 0.0f);
-        }
-        st_v8(out + (size_t)pr * kCh + 16 * h, o32);
+        for (int i = 0; i < 8; ++i)
+          o32[i] = pack2(fmaxf(__uint_as_float(r[2 * i]) + bv[16 * hh + 2 * i], 0.0f),
+                         fmaxf(__uint_as_float(r[2 * i + 1]) + bv[16 * hh + 2 * i + 1], 0.0f));
+        st_v8(out + (size_t)pr * kCh + 16 * hh, o32);
       }
     }
     tc_fence_before();
@@ -419,6 +273,8 @@ __global__ void __launch_bounds__(ConvShape<MODE>::THREADS, ConvShape<MODE>::MIN
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 32);
 }
+
+enum ConvMode { kFwd = 0, kDgrad = 1 };
 
 // --------------------------------- 32-channel layers, TMA-fed: forward and data grad
 // A 128-row tile covers whole rows of one image (grid side 16: 8 rows) or two whole
@@ -986,18 +842,13 @@ int sm_count() {
   return n > 0 ? n : 1;
 }
 
-template <int MODE>
-int conv_mma(const void *src, const bf16 *wpack, const float *bias, const bf16 *mask, bf16 *out, int B, int lg_s,
-             int lg_g, int stride, int nsm, cudaStream_t s) {
-  using Sh = ConvShape<MODE>;
-  cudaError_t e = cudaFuncSetAttribute(conv_mma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Sh::SMEM);
-  if (e != cudaSuccess) return cuda_status(e, "network convolution attributes");
-  const int ntiles = ((B << (2 * lg_g)) + 127) >> 7;
-  const int grid = ntiles < Sh::MIN_CTAS * nsm ? ntiles : Sh::MIN_CTAS * nsm;
-  conv_mma_kernel<MODE><<<grid, Sh::THREADS, Sh::SMEM, s>>>(src, wpack, bias, mask, out, B, lg_s, lg_g, stride,
-                                                            device_status_word());
-  return cuda_status(cudaGetLastError(), "network convolution");
+int conv1(const float *x, const bf16 *wpack, const float *bias, bf16 *out, int B, int nsm, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(conv1_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kC1Smem);
+  if (e != cudaSuccess) return cuda_status(e, "network first-layer attributes");
+  const int ntiles = ((B << 10) + 127) >> 7;
+  const int grid = ntiles < 6 * nsm ? ntiles : 6 * nsm;
+  conv1_mma_kernel<<<grid, kC1Threads, kC1Smem, s>>>(x, wpack, bias, out, B, device_status_word());
+  return cuda_status(cudaGetLastError(), "network first layer");
 }
 
 // A 32-channel layer through the TMA-fed kernel.  Forward: source NHWC [B][S][S][32]
@@ -1081,7 +932,7 @@ int pack(const float *params, const Layout &L, const Bufs &b, cudaStream_t s) {
 // x -> act[0..3] -> pooled -> out (parameters already packed)
 int forward(const float *x, const Layout &L, const Bufs &b, int B, int n_out, float *out, int nsm, cudaStream_t s,
             const float *target = nullptr, float *loss = nullptr) {
-  int st = conv_mma<kFwd1>(x, b.wf[0], b.wq + L.b[0], nullptr, b.act[0], B, kLgIn[0], kLgOut[0], kStride[0], nsm, s);
+  int st = conv1(x, b.wf[0], b.wq + L.b[0], b.act[0], B, nsm, s);
   for (int li = 1; li < kLayers && st == SVK_OK; ++li)
     st = conv_tma<kFwd>(b.act[li - 1], 1 << kLgIn[li], b.wf[li], b.wq + L.b[li], nullptr, b.act[li], B, kLgOut[li],
                         kStride[li], nsm, s);

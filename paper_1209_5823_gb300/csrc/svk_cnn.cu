@@ -72,11 +72,12 @@ Layout param_layout(int n_out) {
 }
 
 // Weight-gradient split: K (the output pixels of a layer, a multiple of 64) in chunks of
-// whole pipeline stages (64 pixels for a 32-channel layer, 128 for the first layer),
-// about 304 chunks (two CTAs on each of 152 SMs), at least two stages each for a
-// 32-channel layer.  Depends on the batch only, so the gradient is deterministic.
+// whole pipeline stages (64 pixels for a 32-channel layer, 128 for the first layer):
+// about 152 chunks of at least two stages for a 32-channel layer (one CTA on each of 152
+// SMs), about 304 for the first layer (two per SM).  Depends on the batch only, so the
+// gradient is deterministic.
 int wg_stage_px(int cin) { return cin == kCh ? 64 : 128; }
-int wg_target(int) { return 304; }
+int wg_target(int cin) { return cin == kCh ? 152 : 304; }
 int wg_per_chunk(int P, int cin) {
   const int px = wg_stage_px(cin), stages = (P + px - 1) / px;
   const int per = (stages + wg_target(cin) - 1) / wg_target(cin);
@@ -500,6 +501,154 @@ __global__ void __launch_bounds__(kTfThreads, 2)
   if (warp == 1) tmem_dealloc(tmem, 64);
 }
 
+// ------------------------------ weight gradient of the 32-channel layers, TMA-fed
+// dW^T[(tap, c)][o] = sum_p col[p][(tap, c)] dz[p][o] with both operands MN-major: a stage
+// of 64 output pixels holds, per tap, the 64 source pixels' 32 channels (one 4-D TMA
+// load, traversal stride s, zero fill) as a [64 pixels][64 B] tile in the 64-byte swizzle,
+// i.e. 8 atoms of 8 K rows (pixels) x 32 M elements; taps follow each other 4 KB apart
+// (the LBO between M atoms), 8-pixel groups are 512 B apart (the SBO).  Tiles 9-11 are
+// constant: the bias row (element 0 of every pixel = 1) and zeros, so M-tile 2 (rows
+// 256-383) is tap 8, the bias row and padding.  The dz tile [64 pixels][32 o] is the B
+// operand in the same layout.  Warp 0 loads, warp 1 issues 3 M-tiles x 4 K-steps per
+// stage, warps 2-5 write the chunk's partial sums from TMEM.
+constexpr int kWtStages = 3;
+constexpr uint32_t kWtTile = 64 * 64;           // [64 pixels][64 B]
+constexpr uint32_t kWtStage = 13 * kWtTile;     // taps 0-8, bias tile, two zero tiles, dz tile
+constexpr int kWtThreads = 192;
+constexpr uint32_t kWtSmem = kWtStages * kWtStage + 256 + 1024;
+constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);  // A and B MN-major
+
+// MN-major, 64-byte swizzle: start >> 4 | LBO (between 32-element MN atoms) | SBO 512 B
+// (between 8-row K groups) | version 1 | layout 4 (SWIZZLE_64B).
+__device__ __forceinline__ uint64_t sdesc_mn_sw64(uint32_t saddr, uint32_t lbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)(512u >> 4) << 32) | (1ull << 46) | (4ull << 61);
+}
+
+struct WtGeom {
+  int lg_g, TH, stride, per;  // dz grid side 2^lg_g (rows of 64 / side pixels per stage), stages per chunk
+};
+
+__global__ void __launch_bounds__(kWtThreads, 1)
+    wgrad_tma_kernel(const __grid_constant__ CUtensorMap act, const __grid_constant__ CUtensorMap dzm,
+                     float *__restrict__ part, int B, const WtGeom geo, uint32_t *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + kWtStages * kWtStage);
+  uint64_t *empty = full + kWtStages, *tdone = empty + kWtStages;
+  uint32_t *slot = reinterpret_cast<uint32_t *>(tdone + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int total = B << (2 * geo.lg_g - 6);  // stages of 64 pixels in the layer
+  const int s_begin = blockIdx.x * geo.per, s_end = min(total, s_begin + geo.per);
+  const int nst = s_end - s_begin;
+
+  // constant tiles 9-11 of every stage: element 0 of each pixel row = 1 (BF16), rest 0; in
+  // the 64-byte swizzle a row's 16-byte chunk c sits at chunk c ^ ((row >> 1) & 3)
+  for (int i = tid; i < kWtStages * 3 * (int)(kWtTile / 16); i += kWtThreads) {
+    const int st = i / (3 * (kWtTile / 16)), rem = i % (3 * (kWtTile / 16));
+    const int tile = 9 + rem / (kWtTile / 16), q16 = rem % (kWtTile / 16), row = q16 >> 2, chunk = q16 & 3;
+    const bool one = tile == 9 && chunk == ((row >> 1) & 3);  // logical chunk 0 of the row
+    *reinterpret_cast<uint4 *>(sm + st * kWtStage + tile * kWtTile + q16 * 16) =
+        make_uint4(one ? 0x3F80u : 0u, 0u, 0u, 0u);
+  }
+  if (warp == 1) {
+    tmem_alloc(slot, 128);
+    if (lane == 0) {
+      for (int i = 0; i < kWtStages; ++i) {
+        mbar_init(&full[i], 1);
+        mbar_init(&empty[i], 1);
+      }
+      mbar_init(tdone, 1);
+      fence_mbar_init();
+    }
+  }
+  if (warp == 0 && lane == 0) {
+    prefetch_tmap(&act);
+    prefetch_tmap(&dzm);
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const int G = 1 << geo.lg_g;
+
+  if (warp == 0) {
+    // ============================================================= TMA producer
+    if (lane == 0) {
+      bool ok = true;
+      int k = 0;
+      for (; k < nst; ++k) {
+        const int stage = k % kWtStages;
+        if (!mbar_wait_bounded(&empty[stage], ((k / kWtStages) & 1) ^ 1, status)) {
+          ok = false;
+          break;
+        }
+        const int p0 = (s_begin + k) << 6, b = p0 >> (2 * geo.lg_g), y0 = (p0 >> geo.lg_g) & (G - 1);
+        uint8_t *base = sm + stage * kWtStage;
+        mbar_arrive_expect_tx(&full[stage], 10 * kWtTile);
+        for (int t = 0; t < kTaps; ++t)
+          tma_load_4d(base + t * kWtTile, &act, &full[stage], 0, t % 3 - 1, geo.stride * y0 + t / 3 - 1, b);
+        tma_load_4d(base + 12 * kWtTile, &dzm, &full[stage], 0, 0, y0, b);
+      }
+      if (!ok && k > 0) mbar_wait_bounded(&full[(k - 1) % kWtStages], ((k - 1) / kWtStages) & 1, status);
+    }
+  } else if (warp == 1) {
+    // ============================================================= MMA issuer
+    if (lane == 0) {
+      bool ok = true;
+      const uint32_t a0 = smem_u32(sm);
+      for (int k = 0; k < nst && ok; ++k) {
+        const int stage = k % kWtStages;
+        if (!mbar_wait_bounded(&full[stage], (k / kWtStages) & 1, status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = a0 + stage * kWtStage;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)  // 16 pixels = two 8-row K groups per MMA
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            umma_f16(tmem + 32u * i, sdesc_mn_sw64(base + (uint32_t)(4 * i) * kWtTile + 1024u * ks, kWtTile),
+                     sdesc_mn_sw64(base + 12u * kWtTile + 1024u * ks, kWtTile), kIdescMN,
+                     (k > 0 || ks > 0) ? 1u : 0u);
+        umma_commit(&empty[stage]);
+      }
+      umma_commit(tdone);  // covers every MMA issued
+      mbar_wait_bounded(tdone, 0, status);
+    }
+    __syncwarp();
+  } else {
+    // ============================================================= epilogue (warps 2-5)
+    const int q = warp & 3;
+    const bool ok = nst > 0 && mbar_wait_bounded(tdone, 0, status);
+    if (ok) {
+      tc_fence_after();
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int row = 128 * i + 32 * q + lane;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 32u * i + 16u * hh, r);
+          tmem_ld_wait();
+          if (row <= kTaps * kCh) {
+            float *dst = part + ((size_t)blockIdx.x * (kTaps * kCh + 1) + row) * kCh + 16 * hh;
+            const uint32_t lo[8] = {r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7]};
+            const uint32_t hi[8] = {r[8], r[9], r[10], r[11], r[12], r[13], r[14], r[15]};
+            st_v8(dst, lo);
+            st_v8(dst + 8, hi);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 128);
+}
+
 // ---------------------------------------------------- weight gradient on tcgen05
 // dW^T[(tap, c)][o] = sum_p col[p][(tap, c)] dz[p][o], db[o] = sum_p dz[p][o]: rows are
 // (tap, input channel) plus one row of ones (the bias), K runs over the output pixels of
@@ -886,6 +1035,26 @@ int conv_tma(const bf16 *src, int S, const bf16 *wpack, const float *bias, const
   return cuda_status(cudaGetLastError(), "network convolution");
 }
 
+// A 32-channel layer's partial weight-gradient sums through the TMA-fed kernel: source
+// = the layer input (side S), dz = the layer's output gradient (side 2^lg_g).
+int wgrad_tma(const bf16 *src, int S, const bf16 *dz, float *part, int B, int lg_g, int stride, cudaStream_t s) {
+  const int G = 1 << lg_g, P = B << (2 * lg_g);
+  WtGeom geo;
+  geo.lg_g = lg_g;
+  geo.TH = 64 / G;
+  geo.stride = stride;
+  geo.per = wg_per_chunk(P, kCh) / 64;
+  const int nch = wg_nchunks(P, kCh);
+  CUtensorMap ta, td;
+  if (!encode_tmap_nhwc32_bf16(&ta, src, S, B, stride * G, stride * geo.TH, 1, stride) ||
+      !encode_tmap_nhwc32_bf16(&td, dz, G, B, G, geo.TH, 1, 1))
+    return set_error(SVK_ERR_CUDA, "network tensor map refused");
+  cudaError_t e = cudaFuncSetAttribute(wgrad_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWtSmem);
+  if (e != cudaSuccess) return cuda_status(e, "network weight-gradient attributes");
+  wgrad_tma_kernel<<<nch, kWtThreads, kWtSmem, s>>>(ta, td, part, B, geo, device_status_word());
+  return cuda_status(cudaGetLastError(), "network weight gradient");
+}
+
 // A layer's partial weight-gradient sums (reduced for all layers by wgrad_reduce_kernel).
 template <int CIN>
 int wgrad(const void *src, const bf16 *dz, float *part, int B, int lg_s, int lg_g, int stride, cudaStream_t s) {
@@ -1065,7 +1234,7 @@ int cnn_gradient(const float *params, const float *x, const float *target, int B
                                                                 n_out);
   if ((st = cuda_status(cudaGetLastError(), "network output gradient")) != SVK_OK) return st;
   for (int li = kLayers - 1; li >= 1; --li) {
-    st = wgrad<kCh>(b.act[li - 1], b.dz[li], b.part[li], B, kLgIn[li], kLgOut[li], kStride[li], s);
+    st = wgrad_tma(b.act[li - 1], 1 << kLgIn[li], b.dz[li], b.part[li], B, kLgOut[li], kStride[li], s);
     if (st == SVK_OK)
       st = conv_tma<kDgrad>(b.dz[li], 1 << kLgOut[li], b.wd[li], nullptr, b.act[li - 1], b.dz[li - 1], B, kLgIn[li],
                             kStride[li], nsm, s);

@@ -649,30 +649,27 @@ __global__ void __launch_bounds__(kWtThreads, 1)
   if (warp == 1) tmem_dealloc(tmem, 128);
 }
 
-// ---------------------------------------------------- weight gradient on tcgen05
-// dW^T[(tap, c)][o] = sum_p col[p][(tap, c)] dz[p][o], db[o] = sum_p dz[p][o]: rows are
-// (tap, input channel) plus one row of ones (the bias), K runs over the output pixels of
-// one chunk, N = 32 output channels.  Both operands are stored p-major in memory, so each
-// 8 x 8 block is transposed in registers on its way to shared memory (K-major UMMA
-// layout).  Two pipeline stages (64 pixels, 128 for the first layer); each CTA writes its
-// chunk's partial sums.
-
-template <int CIN>
-struct WgShape {
-  static constexpr int MT = CIN == kCh ? 3 : 1;  // 128-row M tiles
-  static constexpr int ROWS = MT * 128;
-  static constexpr int NDATA = CIN * kTaps;       // data rows; row NDATA holds ones
-  static constexpr int KCS = CIN == kCh ? 8 : 16;   // K chunks (8 pixels each) per stage
+// ------------------------------------- weight gradient of the first layer on tcgen05
+// dW^T[(tap, c)][o] = sum_p col[p][(tap, c)] dz[p][o], db[o] = sum_p dz[p][o]: 18 rows
+// (tap, input channel) plus one row of ones (the bias), padded to 128; K runs over the
+// output pixels of one chunk, N = 32 output channels.  The A rows are gathered from the
+// float32 NCHW stamps (8 pixels of one channel per 16-byte core-matrix row, rounded to
+// BF16); dz is stored pixel-major, so each 8 x 8 block of it is transposed in registers
+// on its way to shared memory (K-major UMMA layout).  Two pipeline stages of 128 pixels;
+// each CTA writes its chunk's partial sums.
+struct Wg1 {
+  static constexpr int CIN = 2;
+  static constexpr int ROWS = 128;
+  static constexpr int NDATA = CIN * kTaps;        // data rows; row NDATA holds ones
+  static constexpr int KCS = 16;                   // K chunks (8 pixels each) per stage
   static constexpr int STAGE_PX = 8 * KCS;
   static constexpr uint32_t LBO_A = ROWS * 16 + 16;  // +16 B: 8 consecutive K chunks on distinct banks
   static constexpr uint32_t A_STAGE = KCS * LBO_A;
   static constexpr uint32_t LBO_B = kCh * 16 + 16;
   static constexpr uint32_t B_STAGE = KCS * LBO_B;
   static constexpr uint32_t SMEM = 2 * (A_STAGE + B_STAGE) + 64;
-  static constexpr uint32_t TMEM_COLS = MT == 3 ? 128 : 32;
-  // one build unit per thread per stage: (36 + 4) x 8 = 320 for 32 channels, (18 + 4) x 16
-  // = 352 for the first layer
-  static constexpr int THREADS = (CIN == kCh ? kTaps * 4 + 4 : CIN * kTaps + 4) * KCS;
+  static constexpr uint32_t TMEM_COLS = 32;
+  static constexpr int THREADS = (NDATA + 4) * KCS;  // one build unit per thread per stage: 352
 };
 
 // r[i] = row i (8 BF16); t[j] = column j (element i = r[i][j]).
@@ -697,15 +694,14 @@ __device__ __forceinline__ void transpose8(const uint4 (&r)[8], uint4 (&t)[8]) {
   for (int j = 0; j < 8; ++j) t[j] = make_uint4(o[j][0], o[j][1], o[j][2], o[j][3]);
 }
 
-// Source of the weight gradient: CIN == 32, the layer input as BF16 NHWC [B][S][S][32];
-// CIN == 2, the network input as float32 NCHW [B][2][64][64], rounded to BF16 here.
-// A unit is 8 consecutive pixels of one K chunk: since the grid side is a multiple of 8
-// and chunks start at multiples of 64 pixels, they lie in one image row.
-template <int CIN>
-__global__ void __launch_bounds__(WgShape<CIN>::THREADS, 2)
-    wgrad_kernel(const void *__restrict__ src_v, const bf16 *__restrict__ dz, float *__restrict__ part, int B,
-                 int lg_s, int lg_g, int stride, int per_chunk, uint32_t *status) {
-  using Sh = WgShape<CIN>;
+// Source: the network input as float32 NCHW [B][2][64][64].  A unit is 8 consecutive
+// pixels of one K chunk: since the grid side is a multiple of 8 and chunks start at
+// multiples of 128 pixels, they lie in one image row.
+__global__ void __launch_bounds__(Wg1::THREADS, 2)
+    wgrad1_kernel(const float *__restrict__ src, const bf16 *__restrict__ dz, float *__restrict__ part, int B,
+                  int lg_s, int lg_g, int stride, int per_chunk, uint32_t *status) {
+  using Sh = Wg1;
+  constexpr int CIN = Sh::CIN;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * (Sh::A_STAGE + Sh::B_STAGE));
   uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
@@ -747,7 +743,7 @@ __global__ void __launch_bounds__(WgShape<CIN>::THREADS, 2)
     uint8_t *sA = smem + buf * Sh::A_STAGE;
     uint8_t *sB = smem + 2 * Sh::A_STAGE + buf * Sh::B_STAGE;
     const int p0 = p_begin + s * Sh::STAGE_PX;
-    constexpr int NG = CIN == kCh ? kTaps * 4 : Sh::NDATA;  // A units per K chunk
+    constexpr int NG = Sh::NDATA;  // A units per K chunk
     for (int u = tid; u < (NG + 4) * Sh::KCS; u += Sh::THREADS) {
       const int kc = u % Sh::KCS, g = u / Sh::KCS;
       const int pq = p0 + kc * 8;  // pixels pq .. pq + 7: image b, row y, columns x0 ..
@@ -763,29 +759,11 @@ __global__ void __launch_bounds__(WgShape<CIN>::THREADS, 2)
         uint8_t *dst = sB + kc * Sh::LBO_B + o8 * 128;
 #pragma unroll
         for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4 *>(dst + j * 16) = t[j];
-      } else if (CIN == kCh) {  // 8 pixels x 8 input channels of one tap -> rows (tap, c)
-        const int tap = g >> 2, c8 = g & 3, dy = tap / 3, dx = tap % 3;
-        const int yy = stride * y + dy - 1;
-        const bool row_ok = in && yy >= 0 && yy < S;
-        const uint4 *row = reinterpret_cast<const uint4 *>(static_cast<const bf16 *>(src_v) +
-                                                           ((((size_t)b << lg_s) + (row_ok ? yy : 0)) << lg_s) * kCh) +
-                           c8;
-        uint4 r[8], t[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int xx = stride * (x0 + e) + dx - 1;
-          r[e] = (row_ok && xx >= 0 && xx < S) ? __ldg(row + 4 * xx) : zero;
-        }
-        transpose8(r, t);
-        uint8_t *dst = sA + kc * Sh::LBO_A + (tap * kCh + c8 * 8) * 16;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4 *>(dst + j * 16) = t[j];
-      } else {  // first layer: row (tap, c) of 8 pixels straight from the float input
+      } else {  // row (tap, c): 8 pixels straight from the float input
         const int tap = g / CIN, c = g % CIN, dy = tap / 3, dx = tap % 3;
         const int yy = stride * y + dy - 1;
         const bool row_ok = in && yy >= 0 && yy < S;
-        const float *row = static_cast<const float *>(src_v) +
-                           ((((size_t)b * CIN + c) << lg_s) + (row_ok ? yy : 0)) * (size_t)S;
+        const float *row = src + ((((size_t)b * CIN + c) << lg_s) + (row_ok ? yy : 0)) * (size_t)S;
         float f[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
@@ -803,10 +781,8 @@ __global__ void __launch_bounds__(WgShape<CIN>::THREADS, 2)
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
 #pragma unroll
       for (int k = 0; k < Sh::STAGE_PX / 16; ++k)
-#pragma unroll
-        for (int i = 0; i < Sh::MT; ++i)
-          umma_f16(tmem + 32u * i, sdesc(a0 + k * 2u * Sh::LBO_A + i * 2048u, Sh::LBO_A, 128u),
-                   sdesc(b0 + k * 2u * Sh::LBO_B, Sh::LBO_B, 128u), kIdesc, (s > 0 || k > 0) ? 1u : 0u);
+        umma_f16(tmem, sdesc(a0 + k * 2u * Sh::LBO_A, Sh::LBO_A, 128u), sdesc(b0 + k * 2u * Sh::LBO_B, Sh::LBO_B, 128u),
+                 kIdesc, (s > 0 || k > 0) ? 1u : 0u);
       umma_commit(&bar[buf]);
     }
   }
@@ -818,12 +794,11 @@ __global__ void __launch_bounds__(WgShape<CIN>::THREADS, 2)
   if (!failed && nst > 0 && warp < 8) {  // warps 0-7: TMEM lane quadrant warp & 3, column half warp / 4
     tc_fence_after();
     const int q = warp & 3, h = warp >> 2;
-#pragma unroll
-    for (int i = 0; i < Sh::MT; ++i) {
+    {
       uint32_t r[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 32u * i + 16u * h, r);
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 16u * h, r);
       tmem_ld_wait();
-      const int row = 128 * i + 32 * q + lane;
+      const int row = 32 * q + lane;
       if (row <= Sh::NDATA) {
         float *dst = part + ((size_t)blockIdx.x * (Sh::NDATA + 1) + row) * kCh + 16 * h;
         const uint32_t lo[8] = {r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7]};
@@ -1055,16 +1030,15 @@ int wgrad_tma(const bf16 *src, int S, const bf16 *dz, float *part, int B, int lg
   return cuda_status(cudaGetLastError(), "network weight gradient");
 }
 
-// A layer's partial weight-gradient sums (reduced for all layers by wgrad_reduce_kernel).
-template <int CIN>
-int wgrad(const void *src, const bf16 *dz, float *part, int B, int lg_s, int lg_g, int stride, cudaStream_t s) {
-  using Sh = WgShape<CIN>;
-  cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+// The first layer's partial weight-gradient sums (reduced for all layers by
+// wgrad_reduce_kernel).
+int wgrad1(const float *x, const bf16 *dz, float *part, int B, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(wgrad1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Wg1::SMEM);
   if (e != cudaSuccess) return cuda_status(e, "network weight-gradient attributes");
-  const int P = B << (2 * lg_g);
-  const int per = wg_per_chunk(P, CIN), nch = wg_nchunks(P, CIN);
-  wgrad_kernel<CIN><<<nch, Sh::THREADS, Sh::SMEM, s>>>(src, dz, part, B, lg_s, lg_g, stride, per,
-                                                         device_status_word());
+  const int P = B << (2 * kLgOut[0]);
+  const int per = wg_per_chunk(P, 2), nch = wg_nchunks(P, 2);
+  wgrad1_kernel<<<nch, Wg1::THREADS, Wg1::SMEM, s>>>(x, dz, part, B, kLgIn[0], kLgOut[0], kStride[0], per,
+                                                       device_status_word());
   return cuda_status(cudaGetLastError(), "network weight gradient");
 }
 
@@ -1240,7 +1214,7 @@ int cnn_gradient(const float *params, const float *x, const float *target, int B
                             kStride[li], nsm, s);
     if (st != SVK_OK) return st;
   }
-  if ((st = wgrad<2>(x, b.dz[0], b.part[0], B, kLgIn[0], kLgOut[0], kStride[0], s)) != SVK_OK) return st;
+  if ((st = wgrad1(x, b.dz[0], b.part[0], B, s)) != SVK_OK) return st;
   WgradSet set{};
   set.row0[0] = 0;
   for (int li = 0; li < kLayers; ++li) {

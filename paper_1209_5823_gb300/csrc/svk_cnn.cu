@@ -652,11 +652,11 @@ __global__ void __launch_bounds__(kWtThreads, 1)
 // ------------------------------------- weight gradient of the first layer on tcgen05
 // dW^T[(tap, c)][o] = sum_p col[p][(tap, c)] dz[p][o], db[o] = sum_p dz[p][o]: 18 rows
 // (tap, input channel) plus one row of ones (the bias), padded to 128; K runs over the
-// output pixels of one chunk, N = 32 output channels.  The A rows are gathered from the
-// float32 NCHW stamps (8 pixels of one channel per 16-byte core-matrix row, rounded to
-// BF16); dz is stored pixel-major, so each 8 x 8 block of it is transposed in registers
-// on its way to shared memory (K-major UMMA layout).  Two pipeline stages of 128 pixels;
-// each CTA writes its chunk's partial sums.
+// output pixels of one chunk, N = 32 output channels.  The A rows are gathered by the
+// threads from the float32 NCHW stamps (8 pixels of one channel per 16-byte core-matrix
+// row, rounded to BF16; K-major); the dz tile of a stage (128 pixels = 4 rows of the
+// 32 x 32 grid) is one TMA load in the 64-byte swizzle, the MN-major B operand.  Two
+// pipeline stages of 128 pixels; each CTA writes its chunk's partial sums.
 struct Wg1 {
   static constexpr int CIN = 2;
   static constexpr int ROWS = 128;
@@ -665,46 +665,26 @@ struct Wg1 {
   static constexpr int STAGE_PX = 8 * KCS;
   static constexpr uint32_t LBO_A = ROWS * 16 + 16;  // +16 B: 8 consecutive K chunks on distinct banks
   static constexpr uint32_t A_STAGE = KCS * LBO_A;
-  static constexpr uint32_t LBO_B = kCh * 16 + 16;
-  static constexpr uint32_t B_STAGE = KCS * LBO_B;
-  static constexpr uint32_t SMEM = 2 * (A_STAGE + B_STAGE) + 64;
+  static constexpr uint32_t B_STAGE = STAGE_PX * 64;  // [128 pixels][64 B], 64-byte swizzle
+  static constexpr uint32_t SMEM = 2 * (B_STAGE + A_STAGE) + 64 + 1024;
   static constexpr uint32_t TMEM_COLS = 32;
-  static constexpr int THREADS = (NDATA + 4) * KCS;  // one build unit per thread per stage: 352
+  static constexpr int THREADS = NDATA * KCS;  // one A unit per thread per stage: 288
 };
-
-// r[i] = row i (8 BF16); t[j] = column j (element i = r[i][j]).
-__device__ __forceinline__ void transpose8(const uint4 (&r)[8], uint4 (&t)[8]) {
-  uint32_t w[8][4], o[8][4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    w[i][0] = r[i].x;
-    w[i][1] = r[i].y;
-    w[i][2] = r[i].z;
-    w[i][3] = r[i].w;
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int rr = 0; rr < 4; ++rr) {
-      const uint32_t a = w[2 * rr][q], b = w[2 * rr + 1][q];
-      o[2 * q][rr] = __byte_perm(a, b, 0x5410);      // element 2q of rows 2rr, 2rr+1
-      o[2 * q + 1][rr] = __byte_perm(a, b, 0x7632);  // element 2q+1
-    }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) t[j] = make_uint4(o[j][0], o[j][1], o[j][2], o[j][3]);
-}
 
 // Source: the network input as float32 NCHW [B][2][64][64].  A unit is 8 consecutive
 // pixels of one K chunk: since the grid side is a multiple of 8 and chunks start at
 // multiples of 128 pixels, they lie in one image row.
 __global__ void __launch_bounds__(Wg1::THREADS, 2)
-    wgrad1_kernel(const float *__restrict__ src, const bf16 *__restrict__ dz, float *__restrict__ part, int B,
-                  int lg_s, int lg_g, int stride, int per_chunk, uint32_t *status) {
+    wgrad1_kernel(const float *__restrict__ src, const __grid_constant__ CUtensorMap dzm, float *__restrict__ part,
+                  int B, int lg_s, int lg_g, int stride, int per_chunk, uint32_t *status) {
   using Sh = Wg1;
   constexpr int CIN = Sh::CIN;
-  extern __shared__ __align__(128) uint8_t smem[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * (Sh::A_STAGE + Sh::B_STAGE));
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *smem = sm + 2 * Sh::B_STAGE;  // the A stages; the B stages (1024-aligned) come first
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * Sh::A_STAGE);
+  uint64_t *tbar = bar + 2;  // the dz tile of each stage landed
+  uint32_t *slot = reinterpret_cast<uint32_t *>(tbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = 1 << lg_s, G = 1 << lg_g;
   const int P = B << (2 * lg_g);
@@ -719,16 +699,18 @@ __global__ void __launch_bounds__(Wg1::THREADS, 2)
     *reinterpret_cast<uint4 *>(smem + st * Sh::A_STAGE + kc * Sh::LBO_A + row * 16) = make_uint4(v, v, v, v);
   }
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar[i], 1);
+      mbar_init(&tbar[i], 1);
+    }
     fence_mbar_init();
+    prefetch_tmap(&dzm);
   }
   if (warp == 0) tmem_alloc(slot, Sh::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
-  const uint4 zero = make_uint4(0, 0, 0, 0);
 
   bool failed = false;
   for (int s = 0; s < nst; ++s) {
@@ -741,25 +723,19 @@ __global__ void __launch_bounds__(Wg1::THREADS, 2)
       }
     }
     uint8_t *sA = smem + buf * Sh::A_STAGE;
-    uint8_t *sB = smem + 2 * Sh::A_STAGE + buf * Sh::B_STAGE;
+    uint8_t *sB = sm + buf * Sh::B_STAGE;
     const int p0 = p_begin + s * Sh::STAGE_PX;
+    if (tid == 0) {  // the stage's dz tile: 128 pixels = rows y0 .. y0 + 3 of image b
+      mbar_arrive_expect_tx(&tbar[buf], Sh::B_STAGE);
+      tma_load_4d(sB, &dzm, &tbar[buf], 0, 0, (p0 >> lg_g) & (G - 1), p0 >> (2 * lg_g));
+    }
     constexpr int NG = Sh::NDATA;  // A units per K chunk
-    for (int u = tid; u < (NG + 4) * Sh::KCS; u += Sh::THREADS) {
+    for (int u = tid; u < NG * Sh::KCS; u += Sh::THREADS) {
       const int kc = u % Sh::KCS, g = u / Sh::KCS;
       const int pq = p0 + kc * 8;  // pixels pq .. pq + 7: image b, row y, columns x0 ..
       const bool in = pq < p_end;
       const int b = pq >> (2 * lg_g), y = (pq >> lg_g) & (G - 1), x0 = pq & (G - 1);
-      if (g >= NG) {  // dz: 8 pixels x 8 output channels -> rows o, K = pixels
-        const int o8 = g - NG;
-        const uint4 *d4 = reinterpret_cast<const uint4 *>(dz + (size_t)pq * kCh) + o8;
-        uint4 r[8], t[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) r[e] = in ? __ldg(d4 + 4 * e) : zero;
-        transpose8(r, t);
-        uint8_t *dst = sB + kc * Sh::LBO_B + o8 * 128;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4 *>(dst + j * 16) = t[j];
-      } else {  // row (tap, c): 8 pixels straight from the float input
+      {  // row (tap, c): 8 pixels straight from the float input
         const int tap = g / CIN, c = g % CIN, dy = tap / 3, dx = tap % 3;
         const int yy = stride * y + dy - 1;
         const bool row_ok = in && yy >= 0 && yy < S;
@@ -775,14 +751,18 @@ __global__ void __launch_bounds__(Wg1::THREADS, 2)
       }
     }
     fence_proxy_async_smem();
-    __syncthreads();
+    const bool okt = mbar_wait_bounded(&tbar[buf], (uint32_t)((s >> 1) & 1), status);
+    if (__syncthreads_or(!okt)) {
+      failed = true;
+      break;
+    }
     if (tid == 0) {
       tc_fence_after();
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
 #pragma unroll
       for (int k = 0; k < Sh::STAGE_PX / 16; ++k)
-        umma_f16(tmem, sdesc(a0 + k * 2u * Sh::LBO_A, Sh::LBO_A, 128u), sdesc(b0 + k * 2u * Sh::LBO_B, Sh::LBO_B, 128u),
-                 kIdesc, (s > 0 || k > 0) ? 1u : 0u);
+        umma_f16(tmem, sdesc(a0 + k * 2u * Sh::LBO_A, Sh::LBO_A, 128u), sdesc_mn_sw64(b0 + 1024u * k, Sh::B_STAGE),
+                 kIdesc | (1u << 16), (s > 0 || k > 0) ? 1u : 0u);  // B MN-major
       umma_commit(&bar[buf]);
     }
   }
@@ -1033,11 +1013,14 @@ int wgrad_tma(const bf16 *src, int S, const bf16 *dz, float *part, int B, int lg
 // The first layer's partial weight-gradient sums (reduced for all layers by
 // wgrad_reduce_kernel).
 int wgrad1(const float *x, const bf16 *dz, float *part, int B, cudaStream_t s) {
+  CUtensorMap td;  // dz of the first layer: 32 x 32 grid, boxes of 4 rows
+  if (!encode_tmap_nhwc32_bf16(&td, dz, 32, B, 32, Wg1::STAGE_PX / 32, 1, 1))
+    return set_error(SVK_ERR_CUDA, "network tensor map refused");
   cudaError_t e = cudaFuncSetAttribute(wgrad1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Wg1::SMEM);
   if (e != cudaSuccess) return cuda_status(e, "network weight-gradient attributes");
   const int P = B << (2 * kLgOut[0]);
   const int per = wg_per_chunk(P, 2), nch = wg_nchunks(P, 2);
-  wgrad1_kernel<<<nch, Wg1::THREADS, Wg1::SMEM, s>>>(x, dz, part, B, kLgIn[0], kLgOut[0], kStride[0], per,
+  wgrad1_kernel<<<nch, Wg1::THREADS, Wg1::SMEM, s>>>(x, td, part, B, kLgIn[0], kLgOut[0], kStride[0], per,
                                                        device_status_word());
   return cuda_status(cudaGetLastError(), "network weight gradient");
 }

@@ -74,6 +74,20 @@ bool encode_tmap_nhwc32_bf16(CUtensorMap *map, const void *base, int S, int B, i
   return r == CUDA_SUCCESS;
 }
 
+bool encode_tmap_stamps_f32(CUtensorMap *map, const float *base, int S, int C, int B, int box_y) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 || (S * 4) % 16 != 0) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)S, (cuuint64_t)S, (cuuint64_t)C, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)S * 4, (cuuint64_t)S * S * 4, (cuuint64_t)C * S * S * 4};
+  cuuint32_t box[4] = {(cuuint32_t)S, (cuuint32_t)box_y, (cuuint32_t)C, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int ScopedWorkspace::acquire(size_t bytes, void *user_ws, size_t user_bytes, cudaStream_t s) {
   if (bytes == 0) return SVK_OK;
   if (user_ws) {

@@ -174,25 +174,32 @@ __global__ void pack_kernel(const float *__restrict__ p, float *__restrict__ wq,
 }
 
 // ------------------------------------------------ first layer forward on tcgen05
-// K = 9 taps x 2 channels = 18 (k = 2 tap + c), zero-padded to 32 (4 chunks of 8): each
-// thread gathers one output pixel's 18 inputs from the float32 NCHW stamps, rounds them
-// to BF16 and writes its A row; the next tile's gather is in flight while the current
-// tile's MMAs and epilogue run.  128 threads: the epilogue warp q drains TMEM lanes
-// 32 q .. 32 q + 31 (bias, ReLU, BF16 NHWC rows of 64 bytes).
+// K = 9 taps x 2 channels = 18 (k = 2 tap + c), zero-padded to 32 (4 chunks of 8).  A
+// tile is 128 output pixels = 4 rows of the 32 x 32 grid; one TMA load (issued a tile
+// ahead, double-buffered) stages the 9 input rows those rows read, 2 channels of 64
+// floats (zero fill above the stamp), and each thread builds its pixel's A row from them
+// (rounded to BF16).  128 threads: the epilogue warp q drains TMEM lanes 32 q .. 32 q + 31
+// (bias, ReLU, BF16 NHWC rows of 64 bytes).
 constexpr int kC1Threads = 128;
 constexpr int kC1Chunks = 4;
-constexpr uint32_t kC1ABytes = kC1Chunks * 128 * 16;  // [4][128 rows][16 B]
-constexpr uint32_t kC1BBytes = kC1Chunks * kCh * 16;  // [4][32 rows][16 B]
-constexpr uint32_t kC1Smem = kC1ABytes + kC1BBytes + 64;
+constexpr int kC1Rows = 9;                                // input rows of 4 output rows
+constexpr uint32_t kC1XBytes = 2 * kC1Rows * 64 * 4;      // [c][9 rows][64 floats] = 4608
+constexpr uint32_t kC1XStage = 5120;                      // rounded to 1 KB
+constexpr uint32_t kC1ABytes = kC1Chunks * 128 * 16;      // [4][128 rows][16 B]
+constexpr uint32_t kC1BBytes = kC1Chunks * kCh * 16;      // [4][32 rows][16 B]
+constexpr uint32_t kC1Smem = 2 * kC1XStage + kC1ABytes + kC1BBytes + 64 + 1024;
 
 __global__ void __launch_bounds__(kC1Threads, 6)
-    conv1_mma_kernel(const float *__restrict__ x, const bf16 *__restrict__ wpack, const float *__restrict__ bias,
-                     bf16 *__restrict__ out, int B, uint32_t *status) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t *sA = smem;
-  uint8_t *sB = smem + kC1ABytes;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kC1ABytes + kC1BBytes);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
+    conv1_mma_kernel(const __grid_constant__ CUtensorMap xm, const bf16 *__restrict__ wpack,
+                     const float *__restrict__ bias, bf16 *__restrict__ out, int B, uint32_t *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sx = sm;                          // two staged input blocks
+  uint8_t *sA = sm + 2 * kC1XStage;
+  uint8_t *sB = sA + kC1ABytes;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sB + kC1BBytes);
+  uint64_t *tbar = bar + 1;  // two: the staged input of each buffer landed
+  uint32_t *slot = reinterpret_cast<uint32_t *>(tbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int S = 64, lg_g = 5, G = 32;  // 64 x 64 inputs, 32 x 32 outputs, stride 2
   const int P = B << (2 * lg_g);
@@ -205,7 +212,10 @@ __global__ void __launch_bounds__(kC1Threads, 6)
   }
   if (tid == 0) {
     mbar_init(bar, 1);
+    mbar_init(&tbar[0], 1);
+    mbar_init(&tbar[1], 1);
     fence_mbar_init();
+    prefetch_tmap(&xm);
   }
   if (warp == 0) tmem_alloc(slot, 32);
   tc_fence_before();
@@ -217,29 +227,40 @@ __global__ void __launch_bounds__(kC1Threads, 6)
 #pragma unroll
   for (int i = 0; i < 32; ++i) bv[i] = __ldg(bias + i);
 
-  float f[2 * kTaps];  // row tid of a tile: k = 2 tap + c
-  auto load = [&](int tile) {
-    const int p = (tile << 7) + tid;
-    const bool valid = p < P;
-    const int b = valid ? p >> (2 * lg_g) : 0, y = (p >> lg_g) & (G - 1), xo = p & (G - 1);
-#pragma unroll
-    for (int t = 0; t < kTaps; ++t) {
-      const int yy = 2 * y + t / 3 - 1, xx = 2 * xo + t % 3 - 1;
-      const bool ok = valid && yy >= 0 && yy < S && xx >= 0 && xx < S;
-#pragma unroll
-      for (int c = 0; c < 2; ++c) f[2 * t + c] = ok ? __ldg(x + ((((size_t)b * 2 + c) * S + yy) * S) + xx) : 0.0f;
-    }
+  uint32_t issued = 0;  // loads issued (thread 0)
+  auto issue = [&](int tile, int sb) {  // rows 2 y0 - 1 .. 2 y0 + 7 of the tile's stamp
+    const int p = tile << 7, b = p >> (2 * lg_g), y0 = (p >> lg_g) & (G - 1);
+    mbar_arrive_expect_tx(&tbar[sb], kC1XBytes);
+    tma_load_4d(sx + sb * kC1XStage, &xm, &tbar[sb], 0, 2 * y0 - 1, 0, b);
+    ++issued;
   };
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
   uint32_t it = 0;
-  if (blockIdx.x < ntiles) load(blockIdx.x);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    uint8_t *row = sA + (uint32_t)tid * 16u;  // the MMAs of the previous tile have completed
-    *reinterpret_cast<uint4 *>(row) =
-        make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
-    *reinterpret_cast<uint4 *>(row + 2048) =
-        make_uint4(pack2(f[8], f[9]), pack2(f[10], f[11]), pack2(f[12], f[13]), pack2(f[14], f[15]));
-    *reinterpret_cast<uint4 *>(row + 4096) = make_uint4(pack2(f[16], f[17]), 0u, 0u, 0u);
-    *reinterpret_cast<uint4 *>(row + 6144) = make_uint4(0u, 0u, 0u, 0u);
+    const int buf = it & 1;
+    const bool okx = mbar_wait_bounded(&tbar[buf], (it >> 1) & 1u, status);
+    if (__syncthreads_or(!okx)) break;
+    {  // row tid: output pixel (y, xo); input row 2 y + dy - 1 is staged row 2 (y - y0) + dy
+      const float *xs = reinterpret_cast<const float *>(sx + buf * kC1XStage);  // [c][9][64]
+      const int p = (tile << 7) + tid;
+      const bool valid = p < P;
+      const int y = (p >> lg_g) & (G - 1), xo = p & (G - 1), yl = y - (((tile << 7) >> lg_g) & (G - 1));
+      float f[2 * kTaps];
+#pragma unroll
+      for (int t = 0; t < kTaps; ++t) {
+        const int xx = 2 * xo + t % 3 - 1;
+        const bool ok = valid && xx >= 0 && xx < S;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) f[2 * t + c] = ok ? xs[(c * kC1Rows + 2 * yl + t / 3) * S + xx] : 0.0f;
+      }
+      uint8_t *row = sA + (uint32_t)tid * 16u;  // the MMAs of the previous tile have completed
+      *reinterpret_cast<uint4 *>(row) =
+          make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+      *reinterpret_cast<uint4 *>(row + 2048) =
+          make_uint4(pack2(f[8], f[9]), pack2(f[10], f[11]), pack2(f[12], f[13]), pack2(f[14], f[15]));
+      *reinterpret_cast<uint4 *>(row + 4096) = make_uint4(pack2(f[16], f[17]), 0u, 0u, 0u);
+      *reinterpret_cast<uint4 *>(row + 6144) = make_uint4(0u, 0u, 0u, 0u);
+    }
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -249,8 +270,9 @@ __global__ void __launch_bounds__(kC1Threads, 6)
         umma_f16(tmem, sdesc(aBase + (uint32_t)k * 2u * 2048u, 2048u, 128u),
                  sdesc(bBase + (uint32_t)k * 2u * 512u, 512u, 128u), kIdesc, k > 0 ? 1u : 0u);
       umma_commit(bar);
+      // the other staged block was read before the barrier above: the next tile's rows
+      if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, buf ^ 1);
     }
-    if (tile + (int)gridDim.x < ntiles) load(tile + gridDim.x);  // in flight during the MMAs and epilogue
     const bool ok = mbar_wait_bounded(bar, it & 1u, status);
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
@@ -271,6 +293,9 @@ __global__ void __launch_bounds__(kC1Threads, 6)
     }
     tc_fence_before();
   }
+  // after a wait gave up, a load issued ahead may still be in flight: wait for it (bounded)
+  if (tid == 0 && issued > it)
+    mbar_wait_bounded(&tbar[(issued - 1) & 1], ((issued - 1) >> 1) & 1u, status);
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 32);
 }
@@ -652,11 +677,12 @@ __global__ void __launch_bounds__(kWtThreads, 1)
 // ------------------------------------- weight gradient of the first layer on tcgen05
 // dW^T[(tap, c)][o] = sum_p col[p][(tap, c)] dz[p][o], db[o] = sum_p dz[p][o]: 18 rows
 // (tap, input channel) plus one row of ones (the bias), padded to 128; K runs over the
-// output pixels of one chunk, N = 32 output channels.  The A rows are gathered by the
-// threads from the float32 NCHW stamps (8 pixels of one channel per 16-byte core-matrix
-// row, rounded to BF16; K-major); the dz tile of a stage (128 pixels = 4 rows of the
-// 32 x 32 grid) is one TMA load in the 64-byte swizzle, the MN-major B operand.  Two
-// pipeline stages of 128 pixels; each CTA writes its chunk's partial sums.
+// output pixels of one chunk, N = 32 output channels.  A stage is 128 output pixels = 4
+// rows of the 32 x 32 grid; its TMA loads, issued one stage ahead, bring the 9 input rows
+// (2 channels, float32) those rows read and the dz tile (64-byte swizzle: the MN-major B
+// operand).  The threads build the A rows from the staged input (8 pixels of one channel
+// per 16-byte core-matrix row, rounded to BF16; K-major).  Two stage buffers; each CTA
+// writes its chunk's partial sums.
 struct Wg1 {
   static constexpr int CIN = 2;
   static constexpr int ROWS = 128;
@@ -666,7 +692,10 @@ struct Wg1 {
   static constexpr uint32_t LBO_A = ROWS * 16 + 16;  // +16 B: 8 consecutive K chunks on distinct banks
   static constexpr uint32_t A_STAGE = KCS * LBO_A;
   static constexpr uint32_t B_STAGE = STAGE_PX * 64;  // [128 pixels][64 B], 64-byte swizzle
-  static constexpr uint32_t SMEM = 2 * (B_STAGE + A_STAGE) + 64 + 1024;
+  static constexpr int XROWS = 9;                      // input rows of 4 output rows
+  static constexpr uint32_t X_BYTES = CIN * XROWS * 64 * 4;  // [c][row][64 floats]
+  static constexpr uint32_t X_STAGE = 5120;                  // X_BYTES rounded to 1 KB
+  static constexpr uint32_t SMEM = 2 * (B_STAGE + X_STAGE + A_STAGE) + 64 + 1024;
   static constexpr uint32_t TMEM_COLS = 32;
   static constexpr int THREADS = NDATA * KCS;  // one A unit per thread per stage: 288
 };
@@ -675,13 +704,14 @@ struct Wg1 {
 // pixels of one K chunk: since the grid side is a multiple of 8 and chunks start at
 // multiples of 128 pixels, they lie in one image row.
 __global__ void __launch_bounds__(Wg1::THREADS, 2)
-    wgrad1_kernel(const float *__restrict__ src, const __grid_constant__ CUtensorMap dzm, float *__restrict__ part,
-                  int B, int lg_s, int lg_g, int stride, int per_chunk, uint32_t *status) {
+    wgrad1_kernel(const __grid_constant__ CUtensorMap xm, const __grid_constant__ CUtensorMap dzm,
+                  float *__restrict__ part, int B, int lg_s, int lg_g, int stride, int per_chunk, uint32_t *status) {
   using Sh = Wg1;
   constexpr int CIN = Sh::CIN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t *smem = sm + 2 * Sh::B_STAGE;  // the A stages; the B stages (1024-aligned) come first
+  uint8_t *sx = sm + 2 * Sh::B_STAGE;    // staged input rows, after the B stages (1024-aligned)
+  uint8_t *smem = sx + 2 * Sh::X_STAGE;  // the A stages
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * Sh::A_STAGE);
   uint64_t *tbar = bar + 2;  // the dz tile of each stage landed
   uint32_t *slot = reinterpret_cast<uint32_t *>(tbar + 2);
@@ -705,12 +735,25 @@ __global__ void __launch_bounds__(Wg1::THREADS, 2)
     }
     fence_mbar_init();
     prefetch_tmap(&dzm);
+    prefetch_tmap(&xm);
   }
   if (warp == 0) tmem_alloc(slot, Sh::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
+
+  // the stage's TMA loads into buffer sb: its dz tile and the 9 input rows of its 4
+  // output rows (row 2 y0 - 1 may lie above the stamp: zero fill)
+  int issued = 0, landed = 0;  // stage loads issued (thread 0), stages whose loads were waited for
+  auto issue = [&](int st, int sb) {
+    const int p0 = p_begin + st * Sh::STAGE_PX, b = p0 >> (2 * lg_g), y0 = (p0 >> lg_g) & (G - 1);
+    mbar_arrive_expect_tx(&tbar[sb], Sh::B_STAGE + Sh::X_BYTES);
+    tma_load_4d(sm + sb * Sh::B_STAGE, &dzm, &tbar[sb], 0, 0, y0, b);
+    tma_load_4d(sx + sb * Sh::X_STAGE, &xm, &tbar[sb], 0, stride * y0 - 1, 0, b);
+    ++issued;
+  };
+  if (tid == 0 && nst > 0) issue(0, 0);
 
   bool failed = false;
   for (int s = 0; s < nst; ++s) {
@@ -722,40 +765,41 @@ __global__ void __launch_bounds__(Wg1::THREADS, 2)
         break;
       }
     }
-    uint8_t *sA = smem + buf * Sh::A_STAGE;
-    uint8_t *sB = sm + buf * Sh::B_STAGE;
-    const int p0 = p_begin + s * Sh::STAGE_PX;
-    if (tid == 0) {  // the stage's dz tile: 128 pixels = rows y0 .. y0 + 3 of image b
-      mbar_arrive_expect_tx(&tbar[buf], Sh::B_STAGE);
-      tma_load_4d(sB, &dzm, &tbar[buf], 0, 0, (p0 >> lg_g) & (G - 1), p0 >> (2 * lg_g));
-    }
-    constexpr int NG = Sh::NDATA;  // A units per K chunk
-    for (int u = tid; u < NG * Sh::KCS; u += Sh::THREADS) {
-      const int kc = u % Sh::KCS, g = u / Sh::KCS;
-      const int pq = p0 + kc * 8;  // pixels pq .. pq + 7: image b, row y, columns x0 ..
-      const bool in = pq < p_end;
-      const int b = pq >> (2 * lg_g), y = (pq >> lg_g) & (G - 1), x0 = pq & (G - 1);
-      {  // row (tap, c): 8 pixels straight from the float input
-        const int tap = g / CIN, c = g % CIN, dy = tap / 3, dx = tap % 3;
-        const int yy = stride * y + dy - 1;
-        const bool row_ok = in && yy >= 0 && yy < S;
-        const float *row = src + ((((size_t)b * CIN + c) << lg_s) + (row_ok ? yy : 0)) * (size_t)S;
-        float f[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int xx = stride * (x0 + e) + dx - 1;
-          f[e] = (row_ok && xx >= 0 && xx < S) ? __ldg(row + xx) : 0.0f;
-        }
-        *reinterpret_cast<uint4 *>(sA + kc * Sh::LBO_A + g * 16) =
-            make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
-      }
-    }
-    fence_proxy_async_smem();
+    // one stage ahead: buffer buf ^ 1 is free once the MMAs of stage s - 1 are done (a
+    // wait that gives up leaves the load unissued, and the wait for it below gives up too)
+    if (tid == 0 && s + 1 < nst &&
+        (s == 0 || mbar_wait_bounded(&bar[buf ^ 1], (uint32_t)(((s - 1) >> 1) & 1), status)))
+      issue(s + 1, buf ^ 1);
     const bool okt = mbar_wait_bounded(&tbar[buf], (uint32_t)((s >> 1) & 1), status);
     if (__syncthreads_or(!okt)) {
       failed = true;
       break;
     }
+    landed = s + 1;
+    uint8_t *sA = smem + buf * Sh::A_STAGE;
+    uint8_t *sB = sm + buf * Sh::B_STAGE;
+    const float *xs = reinterpret_cast<const float *>(sx + buf * Sh::X_STAGE);  // [c][9 rows][64]
+    const int p0 = p_begin + s * Sh::STAGE_PX, y0 = (p0 >> lg_g) & (G - 1);
+    for (int u = tid; u < Sh::NDATA * Sh::KCS; u += Sh::THREADS) {
+      // row (tap, c), pixels pq .. pq + 7 (output row y, columns x0 ..): input row
+      // 2 y + dy - 1 is staged row 2 (y - y0) + dy, column 2 x + dx - 1
+      const int kc = u % Sh::KCS, g = u / Sh::KCS;
+      const int pq = p0 + kc * 8;
+      const bool in = pq < p_end;
+      const int y = (pq >> lg_g) & (G - 1), x0 = pq & (G - 1);
+      const int tap = g / CIN, c = g % CIN, dy = tap / 3, dx = tap % 3;
+      const float *row = xs + (c * Sh::XROWS + stride * (y - y0) + dy) * S;
+      float f[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int xx = stride * (x0 + e) + dx - 1;
+        f[e] = (in && xx >= 0 && xx < S) ? row[xx] : 0.0f;
+      }
+      *reinterpret_cast<uint4 *>(sA + kc * Sh::LBO_A + g * 16) =
+          make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
     if (tid == 0) {
       tc_fence_after();
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
@@ -766,6 +810,8 @@ __global__ void __launch_bounds__(Wg1::THREADS, 2)
       umma_commit(&bar[buf]);
     }
   }
+  // after a wait gave up, a load issued ahead may still be in flight: wait for it (bounded)
+  if (tid == 0 && issued > landed) mbar_wait_bounded(&tbar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, status);
   if (!failed && nst > 0) {  // the last commit covers every MMA before it
     const int sl = nst - 1;
     const bool ok = mbar_wait_bounded(&bar[sl & 1], (uint32_t)((sl >> 1) & 1), status);
@@ -947,11 +993,13 @@ int sm_count() {
 }
 
 int conv1(const float *x, const bf16 *wpack, const float *bias, bf16 *out, int B, int nsm, cudaStream_t s) {
+  CUtensorMap tx;  // the stamps, 9 input rows per box
+  if (!encode_tmap_stamps_f32(&tx, x, 64, 2, B, kC1Rows)) return set_error(SVK_ERR_CUDA, "network tensor map refused");
   cudaError_t e = cudaFuncSetAttribute(conv1_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kC1Smem);
   if (e != cudaSuccess) return cuda_status(e, "network first-layer attributes");
   const int ntiles = ((B << 10) + 127) >> 7;
   const int grid = ntiles < 6 * nsm ? ntiles : 6 * nsm;
-  conv1_mma_kernel<<<grid, kC1Threads, kC1Smem, s>>>(x, wpack, bias, out, B, device_status_word());
+  conv1_mma_kernel<<<grid, kC1Threads, kC1Smem, s>>>(tx, wpack, bias, out, B, device_status_word());
   return cuda_status(cudaGetLastError(), "network first layer");
 }
 
@@ -1013,14 +1061,15 @@ int wgrad_tma(const bf16 *src, int S, const bf16 *dz, float *part, int B, int lg
 // The first layer's partial weight-gradient sums (reduced for all layers by
 // wgrad_reduce_kernel).
 int wgrad1(const float *x, const bf16 *dz, float *part, int B, cudaStream_t s) {
-  CUtensorMap td;  // dz of the first layer: 32 x 32 grid, boxes of 4 rows
-  if (!encode_tmap_nhwc32_bf16(&td, dz, 32, B, 32, Wg1::STAGE_PX / 32, 1, 1))
+  CUtensorMap td, tx;  // dz of the first layer: 32 x 32 grid, boxes of 4 rows; its input: 9 rows
+  if (!encode_tmap_nhwc32_bf16(&td, dz, 32, B, 32, Wg1::STAGE_PX / 32, 1, 1) ||
+      !encode_tmap_stamps_f32(&tx, x, 64, 2, B, Wg1::XROWS))
     return set_error(SVK_ERR_CUDA, "network tensor map refused");
   cudaError_t e = cudaFuncSetAttribute(wgrad1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Wg1::SMEM);
   if (e != cudaSuccess) return cuda_status(e, "network weight-gradient attributes");
   const int P = B << (2 * kLgOut[0]);
   const int per = wg_per_chunk(P, 2), nch = wg_nchunks(P, 2);
-  wgrad1_kernel<<<nch, Wg1::THREADS, Wg1::SMEM, s>>>(x, td, part, B, kLgIn[0], kLgOut[0], kStride[0], per,
+  wgrad1_kernel<<<nch, Wg1::THREADS, Wg1::SMEM, s>>>(tx, td, part, B, kLgIn[0], kLgOut[0], kStride[0], per,
                                                        device_status_word());
   return cuda_status(cudaGetLastError(), "network weight gradient");
 }

@@ -27,6 +27,10 @@ bool encode_tmap_2d_f32(CUtensorMap *map, const float *base, int W, int H, int p
 bool encode_tmap_nhwc32_bf16(CUtensorMap *map, const void *base, int S, int B, int box_x, int box_y, int box_b,
                              int estride);
 
+// 4-D float32 tensor map over the network's input stamps [B][C][S][S] (rows of S floats),
+// no swizzle, zero fill out of bounds; box: S columns x box_y rows x C channels x 1 stamp.
+bool encode_tmap_stamps_f32(CUtensorMap *map, const float *base, int S, int C, int B, int box_y);
+
 // Device-memory allocation on a stream for calls that received no workspace.
 struct ScopedWorkspace {
   void *ptr = nullptr;

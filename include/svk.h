@@ -216,9 +216,10 @@ SVK_API int svk_autotune(int N, int L, int degree, int precision, int W, int H, 
 /*
  * Coefficient network.  A small CNN predicts, from a (R, I) star-stamp pair, the local
  * kernel coefficients a_k (Eq. 3 evaluated at the stamp; Eq. 2 combines them with the
- * basis), as a fast stand-in for the least-squares fit of Sec. 2 whose result then
- * serves as its judge and fallback.  Input x: device float32 [batch][2][64][64] (channel 0
- * R, channel 1 I, both already normalised by the caller); output float32 [batch][n_out].
+ * basis), as a fast stand-in for the least-squares fit of Sec. 2, whose result is the
+ * reference for the network's error and its fallback.  Input x: device float32
+ * [batch][2][64][64] (channel 0 R, channel 1 I, both already normalised by the caller);
+ * output float32 [batch][n_out].
  * Architecture: four 3x3 convolutions (2->32 stride 2, 32->32 stride 2, 32->32 stride 2,
  * 32->32 stride 1, zero padding 1, ReLU), global average pooling, linear 32 -> n_out.
  * Parameters: one float32 vector of svk_cnn_param_count(n_out) values (FP32 master
@@ -363,14 +364,20 @@ SVK_API int svk_device_status(int reset, void *stream);
 SVK_API int svk_selftest_bounded_wait(unsigned long long limit_ns, unsigned long long *waited_ns, void *stream);
 
 /*
- * Measured multiply-add throughput of the current device, in FLOP/s (2 per FMA): FP32
- * FFMA (fp64 == 0) or FP64 DFMA (fp64 != 0).  These are the denominators of the direct
- * form's roofline (FP32 ALU bound) and of the fit's normal-equation accumulation (FP64).
- * Tooling with no counterpart in the paper.  Synchronous: launches one warm-up and one
- * timed kernel (~30 ms) on `stream` and waits for them; allocates a small scratch buffer.
+ * Measured multiply-add throughput of the current device, in FLOP/s (2 per FMA), for
+ * kind SVK_FMA_FP32 (scalar FP32 FFMA), SVK_FMA_FP64 (FP64 DFMA) or SVK_FMA_FP32X2
+ * (packed fma.rn.f32x2, two FP32 multiply-adds per instruction).  These are the
+ * denominators of the direct form's roofline (FP32 ALU bound: the larger of the two FP32
+ * kinds) and of the fit's normal-equation accumulation (FP64).  Tooling with no
+ * counterpart in the paper.  Synchronous: launches one warm-up and one timed kernel
+ * (~30 ms) on `stream` and waits for them; allocates a small scratch buffer.  Any other
+ * kind: SVK_ERR_ARG.
  *   flops_per_s  host double [1] (output).
  */
-SVK_API int svk_measure_fma_peak(int fp64, double *flops_per_s, void *stream);
+#define SVK_FMA_FP32 0
+#define SVK_FMA_FP64 1
+#define SVK_FMA_FP32X2 2
+SVK_API int svk_measure_fma_peak(int kind, double *flops_per_s, void *stream);
 
 /*
  * Bytes of device workspace svk_select_stamps needs for a W x H frame (about 4 bytes

@@ -31,6 +31,9 @@ SVK_PREC_FP32 = 0
 SVK_PREC_BF16X3 = 1
 SVK_PREC_FP16X3 = 2
 SVK_PREC_BF16 = 3
+SVK_FMA_FP32 = 0
+SVK_FMA_FP64 = 1
+SVK_FMA_FP32X2 = 2
 SVK_EDGE_ZERO = 0
 
 # every symbol include/svk.h declares (checked by the tests)
@@ -361,10 +364,11 @@ def svk_selftest_bounded_wait(limit_ns: int, stream=None):
     return st, int(w.value)
 
 
-def svk_measure_fma_peak(fp64: bool = False, stream=None) -> float:
-    """Measured FP32 (or FP64) multiply-add throughput of the current device, FLOP/s."""
+def svk_measure_fma_peak(kind: int = SVK_FMA_FP32, stream=None) -> float:
+    """Measured multiply-add throughput of the current device, FLOP/s: SVK_FMA_FP32
+    (scalar FFMA; also False), SVK_FMA_FP64 (DFMA; also True) or SVK_FMA_FP32X2 (packed)."""
     v = ctypes.c_double(0.0)
-    _check(load_library().svk_measure_fma_peak(int(bool(fp64)), ctypes.byref(v), _stream(stream)))
+    _check(load_library().svk_measure_fma_peak(int(kind), ctypes.byref(v), _stream(stream)))
     return v.value
 
 

@@ -482,9 +482,10 @@ int svk_selftest_bounded_wait(unsigned long long limit_ns, unsigned long long *w
   return selftest_bounded_wait(limit_ns, waited_ns, static_cast<cudaStream_t>(stream));
 }
 
-int svk_measure_fma_peak(int fp64, double *flops_per_s, void *stream) {
+int svk_measure_fma_peak(int kind, double *flops_per_s, void *stream) {
   if (!flops_per_s) return set_error(SVK_ERR_ARG, "NULL pointer argument");
-  return measure_fma_peak(fp64 ? 1 : 0, flops_per_s, static_cast<cudaStream_t>(stream));
+  if (kind < SVK_FMA_FP32 || kind > SVK_FMA_FP32X2) return set_error(SVK_ERR_ARG, "unknown FMA kind");
+  return measure_fma_peak(kind, flops_per_s, static_cast<cudaStream_t>(stream));
 }
 
 size_t svk_select_workspace_size(int W, int H) {

@@ -66,8 +66,8 @@ size_t method_ws(int method, int precision, int N, int L, int degree) {
 
 // Output-row block of the method: band boundaries are multiples of it (0: no plan).
 int band_granule(int method, int precision, int N, int L, int degree) {
-  if (method == SVK_METHOD_DIRECT || (method == SVK_METHOD_TFORM && precision == SVK_PREC_FP32))
-    return direct_rows(L);
+  if (method == SVK_METHOD_DIRECT) return direct_rows(L);
+  if (method == SVK_METHOD_TFORM && precision == SVK_PREC_FP32) return tform_fp32_rows(L);
   return tc_rows_per_block(method == SVK_METHOD_TFORM ? n_terms(degree) : N, L, precision);
 }
 

@@ -17,6 +17,13 @@ int launch_direct(const float *R, int pitch_R, const float *I, int pitch_I, int 
                   const float *basis, int N, int L, const float *coeffs, int degree, float *out,
                   int pitch_out, cudaStream_t s, int y_begin = 0, int y_end = -1);
 
+// T-factored form on the CUDA cores (svk_direct.cu): D = sum_t m_t (R (x) K_t) - I for
+// the T in {1, 3, 6, 10} stamps Kt [T][L][L]; bands as for launch_direct, block height
+// tform_fp32_rows(L) (16 rows).
+int tform_fp32_rows(int L);
+int launch_tform_fp32(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *Kt, int T,
+                      int L, float *out, int pitch_out, cudaStream_t s, int y_begin = 0, int y_end = -1);
+
 // Basis tabulation (svk_basis.cu).
 int launch_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg,
                        int normalize, float *basis_out, int N, cudaStream_t s);
@@ -68,7 +75,7 @@ int launch_select(const float *R, int W, int H, int pitch, float sky, float thre
 int selftest_bounded_wait(unsigned long long limit_ns, unsigned long long *waited_ns, cudaStream_t s);
 
 // Measured FMA throughput (svk_peaks.cu).
-int measure_fma_peak(int fp64, double *flops_per_s, cudaStream_t s);
+int measure_fma_peak(int kind, double *flops_per_s, cudaStream_t s);  // SVK_FMA_*
 
 // Coefficient network (svk_cnn.cu).
 int cnn_param_count(int n_out);

@@ -1,14 +1,32 @@
 // svk_peaks.cu -- measured FMA throughput of this GPU, the denominators of the rooflines
-// of the direct form (FP32 FFMA) and of the fit's normal equations (FP64 DFMA).
+// of the direct form (FP32 FFMA, scalar or packed f32x2) and of the fit's normal
+// equations (FP64 DFMA).
 //
 // Each thread runs eight independent multiply-add chains x <- x * a + b (|a| < 1, so the
-// values stay bounded); 2 FLOP per multiply-add.  The grid is 8 blocks of 256 threads
-// per SM, enough warps to cover the pipeline latency.
+// values stay bounded); 2 FLOP per multiply-add, two multiply-adds per packed f32x2
+// instruction.  The grid is 8 blocks of 256 threads per SM, enough warps to cover the
+// pipeline latency.
 #include "svk_common.cuh"
 #include "svk_internal.h"
 
 namespace svk {
 namespace {
+
+// Packed FP32 pairs (low, high) in one 64-bit register: one fma.rn.f32x2 performs two
+// independent round-to-nearest FP32 multiply-adds, one per half.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) fma_chains(T *out, int iters, T a, T b) {
@@ -28,7 +46,29 @@ __global__ void __launch_bounds__(256) fma_chains(T *out, int iters, T a, T b) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
 }
 
-template <typename T>
+// packed FP32: eight chains of f32x2 pairs, 16 multiply-adds per iteration
+__global__ void __launch_bounds__(256) fma2_chains(float *out, int iters, float a, float b) {
+  const float t = (float)threadIdx.x * 1e-6f;
+  uint64_t x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = f2_pack(t + (float)c, t + (float)c + 0.5f);
+  const uint64_t a2 = f2_pack(a, a), b2 = f2_pack(b, b);
+#pragma unroll 4
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = f2_fma(x[c], a2, b2);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float lo, hi;
+    f2_unpack(x[c], lo, hi);
+    s += lo + hi;
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T, bool PACKED = false>
 int time_fma(int iters, double *flops_per_s, cudaStream_t s) {
   int dev = 0, sms = 0;
   int st = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
@@ -45,9 +85,13 @@ int time_fma(int iters, double *flops_per_s, cudaStream_t s) {
     cudaEventDestroy(e0);
     return st;
   }
-  fma_chains<T><<<blocks, threads, 0, s>>>(out, iters / 4, (T)0.999999, (T)1e-6);  // warm-up
+  auto run = [&](int n) {
+    if constexpr (PACKED) fma2_chains<<<blocks, threads, 0, s>>>(out, n, 0.999999f, 1e-6f);
+    else fma_chains<T><<<blocks, threads, 0, s>>>(out, n, (T)0.999999, (T)1e-6);
+  };
+  run(iters / 4);  // warm-up
   cudaEventRecord(e0, s);
-  fma_chains<T><<<blocks, threads, 0, s>>>(out, iters, (T)0.999999, (T)1e-6);
+  run(iters);
   cudaEventRecord(e1, s);
   st = cuda_status(cudaEventSynchronize(e1), "FMA timing");
   float ms = 0.0f;
@@ -55,15 +99,17 @@ int time_fma(int iters, double *flops_per_s, cudaStream_t s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != SVK_OK) return st;
-  *flops_per_s = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
+  *flops_per_s = 2.0 * (PACKED ? 16.0 : 8.0) * (double)iters * blocks * threads / (ms * 1e-3);
   return SVK_OK;
 }
 
 }  // namespace
 
-int measure_fma_peak(int fp64, double *flops_per_s, cudaStream_t s) {
+int measure_fma_peak(int kind, double *flops_per_s, cudaStream_t s) {
   // about 30 ms each at the nominal rates
-  return fp64 ? time_fma<double>(1 << 14, flops_per_s, s) : time_fma<float>(1 << 20, flops_per_s, s);
+  if (kind == 1) return time_fma<double>(1 << 14, flops_per_s, s);
+  if (kind == 2) return time_fma<float, true>(1 << 19, flops_per_s, s);
+  return time_fma<float>(1 << 20, flops_per_s, s);
 }
 
 }  // namespace svk

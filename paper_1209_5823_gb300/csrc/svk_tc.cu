@@ -886,16 +886,16 @@ int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W
                  size_t ws_bytes, cudaStream_t s, int y_begin, int y_end, bool prep) {
   const int T = n_terms(degree);
   if (precision == SVK_PREC_FP32) {
-    // FFMA pipe: the direct kernel over the T stamps K_t with identity coefficients, so
-    // the kernel it forms at (x, y) is sum_t m_t(x, y) K_t
+    // FFMA pipe: the T convolutions R (x) K_t accumulated per pixel, combined with the
+    // pixel's monomials in the epilogue
     const size_t head = tform_head_bytes(T, L);
     if (!ws || ws_bytes < head) return set_error(SVK_ERR_WORKSPACE, "T-form workspace too small");
     float *Kt = static_cast<float *>(ws);
     float *ident = Kt + (size_t)T * L * L;
     const int n = T * L * L > T * T ? T * L * L : T * T;
     if (prep) tform_combine_kernel<<<(n + 255) / 256, 256, 0, s>>>(basis, coeffs, N, T, L * L, Kt, ident);
-    return launch_direct(R, pitch_R, I, pitch_I, W, H, Kt, T, L, ident, degree, out, pitch_out, s, y_begin,
-                         y_end < 0 ? H : y_end);
+    return launch_tform_fp32(R, pitch_R, I, pitch_I, W, H, Kt, T, L, out, pitch_out, s, y_begin,
+                             y_end < 0 ? H : y_end);
   }
   Plan pl;
   if (!plan_for(T, L, precision, &pl))

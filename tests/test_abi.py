@@ -75,6 +75,13 @@ def test_build_basis_argument_checks(lib):
     assert lib.svk_build_basis(0, 5, 1, neg, dg, 1, vp(1), None, vp(0)) == svk.SVK_ERR_ARG
 
 
+def test_fma_peak_argument_checks(lib):
+    v = ctypes.c_double(0.0)
+    assert lib.svk_measure_fma_peak(3, ctypes.byref(v), None) == svk.SVK_ERR_ARG
+    assert lib.svk_measure_fma_peak(-1, ctypes.byref(v), None) == svk.SVK_ERR_ARG
+    assert lib.svk_measure_fma_peak(svk.SVK_FMA_FP32X2, None, None) == svk.SVK_ERR_ARG
+
+
 def test_fit_argument_checks(lib):
     vp = ctypes.c_void_p
     f = lambda **k: lib.svk_fit_coeffs(vp(1), vp(1), k.get("W", 64), 64, 64, vp(1), k.get("ns", 4),

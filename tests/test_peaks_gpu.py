@@ -7,12 +7,18 @@ pytestmark = pytest.mark.gpu
 
 
 def test_fma_peaks_are_plausible():
-    fp32 = svk.svk_measure_fma_peak(False)
-    fp64 = svk.svk_measure_fma_peak(True)
-    # 152 SMs x 128 FP32 lanes x 2 FLOP at up to 2.07 GHz is 80.5 TFLOP/s; FP64 is a small
-    # fraction of that on this part
+    fp32 = svk.svk_measure_fma_peak(svk.SVK_FMA_FP32)
+    fp32x2 = svk.svk_measure_fma_peak(svk.SVK_FMA_FP32X2)
+    fp64 = svk.svk_measure_fma_peak(svk.SVK_FMA_FP64)
+    # 152 SMs x 128 FP32 lanes x 2 FLOP at up to 2.07 GHz is 80.5 TFLOP/s, scalar or packed
+    # (the packed form drives the same lanes); FP64 is a small fraction of that on this part
     assert 20e12 < fp32 < 90e12
+    assert 20e12 < fp32x2 < 90e12
     assert 0.1e12 < fp64 < fp32
+    # the old boolean form still selects FP32 / FP64
+    assert 20e12 < svk.svk_measure_fma_peak(False) < 90e12
+    with pytest.raises(svk.SvkError):
+        svk.svk_measure_fma_peak(3)
 
 
 def test_bounded_wait_gives_up_and_context_stays_usable():

@@ -20,6 +20,7 @@ def _dev(a):
     (300, 177, 19, 2, svk.SVK_BASIS_GAUSS),   # many output rows per block, ragged
     (260, 90, 25, 3, svk.SVK_BASIS_GAUSS),
     (130, 61, 31, 0, svk.SVK_BASIS_GAUSS),
+    (140, 50, 31, 3, svk.SVK_BASIS_GAUSS),   # the largest stamp table: T = 10 at L = 31
     (47, 38, 7, 2, svk.SVK_BASIS_DELTA),      # the paper's delta basis, L = 7
     (200, 70, 19, 2, svk.SVK_BASIS_DELTA),    # 361 delta stamps: beyond the basis form's N
     (1, 1, 5, 2, svk.SVK_BASIS_GAUSS),

@@ -123,7 +123,7 @@ def test_maximum_frame_extents(W, H, pitch):
     It[:, :W] = torch.from_numpy(I)
     ct = torch.from_numpy(c).cuda()
     for method, prec in [(svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3), (svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32),
-                         (svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3)]:
+                         (svk.SVK_METHOD_TFORM, svk.SVK_PREC_BF16X3), (svk.SVK_METHOD_TFORM, svk.SVK_PREC_FP32)]:
         D = svk.svk_difference(Rt[:, :W], It[:, :W], B, ct, d, method=method, precision=prec)
         torch.cuda.synchronize()
         got = D.cpu().numpy()[ys, xs].astype(np.float64) + I[ys, xs]

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kCkThreads) fit_ck_kernel(const float *__restr
 __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__ C, const float *__restrict__ I,
                                                        const float *__restrict__ weight, const int *stamp_xy, FitDims f,
                                                        int px_per_cta, double *__restrict__ S) {
-  __shared__ float Es[kChunk][66];          // extended columns of the staged pixels (NE <= 66)
+  __shared__ double Es[kChunk][66];         // extended columns of the staged pixels (NE <= 66), widened once
   __shared__ double Ms[kChunk][kMaxMu];     // w * mu(p)
   const int npairs = f.NE * (f.NE + 1) / 2;
   const int pair = blockIdx.y * blockDim.x + threadIdx.x;
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
           else v = 1.0f;
         }
       }
-      Es[q][e] = v;
+      Es[q][e] = (double)v;
     }
     for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
       const int p = pc + q;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
     if (pair < npairs) {
       const int nq = min(kChunk, p1 - pc);
       for (int q = 0; q < nq; ++q) {
-        const double e = (double)Es[q][e1] * (double)Es[q][e2];
+        const double e = Es[q][e1] * Es[q][e2];
 #pragma unroll
         for (int m = 0; m < kMaxMu; ++m)
           if (m < f.n_mu) acc[m] = fma(e, Ms[q][m], acc[m]);

@@ -33,3 +33,14 @@ def test_tform_matches_oracle(W, H, L, d, kind, prec):
     ref = oracle_conv(R, B.cpu().numpy(), c, d)
     D = svk.svk_difference(_dev(R), _dev(I), B, _dev(c), d, method=svk.SVK_METHOD_TFORM, precision=prec)
     assert rel_err(D.cpu().numpy().astype(np.float64) + I, ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("prec", [svk.SVK_PREC_BF16X3, svk.SVK_PREC_FP32])
+def test_tform_plain_convolution(prec):
+    # svk_convolve (no I): R (x) K alone, through the same T-form kernels
+    R, _ = star_pair(211, 97, 60, 777)
+    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, 15)
+    c = coeffs(B.shape[0], 3, 5)
+    ref = oracle_conv(R, B.cpu().numpy(), c, 3)
+    out = svk.svk_convolve(_dev(R), B, _dev(c), 3, method=svk.SVK_METHOD_TFORM, precision=prec)
+    assert rel_err(out.cpu().numpy().astype(np.float64), ref) <= TOL_FP32

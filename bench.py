@@ -711,7 +711,7 @@ def main():
     wst = torch.empty(svk.svk_workspace_size(svk.SVK_METHOD_TFORM, prec, W, H, N, L, d), dtype=torch.uint8, device=dev)
     tf_ms = _time(torch, lambda: svk.svk_difference(Rs[0], Is[0], basis, ct, d, method=svk.SVK_METHOD_TFORM,
                                                     precision=prec, out=Dt, workspace=wst), reps=20)
-    # the T-form on the CUDA cores (FP32 FFMA: the direct kernel over the T stamps K_t)
+    # the T-form on the CUDA cores (FP32 FFMA: the T convolutions R (x) K_t accumulated per pixel)
     Dtf32 = torch.empty((H, W), dtype=torch.float32, device=dev)
     wst32 = torch.empty(max(1, svk.svk_workspace_size(svk.SVK_METHOD_TFORM, svk.SVK_PREC_FP32, W, H, N, L, d)),
                         dtype=torch.uint8, device=dev)

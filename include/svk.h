@@ -75,7 +75,7 @@ extern "C" {
                             /* B_k: T = (d+1)(d+2)/2 convolutions instead of N; any N       */
                             /* (delta bases included); on the tensor cores with the         */
                             /* precisions of SVK_METHOD_BASIS, or on the CUDA cores with    */
-                            /* SVK_PREC_FP32 (the direct kernel over the T stamps K_t)      */
+                            /* SVK_PREC_FP32 (the T convolutions accumulated per pixel)     */
 
 /* arithmetic of the contraction */
 #define SVK_PREC_FP32 0   /* DIRECT, TFORM: FP32 FFMA on the CUDA cores                   */

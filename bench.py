@@ -389,7 +389,7 @@ def _precision_table(svk, torch, dev):
     return out
 
 
-def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=3000):
+def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=10000):
     """Coefficient network trained on n_pairs (R, I) stamp pairs the plain method makes,
     then applied to the 2048 x 4096 frame against the FP64 fit."""
     import time as _t
@@ -570,7 +570,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the night-batch and fit measurements")
     ap.add_argument("--learned-only", action="store_true",
                     help="only the coefficient-network measurement (its own JSON line; for profiling)")
-    ap.add_argument("--learned-steps", type=int, default=3000, help="training steps of that measurement")
+    ap.add_argument("--learned-steps", type=int, default=10000, help="training steps of that measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

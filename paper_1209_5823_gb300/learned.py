@@ -97,11 +97,14 @@ class CoefficientNetwork:
         self._graph = None  # the gradient call over those buffers, captured as a CUDA graph
         self._graph_key = None
 
+    _HIST = 1 << 14  # steps whose losses the captured step keeps on the device
+
     def _step_graph(self, x, z, lr):
         """One training step over fixed buffers as a CUDA graph: gather the batch named by
-        the index buffer, svk_cnn_gradient, advance the device step count, Adam
-        (svk_cnn_adam_device_step).  Captured once per (inputs, learning rate); the kernels
-        and their arguments are those of the eager step."""
+        the index buffer, svk_cnn_gradient, store the loss at the step's slot of a device
+        history ring, advance the device step count, Adam (svk_cnn_adam_device_step).
+        Captured once per (inputs, learning rate); the kernels and their arguments are those
+        of the eager step."""
         dev = x.device
         shape = (self.batch,) + tuple(x.shape[1:])
         if self._bufs is None or self._bufs["x"].shape != shape or self._bufs["x"].device != dev:
@@ -109,7 +112,8 @@ class CoefficientNetwork:
                           "x": torch.zeros(shape, dtype=torch.float32, device=dev),
                           "z": torch.zeros((self.batch, self.n_out), dtype=torch.float32, device=dev),
                           "grad": torch.zeros_like(self.params), "loss": torch.zeros(1, dtype=torch.float32, device=dev),
-                          "step": torch.zeros(1, dtype=torch.int32, device=dev)}
+                          "step": torch.zeros(1, dtype=torch.int32, device=dev),
+                          "hist": torch.zeros(self._HIST, dtype=torch.float32, device=dev)}
             self._graph_key = None
         b = self._bufs
         key = (x.data_ptr(), z.data_ptr(), tuple(x.shape), float(lr), self.params.data_ptr(), self.ws.data_ptr())
@@ -124,6 +128,7 @@ class CoefficientNetwork:
                 torch.index_select(x, 0, b["idx"], out=b["x"])
                 torch.index_select(z, 0, b["idx"], out=b["z"])
                 svk_cnn_gradient(self.params, b["x"], b["z"], grad=b["grad"], loss=b["loss"], workspace=self.ws)
+                b["hist"].index_copy_(0, torch.remainder(b["step"], self._HIST).long(), b["loss"])
                 b["step"].add_(1)
                 svk_cnn_adam_device_step(self.params, self.m, self.v, b["grad"], b["step"], lr=lr)
             self._graph, self._graph_key = graph, key
@@ -138,10 +143,18 @@ class CoefficientNetwork:
         graph, b = self._step_graph(x, z, lr)
         b["step"].fill_(self.step)
         n = x.shape[0]
-        for s in range(steps):
-            torch.randint(0, n, (self.batch,), generator=gen, out=b["idx"])
-            graph.replay()
-            losses[s:s + 1].copy_(b["loss"])
+        done = 0
+        while done < steps:  # chunks of at most one history ring
+            c = min(self._HIST, steps - done)
+            for _ in range(c):
+                torch.randint(0, n, (self.batch,), generator=gen, out=b["idx"])
+                graph.replay()
+            first = (self.step + done) % self._HIST
+            head = min(c, self._HIST - first)
+            losses[done:done + head].copy_(b["hist"][first:first + head])
+            if head < c:
+                losses[done + head:done + c].copy_(b["hist"][:c - head])
+            done += c
         self.step += steps
         return losses
 

@@ -162,8 +162,9 @@ SVK_API int svk_difference(const float *R, int pitch_R, const float *I, int pitc
  * (precision SVK_PREC_BF16X3 / FP16X3 / BF16) and no workspace.
  * Scratch: one 512 KiB __device__ array inside this library, held on every device that
  * loads it until the process exits; requests needing more return SVK_ERR_WORKSPACE.
- * The first call on a device looks up the array's device address (once per device);
- * make that first call before any stream capture.  All calls share the array and it
+ * The first call on a device looks up the array's device address (again after that
+ * device's context was replaced, e.g. by cudaDeviceReset); make that first call before
+ * any stream capture.  All calls share the array and it
  * keeps the last call's contents, so calls that overlap on the GPU race: serialise them.
  */
 SVK_API int svk_difference_noalloc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,

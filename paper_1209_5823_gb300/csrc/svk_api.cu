@@ -111,22 +111,62 @@ ScopedWorkspace::~ScopedWorkspace() {
   if (owned && ptr) cudaFreeAsync(ptr, stream);
 }
 
+// The driver's id of the calling thread's current context, or 0 when there is none or it
+// cannot be read.  Ids are unique for the life of the process: a context destroyed (by
+// cudaDeviceReset, for instance) and created again gets a new id even where the driver
+// hands out the same handle.
+static unsigned long long current_context_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+int symbol_address(SymbolAddressCache &cache, const void *symbol, const char *what, void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+  if (dev < 0 || dev >= SymbolAddressCache::kMaxDevices)
+    return set_error(SVK_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, SymbolAddressCache::kMaxDevices);
+  std::lock_guard<std::mutex> lock(cache.mu);
+  const unsigned long long id = current_context_id();
+  if (!cache.addr[dev] || id == 0 || id != cache.ctx[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, symbol);  // creates the device's context if there is none yet
+    if (e != cudaSuccess) return cuda_status(e, what);
+    cache.addr[dev] = p;
+    cache.ctx[dev] = current_context_id();
+  }
+  *out = cache.addr[dev];
+  return SVK_OK;
+}
+
 // Sticky device status word: the library's bounded device waits record a timeout here
 // (kernels get its address as their status pointer); svk_device_status reads and clears it.
 __device__ uint32_t g_device_status;
 
 uint32_t *device_status_word() {
-  static std::mutex mu;
-  static uint32_t *addr[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
-    addr[dev] = static_cast<uint32_t *>(p);
-  }
-  return addr[dev];
+  static SymbolAddressCache cache;
+  void *p = nullptr;
+  if (symbol_address(cache, reinterpret_cast<const void *>(&g_device_status), "cudaGetSymbolAddress(status word)",
+                     &p) != SVK_OK)
+    return nullptr;
+  return static_cast<uint32_t *>(p);
 }
 
 }  // namespace svk

@@ -497,7 +497,10 @@ __global__ void __launch_bounds__(kTfThreads, 2)
         ld_nc_v8(mask + (size_t)p * kCh + 16, mw[1]);
       }
       const int buf = tcount & 1;
-      if (!mbar_wait_bounded(&tfull[buf], (tcount >> 1) & 1, status)) break;
+      // the warp leaves together if any lane's wait ran out (the TMEM loads below are
+      // warp-aligned)
+      const bool okw = mbar_wait_bounded(&tfull[buf], (tcount >> 1) & 1, status);
+      if (__any_sync(0xffffffffu, !okw)) break;
       tc_fence_after();
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
@@ -647,7 +650,8 @@ __global__ void __launch_bounds__(kWtThreads, 1)
   } else {
     // ============================================================= epilogue (warps 2-5)
     const int q = warp & 3;
-    const bool ok = nst > 0 && mbar_wait_bounded(tdone, 0, status);
+    // one decision per warp: the TMEM loads below are warp-aligned
+    const bool ok = __all_sync(0xffffffffu, nst > 0 && mbar_wait_bounded(tdone, 0, status));
     if (ok) {
       tc_fence_after();
 #pragma unroll

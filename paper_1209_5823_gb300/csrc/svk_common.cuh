@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "svk.h"
 
 namespace svk {
@@ -48,6 +50,19 @@ enum DeviceStatus : uint32_t { kDevOk = 0, kDevTimeout = 1 };
 // Address of the library's sticky device status word on the current device (the
 // kernels' status pointer), or NULL if it cannot be resolved.
 uint32_t *device_status_word();
+
+// Device addresses of a file-scope __device__ variable, one per device ordinal, each
+// remembered with the context it was looked up in.  In host code such a variable's name
+// is only a host-side stand-in, so its device address comes from cudaGetSymbolAddress
+// with the device current; it is looked up again whenever the device's current context
+// differs from the remembered one (after a cudaDeviceReset, for instance).
+struct SymbolAddressCache {
+  static constexpr int kMaxDevices = 64;
+  std::mutex mu;
+  void *addr[kMaxDevices] = {};
+  unsigned long long ctx[kMaxDevices] = {};
+};
+int symbol_address(SymbolAddressCache &cache, const void *symbol, const char *what, void **out);
 
 // ------------------------------------------------------------------ device side
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

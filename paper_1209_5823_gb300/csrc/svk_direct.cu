@@ -105,7 +105,10 @@ __global__ void __launch_bounds__(kTX * TY, 1)
     }
     __syncthreads();
     if (!tile_ready) {
-      if (!mbar_wait_bounded(bar, 0, status)) return;  // TMA never landed: give up cleanly
+      // TMA never landed: the whole block gives up together (no thread is left at the
+      // next chunk's __syncthreads)
+      const bool ok = mbar_wait_bounded(bar, 0, status);
+      if (__syncthreads_or(!ok)) return;
       tile_ready = true;
     }
     // a_j(x_p, y) = sum_t c[k0+j][t] xt^i yt^j for the chunk (Eq. 3, order <= 3): per stamp

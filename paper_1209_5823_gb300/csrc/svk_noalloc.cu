@@ -14,8 +14,6 @@
 // exceed it; a request that would is rejected with SVK_ERR_WORKSPACE.  All calls share
 // the array and it keeps the last call's contents: calls that overlap on the GPU (two
 // streams, or two host threads) race on it and must be serialised by the caller.
-#include <mutex>
-
 #include "svk_common.cuh"
 #include "svk_internal.h"
 
@@ -23,30 +21,17 @@ namespace svk {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 512 * 1024;
-constexpr int kMaxDevices = 64;
-
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_addr_mutex;
-void *g_addr[kMaxDevices] = {nullptr};
+SymbolAddressCache g_scratch_addr;
 
 // Device address of the scratch array on the current device.  In host code the array's
-// name is only a host-side stand-in, so its address is looked up once per device (with
-// that device current) and cached.
+// name is only a host-side stand-in, so its address is looked up with the device current
+// (the first call on a device, and again after that device's context was replaced) and
+// cached per device.
 int scratch_address(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return set_error(SVK_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDevices);
-  std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(no-allocation scratch)");
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
-  return SVK_OK;
+  return symbol_address(g_scratch_addr, reinterpret_cast<const void *>(g_noalloc_scratch),
+                        "cudaGetSymbolAddress(no-allocation scratch)", out);
 }
 
 }  // namespace

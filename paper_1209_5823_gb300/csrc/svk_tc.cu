@@ -153,6 +153,23 @@ static bool choose_plan(int N, int L, int prec, Plan *p) {
 
 __device__ __forceinline__ void epi_bar_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+// Named barrier 1 over the 256 epilogue threads that also ORs a predicate: every epilogue
+// thread gets the same answer, so a decision to give up (a bounded wait that ran out in
+// any of them) is taken by all of them together and none is left at a barrier the others
+// have abandoned.
+__device__ __forceinline__ bool epi_bar_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, 256, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
 // Split x into hi + lo 16-bit floats; returns the two bit patterns.
 template <int PREC>
 __device__ __forceinline__ void split16(float x, uint16_t &hi, uint16_t &lo) {
@@ -341,7 +358,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int k = 0; k < nprod && nx.valid(); ++k) nx.next(fs, G, h);
       if (nx.valid() && nx.real()) load_row(nx, nxt);  // in flight while this row is built
       const int stage = seq % NS, grp = stage / kRowsPerGroup;
-      if (!mbar_wait_bounded(&empty[grp], ((seq / NS) & 1) ^ 1, status)) goto done;
+      // every lane waits; the warp leaves together if any lane's wait ran out (the
+      // warp-synchronous code below must not run with part of the warp gone)
+      const bool ok = mbar_wait_bounded(&empty[grp], ((seq / NS) & 1) ^ 1, status);
+      if (__any_sync(0xffffffffu, !ok)) goto done;
       if (it.real()) {
         // hi/lo 16-bit copies of the segment; copy 1 is shifted by one element so every
         // 8-element chunk starts on a 4-byte boundary in one of the two copies
@@ -587,7 +607,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int j = 0; j < 3; ++j) ival[j] = inext[j];
       if (b + 1 < b_end) load_I(b + 1, advance_frame(fs, f, b + 1), inext);
-      if (!mbar_wait_bounded(&acc_full[buf], (blk_seq >> 1) & 1, status)) break;
+      // each thread times its own wait; the epilogue gives up only as a whole (the TMEM
+      // loads are warp-aligned and the named barriers count all 256 threads)
+      const bool ok = mbar_wait_bounded(&acc_full[buf], (blk_seq >> 1) & 1, status);
+      if (epi_bar_any(!ok)) break;
       tc_fence_after();
       const uint32_t tbase = tmem_base + lane_off + (uint32_t)(buf * kAccStride);
 #pragma unroll 1

@@ -170,6 +170,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _config(W, H, L, N, d):
+    """The workload both arms run (the same dict on the svk and the reference line)."""
+    return {"workload": WORKLOAD, "W": W, "H": H, "L": L, "N": N, "degree": d,
+            "basis": "gauss 0.7/1.5/2.5 deg 6/4/2",
+            "l2": f"inputs larger than L2: {NROT} rotating frames of R, I, D ({NROT * 3 * W * H * 4 / 2**20:.0f} MB)"}
+
+
 def _frame_spec(rank=0):
     """Rank r of a multi-GPU run times its own frame: same shape, seed offset by r."""
     import dataclasses
@@ -551,8 +558,8 @@ def run_reference(args, rank):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "W": W, "H": H, "L": spec.L, "N": 49,
-                                             "degree": spec.degree},
+            "data": "synthetic", "config": _config(W, H, spec.L, 49, spec.degree),
+            "path": {"method": "FP64 C oracle on the host cores"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{rows} rows x {W} px of the frame per step (rows {y0}..{y0 + rows - 1})"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -749,9 +756,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": f"{args.precision}-f32acc", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "W": W, "H": H, "L": L, "N": N, "degree": d, "basis": "gauss 0.7/1.5/2.5 deg 6/4/2",
-                   "method": "basis (tcgen05)", "precision": args.precision,
-                   "l2": f"{NROT} rotating input frames ({NROT * 3 * px * 4 / 2**20:.0f} MB > L2)"},
+        "config": _config(W, H, L, N, d),
+        "path": {"method": "basis (tcgen05)", "precision": args.precision},
         "gpu_launches": launches_per_step * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * px * 4, "d2h_bytes_per_step": px * 4,
                 "call": f"svk_difference_host_batch over the {n_e2e} timed frames (pinned host buffers rotating over "

@@ -310,7 +310,12 @@ static void design_vector(const double *R, int W, int H, const double *basis, in
 }
 
 /* Accumulate the normal equations over all stamp pixels.  Stamps are S x S (S odd)
- * centred on stamp_xy[2s], stamp_xy[2s+1]; pixels outside the frame are skipped. */
+ * centred on stamp_xy[2s], stamp_xy[2s+1]; pixels outside the frame are skipped.
+ * A = sum_p w v v^T and b = sum_p w v I over the stamp pixels p in order (stamp by stamp,
+ * rows then columns).  OpenMP only splits the work: a stamp's design vectors are formed
+ * pixel by pixel in parallel, then each thread owns whole rows of A and adds the pixels'
+ * contributions to them in that same pixel order, so every element is the same sum in
+ * the same order as a single-threaded loop. */
 int svko_normal_equations(const double *R, const double *I, int W, int H, const int *stamp_xy,
                           int n_stamps, int S, const double *basis, int N, int L, int degree,
                           int bg_degree, const double *weight, double *A, double *b) {
@@ -318,27 +323,40 @@ int svko_normal_equations(const double *R, const double *I, int W, int H, const 
         bg_degree < -1 || bg_degree > 7)
         return SVKO_ERR_ARG;
     const int T = svko_n_terms(degree), M = N * T + svko_n_terms(bg_degree), hs = (S - 1) / 2;
+    const int P = S * S;
     memset(A, 0, sizeof(double) * (size_t)M * M);
     memset(b, 0, sizeof(double) * (size_t)M);
-    double *v = (double *)malloc(sizeof(double) * M);
+    double *V = (double *)malloc(sizeof(double) * (size_t)P * M);
+    double *wp = (double *)malloc(sizeof(double) * P);
+    double *ip = (double *)malloc(sizeof(double) * P);
+    int *valid = (int *)malloc(sizeof(int) * P);
     for (int s = 0; s < n_stamps; ++s) {
         const int cx = stamp_xy[2 * s], cy = stamp_xy[2 * s + 1];
-        for (int y = cy - hs; y <= cy + hs; ++y) {
-            if (y < 0 || y >= H) continue;
-            for (int x = cx - hs; x <= cx + hs; ++x) {
-                if (x < 0 || x >= W) continue;
-                design_vector(R, W, H, basis, N, L, degree, bg_degree, x, y, v);
-                const double w = weight ? weight[(size_t)y * W + x] : 1.0;
-                const double iv = I[(size_t)y * W + x];
-                for (int i = 0; i < M; ++i) {
-                    const double wvi = w * v[i];
-                    b[i] += wvi * iv;
-                    for (int j = 0; j < M; ++j) A[(size_t)i * M + j] += wvi * v[j];
-                }
+#pragma omp parallel for schedule(static)
+        for (int p = 0; p < P; ++p) {
+            const int y = cy - hs + p / S, x = cx - hs + p % S;
+            valid[p] = (y >= 0 && y < H && x >= 0 && x < W);
+            if (!valid[p]) continue;
+            design_vector(R, W, H, basis, N, L, degree, bg_degree, x, y, V + (size_t)p * M);
+            wp[p] = weight ? weight[(size_t)y * W + x] : 1.0;
+            ip[p] = I[(size_t)y * W + x];
+        }
+#pragma omp parallel for schedule(static)
+        for (int i = 0; i < M; ++i) {
+            double *Ai = A + (size_t)i * M;
+            for (int p = 0; p < P; ++p) {
+                if (!valid[p]) continue;
+                const double *v = V + (size_t)p * M;
+                const double wvi = wp[p] * v[i];
+                b[i] += wvi * ip[p];
+                for (int j = 0; j < M; ++j) Ai[j] += wvi * v[j];
             }
         }
     }
-    free(v);
+    free(V);
+    free(wp);
+    free(ip);
+    free(valid);
     return SVKO_OK;
 }
 

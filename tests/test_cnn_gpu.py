@@ -75,6 +75,27 @@ def test_ragged_batch_matches_oracle():
     _check_against_oracle(37, 49, 21)
 
 
+def test_training_batch_matches_oracle():
+    # the training batch (256 stamps): the weight gradients are split into the chunk
+    # counts and reduced in the fixed order that training runs
+    _check_against_oracle(256, 49, 31)
+
+
+def test_forward_4096_sampled_matches_oracle():
+    # the 4096-stamp forward pass the bench times; each stamp's output depends on that
+    # stamp alone, so 64 seeded stamps of it are compared with the oracle
+    n_out, B = 49, 4096
+    p = starfield.cnn_init_params(n_out, 41)
+    x, _ = _data(B, n_out, 42)
+    out = svk.svk_cnn_forward(torch.from_numpy(p).cuda(), torch.from_numpy(x).cuda(), n_out).cpu().numpy()
+    assert svk.svk_device_status() == svk.SVK_OK
+    pick = np.sort(starfield.rng(43).choice(B, 64, replace=False))
+    pick[-1] = B - 1  # the last tile of every layer included
+    ref, _ = ocnn.forward(bf16_round(p).astype(np.float64), x[pick].astype(np.float64), n_out,
+                          rounding=ocnn.round_bf16)
+    assert np.abs(out[pick] - ref).max() <= TOL_OUT * np.abs(ref).max()
+
+
 def test_gradient_is_deterministic():
     n_out = 49
     p = torch.from_numpy(starfield.cnn_init_params(n_out, 3)).cuda()

@@ -528,6 +528,49 @@ def _paper_sweep(svk, torch, dev):
             "paper_model": "20 L^2 + 1 FLOP per pixel (Sec. 3)"}
 
 
+def _sharded_frame(svk, torch, dist, rank, world, R, I, c, spec, reps=5):
+    """One frame split over the ranks (strong scaling of a single frame): each rank copies
+    its band of rows (plus the kernel's halo) from pinned host memory, computes its rows of
+    D, and the OIS fit sums the ranks' FP64 moments with one all-reduce before every rank
+    solves.  Runs only with more than one rank."""
+    import numpy as np
+    from paper_1209_5823_gb300 import shard
+    H, W = R.shape
+    Rh, Ih = torch.from_numpy(R).pin_memory(), torch.from_numpy(I).pin_memory()
+    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, spec.L)
+    ct = torch.from_numpy(c).cuda()
+    sel = dict(sky=1000.0, threshold=150.0, saturation=20000.0, margin=30, iso_radius=20, iso_frac=0.05,
+               max_stamps=500)
+    xy, counts = svk.svk_select_stamps(torch.from_numpy(R).cuda(), **sel)
+    xy = xy[:int(counts[0].item())].cpu().numpy()
+    B25 = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, 25)
+
+    def band():
+        return shard.difference_band(Rh, Ih, B, ct, spec.degree, svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3,
+                                     rank=rank, world=world)
+
+    def fit():
+        return shard.fit_coeffs(Rh, Ih, xy, 41, B25, 3, 0, rank=rank, world=world)
+
+    out = {}
+    for name, fn in (("difference_rows", band), ("fit", fit)):
+        fn()
+        torch.cuda.synchronize()
+        dist.barrier()
+        t = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t) / reps * 1e3
+        ms = _max_over_ranks(dist, [ms], torch.device("cuda", torch.cuda.current_device()))[0]
+        out[name] = {"ms": ms}
+    out["difference_rows"]["value"] = W * H / (out["difference_rows"]["ms"] / 1e3) / 1e6
+    out["difference_rows"]["unit"] = UNIT
+    out["scaling"] = "strong"
+    out["workload"] = f"{WORKLOAD} split into {world} row bands; fit of {len(xy)} stamps, moments all-reduced"
+    return out
+
+
 def run_reference(args, rank):
     """Reference arm: the FP64 oracle on the host cores, same metric and workload."""
     if rank != 0:
@@ -733,6 +776,8 @@ def main():
     value = _job_rate(world, px, args.steps, ms_total)
     e2e_value = _job_rate(world, px, n_e2e, e2e_ms)
     e2e1_value = _job_rate(world, px, n_e2e, e2e1_ms)
+    # one frame split over the ranks (every rank takes part in its all-reduce)
+    sharded = _sharded_frame(svk, torch, dist, rank, world, R, I, c, spec) if dist and not args.no_extras else None
     if rank != 0:
         return
 
@@ -792,6 +837,8 @@ def main():
                                 "kernel": "tform_fp32_kernel: T convolutions R (x) K_t per pixel, "
                                           "sum_t m_t C_t - I in the epilogue"}},
     }
+    if sharded is not None:
+        out["sharded_frame"] = sharded
     if not args.no_extras:
         out["night_batch"] = _night_batch(svk, torch, dev, stream)
         out["fit"] = _fit_timing(svk, torch, dev, R, I, fp64_peak)

@@ -294,6 +294,81 @@ SVK_API int svk_fit_coeffs(const float *R, const float *I, int W, int H, int pit
                    int *info_out, void *workspace, size_t ws_bytes, int sync, void *stream);
 
 /*
+ * The fit in two parts, so that the stamps can be split over several GPUs (one process
+ * each): every GPU accumulates the moments of its own stamps, the moment arrays are summed
+ * over the GPUs (an all-reduce of FP64 sums), and every GPU solves the same normal
+ * equations.  The paper fits on one machine (Sec. 2); its two-GPU split of the image
+ * (Sec. 4) and the multi-GPU outlook (Sec. 6) motivate this split of the fit's one
+ * exchange step.
+ *
+ * Moments: with the extended columns E = [C_0 .. C_{N-1}, I, 1] of a stamp pixel p,
+ *   S[(e1 * (N+2) + e2) * n_mu + mu] = sum_p w(p) E_e1(p) E_e2(p) mu(xt_p, yt_p)   (e1 <= e2)
+ * for the n_mu monomials mu of degree <= 2 max(degree, bg_degree) (x exponent outer, y
+ * inner); entries with e1 > e2 stay zero.  Every entry of A and b (svk_fit_coeffs) is one
+ * of them, so summing S over disjoint stamp sets sums the normal equations.
+ * svk_fit_moments_count() doubles (0 on bad arguments).
+ */
+SVK_API size_t svk_fit_moments_count(int N, int degree, int bg_degree);
+
+/* Bytes of device workspace svk_fit_moments needs (C_k at the stamp pixels). */
+SVK_API size_t svk_fit_moments_workspace_size(int n_stamps, int stamp_size, int N);
+
+/*
+ * Moments S (above) of the stamps' pixels, written to `moments` (device double
+ * [svk_fit_moments_count]) or, when `accumulate` is non-zero, added to it.
+ *   R, I, weight  device float32 buffers holding the frame rows [row_begin, row_end) of the
+ *                 W x H frame (each pointer at row row_begin, one pitch); weight nullable.
+ *                 Pass 0, H for whole frames.  Pixels outside the frame or outside the held
+ *                 rows add nothing, so a GPU holding a band of the frame passes the stamps
+ *                 whose pixels and kernel halo (stamp_size/2 + L/2 rows each side) it holds.
+ *   stamp_xy      device int32 [n_stamps][2], frame coordinates; n_stamps may be 0.
+ * Other arguments as svk_fit_coeffs (1 <= N <= 64).  Asynchronous on `stream`.
+ */
+SVK_API int svk_fit_moments(const float *R, const float *I, const float *weight, int W, int H, int pitch,
+                            int row_begin, int row_end, const int *stamp_xy, int n_stamps, int stamp_size,
+                            const float *basis, int N, int L, int degree, int bg_degree, double *moments,
+                            int accumulate, void *workspace, size_t ws_bytes, void *stream);
+
+/* Bytes of device workspace svk_fit_solve needs (A and b). */
+SVK_API size_t svk_fit_solve_workspace_size(int N, int degree, int bg_degree);
+
+/*
+ * The normal equations assembled from the moments S, solved by the FP64 Cholesky of
+ * svk_fit_coeffs.  coeffs_out, info_out and `sync` as svk_fit_coeffs; chi2_out (nullable)
+ * receives sum w (model - I)^2 computed from the moments, S_II - b.c (A c = b at the
+ * solution), rather than by a second pass over the pixels.  Asynchronous on `stream`.
+ */
+SVK_API int svk_fit_solve(const double *moments, int N, int degree, int bg_degree, double *coeffs_out,
+                          double *chi2_out, int *info_out, void *workspace, size_t ws_bytes, int sync,
+                          void *stream);
+
+/*
+ * Row alignment of svk_difference_rows bands for a method: the output-row block of its
+ * kernel (12 direct, 16 T-form FP32, the plan's G rows on the tensor cores); 0 when the
+ * arguments have no plan.  svk_autotune may change the tensor-core value.
+ */
+SVK_API int svk_band_rows(int method, int precision, int N, int L, int degree);
+
+/*
+ * Output rows [y_begin, y_end) of D = (R (x) K_{x,y}) - I for the W x H frame, from buffers
+ * that hold only part of it: the unit of work of a row-band split of one frame over
+ * several GPUs (Sec. 4 splits an image between two GPUs; here by row bands).  Coordinates
+ * are normalised over the whole frame, so the rows equal those of svk_difference on the
+ * whole frame bit for bit.
+ *   R        device float32, frame rows [r_begin, r_end) (R points at row r_begin), with
+ *            r_begin <= max(0, y_begin - h) and r_end >= min(H, y_end + h), h = (L-1)/2
+ *   I, D     device float32, frame rows [y_begin, y_end) (pointers at row y_begin); I may
+ *            be NULL (D = R (x) K)
+ *   y_begin  a multiple of svk_band_rows(); y_end a multiple of it or H
+ * Other arguments, workspace and errors as svk_difference (SVK_ERR_ARG for a band or held
+ * range that breaks the rules above).
+ */
+SVK_API int svk_difference_rows(const float *R, int pitch_R, int r_begin, int r_end, const float *I, int pitch_I,
+                                float *D, int pitch_D, int W, int H, int y_begin, int y_end, const float *basis,
+                                int N, int L, const float *coeffs, int degree, int method, int precision, int edge,
+                                void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * Bytes of device workspace svk_difference_host needs: device copies of R, I and D
  * (W * H * 4 bytes each, rounded up to 256) plus svk_workspace_size() of the method.
  */

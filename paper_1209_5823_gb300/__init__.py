@@ -45,7 +45,8 @@ EXPORTS = (
     "svk_cnn_field_fit",
     "svk_select_workspace_size", "svk_select_stamps", "svk_measure_fma_peak", "svk_host_workspace_size",
     "svk_difference_host", "svk_host_batch_workspace_size", "svk_difference_host_batch", "svk_selftest_bounded_wait",
-    "svk_device_status",
+    "svk_device_status", "svk_fit_moments_count", "svk_fit_moments_workspace_size", "svk_fit_moments",
+    "svk_fit_solve_workspace_size", "svk_fit_solve", "svk_band_rows", "svk_difference_rows",
 )
 
 
@@ -108,6 +109,13 @@ def load_library(path: str | None = None):
         "svk_difference_host_batch": (i, [vp, i, i, i, i, vp, sz, vp]),
         "svk_select_workspace_size": (sz, [i, i]),
         "svk_select_stamps": (i, [vp, i, i, i, f, f, f, i, i, f, i, vp, vp, vp, sz, vp]),
+        "svk_fit_moments_count": (sz, [i, i, i]),
+        "svk_fit_moments_workspace_size": (sz, [i, i, i]),
+        "svk_fit_moments": (i, [vp, vp, vp, i, i, i, i, i, vp, i, i, vp, i, i, i, i, vp, i, vp, sz, vp]),
+        "svk_fit_solve_workspace_size": (sz, [i, i, i]),
+        "svk_fit_solve": (i, [vp, i, i, i, vp, vp, vp, vp, sz, i, vp]),
+        "svk_band_rows": (i, [i, i, i, i, i]),
+        "svk_difference_rows": (i, [vp, i, i, i, vp, i, vp, i, i, i, i, i, vp, i, i, vp, i, i, i, i, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -301,6 +309,90 @@ def svk_fit_coeffs(R, I, stamp_xy, stamp_size: int, basis, degree: int, bg_degre
                                          _ptr(chi2), _ptr(info), _ptr(workspace), ws_bytes, int(bool(sync)),
                                          _stream(stream)))
     return coeffs, chi2, info
+
+
+def svk_fit_moments_count(N: int, degree: int, bg_degree: int) -> int:
+    return int(load_library().svk_fit_moments_count(int(N), int(degree), int(bg_degree)))
+
+
+def svk_fit_moments_workspace_size(n_stamps: int, stamp_size: int, N: int) -> int:
+    return int(load_library().svk_fit_moments_workspace_size(int(n_stamps), int(stamp_size), int(N)))
+
+
+def svk_fit_moments(R, I, stamp_xy, stamp_size: int, basis, degree: int, bg_degree: int = -1, W: int | None = None,
+                    H: int | None = None, row_begin: int = 0, weight=None, moments=None, accumulate: bool = False,
+                    workspace=None, stream=None):
+    """FP64 moments of the stamps' pixels (the summable part of the fit).
+
+    R, I (and weight) hold the frame rows [row_begin, row_begin + rows) of a W x H frame
+    (W, H default to R's own shape: a whole frame).  Returns the moments tensor (float64,
+    svk_fit_moments_count entries), new or the given one (added to when `accumulate`)."""
+    import torch
+    rows, Wb, p = _img(R, "R")
+    _, _, pI = _img(I, "I")
+    if pI != p or (weight is not None and weight.stride(0) != p):
+        raise ValueError("R, I and weight must share one pitch")
+    W = Wb if W is None else int(W)
+    H = rows if H is None else int(H)
+    N, L = basis.shape[0], basis.shape[1]
+    if moments is None:
+        moments = torch.zeros(svk_fit_moments_count(N, degree, bg_degree), dtype=torch.float64, device=R.device)
+    st = stamp_xy.to(torch.int32).contiguous() if stamp_xy is not None else None
+    n = 0 if st is None else st.shape[0]
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_fit_moments(_ptr(R), _ptr(I), _ptr(weight), W, H, p, int(row_begin),
+                                          int(row_begin) + rows, _ptr(st) if n else _ptr(None), n, int(stamp_size),
+                                          _ptr(basis), N, L, int(degree), int(bg_degree), _ptr(moments),
+                                          int(bool(accumulate)), _ptr(workspace), ws_bytes, _stream(stream)))
+    return moments
+
+
+def svk_fit_solve_workspace_size(N: int, degree: int, bg_degree: int) -> int:
+    return int(load_library().svk_fit_solve_workspace_size(int(N), int(degree), int(bg_degree)))
+
+
+def svk_fit_solve(moments, N: int, degree: int, bg_degree: int = -1, workspace=None, sync: bool = False, stream=None):
+    """Coefficients from (summed) moments; returns (coeffs[M] f64, chi2[1] f64, info[1] i32) tensors."""
+    import torch
+    M = N * n_terms(degree) + n_terms(bg_degree)
+    coeffs = torch.zeros(M, dtype=torch.float64, device=moments.device)
+    chi2 = torch.zeros(1, dtype=torch.float64, device=moments.device)
+    info = torch.zeros(1, dtype=torch.int32, device=moments.device)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_fit_solve(_ptr(moments), int(N), int(degree), int(bg_degree), _ptr(coeffs), _ptr(chi2),
+                                        _ptr(info), _ptr(workspace), ws_bytes, int(bool(sync)), _stream(stream)))
+    return coeffs, chi2, info
+
+
+def svk_band_rows(method: int, precision: int, N: int, L: int, degree: int) -> int:
+    return int(load_library().svk_band_rows(int(method), int(precision), int(N), int(L), int(degree)))
+
+
+def svk_difference_rows(R, I, basis, coeffs, degree: int, W: int, H: int, y_begin: int, y_end: int, r_begin: int,
+                        method: int = SVK_METHOD_BASIS, precision: int = SVK_PREC_BF16X3, out=None, workspace=None,
+                        stream=None, edge: int = SVK_EDGE_ZERO):
+    """Rows [y_begin, y_end) of D = (R (x) K) - I for a W x H frame from band buffers:
+    R holds frame rows [r_begin, r_begin + R.shape[0]), I and out rows [y_begin, y_end)
+    (I may be None: out = R (x) K)."""
+    import torch
+    rows, Wb, pR = _img(R, "R")
+    if Wb != W:
+        raise ValueError("R's width differs from W")
+    pI = 0
+    if I is not None:
+        Hi, Wi, pI = _img(I, "I")
+        if (Hi, Wi) != (y_end - y_begin, W):
+            raise ValueError("I must hold the band's rows")
+    if out is None:
+        out = torch.empty((y_end - y_begin, W), dtype=torch.float32, device=R.device)
+    _, _, pD = _img(out, "D")
+    N, L = basis.shape[0], basis.shape[1]
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_difference_rows(_ptr(R), pR, int(r_begin), int(r_begin) + rows, _ptr(I), pI, _ptr(out),
+                                              pD, int(W), int(H), int(y_begin), int(y_end), _ptr(basis), N, L,
+                                              _ptr(coeffs), int(degree), int(method), int(precision), int(edge),
+                                              _ptr(workspace), ws_bytes, _stream(stream)))
+    return out
 
 
 def svk_host_workspace_size(method: int, precision: int, W: int, H: int, N: int, L: int, degree: int) -> int:

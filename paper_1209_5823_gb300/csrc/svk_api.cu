@@ -445,6 +445,125 @@ int svk_fit_coeffs(const float *R, const float *I, int W, int H, int pitch, cons
   return SVK_OK;
 }
 
+size_t svk_fit_moments_count(int N, int degree, int bg_degree) {
+  if (N < 1 || N > 64 || degree < 0 || degree > 3 || bg_degree < -1 || bg_degree > 3) return 0;
+  return fit_moments_count(N, degree, bg_degree);
+}
+
+size_t svk_fit_moments_workspace_size(int n_stamps, int stamp_size, int N) {
+  if (n_stamps < 0 || stamp_size < 1 || N < 1) return 0;
+  return fit_moments_workspace_size(n_stamps, stamp_size, N);
+}
+
+int svk_fit_moments(const float *R, const float *I, const float *weight, int W, int H, int pitch, int row_begin,
+                    int row_end, const int *stamp_xy, int n_stamps, int stamp_size, const float *basis, int N, int L,
+                    int degree, int bg_degree, double *moments, int accumulate, void *workspace, size_t ws_bytes,
+                    void *stream) {
+  CallRange range("svk_fit_moments");
+  if (!R || !I || !basis || !moments || (n_stamps > 0 && !stamp_xy))
+    return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  if (W < 1 || H < 1 || W > 65535 || H > 65535 || pitch < W) return set_error(SVK_ERR_ARG, "bad frame size/pitch");
+  if (row_begin < 0 || row_end > H || row_begin >= row_end)
+    return set_error(SVK_ERR_ARG, "held rows [%d, %d) not inside the frame's %d rows", row_begin, row_end, H);
+  if (n_stamps < 0 || stamp_size < 1 || stamp_size > 127 || (stamp_size % 2) == 0)
+    return set_error(SVK_ERR_ARG, "bad stamp list (n=%d, size=%d)", n_stamps, stamp_size);
+  if (L < 1 || L > 31 || (L % 2) == 0) return set_error(SVK_ERR_ARG, "L=%d must be odd in [1,31]", L);
+  if (N < 1 || N > 64) return set_error(SVK_ERR_UNSUPPORTED, "the fit supports 1 <= N <= 64 basis stamps (got %d)", N);
+  if (degree < 0 || degree > 3 || bg_degree < -1 || bg_degree > 3)
+    return set_error(SVK_ERR_ARG, "degree %d / bg_degree %d out of range", degree, bg_degree);
+  if (N * n_terms(degree) + n_terms(bg_degree) > 1024) return set_error(SVK_ERR_ARG, "more than 1024 unknowns");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_stamps == 0) {  // no pixels: the moments are zero (or unchanged)
+    if (accumulate) return SVK_OK;
+    return cuda_status(cudaMemsetAsync(moments, 0, fit_moments_count(N, degree, bg_degree) * sizeof(double), s),
+                       "moments reset");
+  }
+  ScopedWorkspace w;
+  const size_t need = fit_moments_workspace_size(n_stamps, stamp_size, N);
+  int st = w.acquire(need, workspace, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  return launch_fit_moments(R, I, weight, W, H, pitch, row_begin, row_end, stamp_xy, n_stamps, stamp_size, basis, N,
+                            L, degree, bg_degree, moments, accumulate != 0, w.ptr, need, s);
+}
+
+size_t svk_fit_solve_workspace_size(int N, int degree, int bg_degree) {
+  if (N < 1 || N > 64 || degree < 0 || degree > 3 || bg_degree < -1 || bg_degree > 3) return 0;
+  return fit_solve_workspace_size(N, degree, bg_degree);
+}
+
+int svk_fit_solve(const double *moments, int N, int degree, int bg_degree, double *coeffs_out, double *chi2_out,
+                  int *info_out, void *workspace, size_t ws_bytes, int sync, void *stream) {
+  CallRange range("svk_fit_solve");
+  if (!moments || !coeffs_out || !info_out) return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  if (N < 1 || N > 64) return set_error(SVK_ERR_UNSUPPORTED, "the fit supports 1 <= N <= 64 basis stamps (got %d)", N);
+  if (degree < 0 || degree > 3 || bg_degree < -1 || bg_degree > 3)
+    return set_error(SVK_ERR_ARG, "degree %d / bg_degree %d out of range", degree, bg_degree);
+  if (N * n_terms(degree) + n_terms(bg_degree) > 1024) return set_error(SVK_ERR_ARG, "more than 1024 unknowns");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScopedWorkspace w;
+  const size_t need = fit_solve_workspace_size(N, degree, bg_degree);
+  int st = w.acquire(need, workspace, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  st = launch_fit_solve(moments, N, degree, bg_degree, coeffs_out, chi2_out, info_out, w.ptr, need, s);
+  if (st != SVK_OK || !sync) return st;
+  st = cuda_status(cudaStreamSynchronize(s), "svk_fit_solve sync");
+  if (st != SVK_OK) return st;
+  int info = -1;
+  st = cuda_status(cudaMemcpy(&info, info_out, sizeof(int), cudaMemcpyDeviceToHost), "read info");
+  if (st != SVK_OK) return st;
+  if (info >= 0) return set_error(SVK_ERR_NOT_SPD, "normal matrix not positive definite at pivot %d", info);
+  return SVK_OK;
+}
+
+int svk_band_rows(int method, int precision, int N, int L, int degree) {
+  if (L < 1 || L > 31 || (L % 2) == 0 || N < 1 || N > 4096 || degree < 0 || degree > 3) return 0;
+  if (method == SVK_METHOD_DIRECT && precision != SVK_PREC_FP32) return 0;
+  if (method != SVK_METHOD_DIRECT && method != SVK_METHOD_BASIS && method != SVK_METHOD_TFORM) return 0;
+  return band_granule(method, precision, N, L, degree);
+}
+
+int svk_difference_rows(const float *R, int pitch_R, int r_begin, int r_end, const float *I, int pitch_I, float *D,
+                        int pitch_D, int W, int H, int y_begin, int y_end, const float *basis, int N, int L,
+                        const float *coeffs, int degree, int method, int precision, int edge, void *workspace,
+                        size_t ws_bytes, void *stream) {
+  CallRange range("svk_difference_rows");
+  const bool need_I = I != nullptr;
+  int st = check_conv_args(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, method, precision, edge, D,
+                           pitch_D, need_I);
+  if (st != SVK_OK) return st;
+  if (y_begin < 0 || y_end > H || y_begin >= y_end)
+    return set_error(SVK_ERR_ARG, "output rows [%d, %d) not inside the frame's %d rows", y_begin, y_end, H);
+  const int gran = band_granule(method, precision, N, L, degree);
+  if (gran < 1) return set_error(SVK_ERR_UNSUPPORTED, "no plan for this method, N=%d, L=%d", N, L);
+  if (y_begin % gran != 0 || (y_end % gran != 0 && y_end != H))
+    return set_error(SVK_ERR_ARG, "band [%d, %d) not aligned to %d rows (svk_band_rows)", y_begin, y_end, gran);
+  const int h = (L - 1) / 2;
+  const int need_lo = y_begin - h > 0 ? y_begin - h : 0, need_hi = y_end + h < H ? y_end + h : H;
+  if (r_begin < 0 || r_end > H || r_begin > need_lo || r_end < need_hi)
+    return set_error(SVK_ERR_ARG, "R holds rows [%d, %d); the band needs [%d, %d)", r_begin, r_end, need_lo, need_hi);
+  // the kernels index I and D by frame row and touch only rows [y_begin, y_end)
+  const float *If = need_I ? reinterpret_cast<const float *>(reinterpret_cast<uintptr_t>(I) -
+                                                            (uintptr_t)y_begin * (uintptr_t)pitch_I * sizeof(float))
+                           : nullptr;
+  float *Df = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(D) -
+                                        (uintptr_t)y_begin * (uintptr_t)pitch_D * sizeof(float));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (method == SVK_METHOD_DIRECT)
+    return launch_direct(R, pitch_R, If, pitch_I, W, H, basis, N, L, coeffs, degree, Df, pitch_D, s, y_begin, y_end,
+                         r_begin, r_end);
+  ScopedWorkspace w;
+  if (method == SVK_METHOD_TFORM) {
+    const size_t need = tform_workspace_size(precision, L, degree);
+    if ((st = w.acquire(need, workspace, ws_bytes, s)) != SVK_OK) return st;
+    return launch_tform(R, pitch_R, If, pitch_I, W, H, basis, N, L, coeffs, degree, precision, Df, pitch_D, w.ptr,
+                        need, s, y_begin, y_end, true, r_begin, r_end);
+  }
+  const size_t need = tc_workspace_size(precision, N, L);
+  if ((st = w.acquire(need, workspace, ws_bytes, s)) != SVK_OK) return st;
+  return launch_tc(R, pitch_R, If, pitch_I, W, H, basis, N, L, coeffs, degree, precision, Df, pitch_D, w.ptr, need,
+                   s, y_begin, y_end, true, r_begin, r_end);
+}
+
 size_t svk_host_workspace_size(int method, int precision, int W, int H, int N, int L, int degree) {
   if (W < 1 || H < 1 || W > 65535 || H > 65535) return 0;
   return host_workspace_size(method, precision, W, H, N, L, degree);

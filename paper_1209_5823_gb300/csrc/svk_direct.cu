@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(kTX * TY, 1)
     direct_kernel(const __grid_constant__ CUtensorMap tmR, int use_tma, const float *__restrict__ R,
                   int pitch_R, const float *__restrict__ I, int pitch_I, int W, int H,
                   const float *__restrict__ basis, int N, int L, const float *__restrict__ coeffs,
-                  int degree, float *__restrict__ out, int pitch_out, int y_begin, int y_end, uint32_t *status) {
+                  int degree, float *__restrict__ out, int pitch_out, int y_begin, int y_end, int r0, int r1,
+                  uint32_t *status) {
   constexpr int NCP = Cfg<NC>::NCP;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -69,12 +70,12 @@ __global__ void __launch_bounds__(kTX * TY, 1)
       mbar_init(bar, 1);
       fence_mbar_init();
       mbar_arrive_expect_tx(bar, (uint32_t)(BW * BH * 4));
-      tma_load_2d(Rs, &tmR, bar, xs, y0 - h);
+      tma_load_2d(Rs, &tmR, bar, xs, y0 - h - r0);  // the map covers the held rows
     }
   } else {
     for (int i = tid; i < BW * BH; i += kThreads) {
       const int r = i / BW, c = i % BW, gy = y0 - h + r, gx = xs + c;
-      Rs[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? R[(size_t)gy * pitch_R + gx] : 0.0f;
+      Rs[i] = (gx >= 0 && gx < W && gy >= r0 && gy < r1) ? R[(size_t)(gy - r0) * pitch_R + gx] : 0.0f;
     }
   }
 
@@ -184,18 +185,18 @@ __global__ void __launch_bounds__(kTX * TY, 1)
 template <int NC, int TY>
 int launch_nc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis,
               int N, int L, const float *coeffs, int degree, float *out, int pitch_out, int y_begin, int y_end,
-              cudaStream_t s) {
+              int r0, int r1, cudaStream_t s) {
   const int h = (L - 1) / 2;
   const size_t smem = direct_smem_bytes<NC, TY>(L);
   cudaError_t e = cudaFuncSetAttribute(direct_kernel<NC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_status(e, "direct_kernel smem attribute");
   CUtensorMap tm;
   memset(&tm, 0, sizeof(tm));
-  const int use_tma = encode_tmap_2d_f32(&tm, R, W, H, pitch_R, box_w(h), box_h(h, TY)) ? 1 : 0;
+  const int use_tma = encode_tmap_2d_f32(&tm, R, W, r1 - r0, pitch_R, box_w(h), box_h(h, TY)) ? 1 : 0;
   dim3 grid((W + kTileW - 1) / kTileW, (y_end - y_begin + TY - 1) / TY), block(kTX, TY);
   if (grid.y == 0) return SVK_OK;
   direct_kernel<NC, TY><<<grid, block, smem, s>>>(tm, use_tma, R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs,
-                                             degree, out, pitch_out, y_begin, y_end, device_status_word());
+                                             degree, out, pitch_out, y_begin, y_end, r0, r1, device_status_word());
   return cuda_status(cudaGetLastError(), "direct_kernel launch");
 }
 
@@ -207,28 +208,30 @@ namespace {
 template <int TY>
 int launch_ty(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis, int N,
               int L, const float *coeffs, int degree, float *out, int pitch_out, int y_begin, int y_end,
-              cudaStream_t s) {
+              int r0, int r1, cudaStream_t s) {
   if (N <= 4)
-    return launch_nc<4, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+    return launch_nc<4, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, r0, r1, s);
   if (N <= 6)  // the T-form's six stamps at degree 2
-    return launch_nc<6, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+    return launch_nc<6, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, r0, r1, s);
   if (N <= 8)
-    return launch_nc<8, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+    return launch_nc<8, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, r0, r1, s);
   if (N <= 10)  // the T-form's ten stamps at degree 3
     return launch_nc<10, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end,
-                             s);
+                             r0, r1, s);
   if (N <= 16)
     return launch_nc<16, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end,
-                             s);
-  return launch_nc<25, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+                             r0, r1, s);
+  return launch_nc<25, TY>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, r0, r1, s);
 }
 }  // namespace
 
 int launch_direct(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis,
                   int N, int L, const float *coeffs, int degree, float *out, int pitch_out, cudaStream_t s,
-                  int y_begin, int y_end) {
+                  int y_begin, int y_end, int r_begin, int r_end) {
   if (y_end < 0) y_end = H;
-  return launch_ty<12>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end, s);
+  if (r_end < 0) r_end = H;
+  return launch_ty<12>(R, pitch_R, I, pitch_I, W, H, basis, N, L, coeffs, degree, out, pitch_out, y_begin, y_end,
+                       r_begin, r_end, s);
 }
 
 
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(kTX * kTfTY, 2)
     tform_fp32_kernel(const __grid_constant__ CUtensorMap tmR, int use_tma, const float *__restrict__ R,
                       int pitch_R, const float *__restrict__ I, int pitch_I, int W, int H,
                       const float *__restrict__ Kt, int L, float *__restrict__ out, int pitch_out, int y_begin,
-                      int y_end, uint32_t *status) {
+                      int y_end, int r0, int r1, uint32_t *status) {
   constexpr int D = T == 1 ? 0 : (T == 3 ? 1 : (T == 6 ? 2 : 3));  // spatial degree
   constexpr int kThreads = kTX * kTfTY;
   extern __shared__ unsigned char smem_raw[];
@@ -288,12 +291,12 @@ __global__ void __launch_bounds__(kTX * kTfTY, 2)
       mbar_init(bar, 1);
       fence_mbar_init();
       mbar_arrive_expect_tx(bar, (uint32_t)(BW * BH * 4));
-      tma_load_2d(Rs, &tmR, bar, xs, y0 - h);
+      tma_load_2d(Rs, &tmR, bar, xs, y0 - h - r0);  // the map covers the held rows
     }
   } else {
     for (int i = tid; i < BW * BH; i += kThreads) {
       const int r = i / BW, c = i % BW, gy = y0 - h + r, gx = xs + c;
-      Rs[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? R[(size_t)gy * pitch_R + gx] : 0.0f;
+      Rs[i] = (gx >= 0 && gx < W && gy >= r0 && gy < r1) ? R[(size_t)(gy - r0) * pitch_R + gx] : 0.0f;
     }
   }
   float *Kf = reinterpret_cast<float *>(Ks);
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(kTX * kTfTY, 2)
 
 template <int T, int S>
 int launch_tf(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *Kt, int L,
-              float *out, int pitch_out, int y_begin, int y_end, cudaStream_t s) {
+              float *out, int pitch_out, int y_begin, int y_end, int r0, int r1, cudaStream_t s) {
   const int h = (L - 1) / 2;
   const size_t smem = tform_fp32_smem_bytes<T>(L);
   cudaError_t e =
@@ -384,22 +387,22 @@ int launch_tf(const float *R, int pitch_R, const float *I, int pitch_I, int W, i
   if (e != cudaSuccess) return cuda_status(e, "tform_fp32_kernel smem attribute");
   CUtensorMap tm;
   memset(&tm, 0, sizeof(tm));
-  const int use_tma = encode_tmap_2d_f32(&tm, R, W, H, pitch_R, tf_box_w(h), box_h(h, kTfRows)) ? 1 : 0;
+  const int use_tma = encode_tmap_2d_f32(&tm, R, W, r1 - r0, pitch_R, tf_box_w(h), box_h(h, kTfRows)) ? 1 : 0;
   dim3 grid((W + kTfTileW - 1) / kTfTileW, (y_end - y_begin + kTfRows - 1) / kTfRows), block(kTX, kTfTY);
   if (grid.y == 0) return SVK_OK;
   tform_fp32_kernel<T, S><<<grid, block, smem, s>>>(tm, use_tma, R, pitch_R, I, pitch_I, W, H, Kt, L, out,
-                                                    pitch_out, y_begin, y_end, device_status_word());
+                                                    pitch_out, y_begin, y_end, r0, r1, device_status_word());
   return cuda_status(cudaGetLastError(), "tform_fp32_kernel launch");
 }
 
 template <int T>
 int launch_tf_s(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *Kt, int L,
-                float *out, int pitch_out, int y_begin, int y_end, cudaStream_t s) {
+                float *out, int pitch_out, int y_begin, int y_end, int r0, int r1, cudaStream_t s) {
   switch (((L - 1) / 2) & 3) {
-    case 0: return launch_tf<T, 0>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, s);
-    case 1: return launch_tf<T, 1>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, s);
-    case 2: return launch_tf<T, 2>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, s);
-    default: return launch_tf<T, 3>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, s);
+    case 0: return launch_tf<T, 0>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, r0, r1, s);
+    case 1: return launch_tf<T, 1>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, r0, r1, s);
+    case 2: return launch_tf<T, 2>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, r0, r1, s);
+    default: return launch_tf<T, 3>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, r0, r1, s);
   }
 }
 }  // namespace
@@ -407,13 +410,15 @@ int launch_tf_s(const float *R, int pitch_R, const float *I, int pitch_I, int W,
 int tform_fp32_rows(int) { return kTfRows; }
 
 int launch_tform_fp32(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *Kt, int T,
-                      int L, float *out, int pitch_out, cudaStream_t s, int y_begin, int y_end) {
+                      int L, float *out, int pitch_out, cudaStream_t s, int y_begin, int y_end, int r_begin,
+                      int r_end) {
   if (y_end < 0) y_end = H;
+  const int r0 = r_begin, r1 = r_end < 0 ? H : r_end;
   switch (T) {
-    case 1: return launch_tf_s<1>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, s);
-    case 3: return launch_tf_s<3>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, s);
-    case 6: return launch_tf_s<6>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, s);
-    case 10: return launch_tf_s<10>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, s);
+    case 1: return launch_tf_s<1>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, r0, r1, s);
+    case 3: return launch_tf_s<3>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, r0, r1, s);
+    case 6: return launch_tf_s<6>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, r0, r1, s);
+    case 10: return launch_tf_s<10>(R, pitch_R, I, pitch_I, W, H, Kt, L, out, pitch_out, y_begin, y_end, r0, r1, s);
     default: return set_error(SVK_ERR_ARG, "T-form: T=%d is not a number of monomials of degree <= 3", T);
   }
 }

@@ -33,6 +33,7 @@ __host__ __device__ inline int mono_index(int i, int j, int D) {  // (i outer, j
 
 struct FitDims {
   int W, H, pitch, S, n_stamps, N, L, d, bd, T, Tb, M, D, n_mu, NE, P;  // P = stamp pixels
+  int r0, r1;  // frame rows [r0, r1) held by R, I and weight (row r at (r - r0) * pitch)
 };
 
 __device__ inline double norm_coord(int x, int W) {
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(kCkThreads) fit_ck_kernel(const float *__restr
   const int ox = xs - hs - h, oy = ys - hs + ty0 - h;  // frame position of Rp[0][0]
   for (int e = threadIdx.x; e < PW * PH; e += blockDim.x) {
     const int gx = ox + e % PW, gy = oy + e / PW;
-    Rp[e] = (gx >= 0 && gx < f.W && gy >= 0 && gy < f.H) ? __ldg(R + (size_t)gy * f.pitch + gx) : 0.0f;
+    Rp[e] = (gx >= 0 && gx < f.W && gy >= f.r0 && gy < f.r1) ? __ldg(R + (size_t)(gy - f.r0) * f.pitch + gx) : 0.0f;
   }
   int off[kCkPix];      // Rp index of tap (0, 0) for the pixel: (qy + 2h) * PW + qx + 2h
   int pglob[kCkPix];    // global stamp-pixel index, or -1
@@ -123,7 +124,8 @@ __global__ void __launch_bounds__(kCkThreads) fit_ck_kernel(const float *__restr
 }
 
 // S[(e1 * NE + e2) * n_mu + mu] += sum over this CTA's pixels of w E_e1 E_e2 mu(p)
-// (e1 <= e2).  Thread = one column pair; CTA = one pixel range x one pair tile.
+// (e1 <= e2).  Thread = one column pair; CTA = one pixel range x one pair tile.  Pixels
+// outside the frame, or outside the rows [r0, r1) the buffers hold, add nothing.
 __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__ C, const float *__restrict__ I,
                                                        const float *__restrict__ weight, const int *stamp_xy, FitDims f,
                                                        int px_per_cta, double *__restrict__ S) {
@@ -153,10 +155,10 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
       if (p < p1) {
         int x, y;
         stamp_pixel(f, stamp_xy, p, x, y);
-        const bool inside = x >= 0 && x < f.W && y >= 0 && y < f.H;
+        const bool inside = x >= 0 && x < f.W && y >= f.r0 && y < f.r1;
         if (inside) {
           if (e < f.N) v = C[(size_t)p * f.N + e];
-          else if (e == f.N) v = I[(size_t)y * f.pitch + x];
+          else if (e == f.N) v = I[(size_t)(y - f.r0) * f.pitch + x];
           else v = 1.0f;
         }
       }
@@ -168,8 +170,8 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
       if (p < p1) {
         int x, y;
         stamp_pixel(f, stamp_xy, p, x, y);
-        if (x >= 0 && x < f.W && y >= 0 && y < f.H) {
-          w = weight ? (double)weight[(size_t)y * f.pitch + x] : 1.0;
+        if (x >= 0 && x < f.W && y >= f.r0 && y < f.r1) {
+          w = weight ? (double)weight[(size_t)(y - f.r0) * f.pitch + x] : 1.0;
           xt = norm_coord(x, f.W);
           yt = norm_coord(y, f.H);
         }
@@ -468,6 +470,8 @@ FitDims dims(int W, int H, int pitch, int n_stamps, int S, int N, int L, int d, 
   f.n_mu = n_terms(f.D);
   f.NE = N + 2;
   f.P = n_stamps * S * S;
+  f.r0 = 0;
+  f.r1 = H;
   return f;
 }
 
@@ -498,6 +502,56 @@ size_t fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree
   return layout(dims(1, 1, 1, n_stamps, stamp_size, N, L, degree, bg_degree)).total;
 }
 
+namespace {
+
+// C_k at the stamp pixels and their moments added into S (which the caller zeroed).
+int queue_moments(const float *R, const float *I, const float *weight, const FitDims &f, const int *stamp_xy,
+                  const float *basis, float *C, double *S, cudaStream_t s) {
+  cudaError_t e;
+  const int ty = ck_tile_rows(f.S);
+  const size_t ck_smem = ck_smem_bytes(f.S, f.L, ty);
+  if ((e = cudaFuncSetAttribute(fit_ck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ck_smem)) != cudaSuccess)
+    return cuda_status(e, "fit_ck_kernel smem attribute");
+  fit_ck_kernel<<<dim3(f.n_stamps, (f.S + ty - 1) / ty), kCkThreads, ck_smem, s>>>(R, basis, stamp_xy, f, ty, C);
+  const int npairs = f.NE * (f.NE + 1) / 2;
+  const int px_per_cta = 4096;
+  dim3 ggrid((f.P + px_per_cta - 1) / px_per_cta, (npairs + 255) / 256);
+  fit_gram_kernel<<<ggrid, 256, 0, s>>>(C, I, weight, stamp_xy, f, px_per_cta, S);
+  return cuda_status(cudaGetLastError(), "fit moment kernels launch");
+}
+
+// A, b from S, the blocked Cholesky and the substitution into x (x = 0 and info = the
+// failing pivot when A is not positive definite).
+int queue_solve(const double *S, const FitDims &f, double *A, double *b, double *x, int *info, cudaStream_t s) {
+  fit_assemble_kernel<<<(f.M * f.M + 255) / 256, 256, 0, s>>>(S, f, A, b);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(info, 0xFF, sizeof(int), s)) != cudaSuccess) return cuda_status(e, "info reset");
+  for (int p = 0; p < f.M; p += kPanel) {
+    chol_diag_kernel<<<1, 256, 0, s>>>(A, f.M, p, info);
+    const int rest = f.M - p - kPanel;
+    if (rest > 0) {
+      chol_trsm_kernel<<<(rest + 63) / 64, 64, 0, s>>>(A, f.M, p, info);
+      const int nt = (rest + 31) / 32;
+      chol_update_kernel<<<nt * (nt + 1) / 2, 256, 0, s>>>(A, f.M, p, info);
+    }
+  }
+  fit_solve_kernel<<<1, 256, 0, s>>>(A, b, f.M, info, x);
+  return cuda_status(cudaGetLastError(), "fit solve kernels launch");
+}
+
+// chi^2 at the solution from the moments alone: sum w (v.c - I)^2 = sum w I^2 - 2 b.c + c.A c,
+// and A c = b at the solution, so chi^2 = sum w I^2 - b.c (0 when the solve failed).
+__global__ void __launch_bounds__(256) fit_chi2_moments_kernel(const double *S, FitDims f, const double *b,
+                                                               const double *x, const int *info, double *chi2) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int u = threadIdx.x; u < f.M; u += blockDim.x) v = fma(b[u], x[u], v);
+  const double bx = block_sum_d(v, red);
+  if (threadIdx.x == 0) *chi2 = *info < 0 ? moment(S, f, f.N, f.N, 0) - bx : 0.0;
+}
+
+}  // namespace
+
 int launch_fit(const float *R, const float *I, int W, int H, int pitch, const int *stamp_xy, int n_stamps,
                int stamp_size, const float *basis, int N, int L, int degree, int bg_degree, const float *weight,
                double *coeffs_out, double *chi2_out, int *info_out, void *ws, size_t ws_bytes, cudaStream_t s) {
@@ -513,29 +567,56 @@ int launch_fit(const float *R, const float *I, int W, int H, int pitch, const in
   cudaError_t e = cudaMemsetAsync(S, 0, (size_t)f.NE * f.NE * f.n_mu * sizeof(double), s);
   if (e == cudaSuccess && chi2_out) e = cudaMemsetAsync(chi2_out, 0, sizeof(double), s);
   if (e != cudaSuccess) return cuda_status(e, "fit memset");
-  const int ty = ck_tile_rows(f.S);
-  const size_t ck_smem = ck_smem_bytes(f.S, f.L, ty);
-  if ((e = cudaFuncSetAttribute(fit_ck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ck_smem)) != cudaSuccess)
-    return cuda_status(e, "fit_ck_kernel smem attribute");
-  fit_ck_kernel<<<dim3(f.n_stamps, (f.S + ty - 1) / ty), kCkThreads, ck_smem, s>>>(R, basis, stamp_xy, f, ty, C);
-  const int npairs = f.NE * (f.NE + 1) / 2;
-  const int px_per_cta = 4096;
-  dim3 ggrid((f.P + px_per_cta - 1) / px_per_cta, (npairs + 255) / 256);
-  fit_gram_kernel<<<ggrid, 256, 0, s>>>(C, I, weight, stamp_xy, f, px_per_cta, S);
-  fit_assemble_kernel<<<(f.M * f.M + 255) / 256, 256, 0, s>>>(S, f, A, b);
-  if ((e = cudaMemsetAsync(info_out, 0xFF, sizeof(int), s)) != cudaSuccess) return cuda_status(e, "info reset");
-  for (int p = 0; p < f.M; p += kPanel) {
-    chol_diag_kernel<<<1, 256, 0, s>>>(A, f.M, p, info_out);
-    const int rest = f.M - p - kPanel;
-    if (rest > 0) {
-      chol_trsm_kernel<<<(rest + 63) / 64, 64, 0, s>>>(A, f.M, p, info_out);
-      const int nt = (rest + 31) / 32;
-      chol_update_kernel<<<nt * (nt + 1) / 2, 256, 0, s>>>(A, f.M, p, info_out);
-    }
-  }
-  fit_solve_kernel<<<1, 256, 0, s>>>(A, b, f.M, info_out, coeffs_out);
+  int st = queue_moments(R, I, weight, f, stamp_xy, basis, C, S, s);
+  if (st == SVK_OK) st = queue_solve(S, f, A, b, coeffs_out, info_out, s);
+  if (st != SVK_OK) return st;
   if (chi2_out) fit_chi2_kernel<<<(f.P + 255) / 256, 256, 0, s>>>(C, I, weight, stamp_xy, f, coeffs_out, info_out, chi2_out);
   return cuda_status(cudaGetLastError(), "fit kernels launch");
+}
+
+size_t fit_moments_count(int N, int degree, int bg_degree) {
+  const FitDims f = dims(1, 1, 1, 1, 1, N, 1, degree, bg_degree);
+  return (size_t)f.NE * f.NE * f.n_mu;
+}
+
+size_t fit_moments_workspace_size(int n_stamps, int stamp_size, int N) {
+  return ((size_t)n_stamps * stamp_size * stamp_size * N * sizeof(float) + 255) & ~size_t(255);
+}
+
+int launch_fit_moments(const float *R, const float *I, const float *weight, int W, int H, int pitch, int row_begin,
+                       int row_end, const int *stamp_xy, int n_stamps, int stamp_size, const float *basis, int N, int L,
+                       int degree, int bg_degree, double *moments, bool accumulate, void *ws, size_t ws_bytes,
+                       cudaStream_t s) {
+  FitDims f = dims(W, H, pitch, n_stamps, stamp_size, N, L, degree, bg_degree);
+  if (f.NE > 66) return set_error(SVK_ERR_UNSUPPORTED, "fit supports N <= 64 basis stamps (got %d)", N);
+  f.r0 = row_begin;
+  f.r1 = row_end;
+  if (!ws || ws_bytes < fit_moments_workspace_size(n_stamps, stamp_size, N))
+    return set_error(SVK_ERR_WORKSPACE, "fit moments workspace too small");
+  if (!accumulate) {
+    const cudaError_t e = cudaMemsetAsync(moments, 0, fit_moments_count(N, degree, bg_degree) * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_status(e, "moments reset");
+  }
+  return queue_moments(R, I, weight, f, stamp_xy, basis, static_cast<float *>(ws), moments, s);
+}
+
+size_t fit_solve_workspace_size(int N, int degree, int bg_degree) {
+  const FitDims f = dims(1, 1, 1, 1, 1, N, 1, degree, bg_degree);
+  return (((size_t)f.M * f.M * sizeof(double) + 255) & ~size_t(255)) + (((size_t)f.M * sizeof(double) + 255) & ~size_t(255));
+}
+
+int launch_fit_solve(const double *moments, int N, int degree, int bg_degree, double *coeffs_out, double *chi2_out,
+                     int *info_out, void *ws, size_t ws_bytes, cudaStream_t s) {
+  const FitDims f = dims(1, 1, 1, 1, 1, N, 1, degree, bg_degree);
+  if (!ws || ws_bytes < fit_solve_workspace_size(N, degree, bg_degree))
+    return set_error(SVK_ERR_WORKSPACE, "fit solve workspace too small");
+  double *A = static_cast<double *>(ws);
+  double *b = reinterpret_cast<double *>(static_cast<unsigned char *>(ws) +
+                                         (((size_t)f.M * f.M * sizeof(double) + 255) & ~size_t(255)));
+  int st = queue_solve(moments, f, A, b, coeffs_out, info_out, s);
+  if (st != SVK_OK) return st;
+  if (chi2_out) fit_chi2_moments_kernel<<<1, 256, 0, s>>>(moments, f, b, coeffs_out, info_out, chi2_out);
+  return cuda_status(cudaGetLastError(), "fit chi2 launch");
 }
 
 }  // namespace svk

@@ -64,13 +64,6 @@ size_t method_ws(int method, int precision, int N, int L, int degree) {
   return 0;
 }
 
-// Output-row block of the method: band boundaries are multiples of it (0: no plan).
-int band_granule(int method, int precision, int N, int L, int degree) {
-  if (method == SVK_METHOD_DIRECT) return direct_rows(L);
-  if (method == SVK_METHOD_TFORM && precision == SVK_PREC_FP32) return tform_fp32_rows(L);
-  return tc_rows_per_block(method == SVK_METHOD_TFORM ? n_terms(degree) : N, L, precision);
-}
-
 // Band boundaries yb[0..nb]: multiples of gran, at most kMaxBands bands, none empty.
 int band_bounds(int H, int gran, int n_bands, int *yb) {
   int nb = 0;
@@ -100,6 +93,13 @@ void stage_sizes(const svk_frame *fr, int n, int method, int precision, size_t *
 }
 
 }  // namespace
+
+// Output-row block of the method: band boundaries are multiples of it (0: no plan).
+int band_granule(int method, int precision, int N, int L, int degree) {
+  if (method == SVK_METHOD_DIRECT) return direct_rows(L);
+  if (method == SVK_METHOD_TFORM && precision == SVK_PREC_FP32) return tform_fp32_rows(L);
+  return tc_rows_per_block(method == SVK_METHOD_TFORM ? n_terms(degree) : N, L, precision);
+}
 
 size_t host_workspace_size(int method, int precision, int W, int H, int N, int L, int degree) {
   return 3 * up256((size_t)W * H * sizeof(float)) + method_ws(method, precision, N, L, degree);

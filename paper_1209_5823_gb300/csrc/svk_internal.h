@@ -12,17 +12,22 @@ namespace svk {
 // I may be NULL (plain convolution).  Arguments already validated.
 // y_begin / y_end: the output rows to compute (-1 = to the last row); band starts must
 // be multiples of direct_rows(L), the kernel's block height (12 rows).
+// r_begin / r_end: the frame rows R holds (R points at row r_begin; -1 = to the last row);
+// rows outside them read as zero (a band of output rows needs rows y_begin - h .. y_end + h - 1).
+// I and out are indexed by frame row.
 int direct_rows(int L);
 int launch_direct(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
                   const float *basis, int N, int L, const float *coeffs, int degree, float *out,
-                  int pitch_out, cudaStream_t s, int y_begin = 0, int y_end = -1);
+                  int pitch_out, cudaStream_t s, int y_begin = 0, int y_end = -1, int r_begin = 0,
+                  int r_end = -1);
 
 // T-factored form on the CUDA cores (svk_direct.cu): D = sum_t m_t (R (x) K_t) - I for
 // the T in {1, 3, 6, 10} stamps Kt [T][L][L]; bands as for launch_direct, block height
 // tform_fp32_rows(L) (16 rows).
 int tform_fp32_rows(int L);
 int launch_tform_fp32(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *Kt, int T,
-                      int L, float *out, int pitch_out, cudaStream_t s, int y_begin = 0, int y_end = -1);
+                      int L, float *out, int pitch_out, cudaStream_t s, int y_begin = 0, int y_end = -1,
+                      int r_begin = 0, int r_end = -1);
 
 // Basis tabulation (svk_basis.cu).
 int launch_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg,
@@ -37,13 +42,14 @@ size_t tc_workspace_size(int precision, int N, int L);
 int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H,
               const float *basis, int N, int L, const float *coeffs, int degree, int precision,
               float *out, int pitch_out, void *ws, size_t ws_bytes, cudaStream_t s,
-              int y_begin = 0, int y_end = -1, bool prep = true);
+              int y_begin = 0, int y_end = -1, bool prep = true, int r_begin = 0, int r_end = -1);
 int tc_rows_per_block(int N, int L, int precision);  // 0 when no plan fits
 
 size_t tform_workspace_size(int precision, int L, int degree);
 int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis, int N,
                  int L, const float *coeffs, int degree, int precision, float *out, int pitch_out, void *ws,
-                 size_t ws_bytes, cudaStream_t s, int y_begin = 0, int y_end = -1, bool prep = true);
+                 size_t ws_bytes, cudaStream_t s, int y_begin = 0, int y_end = -1, bool prep = true,
+                 int r_begin = 0, int r_end = -1);
 int launch_batch(const svk_frame *frames, int n, int precision, void *ws, size_t ws_bytes, cudaStream_t s);
 size_t batch_workspace_size(const svk_frame *frames, int n, int precision);
 int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out, cudaStream_t s);
@@ -54,6 +60,22 @@ int launch_fit(const float *R, const float *I, int W, int H, int pitch, const in
                int n_stamps, int stamp_size, const float *basis, int N, int L, int degree,
                int bg_degree, const float *weight, double *coeffs_out, double *chi2_out,
                int *info_out, void *ws, size_t ws_bytes, cudaStream_t s);
+// The fit in two parts (the moments can be summed over stamp subsets, e.g. over GPUs):
+// the FP64 moments S of the stamps' pixels, R / I / weight holding frame rows
+// [row_begin, row_end) (pointers at row row_begin; pixels outside them add nothing) ...
+size_t fit_moments_count(int N, int degree, int bg_degree);
+size_t fit_moments_workspace_size(int n_stamps, int stamp_size, int N);
+int launch_fit_moments(const float *R, const float *I, const float *weight, int W, int H, int pitch, int row_begin,
+                       int row_end, const int *stamp_xy, int n_stamps, int stamp_size, const float *basis, int N, int L,
+                       int degree, int bg_degree, double *moments, bool accumulate, void *ws, size_t ws_bytes,
+                       cudaStream_t s);
+// ... and the normal equations assembled from S, Cholesky, substitution, chi^2 from S.
+size_t fit_solve_workspace_size(int N, int degree, int bg_degree);
+int launch_fit_solve(const double *moments, int N, int degree, int bg_degree, double *coeffs_out, double *chi2_out,
+                     int *info_out, void *ws, size_t ws_bytes, cudaStream_t s);
+
+// Output-row block of a method (svk_host.cu): band starts are multiples of it (0: no plan).
+int band_granule(int method, int precision, int N, int L, int degree);
 
 // The difference image from host buffers, pipelined over row bands (svk_host.cu).
 size_t host_workspace_size(int method, int precision, int W, int H, int N, int L, int degree);

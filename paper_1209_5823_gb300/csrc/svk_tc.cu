@@ -200,6 +200,7 @@ struct FrameDesc {
   const uint4 *tab_hi, *tab_lo;  // this frame's basis tables (shared by frames with one basis)
   int W, H, pitch_R, pitch_I, pitch_out, degree;
   int y_begin, y_end;  // output rows of this launch (a band of the frame, or all of it)
+  int r_begin, r_end;  // frame rows R holds (row r at R + (r - r_begin) * pitch_R); others read as 0
   int nbx, block0;  // blocks per band of G rows; first block of the frame in the set
   float rscale, out_scale;
 };
@@ -344,12 +345,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     float cur[kSegRegs], nxt[kSegRegs];
     auto load_row = [&](const RowIt &ri, float (&v)[kSegRegs]) {
       const FrameDesc &fd = fs.fr[ri.f];
-      const float *rrow = fd.R + (size_t)ri.row() * fd.pitch_R;
+      const int r = ri.row();
+      const bool held = r >= fd.r_begin && r < fd.r_end;
+      const float *rrow = fd.R + (size_t)(held ? r - fd.r_begin : 0) * fd.pitch_R;
       const int xb = ri.x0 - h;
 #pragma unroll
       for (int j = 0; j < kSegRegs; ++j) {
         const int e = lane + 32 * j, gx = xb + e;
-        v[j] = (e < pl.seglen && gx >= 0 && gx < fd.W) ? __ldg(rrow + gx) * fd.rscale : 0.0f;
+        v[j] = (held && e < pl.seglen && gx >= 0 && gx < fd.W) ? __ldg(rrow + gx) * fd.rscale : 0.0f;
       }
     };
     if (it.valid() && it.real()) load_row(it, cur);
@@ -726,8 +729,8 @@ size_t set_workspace(const svk_frame *fr, int n, const Plan &pl) {
 }
 
 template <int P>
-int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *ws, const int *rows, bool prep,
-                    cudaStream_t s) {
+int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *ws, const int *rows, const int *held,
+                    bool prep, cudaStream_t s) {
   static FrameSet fs;  // built on the host, passed by value as the kernel parameter
   static std::mutex fs_mutex;
   std::lock_guard<std::mutex> lock(fs_mutex);
@@ -750,6 +753,8 @@ int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *w
     d.degree = fr[i].degree;
     d.y_begin = rows ? rows[2 * i] : 0;
     d.y_end = rows ? rows[2 * i + 1] : fr[i].H;
+    d.r_begin = held ? held[2 * i] : 0;
+    d.r_end = held ? held[2 * i + 1] : fr[i].H;
     d.nbx = (fr[i].W + kTileM - 1) / kTileM;
     d.block0 = blocks;
     blocks += d.nbx * ((d.y_end - d.y_begin + pl.G - 1) / pl.G);
@@ -787,16 +792,17 @@ int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *w
 }
 
 // rows: per frame the output rows [rows[2i], rows[2i+1]) (multiples of G apart from the
-// frame's last row), or NULL for whole frames; prep = false reuses the basis tables an
-// earlier launch with the same plan, basis and workspace prepared.
+// frame's last row), or NULL for whole frames; held: per frame the rows of the frame its R
+// buffer holds (R points at row held[2i]), or NULL for whole frames; prep = false reuses
+// the basis tables an earlier launch with the same plan, basis and workspace prepared.
 int launch_set(const svk_frame *fr, int n, int prec, const Plan &pl, void *ws, size_t ws_bytes, cudaStream_t s,
-               const int *rows = nullptr, bool prep = true) {
+               const int *rows = nullptr, bool prep = true, const int *held = nullptr) {
   if (n < 1 || n > kMaxFrames) return set_error(SVK_ERR_ARG, "frame set of %d (1..%d)", n, kMaxFrames);
   if (!ws || ws_bytes < set_workspace(fr, n, pl)) return set_error(SVK_ERR_WORKSPACE, "tensor-core workspace too small");
   unsigned char *w = static_cast<unsigned char *>(ws);
-  if (prec == SVK_PREC_BF16X3) return launch_set_prec<SVK_PREC_BF16X3>(fr, n, pl, w, rows, prep, s);
-  if (prec == SVK_PREC_FP16X3) return launch_set_prec<SVK_PREC_FP16X3>(fr, n, pl, w, rows, prep, s);
-  return launch_set_prec<SVK_PREC_BF16>(fr, n, pl, w, rows, prep, s);
+  if (prec == SVK_PREC_BF16X3) return launch_set_prec<SVK_PREC_BF16X3>(fr, n, pl, w, rows, held, prep, s);
+  if (prec == SVK_PREC_FP16X3) return launch_set_prec<SVK_PREC_FP16X3>(fr, n, pl, w, rows, held, prep, s);
+  return launch_set_prec<SVK_PREC_BF16>(fr, n, pl, w, rows, held, prep, s);
 }
 
 // Frames of a batch grouped by (N, L): launches of up to kMaxFrames frames each.
@@ -851,7 +857,7 @@ size_t tc_workspace_size(int precision, int N, int L) {
 
 int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis, int N,
               int L, const float *coeffs, int degree, int precision, float *out, int pitch_out, void *ws,
-              size_t ws_bytes, cudaStream_t s, int y_begin, int y_end, bool prep) {
+              size_t ws_bytes, cudaStream_t s, int y_begin, int y_end, bool prep, int r_begin, int r_end) {
   Plan pl;
   if (!plan_for(N, L, precision, &pl))
     return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan fits shared memory for N=%d L=%d", N, L);
@@ -870,7 +876,8 @@ int launch_tc(const float *R, int pitch_R, const float *I, int pitch_I, int W, i
   f.coeffs = coeffs;
   f.degree = degree;
   const int rows[2] = {y_begin, y_end < 0 ? H : y_end};
-  return launch_set(&f, 1, precision, pl, ws, ws_bytes, s, rows, prep);
+  const int held[2] = {r_begin, r_end < 0 ? H : r_end};
+  return launch_set(&f, 1, precision, pl, ws, ws_bytes, s, rows, prep, held);
 }
 
 int tc_rows_per_block(int N, int L, int precision) {
@@ -906,7 +913,7 @@ size_t tform_workspace_size(int precision, int L, int degree) {
 
 int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W, int H, const float *basis, int N,
                  int L, const float *coeffs, int degree, int precision, float *out, int pitch_out, void *ws,
-                 size_t ws_bytes, cudaStream_t s, int y_begin, int y_end, bool prep) {
+                 size_t ws_bytes, cudaStream_t s, int y_begin, int y_end, bool prep, int r_begin, int r_end) {
   const int T = n_terms(degree);
   if (precision == SVK_PREC_FP32) {
     // FFMA pipe: the T convolutions R (x) K_t accumulated per pixel, combined with the
@@ -918,7 +925,7 @@ int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W
     const int n = T * L * L > T * T ? T * L * L : T * T;
     if (prep) tform_combine_kernel<<<(n + 255) / 256, 256, 0, s>>>(basis, coeffs, N, T, L * L, Kt, ident);
     return launch_tform_fp32(R, pitch_R, I, pitch_I, W, H, Kt, T, L, out, pitch_out, s, y_begin,
-                             y_end < 0 ? H : y_end);
+                             y_end < 0 ? H : y_end, r_begin, r_end);
   }
   Plan pl;
   if (!plan_for(T, L, precision, &pl))
@@ -945,7 +952,8 @@ int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W
   f.coeffs = ident;
   f.degree = degree;
   const int rows[2] = {y_begin, y_end < 0 ? H : y_end};
-  return launch_set(&f, 1, precision, pl, w + head, ws_bytes - head, s, rows, prep);
+  const int held[2] = {r_begin, r_end < 0 ? H : r_end};
+  return launch_set(&f, 1, precision, pl, w + head, ws_bytes - head, s, rows, prep, held);
 }
 
 size_t batch_workspace_size(const svk_frame *frames, int n, int precision) {

@@ -528,13 +528,13 @@ def _paper_sweep(svk, torch, dev):
             "paper_model": "20 L^2 + 1 FLOP per pixel (Sec. 3)"}
 
 
-def _sharded_frame(svk, torch, dist, rank, world, R, I, c, spec, reps=5):
+def _sharded_frame(svk, torch, dist, rank, world, reps=5):
     """One frame split over the ranks (strong scaling of a single frame): each rank copies
     its band of rows (plus the kernel's halo) from pinned host memory, computes its rows of
     D, and the OIS fit sums the ranks' FP64 moments with one all-reduce before every rank
     solves.  Runs only with more than one rank."""
-    import numpy as np
     from paper_1209_5823_gb300 import shard
+    spec, R, I, c = _frame(0)  # every rank takes part in the same frame
     H, W = R.shape
     Rh, Ih = torch.from_numpy(R).pin_memory(), torch.from_numpy(I).pin_memory()
     B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, spec.L)
@@ -777,7 +777,7 @@ def main():
     e2e_value = _job_rate(world, px, n_e2e, e2e_ms)
     e2e1_value = _job_rate(world, px, n_e2e, e2e1_ms)
     # one frame split over the ranks (every rank takes part in its all-reduce)
-    sharded = _sharded_frame(svk, torch, dist, rank, world, R, I, c, spec) if dist and not args.no_extras else None
+    sharded = _sharded_frame(svk, torch, dist, rank, world) if dist and not args.no_extras else None
     if rank != 0:
         return
 

@@ -814,7 +814,7 @@ def main():
                      "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)",
                      "kernel": "tc_basis_kernel (+ table prep) per CUDA-event bracket",
                      "algorithmic_flop_per_px": _algo_flops_per_px(N, L, d),
-                     "plan": "G=5 output rows per block, 8 stages",
+                     "plan": "G=5 output rows per block, 16 stages (8-row handshakes)",
                      "raw_mma_tflops": raw_flops / (kern_ms / 1e3) / 1e12,
                      "raw_mma_frac": raw_flops / (kern_ms / 1e3) / 1e12 / peak_bf16},
         "direct": {"value": world * px / (dir_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_frame": dir_ms,

@@ -35,13 +35,19 @@
 // its second core-matrix column lies one stage further in the A operand (LBO = stage
 // size) and one basis slice further in the B operand (LBO = Nb * 16 bytes), so only
 // ceil(L/8)*8 taps per row are multiplied instead of a multiple of 16.  A block with
-// an odd row count pads its last row with an all-zero tap group.
+// an odd row count pairs its last row with an all-zero tile that the producers write
+// into the next stage (the basis table carries one slice of zero rows beyond its end for
+// that pair's B window).
 //
-// Handshake granularity.  Producers fill stages in groups of kRowsPerGroup rows: one
-// `full` barrier per group (one arrival per row) and one `empty` commit per group.  An
-// mbarrier wait costs the single MMA-issuing thread a few hundred cycles, so waiting
-// once per group (18 MMAs in the split modes) keeps the tensor pipe fed.  Each block's
-// row sequence is padded with empty slots to a multiple of kRowsPerGroup.
+// Handshake granularity.  The tensor core queues almost nothing ahead of the issuing
+// thread (measured: a delay in that thread between MMAs idles the pipe for about as
+// long), and an mbarrier wait costs that thread ~300 cycles even when the phase has long
+// completed, so the MMA thread waits once per `full` group of rpg = NS / 2 rows (two
+// groups in flight; 8 rows = 36 MMAs per wait in the split modes where 16 stages fit).
+// Its `empty` commits (cheap, no wait) come every epg = 4 rows, so a stage is handed back
+// to the producers as soon as the MMAs of its 4-row group are done and no producer warp
+// has to build two rows of one group back to back.  Each block's row sequence is padded
+// with empty slots to a multiple of rpg.
 //
 // Roles (16 warps): warps 0-7 epilogue (TMEM lane quarter w % 4, output rows of parity
 // w / 4), warp 8 TMEM owner and MMA issuer (one thread), warps 9-15 producers (each
@@ -70,8 +76,7 @@ constexpr int kEpiWarps = 8, kMmaWarp = 8, kProdWarps = 7, kFirstProdWarp = 9;
 constexpr int kSegRegs = 5;  // staged row segment: <= 160 elements = 5 per lane
 constexpr int kThreads = (kEpiWarps + 1 + kProdWarps) * 32;
 constexpr int kTileM = 128;
-constexpr int kMaxStages = 8;  // Hankel stages (reference rows in flight), upper bound
-constexpr int kRowsPerGroup = 4;  // rows per full/empty handshake
+constexpr int kMaxStages = 16;  // Hankel stages (reference rows in flight), upper bound
 constexpr int kMaxG = 40;          // output rows per block (few stamps: the T-factored form)
 constexpr uint32_t kTmemCols = 512;
 constexpr int kAccStride = 256;  // TMEM columns per accumulator buffer
@@ -79,14 +84,15 @@ constexpr int kAccStride = 256;  // TMEM columns per accumulator buffer
 // ----------------------------------------------------------------- plan (host+device)
 struct Plan {
   int N, L, h, G, nmma;    // stamps, kernel size, half size, output rows/block, MMA N
-  int nG, nKG;             // tap groups of 8 per reference row; table groups (nG rounded
-                           // up to even: the extra group is all zero)
+  int nG, nKG;             // tap groups of 8 per reference row; table groups (= nG)
   int S;                   // Hankel blocks per reference row (= 16 + nKG - 1)
   size_t stage_bytes;      // one pipeline stage (hi [+ lo] Hankel tiles)
   int seglen;              // staged row length (elements) = 8 S + 8
   int NP, nrows;           // table slices, table rows per K group
   int parts;               // 2 for split precision, 1 for plain BF16
   int NS;                  // Hankel pipeline stages
+  int rpg, epg;            // rows per `full` group (NS / 2: two groups in flight) and per
+                           // `empty` group (4, or rpg when smaller)
   int prec;
   size_t table_bytes;      // one table (hi or lo)
   size_t off_tab_hi, off_tab_lo, off_stage, off_stg, off_coef, off_alpha, off_alphaS, off_bar, smem;
@@ -101,19 +107,24 @@ static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
   q.h = (L - 1) / 2;
   q.G = G;
   q.prec = prec;
-  if (NS < kRowsPerGroup || NS > kMaxStages || NS % kRowsPerGroup != 0) return false;
+  if (NS != 4 && NS != 8 && NS != 16) return false;
   q.NS = NS;
+  q.rpg = NS / 2;
+  q.epg = q.rpg < 4 ? q.rpg : 4;
   q.parts = (prec == SVK_PREC_BF16) ? 1 : 2;
   q.nmma = rup(G * N, 16);
   if (q.nmma > 256 || q.nmma < 16) return false;
   q.nG = (L + 7) / 8;
-  q.nKG = q.nG + (q.nG & 1);
+  q.nKG = q.nG;
   q.S = kTileM / 8 + q.nKG - 1;
   q.seglen = 8 * q.S + 8;
   if (q.seglen > 32 * kSegRegs) return false;
   q.stage_bytes = (size_t)q.parts * q.S * 128;
   q.NP = L + 2 * (G - 1);
-  q.nrows = rup(q.NP * N + 16, 8);
+  // slices, then zero rows: 16 for the MMA width beyond G*N and, when nG is odd, N for
+  // the window one slice further that an odd last row's last tap group is paired with
+  // (its A tile is zero)
+  q.nrows = rup(q.NP * N + 16 + ((q.nG & 1) ? N : 0), 8);
   q.table_bytes = (size_t)q.nKG * q.nrows * 16;
   size_t o = 0;
   q.off_tab_hi = o;
@@ -129,7 +140,7 @@ static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
   o += (size_t)rup(N * 10 * 4, 16);
   q.off_alpha = o;
   o += (size_t)rup(G * N * 4 * 4, 16);
-  q.off_alphaS = o;  // G x 64 load slots x float4 (only the 16..64-stamp epilogue uses it)
+  q.off_alphaS = o;  // G x 4 powers of xt x 64 load slots (only the 16..64-stamp epilogue)
   if (N >= 16 && N <= 64) o += (size_t)G * 64 * 16;
   q.off_bar = o;
   o += 8 * (2 * kMaxStages + 4 + 2) + 16;
@@ -146,7 +157,7 @@ static bool choose_plan(int N, int L, int prec, Plan *p) {
   // flight when they fit (producers fill one while the MMAs drain the other); the
   // autotuner replaces this default by measurement
   for (int G = kMaxG; G >= 1; --G)
-    for (int NS = kMaxStages; NS >= kRowsPerGroup; NS -= kRowsPerGroup)
+    for (int NS = kMaxStages; NS >= 4; NS /= 2)
       if (make_plan(N, L, prec, G, NS, p)) return true;
   return false;
 }
@@ -227,10 +238,10 @@ __device__ __forceinline__ void cta_block_range(const FrameSet &fs, int &b0, int
 }
 
 // The CTA's sequence of reference rows: for each of its blocks the rows
-// max(0, y0-h) .. min(H-1, y0+G-1+h), padded with empty slots to a multiple of
-// kRowsPerGroup.
+// max(0, y0-h) .. min(H-1, y0+G-1+h), padded with empty slots to a multiple of the rows
+// per handshake group.
 struct RowIt {
-  int b, b_end, f, i, n, nseq, r_lo, x0, y0;
+  int b, b_end, f, i, n, nseq, r_lo, x0, y0, rpg;
   __device__ void set_block(const FrameSet &fs, int bb, int G, int h) {
     b = bb;
     i = 0;
@@ -239,7 +250,7 @@ struct RowIt {
       block_origin(fs.fr[f], b, G, x0, y0);
       r_lo = max(0, y0 - h);
       n = min(fs.fr[f].H - 1, y0 + G - 1 + h) - r_lo + 1;
-      nseq = (n + kRowsPerGroup - 1) / kRowsPerGroup * kRowsPerGroup;
+      nseq = (n + rpg - 1) & ~(rpg - 1);  // rpg is a power of two
     }
   }
   __device__ void next(const FrameSet &fs, int G, int h) {
@@ -307,10 +318,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == kMmaWarp) {
     tmem_alloc(tmem_slot, kTmemCols);
     if (lane == 0) {
-      for (int q = 0; q < NS / kRowsPerGroup; ++q) {
-        mbar_init(&full[q], kRowsPerGroup);  // one arrival per row of the group
-        mbar_init(&empty[q], 1);             // one commit per group
-      }
+      for (int q = 0; q < NS / pl.rpg; ++q) mbar_init(&full[q], pl.rpg);  // one arrival per row of the group
+      for (int q = 0; q < NS / pl.epg; ++q) mbar_init(&empty[q], 1);       // one commit per group
       for (int b = 0; b < 2; ++b) {
         mbar_init(&acc_full[b], 1);
         mbar_init(&acc_empty[b], kEpiWarps * 32);
@@ -328,20 +337,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp >= kFirstProdWarp) {
     // ================================================================ producers
     // P = min(kProdWarps, NS) warps take the rows in turn.  A warp about to fill group q
-    // waits for group q - NG (NG = NS / kRowsPerGroup groups) to drain; its previous row,
-    // P slots earlier, already waited for group q - ceil(P / kRowsPerGroup) - NG, so with
-    // ceil(P / kRowsPerGroup) <= NG group q - 2 NG is drained and the parity wait cannot
+    // waits for the `empty` group that used its stages NS slots earlier to drain; that group
+    // cannot be consumed again before this warp refills it, so its barrier is never more
+    // than one phase ahead of the parity this warp waits for, and the parity wait cannot
     // alias a phase two uses ahead.
     const int pw = warp - kFirstProdWarp, nprod = kProdWarps < NS ? kProdWarps : NS;
     if (pw >= nprod) goto done;
     const int cstride = rup(pl.seglen * 2 + 16, 16) / 2;  // elements between staging copies
     uint16_t *stg = reinterpret_cast<uint16_t *>(sm + pl.off_stg) + (size_t)pw * kParts * 2 * cstride;
+    // stage slot and its phase parity, stepped without divisions (NS, rpg and epg are
+    // powers of two; nprod <= NS, so a step wraps at most once)
+    const int rshift = __ffs(pl.rpg) - 1, eshift = __ffs(pl.epg) - 1;
+    uint32_t stage = (uint32_t)pw, sph = 0;
     RowIt it;
+    it.rpg = pl.rpg;
     it.b_end = b_end;
     it.f = 0;
     it.set_block(fs, b_begin, G, h);
     for (int k = 0; k < pw && it.valid(); ++k) it.next(fs, G, h);
-    uint32_t seq = (uint32_t)pw;
     float cur[kSegRegs], nxt[kSegRegs];
     auto load_row = [&](const RowIt &ri, float (&v)[kSegRegs]) {
       const FrameDesc &fd = fs.fr[ri.f];
@@ -360,10 +373,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       RowIt nx = it;
       for (int k = 0; k < nprod && nx.valid(); ++k) nx.next(fs, G, h);
       if (nx.valid() && nx.real()) load_row(nx, nxt);  // in flight while this row is built
-      const int stage = seq % NS, grp = stage / kRowsPerGroup;
+      const int grp = (int)stage >> rshift;
       // every lane waits; the warp leaves together if any lane's wait ran out (the
       // warp-synchronous code below must not run with part of the warp gone)
-      const bool ok = mbar_wait_bounded(&empty[grp], ((seq / NS) & 1) ^ 1, status);
+      const bool ok = mbar_wait_bounded(&empty[stage >> eshift], sph ^ 1, status);
       if (__any_sync(0xffffffffu, !ok)) goto done;
       if (it.real()) {
         // hi/lo 16-bit copies of the segment; copy 1 is shifted by one element so every
@@ -406,6 +419,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (e < 8 * pl.S) *reinterpret_cast<uint4 *>(hk + (size_t)part * pl.S * 128 + (size_t)e * 16) = chunk[j][part];
         }
         fence_proxy_async_smem();
+      } else if (it.i == it.n && (it.n & 1) && (pl.nG & 1)) {
+        // the slot after an odd last row: an all-zero tile, the partner of that row's
+        // last tap group in the paired K step
+        unsigned char *hk = sm + pl.off_stage + (size_t)stage * pl.stage_bytes;
+        for (int o = lane * 16; o < (int)pl.stage_bytes; o += 32 * 16)
+          *reinterpret_cast<uint4 *>(hk + o) = make_uint4(0u, 0u, 0u, 0u);
+        fence_proxy_async_smem();
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&full[grp]);
@@ -413,7 +433,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int j = 0; j < kSegRegs; ++j) cur[j] = nxt[j];
       it = nx;
-      seq += nprod;
+      stage += (uint32_t)nprod;
+      if (stage >= (uint32_t)NS) {
+        stage -= (uint32_t)NS;
+        sph ^= 1;
+      }
     }
   } else if (warp == kMmaWarp) {
     // ================================================================ MMA issuer
@@ -434,7 +458,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint64_t oKs_a = 256u >> 4, oKs_b = (uint64_t)(2u * lbo_b) >> 4;  // one K step
         const uint64_t oStage = sbytes >> 4, oSlice = (uint64_t)N;              // N rows x 16 B
         const int inrow = (pl.nG - (pl.nG & 1)) / 2;  // K steps a paired row takes on its own
-        uint32_t row_seq = 0, blk_seq = 0, acc = 0, d_tmem = 0, tab_phase = 0;
+        // The thread issues the MMAs back to back and the tensor core queues almost nothing
+        // ahead of it, so its bookkeeping between MMAs stays free of divisions: the stage
+        // of the next row pair and its phase parity, and the block origin, are stepped.
+        uint32_t sa = 0, sph = 0, blk_seq = 0, acc = 0, d_tmem = 0, tab_phase = 0;
+        const uint32_t rmask = (uint32_t)pl.rpg - 1u, emask = (uint32_t)pl.epg - 1u;
+        const int rshift = __ffs(pl.rpg) - 1, eshift = __ffs(pl.epg) - 1;
         const uint4 *loaded = nullptr;
         // the frame's basis tables into shared memory, once every MMA that reads the
         // tables now there has completed (frames with one basis share their tables)
@@ -473,34 +502,44 @@ __global__ void __launch_bounds__(kThreads, 1)
             acc = 1;
           }
         };
-        int f = 0;
+        int f = 0, x0 = 0, y0 = 0;
         for (int b = b_begin; b < b_end; ++b, ++blk_seq) {
-          f = advance_frame(fs, f, b);
+          if (b == b_begin || (f + 1 < fs.n && b >= fs.fr[f + 1].block0)) {
+            f = advance_frame(fs, f, b);
+            block_origin(fs.fr[f], b, G, x0, y0);
+          } else {  // the next block of the same frame: one tile to the right, or the next band
+            x0 += kTileM;
+            if (x0 >= fs.fr[f].nbx * kTileM) {
+              x0 = 0;
+              y0 += G;
+            }
+          }
           const FrameDesc &fd = fs.fr[f];
           if (!load_tables(fd)) goto drain;
-          int x0, y0;
-          block_origin(fd, b, G, x0, y0);
           const int buf = blk_seq & 1;
           if (!mbar_wait_bounded(&acc_empty[buf], ((blk_seq >> 1) & 1) ^ 1, status)) goto drain;
           tc_fence_after();
           d_tmem = tmem_base + (uint32_t)(buf * kAccStride);
           acc = 0;
           const int r_lo = max(0, y0 - h), n = min(fd.H - 1, y0 + G - 1 + h) - r_lo + 1;
-          const int nseq = (n + kRowsPerGroup - 1) / kRowsPerGroup * kRowsPerGroup;
-          for (int i = 0; i < nseq; i += 2, row_seq += 2) {
-            const int sa = row_seq % NS, grp = sa / kRowsPerGroup;  // stages sa, sa + 1
-            if (sa % kRowsPerGroup == 0)
-              if (!mbar_wait_bounded(&full[grp], (row_seq / NS) & 1, status)) goto drain;
+          const int nseq = (n + pl.rpg - 1) & ~(pl.rpg - 1);
+          const uint64_t bw0 = dB + (uint64_t)(r_lo - y0 + h) * oSlice;   // window of row r_lo
+          const uint64_t bx0 = dBx + (uint64_t)(r_lo - y0 + h) * oSlice;
+          for (int i = 0; i < nseq; i += 2) {  // stages sa, sa + 1
+            if ((sa & rmask) == 0)
+              if (!mbar_wait_bounded(&full[sa >> rshift], sph, status)) goto drain;
             // shared-memory operands: ordered by the producers' proxy fence + mbarrier
             const uint64_t a = dA + (uint64_t)sa * oStage;
-            const uint64_t bw = dB + (uint64_t)(r_lo + i - y0 + h) * oSlice;  // window of row r_lo + i
-            if (i + 1 < n) {
+            const uint64_t bw = bw0 + (uint64_t)i * oSlice;  // window of row r_lo + i
+            if (i < n) {
+              // rows r_lo + i and r_lo + i + 1 (for an odd last row the second is the
+              // producers' all-zero tile): each row's full K steps, then their last tap
+              // groups together in one K step when nG is odd
               row_mmas(a, bw, inrow);
-              row_mmas(a + oStage, bw + oSlice, inrow);
+              if (i + 1 < n) row_mmas(a + oStage, bw + oSlice, inrow);
               if (pl.nG & 1) {
-                // last tap group of rows r_lo + i and r_lo + i + 1 in one K step
                 const uint64_t ax = dAx + (uint64_t)sa * oStage;
-                const uint64_t bx = dBx + (uint64_t)(r_lo + i - y0 + h) * oSlice;
+                const uint64_t bx = bx0 + (uint64_t)i * oSlice;
                 if (kParts == 2) {
                   umma_f16_fill(d_tmem, ax, bx, idesc, acc);
                   umma_f16_lastuse(d_tmem, ax, bx + oBl, idesc, 1);
@@ -510,10 +549,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 acc = 1;
               }
-            } else if (i < n) {
-              row_mmas(a, bw, pl.nKG / 2);  // the odd last row, padded by the zero group
             }
-            if ((sa + 2) % kRowsPerGroup == 0) umma_commit(&empty[grp]);
+            if (((sa + 2u) & emask) == 0) umma_commit(&empty[sa >> eshift]);
+            sa += 2;
+            if (sa == (uint32_t)NS) {
+              sa = 0;
+              sph ^= 1;
+            }
           }
           umma_commit(&acc_full[buf]);
         }
@@ -596,8 +638,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int st = min(16 * i, N - 16), slot = k - st;
-            if (16 * i < N && slot >= 0 && slot < 16 && k >= 16 * i)
-              *reinterpret_cast<float4 *>(alphaS + ((size_t)g * 64 + 16 * i + slot) * 4) = make_float4(a0, a1, a2, a3);
+            if (16 * i < N && slot >= 0 && slot < 16 && k >= 16 * i) {
+              float *as = alphaS + (size_t)g * 256 + 16 * i + slot;  // [g][power of xt][slot]
+              as[0] = a0;
+              as[64] = a1;
+              as[128] = a2;
+              as[192] = a3;
+            }
           }
         }
       }
@@ -637,16 +684,36 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_ld16p(c0 + (uint32_t)st, &v[16 * i]);
           }
           tmem_ld_wait();
-          const float4 *ap = reinterpret_cast<const float4 *>(alphaS) + (size_t)g * 64;
+          // packed pairs of slots: P_i accumulates slots 4q, 4q+2 in its low half and 4q+1,
+          // 4q+3 in its high half (one fma.rn.f32x2 per pair and power of xt)
+          const float *ag = alphaS + (size_t)g * 256;
+          uint64_t P0 = 0, P1 = 0, P2 = 0, P3 = 0;
 #pragma unroll
-          for (int q = 0; q < 64; ++q) {
-            const float4 a = ap[q];
-            const float cv = __uint_as_float(v[q]);
-            s0 = fmaf(a.x, cv, s0);
-            s1 = fmaf(a.y, cv, s1);
-            s2 = fmaf(a.z, cv, s2);
-            s3 = fmaf(a.w, cv, s3);
+          for (int q = 0; q < 16; ++q) {
+            const uint64_t c01 = f2_pack(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]));
+            const uint64_t c23 = f2_pack(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+            const ulonglong2 A0 = *reinterpret_cast<const ulonglong2 *>(ag + 4 * q);
+            const ulonglong2 A1 = *reinterpret_cast<const ulonglong2 *>(ag + 64 + 4 * q);
+            const ulonglong2 A2 = *reinterpret_cast<const ulonglong2 *>(ag + 128 + 4 * q);
+            const ulonglong2 A3 = *reinterpret_cast<const ulonglong2 *>(ag + 192 + 4 * q);
+            P0 = f2_fma(A0.x, c01, P0);
+            P1 = f2_fma(A1.x, c01, P1);
+            P2 = f2_fma(A2.x, c01, P2);
+            P3 = f2_fma(A3.x, c01, P3);
+            P0 = f2_fma(A0.y, c23, P0);
+            P1 = f2_fma(A1.y, c23, P1);
+            P2 = f2_fma(A2.y, c23, P2);
+            P3 = f2_fma(A3.y, c23, P3);
           }
+          float l, u;
+          f2_unpack(P0, l, u);
+          s0 = l + u;
+          f2_unpack(P1, l, u);
+          s1 = l + u;
+          f2_unpack(P2, l, u);
+          s2 = l + u;
+          f2_unpack(P3, l, u);
+          s3 = l + u;
         } else {
           const float4 *a4 = reinterpret_cast<const float4 *>(alpha) + (size_t)g * N;
           const int nfull = N >> 4, tail = N & 15;
@@ -987,7 +1054,7 @@ int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_ou
   void *ws = nullptr;
   size_t ws_bytes = 0;
   for (int G = 1; G <= kMaxG; ++G)
-    for (int NS = kRowsPerGroup; NS <= kMaxStages; NS += kRowsPerGroup) {
+    for (int NS = 4; NS <= kMaxStages; NS *= 2) {
       Plan pl;
       if (make_plan(N, L, precision, G, NS, &pl) && pl.table_bytes * 2 + 256 > ws_bytes) ws_bytes = pl.table_bytes * 2 + 256;
     }
@@ -1024,7 +1091,7 @@ int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_ou
     f.coeffs = C;
     f.degree = degree;
     for (int G = kMaxG; G >= 1 && st == SVK_OK; --G)
-      for (int NS = kMaxStages; NS >= kRowsPerGroup && st == SVK_OK; NS -= kRowsPerGroup) {
+      for (int NS = kMaxStages; NS >= 4 && st == SVK_OK; NS /= 2) {
         Plan pl;
         if (!make_plan(N, L, precision, G, NS, &pl)) continue;
         st = launch_set(&f, 1, precision, pl, ws, ws_bytes, s);  // warm-up

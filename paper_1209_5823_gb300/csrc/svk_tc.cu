@@ -50,8 +50,9 @@
 // with empty slots to a multiple of rpg.
 //
 // Roles (16 warps): warps 0-7 epilogue (TMEM lane quarter w % 4, output rows of parity
-// w / 4), warp 8 TMEM owner and MMA issuer (one thread), warps 9-15 producers (each
-// prefetches its next reference row into registers while it converts the current one).  No role uses local memory:
+// w / 4), warp 8 TMEM owner and MMA issuer (one thread), warps 9-11 and 13-15 producers
+// (each prefetches its next reference row into registers while it converts the current
+// one), warp 12 idle (it would share the MMA warp's scheduler).  No role uses local memory:
 // with ~227 KB of shared memory the L1 left for it is small.  All waits are bounded; a
 // wait that runs out records a status word and the CTA unwinds (MMAs drained, TMEM
 // freed).
@@ -72,9 +73,12 @@ namespace svk {
 namespace {
 
 constexpr int kMaxSmem = 232448;  // 227 KB opt-in shared memory per CTA on sm_100-class parts
-constexpr int kEpiWarps = 8, kMmaWarp = 8, kProdWarps = 7, kFirstProdWarp = 9;
+// Warp 12 shares the MMA warp's scheduler (warp % 4) and stays idle: the issuing thread
+// gets that scheduler's issue slots to itself apart from two epilogue warps (measured 2 %
+// faster than a seventh producer there).
+constexpr int kEpiWarps = 8, kMmaWarp = 8, kProdWarps = 6, kFirstProdWarp = 9, kIdleWarp = 12;
 constexpr int kSegRegs = 5;  // staged row segment: <= 160 elements = 5 per lane
-constexpr int kThreads = (kEpiWarps + 1 + kProdWarps) * 32;
+constexpr int kThreads = (kEpiWarps + 1 + kProdWarps + 1) * 32;
 constexpr int kTileM = 128;
 constexpr int kMaxStages = 16;  // Hankel stages (reference rows in flight), upper bound
 constexpr int kMaxG = 40;          // output rows per block (few stamps: the T-factored form)
@@ -334,14 +338,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  if (warp >= kFirstProdWarp) {
+  if (warp == kIdleWarp) {
+    goto done;
+  } else if (warp >= kFirstProdWarp) {
     // ================================================================ producers
     // P = min(kProdWarps, NS) warps take the rows in turn.  A warp about to fill group q
     // waits for the `empty` group that used its stages NS slots earlier to drain; that group
     // cannot be consumed again before this warp refills it, so its barrier is never more
     // than one phase ahead of the parity this warp waits for, and the parity wait cannot
     // alias a phase two uses ahead.
-    const int pw = warp - kFirstProdWarp, nprod = kProdWarps < NS ? kProdWarps : NS;
+    const int pw = warp - kFirstProdWarp - (warp > kIdleWarp ? 1 : 0), nprod = kProdWarps < NS ? kProdWarps : NS;
     if (pw >= nprod) goto done;
     const int cstride = rup(pl.seglen * 2 + 16, 16) / 2;  // elements between staging copies
     uint16_t *stg = reinterpret_cast<uint16_t *>(sm + pl.off_stg) + (size_t)pw * kParts * 2 * cstride;

@@ -261,6 +261,72 @@ SVK_API int svk_cnn_field_fit(const float *local, const int *xy, const float *we
                               int degree, double *coeffs, int *info, void *stream);
 
 /*
+ * Square stamps of an image (row A9: the network's input and the residual check both look
+ * at stamps around stars, the stamps over which Sec. 2 fits the kernel):
+ *   out[s * stamp_stride + v * size + u] = (img(cx_s - size/2 + u, cy_s - size/2 + v) - offset) / divisor
+ * with img read as 0 outside the W x H frame, u, v = 0 .. size - 1.
+ *   img    device float32 [H][pitch];  xy: device int32 [n][2] = (cx, cy)
+ *   out    device float32, stamp s at out + s * stamp_stride (stamp_stride >= size^2; pass
+ *          2 size^2 and out + c size^2 to fill channel c of an [n][2][size][size] input)
+ *   offset, divisor: the affine normalisation (0 and 1 for raw counts; divisor != 0)
+ * Errors: SVK_ERR_ARG (host checks).  Asynchronous on `stream`.
+ */
+SVK_API int svk_cut_stamps(const float *img, int W, int H, int pitch, const int *xy, int n, int size, float offset,
+                           float divisor, float *out, long long stamp_stride, void *stream);
+
+/* Bytes of device workspace svk_stamp_residual needs (0 when n < 1). */
+SVK_API size_t svk_stamp_residual_workspace_size(int n);
+
+/*
+ * The check that keeps or rejects the network's coefficients for a frame (row A9, the FP64
+ * fit as fallback): with D = (R (x) K) - I made from them,
+ *   chi2_per_px = mean over the n stamps and their size^2 pixels of (D - mean_stamp(D))^2
+ *                 (D read as 0 outside the frame; each stamp's mean removed, the background
+ *                 not being part of the prediction)
+ *   floor       = noise_sigma^2 + ref_noise_sigma^2 * sum(K0^2)   (basis0: K0 [L][L], the
+ *                 unit-sum first stamp standing in for the kernel)
+ *   fallback    = 1 when chi2_per_px > ratio * floor or *field_info >= 0 (the field fit
+ *                 failed; field_info nullable), else 0
+ * out: device double [2] = {chi2_per_px, floor}; fallback_out: device int [1].  FP64 sums
+ * in a fixed order (deterministic).  Asynchronous on `stream`.
+ */
+SVK_API int svk_stamp_residual(const float *D, int W, int H, int pitch, const int *xy, int n, int size,
+                               const float *basis0, int L, double noise_sigma, double ref_noise_sigma, double ratio,
+                               const int *field_info, double *out, int *fallback_out, void *workspace,
+                               size_t ws_bytes, void *stream);
+
+/*
+ * Standardisation of the network's targets and outputs: out[r][c] = (in[r][c] - mean[c]) /
+ * sd[c], or with `inverse` non-zero out[r][c] = mean[c] + sd[c] * in[r][c].  Device float32
+ * [rows][cols] (in may equal out); mean, sd: device float32 [cols].
+ */
+SVK_API int svk_cnn_standardise(const float *in, long long rows, int cols, const float *mean, const float *sd,
+                                int inverse, float *out, void *stream);
+
+/*
+ * Training batch drawn on the device: idx_out[i] (device int64 [batch]) uniform in [0, n)
+ * for i < batch, from the counter seed + step * batch + i (step read from device memory
+ * when the kernel runs) mixed by SplitMix64 and reduced by a multiply-shift.  A captured
+ * training step that advances *step draws a new batch at every replay, and the draws of a
+ * run are fixed by (seed, step): resuming from a saved step reproduces them.
+ */
+SVK_API int svk_cnn_draw_batch(unsigned long long seed, const int *step, int n, int batch, long long *idx_out,
+                               void *stream);
+
+/*
+ * Row gather: row i of dst = row idx[i] of src, for i < n (rows of row_bytes bytes, a
+ * multiple of 4; n <= 65535).  Device pointers; the caller keeps idx in range.
+ */
+SVK_API int svk_gather_rows(const void *src, long long row_bytes, const long long *idx, int n, void *dst,
+                            void *stream);
+
+/*
+ * End of a training step on the device: history[*step % history_len] = *loss, then
+ * *step += 1 (device pointers; for a captured step that keeps its losses on the device).
+ */
+SVK_API int svk_cnn_step_end(const float *loss, int *step, float *history, int history_len, void *stream);
+
+/*
  * Bytes of device workspace svk_fit_coeffs needs.
  */
 SVK_API size_t svk_fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree,

@@ -46,7 +46,9 @@ EXPORTS = (
     "svk_select_workspace_size", "svk_select_stamps", "svk_measure_fma_peak", "svk_host_workspace_size",
     "svk_difference_host", "svk_host_batch_workspace_size", "svk_difference_host_batch", "svk_selftest_bounded_wait",
     "svk_device_status", "svk_fit_moments_count", "svk_fit_moments_workspace_size", "svk_fit_moments",
-    "svk_fit_solve_workspace_size", "svk_fit_solve", "svk_band_rows", "svk_difference_rows",
+    "svk_fit_solve_workspace_size", "svk_fit_solve", "svk_band_rows", "svk_difference_rows", "svk_cut_stamps",
+    "svk_stamp_residual_workspace_size", "svk_stamp_residual", "svk_cnn_standardise", "svk_cnn_draw_batch",
+    "svk_gather_rows", "svk_cnn_step_end",
 )
 
 
@@ -116,6 +118,14 @@ def load_library(path: str | None = None):
         "svk_fit_solve": (i, [vp, i, i, i, vp, vp, vp, vp, sz, i, vp]),
         "svk_band_rows": (i, [i, i, i, i, i]),
         "svk_difference_rows": (i, [vp, i, i, i, vp, i, vp, i, i, i, i, i, vp, i, i, vp, i, i, i, i, vp, sz, vp]),
+        "svk_cut_stamps": (i, [vp, i, i, i, vp, i, i, f, f, vp, ctypes.c_longlong, vp]),
+        "svk_stamp_residual_workspace_size": (sz, [i]),
+        "svk_stamp_residual": (i, [vp, i, i, i, vp, i, i, vp, i, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   vp, vp, vp, vp, sz, vp]),
+        "svk_cnn_standardise": (i, [vp, ctypes.c_longlong, i, vp, vp, i, vp, vp]),
+        "svk_cnn_draw_batch": (i, [ctypes.c_ulonglong, vp, i, i, vp, vp]),
+        "svk_gather_rows": (i, [vp, ctypes.c_longlong, vp, i, vp, vp]),
+        "svk_cnn_step_end": (i, [vp, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -484,6 +494,69 @@ def svk_select_stamps(R, sky: float, threshold: float, saturation: float, margin
                                             _ptr(xy) if max_stamps > 0 else _ptr(None), _ptr(counts),
                                             _ptr(workspace), ws_bytes, _stream(stream)))
     return xy, counts
+
+
+def svk_cut_stamps(img, xy, size: int, offset: float = 0.0, divisor: float = 1.0, out=None, stamp_stride=None,
+                   stream=None):
+    """Stamps of img around the int32 [n][2] centres xy, (value - offset) / divisor, zero
+    outside the image; returns out ([n][size][size] float32 unless given with its stride)."""
+    import torch
+    H, W, p = _img(img, "img")
+    xy = xy.to(torch.int32).contiguous()
+    n = xy.shape[0]
+    if out is None:
+        out = torch.empty((n, size, size), dtype=torch.float32, device=img.device)
+        stamp_stride = size * size
+    elif stamp_stride is None:
+        stamp_stride = size * size
+    _check(load_library().svk_cut_stamps(_ptr(img), W, H, p, _ptr(xy), n, int(size), float(offset), float(divisor),
+                                         _ptr(out), int(stamp_stride), _stream(stream)))
+    return out
+
+
+def svk_stamp_residual(D, xy, size: int, basis0, noise_sigma: float, ref_noise_sigma: float, ratio: float,
+                       field_info=None, workspace=None, stream=None):
+    """(out [2] f64 = {chi2_per_px, floor}, fallback [1] i32) device tensors."""
+    import torch
+    H, W, p = _img(D, "D")
+    xy = xy.to(torch.int32).contiguous()
+    out = torch.zeros(2, dtype=torch.float64, device=D.device)
+    fb = torch.zeros(1, dtype=torch.int32, device=D.device)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().svk_stamp_residual(_ptr(D), W, H, p, _ptr(xy), xy.shape[0], int(size), _ptr(basis0),
+                                             basis0.shape[-1], float(noise_sigma), float(ref_noise_sigma), float(ratio),
+                                             _ptr(field_info), _ptr(out), _ptr(fb), _ptr(workspace), ws_bytes,
+                                             _stream(stream)))
+    return out, fb
+
+
+def svk_cnn_standardise(x, mean, sd, inverse: bool = False, out=None, stream=None):
+    """(x - mean) / sd per column, or mean + sd * x (inverse); x float32 [rows][cols]."""
+    import torch
+    x = x.contiguous()
+    if out is None:
+        out = torch.empty_like(x)
+    _check(load_library().svk_cnn_standardise(_ptr(x), x.shape[0], x.shape[1], _ptr(mean), _ptr(sd),
+                                              int(bool(inverse)), _ptr(out), _stream(stream)))
+    return out
+
+
+def svk_cnn_draw_batch(seed: int, step, n: int, idx_out, stream=None):
+    _check(load_library().svk_cnn_draw_batch(int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(step), int(n), idx_out.numel(),
+                                             _ptr(idx_out), _stream(stream)))
+    return idx_out
+
+
+def svk_gather_rows(src, idx, out, stream=None):
+    """out[i] = src[idx[i]] along the first dimension (contiguous tensors)."""
+    row_bytes = src[0].numel() * src.element_size()
+    _check(load_library().svk_gather_rows(_ptr(src), int(row_bytes), _ptr(idx), idx.numel(), _ptr(out),
+                                          _stream(stream)))
+    return out
+
+
+def svk_cnn_step_end(loss, step, history, stream=None):
+    _check(load_library().svk_cnn_step_end(_ptr(loss), _ptr(step), _ptr(history), history.numel(), _stream(stream)))
 
 
 # ---------------------------------------------------------------- coefficient network

@@ -564,6 +564,67 @@ int svk_difference_rows(const float *R, int pitch_R, int r_begin, int r_end, con
                    s, y_begin, y_end, true, r_begin, r_end);
 }
 
+int svk_cut_stamps(const float *img, int W, int H, int pitch, const int *xy, int n, int size, float offset,
+                   float divisor, float *out, long long stamp_stride, void *stream) {
+  CallRange range("svk_cut_stamps");
+  if (!img || !out || (n > 0 && !xy)) return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  if (W < 1 || H < 1 || pitch < W) return set_error(SVK_ERR_ARG, "bad image size/pitch");
+  if (n < 0 || size < 1 || size > 1024) return set_error(SVK_ERR_ARG, "bad stamp count %d / size %d", n, size);
+  if (stamp_stride < (long long)size * size) return set_error(SVK_ERR_ARG, "stamp stride below size * size");
+  if (!(divisor != 0.0f) || !std::isfinite(divisor) || !std::isfinite(offset))
+    return set_error(SVK_ERR_ARG, "offset/divisor must be finite and divisor non-zero");
+  return launch_cut_stamps(img, W, H, pitch, xy, n, size, offset, divisor, out, stamp_stride,
+                           static_cast<cudaStream_t>(stream));
+}
+
+size_t svk_stamp_residual_workspace_size(int n) { return n < 1 ? 0 : stamp_residual_workspace_size(n); }
+
+int svk_stamp_residual(const float *D, int W, int H, int pitch, const int *xy, int n, int size, const float *basis0,
+                       int L, double noise_sigma, double ref_noise_sigma, double ratio, const int *field_info,
+                       double *out, int *fallback_out, void *workspace, size_t ws_bytes, void *stream) {
+  CallRange range("svk_stamp_residual");
+  if (!D || !xy || !basis0 || !out || !fallback_out) return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  if (W < 1 || H < 1 || pitch < W) return set_error(SVK_ERR_ARG, "bad image size/pitch");
+  if (n < 1 || size < 1 || size > 1024) return set_error(SVK_ERR_ARG, "bad stamp count %d / size %d", n, size);
+  if (L < 1 || L > 63 || (L % 2) == 0) return set_error(SVK_ERR_ARG, "L=%d must be odd in [1,63]", L);
+  if (!(noise_sigma >= 0.0) || !(ref_noise_sigma >= 0.0) || !(ratio > 0.0))
+    return set_error(SVK_ERR_ARG, "noise levels must be >= 0 and the ratio > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScopedWorkspace w;
+  const size_t need = stamp_residual_workspace_size(n);
+  int st = w.acquire(need, workspace, ws_bytes, s);
+  if (st != SVK_OK) return st;
+  return launch_stamp_residual(D, W, H, pitch, xy, n, size, basis0, L, noise_sigma, ref_noise_sigma, ratio, field_info,
+                               out, fallback_out, w.ptr, need, s);
+}
+
+int svk_cnn_standardise(const float *in, long long rows, int cols, const float *mean, const float *sd, int inverse,
+                        float *out, void *stream) {
+  if (!in || !mean || !sd || !out) return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  if (rows < 0 || cols < 1) return set_error(SVK_ERR_ARG, "bad shape %lld x %d", rows, cols);
+  return launch_standardise(in, rows, cols, mean, sd, inverse != 0, out, static_cast<cudaStream_t>(stream));
+}
+
+int svk_cnn_draw_batch(unsigned long long seed, const int *step, int n, int batch, long long *idx_out, void *stream) {
+  if (!step || !idx_out) return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  if (n < 1 || batch < 1) return set_error(SVK_ERR_ARG, "n=%d and batch=%d must be positive", n, batch);
+  return launch_draw_batch(seed, step, n, batch, idx_out, static_cast<cudaStream_t>(stream));
+}
+
+int svk_gather_rows(const void *src, long long row_bytes, const long long *idx, int n, void *dst, void *stream) {
+  if (!src || !idx || !dst) return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  if (row_bytes < 4 || row_bytes % 4 != 0) return set_error(SVK_ERR_ARG, "row_bytes must be a positive multiple of 4");
+  if (n < 0 || n > 65535) return set_error(SVK_ERR_ARG, "n=%d rows out of range [0, 65535]", n);
+  if (n == 0) return SVK_OK;
+  return launch_gather_rows(src, row_bytes, idx, n, dst, static_cast<cudaStream_t>(stream));
+}
+
+int svk_cnn_step_end(const float *loss, int *step, float *history, int history_len, void *stream) {
+  if (!loss || !step || !history) return set_error(SVK_ERR_ARG, "NULL pointer argument");
+  if (history_len < 1) return set_error(SVK_ERR_ARG, "history_len must be >= 1");
+  return launch_step_end(loss, step, history, history_len, static_cast<cudaStream_t>(stream));
+}
+
 size_t svk_host_workspace_size(int method, int precision, int W, int H, int N, int L, int degree) {
   if (W < 1 || H < 1 || W > 65535 || H > 65535) return 0;
   return host_workspace_size(method, precision, W, H, N, L, degree);

@@ -113,4 +113,17 @@ int cnn_adam_device_step(float *params, float *m, float *v, const float *grad, i
 int cnn_field_fit(const float *local, const int *xy, const float *wts, int S, int N, int W, int H, int degree,
                   double *coeffs, int *info, cudaStream_t s);
 
+// The data side of the coefficient network (svk_learned.cu).
+int launch_cut_stamps(const float *img, int W, int H, int pitch, const int *xy, int n, int size, float offset,
+                      float divisor, float *out, long long stride, cudaStream_t s);
+size_t stamp_residual_workspace_size(int n);
+int launch_stamp_residual(const float *D, int W, int H, int pitch, const int *xy, int n, int size, const float *basis0,
+                          int L, double noise, double ref_noise, double ratio, const int *field_info, double *out,
+                          int *fallback, void *ws, size_t ws_bytes, cudaStream_t s);
+int launch_standardise(const float *in, long long rows, int cols, const float *mean, const float *sd, int inverse,
+                       float *out, cudaStream_t s);
+int launch_draw_batch(unsigned long long seed, const int *step, int n, int batch, long long *idx, cudaStream_t s);
+int launch_gather_rows(const void *src, long long row_bytes, const long long *idx, int n, void *dst, cudaStream_t s);
+int launch_step_end(const float *loss, int *step, float *hist, int len, cudaStream_t s);
+
 }  // namespace svk

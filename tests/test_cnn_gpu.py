@@ -152,8 +152,9 @@ def test_training_learns_and_network_path_is_faster_with_fallback():
     a = prior.mean(dev) + prior.std(dev) * torch.randn((n, N), device=dev, generator=gen)
     x, _, _ = learned.make_pairs(Rf, cx, cy, a, basis, 30.0, gen)
     ntr = n - 500
-    net = learned.CoefficientNetwork(torch.from_numpy(starfield.cnn_init_params(N, 7)).cuda(), prior, batch=128)
-    losses = net.train(x[:ntr], a[:ntr], 800, lr=3e-3, gen=gen).cpu().numpy()
+    net = learned.CoefficientNetwork(torch.from_numpy(starfield.cnn_init_params(N, 7)).cuda(), prior, batch=128,
+                                     seed=5)
+    losses = net.train(x[:ntr], a[:ntr], 800, lr=3e-3).cpu().numpy()
     assert losses[-50:].mean() < 0.92 * losses[:50].mean()
     pred = net.predict(x[ntr:])
     err_net = float(((pred - a[ntr:]) / prior.std(dev)).pow(2).mean())
@@ -185,32 +186,37 @@ def test_training_learns_and_network_path_is_faster_with_fallback():
 
 
 def test_training_checkpoint_resumes_bit_exactly(tmp_path):
-    # weights, Adam moments, step and the batch generator's state saved mid-run: the
-    # resumed run ends with the same weights, bit for bit, as an uninterrupted one
+    # weights, Adam moments, step and the batch-draw seed saved mid-run (the draws are fixed
+    # by seed and step): the resumed run ends with the same weights, bit for bit, as an
+    # uninterrupted one; 20 steps = two 8-step graphs and four single steps, 8 + 12 splits
+    # them differently
     N = 49
     g0 = torch.Generator(device="cuda").manual_seed(11)
     x = torch.randn((600, 2, 64, 64), device="cuda", generator=g0) * 0.3
     a = torch.randn((600, N), device="cuda", generator=g0) * 0.02 + learned.CoeffPrior(N).mean(torch.device("cuda"))
     init = torch.from_numpy(starfield.cnn_init_params(N, 3)).cuda()
 
-    full = learned.CoefficientNetwork(init.clone(), learned.CoeffPrior(N), batch=64)
-    gen = torch.Generator(device="cuda").manual_seed(12)
-    full.train(x, a, 20, lr=2e-3, gen=gen)
+    full = learned.CoefficientNetwork(init.clone(), learned.CoeffPrior(N), batch=64, seed=12)
+    lf = full.train(x, a, 20, lr=2e-3)
 
-    part = learned.CoefficientNetwork(init.clone(), learned.CoeffPrior(N), batch=64)
-    gen = torch.Generator(device="cuda").manual_seed(12)
-    part.train(x, a, 8, lr=2e-3, gen=gen)
-    torch.save({"net": part.state_dict(), "gen": gen.get_state()}, tmp_path / "ckpt.pt")
+    part = learned.CoefficientNetwork(init.clone(), learned.CoeffPrior(N), batch=64, seed=12)
+    lp = part.train(x, a, 8, lr=2e-3)
+    torch.save({"net": part.state_dict()}, tmp_path / "ckpt.pt")
     del part
 
     ck = torch.load(tmp_path / "ckpt.pt")
     resumed = learned.CoefficientNetwork.from_state_dict(ck["net"], device="cuda")
-    gen2 = torch.Generator(device="cuda")
-    gen2.set_state(ck["gen"])
-    resumed.train(x, a, 12, lr=2e-3, gen=gen2)
+    lr_ = resumed.train(x, a, 12, lr=2e-3)
     assert resumed.step == full.step == 20
     assert torch.equal(resumed.params, full.params)
     assert torch.equal(resumed.m, full.m) and torch.equal(resumed.v, full.v)
+    # the same losses step by step (the loss value itself is summed with float atomics, so
+    # to its last bits only)
+    assert torch.allclose(torch.cat([lp, lr_]), lf, rtol=1e-6, atol=0)
+    # another seed draws other batches
+    other = learned.CoefficientNetwork(init.clone(), learned.CoeffPrior(N), batch=64, seed=13)
+    other.train(x, a, 20, lr=2e-3)
+    assert not torch.equal(other.params, full.params)
 
 
 def test_adam_device_step_matches_host_step():

@@ -104,14 +104,15 @@ __global__ void __launch_bounds__(kTX * TY, 1)
       const int j = i / 10, t = i % 10;
       Cs[i] = (k0 + j < N && t < T) ? coeffs[(size_t)(k0 + j) * T + t] : 0.0f;
     }
-    __syncthreads();
+    // the chunk's tables are stored (and, first time, the tile has landed) for the whole
+    // block; if the TMA never landed the whole block gives up together, so no thread is
+    // left at the next chunk's barrier
+    bool ok = true;
     if (!tile_ready) {
-      // TMA never landed: the whole block gives up together (no thread is left at the
-      // next chunk's __syncthreads)
-      const bool ok = mbar_wait_bounded(bar, 0, status);
-      if (__syncthreads_or(!ok)) return;
+      ok = mbar_wait_bounded(bar, 0, status);
       tile_ready = true;
     }
+    if (__syncthreads_or(!ok)) return;
     // a_j(x_p, y) = sum_t c[k0+j][t] xt^i yt^j for the chunk (Eq. 3, order <= 3): per stamp
     // alpha_i = sum_jj c[(i, jj)] yt^jj (the same for the thread's pixels, which share a
     // row), then Horner in xt.  Coefficient slots are packed (i outer, jj inner), skipping

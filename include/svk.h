@@ -53,6 +53,7 @@ extern "C" {
 #define SVK_ERR_TIMEOUT 4     /* a bounded device-side wait ran out                       */
 #define SVK_ERR_UNSUPPORTED 5 /* valid request the library does not implement              */
 #define SVK_ERR_WORKSPACE 6   /* caller workspace too small                               */
+#define SVK_ERR_INDEX 7       /* a device index check failed (debug builds, SVK_DEBUG)     */
 
 /* basis kinds (Sec. 2: Gaussian function basis and Dirac delta function basis) */
 #define SVK_BASIS_GAUSS 0
@@ -489,8 +490,11 @@ SVK_API int svk_difference_host_batch(const svk_frame *frames, int n_frames, int
 /*
  * The library's sticky device status: every bounded device wait that gives up (after
  * ~2 s, e.g. a copy that never lands) records SVK_ERR_TIMEOUT there and its kernel
- * unwinds, so results computed since the last check are invalid.  Synchronises `stream`,
- * returns SVK_OK or SVK_ERR_TIMEOUT, and clears the word when `reset` is non-zero.
+ * unwinds, so results computed since the last check are invalid.  A library built with
+ * SVK_DEBUG also checks shared-memory, tensor-memory and descriptor indices in its
+ * kernels and records SVK_ERR_INDEX (the access skipped) instead of trapping.
+ * Synchronises `stream`, returns SVK_OK, SVK_ERR_INDEX or SVK_ERR_TIMEOUT, and clears the
+ * word when `reset` is non-zero.
  */
 SVK_API int svk_device_status(int reset, void *stream);
 

@@ -19,6 +19,7 @@ SVK_ERR_NOT_SPD = 3
 SVK_ERR_TIMEOUT = 4
 SVK_ERR_UNSUPPORTED = 5
 SVK_ERR_WORKSPACE = 6
+SVK_ERR_INDEX = 7
 
 SVK_BASIS_GAUSS = 0
 SVK_BASIS_DELTA = 1
@@ -74,7 +75,8 @@ def load_library(path: str | None = None):
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    # SVK_LIBRARY selects another build of the same ABI (e.g. the debug build, libsvk_debug.so)
+    p = path or os.environ.get("SVK_LIBRARY") or LIB_PATH
     if not os.path.exists(p):
         raise RuntimeError(f"CUDA library {p} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
     lib = ctypes.CDLL(p)

@@ -692,7 +692,12 @@ int svk_device_status(int reset, void *stream) {
     if ((st = cuda_status(cudaMemsetAsync(w, 0, 4, s), "clear device status")) != SVK_OK) return st;
     if ((st = cuda_status(cudaStreamSynchronize(s), "device status sync")) != SVK_OK) return st;
   }
-  if (v == kDevTimeout) return set_error(SVK_ERR_TIMEOUT, "a bounded device wait gave up (results since the last check are invalid)");
+  if (v & kDevIndex)
+    return set_error(SVK_ERR_INDEX,
+                     "a device index check failed (debug build; check sites 0x%x; the access was skipped, results invalid)",
+                     v >> 8);
+  if (v & kDevTimeout)
+    return set_error(SVK_ERR_TIMEOUT, "a bounded device wait gave up (results since the last check are invalid)");
   return v == 0 ? SVK_OK : set_error(SVK_ERR_CUDA, "device status 0x%x", v);
 }
 

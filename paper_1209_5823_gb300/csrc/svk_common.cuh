@@ -44,8 +44,9 @@ struct ScopedWorkspace {
 
 __host__ __device__ inline int n_terms(int d) { return d < 0 ? 0 : (d + 1) * (d + 2) / 2; }
 
-// Device status word written by kernels with bounded waits (0 = fine).
-enum DeviceStatus : uint32_t { kDevOk = 0, kDevTimeout = 1 };
+// Device status word written by kernels (0 = fine; bits OR-ed in): a bounded wait that
+// gave up, or (debug builds only, SVK_DEBUG) an index check that failed.
+enum DeviceStatus : uint32_t { kDevOk = 0, kDevTimeout = 1, kDevIndex = 2 };
 
 // Address of the library's sticky device status word on the current device (the
 // kernels' status pointer), or NULL if it cannot be resolved.
@@ -133,11 +134,27 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   for (;;) {
     if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
     if (globaltimer_ns() - t0 > limit_ns) {
-      if (status) atomicExch(status, (uint32_t)kDevTimeout);
+      if (status) atomicOr(status, (uint32_t)kDevTimeout);
       return false;
     }
   }
 }
+
+// Index checks of the debug build (compiled with -DSVK_DEBUG, see build.py): SVK_CHECK(c, st, id)
+// is `c`, and when `c` is false it also records kDevIndex in *st, so the caller skips the
+// access it guards and the host learns of it through svk_device_status; a release build
+// compiles it to `true` (no check, no cost).  No check traps.
+// Each check site has a number (1..23) whose bit 8 + id is OR-ed in beside kDevIndex, so
+// the status word names the sites that fired.
+#ifdef SVK_DEBUG
+__device__ __forceinline__ bool svk_check(bool c, uint32_t *status, int id) {
+  if (!c && status) atomicOr(status, (uint32_t)kDevIndex | (1u << (8 + id)));
+  return c;
+}
+#define SVK_CHECK(c, st, id) (::svk::svk_check((c), (st), (id)))
+#else
+#define SVK_CHECK(c, st, id) true
+#endif
 
 // 2-D tiled TMA load of one box into shared memory, completing on `bar`.
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,

@@ -143,7 +143,10 @@ __global__ void __launch_bounds__(kTX * TY, 1)
       for (int ui = 0; ui < L; ++ui) {
         float r[kP];
 #pragma unroll
-        for (int p = 0; p < kP; ++p) r[p] = rrow[32 * p - ui];
+        for (int p = 0; p < kP; ++p) {
+          const long long ri = (rrow - Rs) + 32 * p - ui;  // the staged tile holds BW x BH values
+          r[p] = SVK_CHECK(ri >= 0 && ri < (long long)BW * BH, status, 6) ? rrow[32 * p - ui] : 0.0f;
+        }
         float k0s[kP], k1s[kP];
 #pragma unroll
         for (int p = 0; p < kP; ++p) k0s[p] = k1s[p] = 0.0f;
@@ -327,8 +330,10 @@ __global__ void __launch_bounds__(kTX * kTfTY, 2)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if ((c == 0 && S <= 2) || c == 1 || (c == 2 && S >= 1)) {
-          const float4 q0 = *reinterpret_cast<const float4 *>(row0 - 4 * g + 4 * c);
-          const float4 q1 = *reinterpret_cast<const float4 *>(row1 - 4 * g + 4 * c);
+          const long long i0 = (row0 - Rs) - 4 * g + 4 * c, i1 = i0 + (long long)kTfTY * BW;  // tile: BW x BH
+          const bool in = SVK_CHECK(i0 >= 0 && i1 + 4 <= (long long)BW * BH, status, 7);
+          const float4 q0 = in ? *reinterpret_cast<const float4 *>(row0 - 4 * g + 4 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 q1 = in ? *reinterpret_cast<const float4 *>(row1 - 4 * g + 4 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
           w0[4 * c] = q0.x, w0[4 * c + 1] = q0.y, w0[4 * c + 2] = q0.z, w0[4 * c + 3] = q0.w;
           w1[4 * c] = q1.x, w1[4 * c + 1] = q1.y, w1[4 * c + 2] = q1.z, w1[4 * c + 3] = q1.w;
         }

@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < kSegRegs; ++j) {
           const int e = lane + 32 * j;
-          if (e < pl.seglen) {
+          if (e < pl.seglen && SVK_CHECK(3 * cstride + e < kParts * 2 * cstride + (kParts == 1 ? 2 * cstride : 0), status, 1)) {
             uint16_t hv, lv;
             split16<PREC>(cur[j], hv, lv);
             stg[e] = hv;
@@ -422,7 +422,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int e = lane + 32 * j;
 #pragma unroll
           for (int part = 0; part < kParts; ++part)
-            if (e < 8 * pl.S) *reinterpret_cast<uint4 *>(hk + (size_t)part * pl.S * 128 + (size_t)e * 16) = chunk[j][part];
+            if (e < 8 * pl.S &&
+                SVK_CHECK((size_t)part * pl.S * 128 + (size_t)e * 16 + 16 <= pl.stage_bytes && stage < (uint32_t)NS, status, 2))
+              *reinterpret_cast<uint4 *>(hk + (size_t)part * pl.S * 128 + (size_t)e * 16) = chunk[j][part];
         }
         fence_proxy_async_smem();
       } else if (it.i == it.n && (it.n & 1) && (pl.nG & 1)) {
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // last tap group in the paired K step
         unsigned char *hk = sm + pl.off_stage + (size_t)stage * pl.stage_bytes;
         for (int o = lane * 16; o < (int)pl.stage_bytes; o += 32 * 16)
-          *reinterpret_cast<uint4 *>(hk + o) = make_uint4(0u, 0u, 0u, 0u);
+          if (SVK_CHECK(stage < (uint32_t)NS, status, 3)) *reinterpret_cast<uint4 *>(hk + o) = make_uint4(0u, 0u, 0u, 0u);
         fence_proxy_async_smem();
       }
       __syncwarp();
@@ -535,6 +537,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             if ((sa & rmask) == 0)
               if (!mbar_wait_bounded(&full[sa >> rshift], sph, status)) goto drain;
             // shared-memory operands: ordered by the producers' proxy fence + mbarrier
+            // the pair's two stages inside the ring; the B window of the pair's first row (and
+            // the slice after it, read by the paired last tap groups) inside the table
+            if (!SVK_CHECK(sa + 1 < (uint32_t)NS && (i >= n || (r_lo + i - y0 + h >= 0 &&
+                               (r_lo + i - y0 + h + ((i + 1 < n || (pl.nG & 1)) ? 1 : 0)) * N + pl.nmma <= pl.nrows)),
+                           status, 5))
+              goto drain;
             const uint64_t a = dA + (uint64_t)sa * oStage;
             const uint64_t bw = bw0 + (uint64_t)i * oSlice;  // window of row r_lo + i
             if (i < n) {
@@ -687,7 +695,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int st = 16 * i < N ? min(16 * i, N - 16) : 0;  // unused slots re-read chunk 0
-            tmem_ld16p(c0 + (uint32_t)st, &v[16 * i]);
+            if (SVK_CHECK((G - 1 - g) * N + st + 16 <= kAccStride, status, 4)) tmem_ld16p(c0 + (uint32_t)st, &v[16 * i]);
           }
           tmem_ld_wait();
           // packed pairs of slots: P_i accumulates slots 4q, 4q+2 in its low half and 4q+1,

@@ -104,15 +104,17 @@ __global__ void __launch_bounds__(kTX * TY, 1)
       const int j = i / 10, t = i % 10;
       Cs[i] = (k0 + j < N && t < T) ? coeffs[(size_t)(k0 + j) * T + t] : 0.0f;
     }
-    // the chunk's tables are stored (and, first time, the tile has landed) for the whole
-    // block; if the TMA never landed the whole block gives up together, so no thread is
-    // left at the next chunk's barrier
-    bool ok = true;
+    __syncthreads();
     if (!tile_ready) {
-      ok = mbar_wait_bounded(bar, 0, status);
+      // Every thread waits for the tile with the same limit, started at the same barrier,
+      // so they give up together unless the copy lands within the microseconds between
+      // their deadlines after 2 s; a thread that gives up leaves, and the hardware counts
+      // exited threads as arrived at the block's later barriers.  A block-wide vote here
+      // (or a thread-0 decision broadcast through shared memory) makes the compiler spill
+      // in the main loop at the 168-register budget: measured 6 % slower.
+      if (!mbar_wait_bounded(bar, 0, status)) return;
       tile_ready = true;
     }
-    if (__syncthreads_or(!ok)) return;
     // a_j(x_p, y) = sum_t c[k0+j][t] xt^i yt^j for the chunk (Eq. 3, order <= 3): per stamp
     // alpha_i = sum_jj c[(i, jj)] yt^jj (the same for the thread's pixels, which share a
     // row), then Horner in xt.  Coefficient slots are packed (i outer, jj inner), skipping

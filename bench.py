@@ -303,6 +303,26 @@ def _night_batch(svk, torch, dev, stream, reps=3):
     out["mpixels"] = px / 1e6
     out["tuned_plans"] = {str(L): {"G": v[0], "stages": v[1]} for L, v in tuned.items()}
     out["workload"] = "night_60_frames_2048sq_2048x4096_4096sq_L15-31_d0-3"
+    # roofline of the graph-captured night: the algorithmic FLOP of every frame (basis
+    # contraction, coefficient polynomials, combination, subtraction) over the night's time
+    flop = sum(_algo_flops_per_px(49, it["basis"].shape[1], it["degree"]) * it["R"].numel() for it in items)
+    peak_bf16 = _peaks()[0]
+    ach = flop / (out["graph_batch"]["ms_per_night"] / 1e3) / 1e12
+    out["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak_bf16, "unit": "TFLOP/s",
+                       "frac": ach / peak_bf16, "algorithmic_tflop_per_night": flop / 1e12,
+                       "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}
+    # where the night's time goes: one 2048^2 frame per kernel size with its tuned plan
+    per_L = {}
+    R0 = torch.empty((2048, 2048), device=dev).uniform_(900.0, 1500.0)
+    D0 = torch.empty_like(R0)
+    for L in sorted(bases):
+        c = torch.from_numpy(starfield.planted_coeffs(49, 2, starfield.rng(L)).astype(np.float32)).to(dev)
+        wsl = torch.empty(svk.svk_workspace_size(1, svk.SVK_PREC_BF16X3, 0, 0, 49, L, 2), dtype=torch.uint8, device=dev)
+        ms = _time(torch, lambda: svk.svk_difference(R0, R0, bases[L], c, 2, method=svk.SVK_METHOD_BASIS,
+                                                     precision=svk.SVK_PREC_BF16X3, out=D0, workspace=wsl), reps=10)
+        f = _algo_flops_per_px(49, L, 2) * R0.numel()
+        per_L[str(L)] = {"ms_2048sq": ms, "tflops": f / (ms / 1e3) / 1e12, "frac": f / (ms / 1e3) / 1e12 / peak_bf16}
+    out["per_kernel_size"] = per_L
     return out
 
 

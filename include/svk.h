@@ -207,13 +207,35 @@ SVK_API int svk_difference_batch(const svk_frame *frames, int n_frames, int prec
                                  size_t ws_bytes, void *stream);
 
 /*
- * Time every tensor-core plan (output rows per block G in 1..5, pipeline stages 4 or 8)
- * on a synthetic W x H frame for (N, L, degree, precision), keep the fastest for later
- * calls with that (N, L, precision) in this process, and report it through G_out /
- * stages_out (nullable).  Allocates its test buffers on `stream` and synchronises it.
+ * Time every tensor-core plan that fits shared memory -- output rows per block G (up to
+ * 256 MMA columns, G * N <= 256), pipeline stages 4, 8 or 16, basis tables resident in
+ * shared memory or their slices streamed through a ring beside the stages -- on a
+ * synthetic W x H frame for (N, L, degree, precision), keep the fastest for later calls
+ * with that (N, L, precision) in this process, and report it through G_out / stages_out
+ * (nullable; svk_tc_plan also reports whether the tables are streamed).  Allocates its
+ * test buffers on `stream` and synchronises it.
  */
 SVK_API int svk_autotune(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out,
                          void *stream);
+
+/*
+ * The tensor-core plan later calls with (N, L, precision) use: output rows per block G,
+ * pipeline stages, and streamed = 1 when the basis slices stream through a shared-memory
+ * ring (each reference row's slot carries the slice its window ends with) instead of
+ * resident tables.  Without svk_autotune or svk_set_plan: the most output rows per block
+ * that fit, resident tables preferred.  Outputs nullable.  SVK_ERR_UNSUPPORTED when no plan
+ * fits (N, L).  Host-only: no device work.
+ */
+SVK_API int svk_tc_plan(int N, int L, int precision, int *G, int *stages, int *streamed);
+
+/*
+ * Set the plan for later calls with (N, L, precision) in this process, as svk_autotune
+ * would (e.g. a plan an earlier process tuned); G = 0 restores the default.
+ * SVK_ERR_UNSUPPORTED when the plan does not fit shared memory or breaks the streamed
+ * ring's rules (stages 8 or 16, G - 1 + (ceil(L/8) odd) <= stages / 4).  Workspace sizes
+ * follow the plan: query them after setting it.  Host-only: no device work.
+ */
+SVK_API int svk_set_plan(int N, int L, int precision, int G, int stages, int streamed);
 
 /*
  * Coefficient network.  A small CNN predicts, from a (R, I) star-stamp pair, the local

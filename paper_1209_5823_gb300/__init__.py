@@ -49,7 +49,7 @@ EXPORTS = (
     "svk_device_status", "svk_fit_moments_count", "svk_fit_moments_workspace_size", "svk_fit_moments",
     "svk_fit_solve_workspace_size", "svk_fit_solve", "svk_band_rows", "svk_difference_rows", "svk_cut_stamps",
     "svk_stamp_residual_workspace_size", "svk_stamp_residual", "svk_cnn_standardise", "svk_cnn_draw_batch",
-    "svk_gather_rows", "svk_cnn_step_end",
+    "svk_gather_rows", "svk_cnn_step_end", "svk_tc_plan", "svk_set_plan",
 )
 
 
@@ -95,6 +95,8 @@ def load_library(path: str | None = None):
         "svk_batch_workspace_size": (sz, [vp, i, i]),
         "svk_difference_batch": (i, [vp, i, i, vp, sz, vp]),
         "svk_autotune": (i, [i, i, i, i, i, i, vp, vp, vp]),
+        "svk_tc_plan": (i, [i, i, i, vp, vp, vp]),
+        "svk_set_plan": (i, [i, i, i, i, i, i]),
         "svk_cnn_param_count": (i, [i]),
         "svk_cnn_workspace_size": (sz, [i, i]),
         "svk_cnn_forward": (i, [vp, vp, i, i, vp, vp, sz, vp]),
@@ -295,6 +297,19 @@ def svk_autotune(N: int, L: int, degree: int, precision: int = SVK_PREC_BF16X3, 
     _check(load_library().svk_autotune(int(N), int(L), int(degree), int(precision), int(W), int(H),
                                        ctypes.byref(g), ctypes.byref(st), _stream(stream)))
     return g.value, st.value
+
+
+def svk_tc_plan(N: int, L: int, precision: int = SVK_PREC_BF16X3):
+    """The tensor-core plan calls with (N, L, precision) use: (G, stages, streamed)."""
+    g, st, sm = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load_library().svk_tc_plan(int(N), int(L), int(precision), ctypes.byref(g), ctypes.byref(st),
+                                       ctypes.byref(sm)))
+    return g.value, st.value, sm.value
+
+
+def svk_set_plan(N: int, L: int, precision: int, G: int, stages: int = 16, streamed: int = 0):
+    """Pin the tensor-core plan for (N, L, precision); G = 0 restores the default."""
+    _check(load_library().svk_set_plan(int(N), int(L), int(precision), int(G), int(stages), int(streamed)))
 
 
 def svk_fit_workspace_size(n_stamps: int, stamp_size: int, N: int, L: int, degree: int, bg_degree: int) -> int:

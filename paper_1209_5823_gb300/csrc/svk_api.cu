@@ -343,6 +343,21 @@ int svk_autotune(int N, int L, int degree, int precision, int W, int H, int *G_o
   return autotune_tc(N, L, degree, precision, W, H, G_out, stages_out, static_cast<cudaStream_t>(stream));
 }
 
+static bool tc_plan_args(int N, int L, int precision) {
+  return (precision == SVK_PREC_BF16X3 || precision == SVK_PREC_FP16X3 || precision == SVK_PREC_BF16) && N >= 1 &&
+         N <= 256 && L >= 1 && L <= 31 && (L % 2) == 1;
+}
+
+int svk_tc_plan(int N, int L, int precision, int *G, int *stages, int *streamed) {
+  if (!tc_plan_args(N, L, precision)) return set_error(SVK_ERR_ARG, "bad tensor-core plan query");
+  return get_tc_plan(N, L, precision, G, stages, streamed);
+}
+
+int svk_set_plan(int N, int L, int precision, int G, int stages, int streamed) {
+  if (!tc_plan_args(N, L, precision) || G < 0) return set_error(SVK_ERR_ARG, "bad tensor-core plan");
+  return set_tc_plan(N, L, precision, G, stages, streamed);
+}
+
 int svk_cnn_param_count(int n_out) { return (n_out < 1 || n_out > 256) ? -1 : cnn_param_count(n_out); }
 
 size_t svk_cnn_workspace_size(int batch, int n_out) {

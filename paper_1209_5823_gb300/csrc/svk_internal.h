@@ -53,6 +53,8 @@ int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W
 int launch_batch(const svk_frame *frames, int n, int precision, void *ws, size_t ws_bytes, cudaStream_t s);
 size_t batch_workspace_size(const svk_frame *frames, int n, int precision);
 int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out, cudaStream_t s);
+int set_tc_plan(int N, int L, int precision, int G, int stages, int streamed);
+int get_tc_plan(int N, int L, int precision, int *G, int *stages, int *streamed);
 
 // Least-squares fit (svk_fit.cu).
 size_t fit_workspace_size(int n_stamps, int stamp_size, int N, int L, int degree, int bg_degree);

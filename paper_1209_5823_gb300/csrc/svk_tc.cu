@@ -92,19 +92,24 @@ struct Plan {
   int S;                   // Hankel blocks per reference row (= 16 + nKG - 1)
   size_t stage_bytes;      // one pipeline stage (hi [+ lo] Hankel tiles)
   int seglen;              // staged row length (elements) = 8 S + 8
-  int NP, nrows;           // table slices, table rows per K group
+  int NP, nrows;           // table slices, table rows per K group (global tables)
   int parts;               // 2 for split precision, 1 for plain BF16
   int NS;                  // Hankel pipeline stages
-  int rpg, epg;            // rows per `full` group (NS / 2: two groups in flight) and per
-                           // `empty` group (4, or rpg when smaller)
+  int rpg, epg;            // rows per `full` group (NS / 2: two groups in flight, NS / 4 when
+                           // streamed) and per `empty` group (4, or rpg when smaller)
+  int stream;              // 1: basis slices streamed through a ring (below), 0: tables resident
+  int xr;                  // rows a block's sequence carries beyond its reference rows (G - 1
+                           // when streamed: the owners of its last window's slices)
+  int M, srows;            // ring: mirror slots; shared-memory rows per K group (table or ring)
   int prec;
-  size_t table_bytes;      // one table (hi or lo)
+  size_t table_bytes;      // one global table (hi or lo)
+  size_t smem_tab_bytes;   // its shared-memory copy or ring (hi or lo)
   size_t off_tab_hi, off_tab_lo, off_stage, off_stg, off_coef, off_alpha, off_alphaS, off_bar, smem;
 };
 
 __host__ __device__ inline int rup(int v, int m) { return (v + m - 1) / m * m; }
 
-static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
+static bool make_plan(int N, int L, int prec, int G, int NS, int stream, Plan *p) {
   Plan q{};
   q.N = N;
   q.L = L;
@@ -113,7 +118,8 @@ static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
   q.prec = prec;
   if (NS != 4 && NS != 8 && NS != 16) return false;
   q.NS = NS;
-  q.rpg = NS / 2;
+  q.stream = stream ? 1 : 0;
+  q.rpg = stream ? NS / 4 : NS / 2;
   q.epg = q.rpg < 4 ? q.rpg : 4;
   q.parts = (prec == SVK_PREC_BF16) ? 1 : 2;
   q.nmma = rup(G * N, 16);
@@ -130,11 +136,28 @@ static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
   // (its A tile is zero)
   q.nrows = rup(q.NP * N + 16 + ((q.nG & 1) ? N : 0), 8);
   q.table_bytes = (size_t)q.nKG * q.nrows * 16;
+  if (stream) {
+    // the MMA of a group of rpg rows reads the slices of the next group's first
+    // G - 1 + (nG & 1) rows and no further, so it waits for one group ahead of it; the
+    // producers fill that group while the tensor core runs the one before (NS / rpg = 4)
+    if (NS < 8 || G - 1 + (q.nG & 1) > q.rpg) return false;
+    q.xr = G - 1;
+    // slot k holds the slice of the row in stage k; a window (and the paired window one
+    // slot further) covers ceil(nmma / N) slots from its row's slot on, so the first M
+    // slots are mirrored after the last and every window is contiguous
+    q.M = (q.nmma + N - 1) / N - 1;
+    q.srows = rup((NS + q.M) * N, 8);
+  } else {
+    q.xr = 0;
+    q.M = 0;
+    q.srows = q.nrows;
+  }
+  q.smem_tab_bytes = (size_t)q.nKG * q.srows * 16;
   size_t o = 0;
   q.off_tab_hi = o;
-  o += q.table_bytes;
+  o += q.smem_tab_bytes;
   q.off_tab_lo = o;
-  if (q.parts == 2) o += q.table_bytes;
+  if (q.parts == 2) o += q.smem_tab_bytes;
   o = rup((int)o, 128);
   q.off_stage = o;
   o += (size_t)NS * q.stage_bytes;
@@ -157,12 +180,15 @@ static bool make_plan(int N, int L, int prec, int G, int NS, Plan *p) {
 }
 
 static bool choose_plan(int N, int L, int prec, Plan *p) {
-  // the widest MMA (most output rows per block) that fits, with two handshake groups in
-  // flight when they fit (producers fill one while the MMAs drain the other); the
-  // autotuner replaces this default by measurement
-  for (int G = kMaxG; G >= 1; --G)
+  // the widest MMA (most output rows per block) that fits, with resident tables and the
+  // most stages when they fit, else with the slices streamed (large L, whose tables
+  // leave no room for wide blocks); the autotuner replaces this default by measurement
+  for (int G = kMaxG; G >= 1; --G) {
     for (int NS = kMaxStages; NS >= 4; NS /= 2)
-      if (make_plan(N, L, prec, G, NS, p)) return true;
+      if (make_plan(N, L, prec, G, NS, 0, p)) return true;
+    for (int NS = kMaxStages; NS >= 8; NS /= 2)
+      if (make_plan(N, L, prec, G, NS, 1, p)) return true;
+  }
   return false;
 }
 
@@ -242,10 +268,10 @@ __device__ __forceinline__ void cta_block_range(const FrameSet &fs, int &b0, int
 }
 
 // The CTA's sequence of reference rows: for each of its blocks the rows
-// max(0, y0-h) .. min(H-1, y0+G-1+h), padded with empty slots to a multiple of the rows
-// per handshake group.
+// max(0, y0-h) .. min(H-1, y0+G-1+h), then xr slots that only carry basis slices (streamed
+// plans), padded with empty slots to a multiple of the rows per handshake group.
 struct RowIt {
-  int b, b_end, f, i, n, nseq, r_lo, x0, y0, rpg;
+  int b, b_end, f, i, n, nseq, r_lo, x0, y0, rpg, xr;
   __device__ void set_block(const FrameSet &fs, int bb, int G, int h) {
     b = bb;
     i = 0;
@@ -254,7 +280,7 @@ struct RowIt {
       block_origin(fs.fr[f], b, G, x0, y0);
       r_lo = max(0, y0 - h);
       n = min(fs.fr[f].H - 1, y0 + G - 1 + h) - r_lo + 1;
-      nseq = (n + rpg - 1) & ~(rpg - 1);  // rpg is a power of two
+      nseq = (n + xr + rpg - 1) & ~(rpg - 1);  // rpg is a power of two
     }
   }
   __device__ void next(const FrameSet &fs, int G, int h) {
@@ -333,6 +359,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_mbar_init();
     }
   }
+  if (pl.stream) {
+    // the ring starts as zeros: slots a window reads beyond its slices (the MMA columns
+    // past G*N, the partner window of an odd last row, whose A tile is zero) always hold
+    // finite values
+    for (size_t o = (size_t)threadIdx.x * 16; o < pl.smem_tab_bytes * kParts; o += (size_t)kThreads * 16)
+      *reinterpret_cast<uint4 *>(sm + pl.off_tab_hi + o) = make_uint4(0u, 0u, 0u, 0u);
+    fence_proxy_async_smem();
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -357,6 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t stage = (uint32_t)pw, sph = 0;
     RowIt it;
     it.rpg = pl.rpg;
+    it.xr = pl.xr;
     it.b_end = b_end;
     it.f = 0;
     it.set_block(fs, b_begin, G, h);
@@ -436,7 +471,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_proxy_async_smem();
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&full[grp]);
+      // streamed plans: the slice this row's slot holds (slice P0 + i of the block's table,
+      // the last of the window of row i - G + 1) copied by the bulk-copy engine, in every K
+      // group and part, and again into the mirror slot; the row's arrival then also waits
+      // for those bytes
+      const int t = pl.stream && it.valid() ? it.r_lo - it.y0 + h + it.i : pl.NP;
+      const int ncopy = t < pl.NP ? kParts * pl.nKG * ((int)stage < pl.M ? 2 : 1) : 0;
+      if (lane == 0) {
+        if (ncopy) mbar_arrive_expect_tx(&full[grp], (uint32_t)(ncopy * N * 16));
+        else mbar_arrive(&full[grp]);
+      }
+      __syncwarp();
+      if (lane < ncopy) {
+        const int c = lane % (kParts * pl.nKG), part = c / pl.nKG, kg = c % pl.nKG;
+        const uint4 *src = (part ? fs.fr[it.f].tab_lo : fs.fr[it.f].tab_hi) + (size_t)kg * pl.nrows + (size_t)t * N;
+        const size_t slot = lane < kParts * pl.nKG ? stage : stage + NS;  // copy 2: the mirror
+        const size_t dst = (part ? pl.off_tab_lo : pl.off_tab_hi) + ((size_t)kg * pl.srows + slot * N) * 16;
+        if (SVK_CHECK(dst + (size_t)N * 16 <= (part ? pl.off_tab_lo : pl.off_tab_hi) + pl.smem_tab_bytes &&
+                          (slot + 1) * N <= (size_t)pl.srows && ((size_t)t + 1) * N <= (size_t)pl.nrows,
+                      status, 8))
+          bulk_load(sm + dst, src, (uint32_t)(N * 16), &full[grp]);
+      }
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < kSegRegs; ++j) cur[j] = nxt[j];
@@ -456,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       {
         const uint32_t idesc = idesc_f16(kFmt, kTileM, pl.nmma);
-        const uint32_t lbo_b = (uint32_t)pl.nrows * 16u, sbytes = (uint32_t)pl.stage_bytes;
+        const uint32_t lbo_b = (uint32_t)pl.srows * 16u, sbytes = (uint32_t)pl.stage_bytes;
         const uint64_t dA = sdesc(smem_u32(sm + pl.off_stage), 128u, 128u);
         const uint64_t dB = sdesc(smem_u32(sm + pl.off_tab_hi), lbo_b, 128u);
         const uint64_t dAx = sdesc(smem_u32(sm + pl.off_stage) + (uint32_t)(pl.nG - 1) * 128u, sbytes, 128u);
@@ -511,6 +566,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         };
         int f = 0, x0 = 0, y0 = 0;
+        // streamed plans wait one group ahead (its first rows hold the slices this group's
+        // windows end with): the CTA's first group before its first block
+        if (pl.stream && b_begin < b_end)
+          if (!mbar_wait_bounded(&full[0], 0, status)) goto drain;
         for (int b = b_begin; b < b_end; ++b, ++blk_seq) {
           if (b == b_begin || (f + 1 < fs.n && b >= fs.fr[f + 1].block0)) {
             f = advance_frame(fs, f, b);
@@ -523,28 +582,41 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           const FrameDesc &fd = fs.fr[f];
-          if (!load_tables(fd)) goto drain;
+          if (!pl.stream && !load_tables(fd)) goto drain;
           const int buf = blk_seq & 1;
           if (!mbar_wait_bounded(&acc_empty[buf], ((blk_seq >> 1) & 1) ^ 1, status)) goto drain;
           tc_fence_after();
           d_tmem = tmem_base + (uint32_t)(buf * kAccStride);
           acc = 0;
           const int r_lo = max(0, y0 - h), n = min(fd.H - 1, y0 + G - 1 + h) - r_lo + 1;
-          const int nseq = (n + pl.rpg - 1) & ~(pl.rpg - 1);
-          const uint64_t bw0 = dB + (uint64_t)(r_lo - y0 + h) * oSlice;   // window of row r_lo
-          const uint64_t bx0 = dBx + (uint64_t)(r_lo - y0 + h) * oSlice;
+          const int nseq = (n + pl.xr + pl.rpg - 1) & ~(pl.rpg - 1);
+          // resident tables: the window of row r_lo + i starts at slice r_lo + i - y0 + h of
+          // the table; streamed: at the slot of the row's own stage
+          const uint64_t bw0 = pl.stream ? dB : dB + (uint64_t)(r_lo - y0 + h) * oSlice;
+          const uint64_t bx0 = pl.stream ? dBx : dBx + (uint64_t)(r_lo - y0 + h) * oSlice;
           for (int i = 0; i < nseq; i += 2) {  // stages sa, sa + 1
-            if ((sa & rmask) == 0)
-              if (!mbar_wait_bounded(&full[sa >> rshift], sph, status)) goto drain;
+            if ((sa & rmask) == 0) {
+              if (!pl.stream) {
+                if (!mbar_wait_bounded(&full[sa >> rshift], sph, status)) goto drain;
+              } else if (b + 1 < b_end || i + pl.rpg < nseq) {  // the next group, if any
+                uint32_t na = sa + (uint32_t)pl.rpg, nph = sph;
+                if (na >= (uint32_t)NS) {
+                  na -= (uint32_t)NS;
+                  nph ^= 1;
+                }
+                if (!mbar_wait_bounded(&full[na >> rshift], nph, status)) goto drain;
+              }
+            }
             // shared-memory operands: ordered by the producers' proxy fence + mbarrier
             // the pair's two stages inside the ring; the B window of the pair's first row (and
-            // the slice after it, read by the paired last tap groups) inside the table
+            // the slice after it, read by the paired last tap groups) inside the table or ring
+            const uint32_t wrow = pl.stream ? sa : (uint32_t)(r_lo + i - y0 + h);
             if (!SVK_CHECK(sa + 1 < (uint32_t)NS && (i >= n || (r_lo + i - y0 + h >= 0 &&
-                               (r_lo + i - y0 + h + ((i + 1 < n || (pl.nG & 1)) ? 1 : 0)) * N + pl.nmma <= pl.nrows)),
+                               (wrow + ((i + 1 < n || (pl.nG & 1)) ? 1 : 0)) * N + pl.nmma <= (uint32_t)pl.srows)),
                            status, 5))
               goto drain;
             const uint64_t a = dA + (uint64_t)sa * oStage;
-            const uint64_t bw = bw0 + (uint64_t)i * oSlice;  // window of row r_lo + i
+            const uint64_t bw = bw0 + (uint64_t)(pl.stream ? sa : (uint32_t)i) * oSlice;  // window of row r_lo + i
             if (i < n) {
               // rows r_lo + i and r_lo + i + 1 (for an odd last row the second is the
               // producers' all-zero tile): each row's full K steps, then their last tap
@@ -553,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (i + 1 < n) row_mmas(a + oStage, bw + oSlice, inrow);
               if (pl.nG & 1) {
                 const uint64_t ax = dAx + (uint64_t)sa * oStage;
-                const uint64_t bx = bx0 + (uint64_t)i * oSlice;
+                const uint64_t bx = bx0 + (uint64_t)(pl.stream ? sa : (uint32_t)i) * oSlice;
                 if (kParts == 2) {
                   umma_f16_fill(d_tmem, ax, bx, idesc, acc);
                   umma_f16_lastuse(d_tmem, ax, bx + oBl, idesc, 1);
@@ -777,13 +849,16 @@ done:
 namespace {
 
 std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;  // (N, L, prec) -> (G, stages)
+// (N, L, prec) -> (G, stages, streamed): plans set by the autotuner or svk_set_plan
+std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> g_tuned;
 
 bool plan_for(int N, int L, int prec, Plan *pl) {
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find(std::make_tuple(N, L, prec));
-    if (it != g_tuned.end() && make_plan(N, L, prec, it->second.first, it->second.second, pl)) return true;
+    if (it != g_tuned.end() &&
+        make_plan(N, L, prec, std::get<0>(it->second), std::get<1>(it->second), std::get<2>(it->second), pl))
+      return true;
   }
   return choose_plan(N, L, prec, pl);
 }
@@ -1068,10 +1143,12 @@ int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_ou
   void *ws = nullptr;
   size_t ws_bytes = 0;
   for (int G = 1; G <= kMaxG; ++G)
-    for (int NS = 4; NS <= kMaxStages; NS *= 2) {
-      Plan pl;
-      if (make_plan(N, L, precision, G, NS, &pl) && pl.table_bytes * 2 + 256 > ws_bytes) ws_bytes = pl.table_bytes * 2 + 256;
-    }
+    for (int NS = 4; NS <= kMaxStages; NS *= 2)
+      for (int sm = 0; sm < 2; ++sm) {
+        Plan pl;
+        if (make_plan(N, L, precision, G, NS, sm, &pl) && pl.table_bytes * 2 + 256 > ws_bytes)
+          ws_bytes = pl.table_bytes * 2 + 256;
+      }
   if (ws_bytes == 0) return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan for N=%d L=%d", N, L);
   cudaError_t e = cudaMallocAsync(&R, px * 4, s);
   if (e == cudaSuccess) e = cudaMallocAsync(&I, px * 4, s);
@@ -1081,7 +1158,7 @@ int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_ou
   if (e == cudaSuccess) e = cudaMallocAsync(&ws, ws_bytes, s);
   int st = cuda_status(e, "autotune buffers");
   float best = 1e30f;
-  int bestG = 0, bestNS = 0;
+  int bestG = 0, bestNS = 0, bestSM = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (st == SVK_OK) {
     tune_fill_kernel<<<256, 256, 0, s>>>(R, px, 1500.0f, 1000.0f, 1u);
@@ -1105,9 +1182,10 @@ int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_ou
     f.coeffs = C;
     f.degree = degree;
     for (int G = kMaxG; G >= 1 && st == SVK_OK; --G)
-      for (int NS = kMaxStages; NS >= 4 && st == SVK_OK; NS /= 2) {
+      for (int v = 0; v < 6 && st == SVK_OK; ++v) {  // resident 16, 8, 4 stages; streamed 16, 8
+        const int sm = v >= 3, NS = sm ? kMaxStages >> (v - 3) : kMaxStages >> v;
         Plan pl;
-        if (!make_plan(N, L, precision, G, NS, &pl)) continue;
+        if (!make_plan(N, L, precision, G, NS, sm, &pl)) continue;
         st = launch_set(&f, 1, precision, pl, ws, ws_bytes, s);  // warm-up
         cudaEventRecord(e0, s);
         for (int r = 0; r < 3 && st == SVK_OK; ++r) st = launch_set(&f, 1, precision, pl, ws, ws_bytes, s);
@@ -1119,6 +1197,7 @@ int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_ou
           best = ms;
           bestG = G;
           bestNS = NS;
+          bestSM = sm;
         }
       }
     cudaEventDestroy(e0);
@@ -1134,10 +1213,34 @@ int autotune_tc(int N, int L, int degree, int precision, int W, int H, int *G_ou
   if (bestG == 0) return set_error(SVK_ERR_UNSUPPORTED, "autotune found no plan");
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[std::make_tuple(N, L, precision)] = std::make_pair(bestG, bestNS);
+    g_tuned[std::make_tuple(N, L, precision)] = std::make_tuple(bestG, bestNS, bestSM);
   }
   if (G_out) *G_out = bestG;
   if (stages_out) *stages_out = bestNS;
+  return SVK_OK;
+}
+
+int set_tc_plan(int N, int L, int precision, int G, int stages, int streamed) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  const auto key = std::make_tuple(N, L, precision);
+  if (G == 0) {  // back to the default plan
+    g_tuned.erase(key);
+    return SVK_OK;
+  }
+  Plan pl;
+  if (!make_plan(N, L, precision, G, stages, streamed, &pl))
+    return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan G=%d stages=%d streamed=%d for N=%d L=%d", G, stages,
+                     streamed, N, L);
+  g_tuned[key] = std::make_tuple(G, stages, streamed ? 1 : 0);
+  return SVK_OK;
+}
+
+int get_tc_plan(int N, int L, int precision, int *G, int *stages, int *streamed) {
+  Plan pl;
+  if (!plan_for(N, L, precision, &pl)) return set_error(SVK_ERR_UNSUPPORTED, "no tensor-core plan for N=%d L=%d", N, L);
+  if (G) *G = pl.G;
+  if (stages) *stages = pl.NS;
+  if (streamed) *streamed = pl.stream;
   return SVK_OK;
 }
 

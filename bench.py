@@ -48,6 +48,13 @@ def _peaks():
     return 1900.0, 6800.0, "fallback"
 
 
+def _plan_str(svk, N, L, prec=None):
+    G, st, sm = svk.svk_tc_plan(N, L, svk.SVK_PREC_BF16X3 if prec is None else prec)
+    rpg = st // 4 if sm else st // 2
+    return (f"G={G} output rows per block, {st} stages ({rpg}-row handshakes), "
+            + ("basis slices streamed through a ring" if sm else "basis tables resident"))
+
+
 def _algo_flops_per_px(N, L, degree):
     T = (degree + 1) * (degree + 2) // 2
     # basis contraction 2 N L^2, coefficient polynomials 2 N T, combination 2 N, subtraction 1
@@ -181,7 +188,7 @@ def _frame_spec(rank=0):
     """Rank r of a multi-GPU run times its own frame: same shape, seed offset by r."""
     import dataclasses
     import starfield
-    spec = starfield.WORKLOADS["ccd_2048x4096_L19_d2"]
+    spec = starfield.WORKLOADS[WORKLOAD]
     return spec if rank == 0 else dataclasses.replace(spec, seed=spec.seed + 1000 * rank)
 
 
@@ -301,7 +308,8 @@ def _night_batch(svk, torch, dev, stream, reps=3):
                                   f"({3 * px * 4 / 2**30:.1f} GiB copied per night)")
     out["frames"] = len(items)
     out["mpixels"] = px / 1e6
-    out["tuned_plans"] = {str(L): {"G": v[0], "stages": v[1]} for L, v in tuned.items()}
+    out["tuned_plans"] = {str(L): {"G": v[0], "stages": v[1], "streamed": svk.svk_tc_plan(49, L)[2]}
+                          for L, v in tuned.items()}
     out["workload"] = "night_60_frames_2048sq_2048x4096_4096sq_L15-31_d0-3"
     # roofline of the graph-captured night: the algorithmic FLOP of every frame (basis
     # contraction, coefficient polynomials, combination, subtraction) over the night's time
@@ -654,6 +662,7 @@ def run_reference(args, rank):
 
 
 def main():
+    global WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
@@ -662,11 +671,15 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the night-batch and fit measurements")
+    ap.add_argument("--workload", default="ccd_2048x4096_L19_d2", choices=["ccd_2048x4096_L19_d2", "ccd_4096x4096_L25_d3"],
+                    help="the frame the step times (the default is the metric's; the other one profiles a "
+                         "25-tap kernel)")
     ap.add_argument("--learned-only", action="store_true",
                     help="only the coefficient-network measurement (its own JSON line; for profiling)")
     ap.add_argument("--learned-steps", type=int, default=10000, help="training steps of that measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    WORKLOAD = args.workload
 
     if args.impl == "reference":
         # rank 0 alone runs the oracle; the other ranks of a torchrun launch exit at once
@@ -838,7 +851,9 @@ def main():
     achieved = algo / (kern_ms / 1e3) / 1e12
     # raw MMA work of the launch (split products, padded taps, window rows), for context:
     # the default plan for N = 49, L = 19 stacks G = 5 output rows per block (MMA N = 256)
-    raw_flops = _raw_mma_flops(W, H, L, G=5, nmma=256, n_prod={"bf16x3": 3, "fp16x3": 3, "bf16": 1}[args.precision])
+    Gp = svk.svk_tc_plan(N, L, prec)[0]
+    raw_flops = _raw_mma_flops(W, H, L, G=Gp, nmma=(Gp * N + 15) // 16 * 16,
+                               n_prod={"bf16x3": 3, "fp16x3": 3, "bf16": 1}[args.precision])
     traffic = _traffic(args.precision)
 
     out = {
@@ -858,7 +873,7 @@ def main():
                      "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)",
                      "kernel": "tc_basis_kernel (+ table prep) per CUDA-event bracket",
                      "algorithmic_flop_per_px": _algo_flops_per_px(N, L, d),
-                     "plan": "G=5 output rows per block, 16 stages (8-row handshakes)",
+                     "plan": _plan_str(svk, N, L, prec),
                      "raw_mma_tflops": raw_flops / (kern_ms / 1e3) / 1e12,
                      "raw_mma_frac": raw_flops / (kern_ms / 1e3) / 1e12 / peak_bf16},
         "direct": {"value": world * px / (dir_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_frame": dir_ms,

@@ -323,7 +323,9 @@ __global__ void tc_prep_table(const float *__restrict__ basis, Plan pl, float bs
 }
 
 // ----------------------------------------------------------------- main kernel
-template <int PREC>
+// STREAM: the plan streams its basis slices (pl.stream); a template parameter, so the
+// resident-table kernel carries none of the streamed bookkeeping in its issuing loop
+template <int PREC, bool STREAM>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_basis_kernel(const __grid_constant__ FrameSet fs, const Plan pl, uint32_t *status) {
   extern __shared__ unsigned char smem_raw[];
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_mbar_init();
     }
   }
-  if (pl.stream) {
+  if (STREAM) {
     // the ring starts as zeros: slots a window reads beyond its slices (the MMA columns
     // past G*N, the partner window of an odd last row, whose A tile is zero) always hold
     // finite values
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t stage = (uint32_t)pw, sph = 0;
     RowIt it;
     it.rpg = pl.rpg;
-    it.xr = pl.xr;
+    it.xr = STREAM ? pl.xr : 0;
     it.b_end = b_end;
     it.f = 0;
     it.set_block(fs, b_begin, G, h);
@@ -471,26 +473,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_proxy_async_smem();
       }
       __syncwarp();
-      // streamed plans: the slice this row's slot holds (slice P0 + i of the block's table,
-      // the last of the window of row i - G + 1) copied by the bulk-copy engine, in every K
-      // group and part, and again into the mirror slot; the row's arrival then also waits
-      // for those bytes
-      const int t = pl.stream && it.valid() ? it.r_lo - it.y0 + h + it.i : pl.NP;
-      const int ncopy = t < pl.NP ? kParts * pl.nKG * ((int)stage < pl.M ? 2 : 1) : 0;
-      if (lane == 0) {
-        if (ncopy) mbar_arrive_expect_tx(&full[grp], (uint32_t)(ncopy * N * 16));
-        else mbar_arrive(&full[grp]);
-      }
-      __syncwarp();
-      if (lane < ncopy) {
-        const int c = lane % (kParts * pl.nKG), part = c / pl.nKG, kg = c % pl.nKG;
-        const uint4 *src = (part ? fs.fr[it.f].tab_lo : fs.fr[it.f].tab_hi) + (size_t)kg * pl.nrows + (size_t)t * N;
-        const size_t slot = lane < kParts * pl.nKG ? stage : stage + NS;  // copy 2: the mirror
-        const size_t dst = (part ? pl.off_tab_lo : pl.off_tab_hi) + ((size_t)kg * pl.srows + slot * N) * 16;
-        if (SVK_CHECK(dst + (size_t)N * 16 <= (part ? pl.off_tab_lo : pl.off_tab_hi) + pl.smem_tab_bytes &&
-                          (slot + 1) * N <= (size_t)pl.srows && ((size_t)t + 1) * N <= (size_t)pl.nrows,
-                      status, 8))
-          bulk_load(sm + dst, src, (uint32_t)(N * 16), &full[grp]);
+      if (!STREAM) {
+        if (lane == 0) mbar_arrive(&full[grp]);
+      } else {
+        // the slice this row's slot holds (slice P0 + i of the block's table, the last of
+        // the window of row i - G + 1) copied by the bulk-copy engine, in every K group and
+        // part, and again into the mirror slot; the row's arrival then also waits for those
+        // bytes
+        const int t = it.r_lo - it.y0 + h + it.i;
+        const int ncopy = t < pl.NP ? kParts * pl.nKG * ((int)stage < pl.M ? 2 : 1) : 0;
+        if (lane == 0) {
+          if (ncopy) mbar_arrive_expect_tx(&full[grp], (uint32_t)(ncopy * N * 16));
+          else mbar_arrive(&full[grp]);
+        }
+        __syncwarp();
+        if (lane < ncopy) {
+          const int c = lane % (kParts * pl.nKG), part = c / pl.nKG, kg = c % pl.nKG;
+          const uint4 *src = (part ? fs.fr[it.f].tab_lo : fs.fr[it.f].tab_hi) + (size_t)kg * pl.nrows + (size_t)t * N;
+          const size_t slot = lane < kParts * pl.nKG ? stage : stage + NS;  // copy 2: the mirror
+          const size_t dst = (part ? pl.off_tab_lo : pl.off_tab_hi) + ((size_t)kg * pl.srows + slot * N) * 16;
+          if (SVK_CHECK(dst + (size_t)N * 16 <= (part ? pl.off_tab_lo : pl.off_tab_hi) + pl.smem_tab_bytes &&
+                            (slot + 1) * N <= (size_t)pl.srows && ((size_t)t + 1) * N <= (size_t)pl.nrows,
+                        status, 8))
+            bulk_load(sm + dst, src, (uint32_t)(N * 16), &full[grp]);
+        }
       }
       __syncwarp();
 #pragma unroll
@@ -568,7 +574,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int f = 0, x0 = 0, y0 = 0;
         // streamed plans wait one group ahead (its first rows hold the slices this group's
         // windows end with): the CTA's first group before its first block
-        if (pl.stream && b_begin < b_end)
+        if (STREAM && b_begin < b_end)
           if (!mbar_wait_bounded(&full[0], 0, status)) goto drain;
         for (int b = b_begin; b < b_end; ++b, ++blk_seq) {
           if (b == b_begin || (f + 1 < fs.n && b >= fs.fr[f + 1].block0)) {
@@ -582,21 +588,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           const FrameDesc &fd = fs.fr[f];
-          if (!pl.stream && !load_tables(fd)) goto drain;
+          if (!STREAM && !load_tables(fd)) goto drain;
           const int buf = blk_seq & 1;
           if (!mbar_wait_bounded(&acc_empty[buf], ((blk_seq >> 1) & 1) ^ 1, status)) goto drain;
           tc_fence_after();
           d_tmem = tmem_base + (uint32_t)(buf * kAccStride);
           acc = 0;
           const int r_lo = max(0, y0 - h), n = min(fd.H - 1, y0 + G - 1 + h) - r_lo + 1;
-          const int nseq = (n + pl.xr + pl.rpg - 1) & ~(pl.rpg - 1);
+          const int nseq = (n + (STREAM ? pl.xr : 0) + pl.rpg - 1) & ~(pl.rpg - 1);
           // resident tables: the window of row r_lo + i starts at slice r_lo + i - y0 + h of
           // the table; streamed: at the slot of the row's own stage
-          const uint64_t bw0 = pl.stream ? dB : dB + (uint64_t)(r_lo - y0 + h) * oSlice;
-          const uint64_t bx0 = pl.stream ? dBx : dBx + (uint64_t)(r_lo - y0 + h) * oSlice;
+          const uint64_t bw0 = STREAM ? dB : dB + (uint64_t)(r_lo - y0 + h) * oSlice;
+          const uint64_t bx0 = STREAM ? dBx : dBx + (uint64_t)(r_lo - y0 + h) * oSlice;
           for (int i = 0; i < nseq; i += 2) {  // stages sa, sa + 1
             if ((sa & rmask) == 0) {
-              if (!pl.stream) {
+              if (!STREAM) {
                 if (!mbar_wait_bounded(&full[sa >> rshift], sph, status)) goto drain;
               } else if (b + 1 < b_end || i + pl.rpg < nseq) {  // the next group, if any
                 uint32_t na = sa + (uint32_t)pl.rpg, nph = sph;
@@ -610,13 +616,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             // shared-memory operands: ordered by the producers' proxy fence + mbarrier
             // the pair's two stages inside the ring; the B window of the pair's first row (and
             // the slice after it, read by the paired last tap groups) inside the table or ring
-            const uint32_t wrow = pl.stream ? sa : (uint32_t)(r_lo + i - y0 + h);
+            const uint32_t wrow = STREAM ? sa : (uint32_t)(r_lo + i - y0 + h);
             if (!SVK_CHECK(sa + 1 < (uint32_t)NS && (i >= n || (r_lo + i - y0 + h >= 0 &&
                                (wrow + ((i + 1 < n || (pl.nG & 1)) ? 1 : 0)) * N + pl.nmma <= (uint32_t)pl.srows)),
                            status, 5))
               goto drain;
             const uint64_t a = dA + (uint64_t)sa * oStage;
-            const uint64_t bw = bw0 + (uint64_t)(pl.stream ? sa : (uint32_t)i) * oSlice;  // window of row r_lo + i
+            const uint64_t bw = bw0 + (uint64_t)(STREAM ? sa : (uint32_t)i) * oSlice;  // window of row r_lo + i
             if (i < n) {
               // rows r_lo + i and r_lo + i + 1 (for an odd last row the second is the
               // producers' all-zero tile): each row's full K steps, then their last tap
@@ -625,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (i + 1 < n) row_mmas(a + oStage, bw + oSlice, inrow);
               if (pl.nG & 1) {
                 const uint64_t ax = dAx + (uint64_t)sa * oStage;
-                const uint64_t bx = bx0 + (uint64_t)(pl.stream ? sa : (uint32_t)i) * oSlice;
+                const uint64_t bx = bx0 + (uint64_t)(STREAM ? sa : (uint32_t)i) * oSlice;
                 if (kParts == 2) {
                   umma_f16_fill(d_tmem, ax, bx, idesc, acc);
                   umma_f16_lastuse(d_tmem, ax, bx + oBl, idesc, 1);
@@ -937,13 +943,14 @@ int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *w
   // cannot be resolved
   uint32_t *status = device_status_word();
   if (!status) status = reinterpret_cast<uint32_t *>(ws + (size_t)ntab * pl.table_bytes * 2);
-  cudaError_t e = cudaFuncSetAttribute(tc_basis_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  auto kern = pl.stream ? tc_basis_kernel<P, true> : tc_basis_kernel<P, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) return cuda_status(e, "tc_basis_kernel smem attribute");
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int grid = blocks < nsm ? blocks : nsm;
-  if (grid > 0) tc_basis_kernel<P><<<grid, kThreads, pl.smem, s>>>(fs, pl, status);
+  if (grid > 0) kern<<<grid, kThreads, pl.smem, s>>>(fs, pl, status);
   return cuda_status(cudaGetLastError(), "tc_basis_kernel launch");
 }
 

@@ -64,7 +64,7 @@ def test_batch_matches_oracle_and_graph_replay():
 
 def test_autotune_keeps_parity():
     G, stages = svk.svk_autotune(49, 19, 2, svk.SVK_PREC_BF16X3, W=1024, H=256)
-    assert 1 <= G <= 5 and stages in (4, 8)
+    assert 1 <= G <= 5 and stages in (4, 8, 16)
     R, I = star_pair(300, 77, 70, 7)
     B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, 19)
     c = coeffs(49, 2, 7)

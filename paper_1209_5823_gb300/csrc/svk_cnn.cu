@@ -150,7 +150,10 @@ __device__ __forceinline__ float hi_f(uint32_t w) { return __uint_as_float(w & 0
 // (K = 2 tap + c < 18, zero above): wf0[j][o][t] = W0[o][c][tap].
 __global__ void pack_kernel(const float *__restrict__ p, float *__restrict__ wq, int n_params, bf16 *wf0, bf16 *wf1,
                             bf16 *wd1, bf16 *wf2, bf16 *wd2, bf16 *wf3, bf16 *wd3, size_t w0, size_t w1, size_t w2,
-                            size_t w3) {
+                            size_t w3, float *loss) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
+  if (loss && blockIdx.x == 0 && threadIdx.x == 0) *loss = 0.0f;  // the gradient call's loss sum starts here
   const int n = n_params + kPack0 + 3 * kPack;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (i < n_params) {
@@ -192,6 +195,8 @@ constexpr uint32_t kC1Smem = 2 * kC1XStage + kC1ABytes + kC1BBytes + 64 + 1024;
 __global__ void __launch_bounds__(kC1Threads, 6)
     conv1_mma_kernel(const __grid_constant__ CUtensorMap xm, const bf16 *__restrict__ wpack,
                      const float *__restrict__ bias, bf16 *__restrict__ out, int B, uint32_t *status) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *sx = sm;                          // two staged input blocks
@@ -367,6 +372,8 @@ __global__ void __launch_bounds__(kTfThreads, 2)
     conv_tma_kernel(const __grid_constant__ CUtensorMap src, const bf16 *__restrict__ wpack,
                     const float *__restrict__ bias, const bf16 *__restrict__ mask, bf16 *__restrict__ out, int B,
                     const TfGeom geo, uint32_t *status) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *sA = sm;                                  // kTfStages x 8 KB, 1024-byte aligned
@@ -560,6 +567,8 @@ struct WtGeom {
 __global__ void __launch_bounds__(kWtThreads, 1)
     wgrad_tma_kernel(const __grid_constant__ CUtensorMap act, const __grid_constant__ CUtensorMap dzm,
                      float *__restrict__ part, int B, const WtGeom geo, uint32_t *status) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(sm + kWtStages * kWtStage);
@@ -710,6 +719,8 @@ struct Wg1 {
 __global__ void __launch_bounds__(Wg1::THREADS, 2)
     wgrad1_kernel(const __grid_constant__ CUtensorMap xm, const __grid_constant__ CUtensorMap dzm,
                   float *__restrict__ part, int B, int lg_s, int lg_g, int stride, int per_chunk, uint32_t *status) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   using Sh = Wg1;
   constexpr int CIN = Sh::CIN;
   extern __shared__ uint8_t smem_raw[];
@@ -855,6 +866,8 @@ struct WgradSet {
 };
 
 __global__ void __launch_bounds__(kRedSlices * kCh) wgrad_reduce_kernel(const __grid_constant__ WgradSet ws) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   __shared__ float red[kRedSlices][kCh];
   int l = 0;
   while (l + 1 < kLayers && (int)blockIdx.x >= ws.row0[l + 1]) ++l;
@@ -881,6 +894,8 @@ __global__ void pool_fc_kernel(const bf16 *__restrict__ act, const float *__rest
                                const float *__restrict__ fcb, float *__restrict__ pooled, float *__restrict__ out,
                                int n_out, const float *__restrict__ target, float *__restrict__ dout, float *loss,
                                int B) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   __shared__ float pl[kCh];
   __shared__ float red[2];
   const int b = blockIdx.x;
@@ -920,6 +935,8 @@ __global__ void __launch_bounds__(256) fc_grad_kernel(const float *__restrict__ 
                                                       const float *__restrict__ fcw, const bf16 *__restrict__ act,
                                                       float *__restrict__ dfcw, float *__restrict__ dfcb,
                                                       bf16 *__restrict__ dz, int B, int n_out) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   if ((int)blockIdx.x < n_out) {
     __shared__ float red[8][kCh + 1];
     const int j = blockIdx.x, c = threadIdx.x & 31, part = threadIdx.x >> 5;
@@ -958,6 +975,8 @@ __global__ void __launch_bounds__(256) fc_grad_kernel(const float *__restrict__ 
 __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
                             const float *__restrict__ g, int n, float lr, float b1, float b2, float eps, float c1,
                             float c2) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
@@ -972,6 +991,8 @@ __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float 
 __global__ void adam_dstep_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
                                   const float *__restrict__ g, int n, const int *__restrict__ step, float lr, float b1,
                                   float b2, float eps) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const float t = (float)*step;
   const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1003,8 +1024,9 @@ int conv1(const float *x, const bf16 *wpack, const float *bias, bf16 *out, int B
   if (e != cudaSuccess) return cuda_status(e, "network first-layer attributes");
   const int ntiles = ((B << 10) + 127) >> 7;
   const int grid = ntiles < 6 * nsm ? ntiles : 6 * nsm;
-  conv1_mma_kernel<<<grid, kC1Threads, kC1Smem, s>>>(tx, wpack, bias, out, B, device_status_word());
-  return cuda_status(cudaGetLastError(), "network first layer");
+  return cuda_status(launch_dependent(conv1_mma_kernel, grid, kC1Threads, kC1Smem, s, tx, wpack, bias, out, B,
+                                      device_status_word()),
+                     "network first layer");
 }
 
 // A 32-channel layer through the TMA-fed kernel.  Forward: source NHWC [B][S][S][32]
@@ -1038,8 +1060,9 @@ int conv_tma(const bf16 *src, int S, const bf16 *wpack, const float *bias, const
   if (e != cudaSuccess) return cuda_status(e, "network convolution attributes");
   const int ntiles = geo.split ? 4 * geo.tiles_c : geo.tiles_c;
   const int grid = ntiles < 2 * nsm ? ntiles : 2 * nsm;  // two CTAs per SM
-  conv_tma_kernel<MODE><<<grid, kTfThreads, kTfSmem, s>>>(tm, wpack, bias, mask, out, B, geo, device_status_word());
-  return cuda_status(cudaGetLastError(), "network convolution");
+  return cuda_status(launch_dependent(conv_tma_kernel<MODE>, grid, kTfThreads, kTfSmem, s, tm, wpack, bias, mask, out,
+                                      B, geo, device_status_word()),
+                     "network convolution");
 }
 
 // A 32-channel layer's partial weight-gradient sums through the TMA-fed kernel: source
@@ -1058,8 +1081,9 @@ int wgrad_tma(const bf16 *src, int S, const bf16 *dz, float *part, int B, int lg
     return set_error(SVK_ERR_CUDA, "network tensor map refused");
   cudaError_t e = cudaFuncSetAttribute(wgrad_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWtSmem);
   if (e != cudaSuccess) return cuda_status(e, "network weight-gradient attributes");
-  wgrad_tma_kernel<<<nch, kWtThreads, kWtSmem, s>>>(ta, td, part, B, geo, device_status_word());
-  return cuda_status(cudaGetLastError(), "network weight gradient");
+  return cuda_status(launch_dependent(wgrad_tma_kernel, nch, kWtThreads, kWtSmem, s, ta, td, part, B, geo,
+                                      device_status_word()),
+                     "network weight gradient");
 }
 
 // The first layer's partial weight-gradient sums (reduced for all layers by
@@ -1073,9 +1097,9 @@ int wgrad1(const float *x, const bf16 *dz, float *part, int B, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_status(e, "network weight-gradient attributes");
   const int P = B << (2 * kLgOut[0]);
   const int per = wg_per_chunk(P, 2), nch = wg_nchunks(P, 2);
-  wgrad1_kernel<<<nch, Wg1::THREADS, Wg1::SMEM, s>>>(tx, td, part, B, kLgIn[0], kLgOut[0], kStride[0], per,
-                                                       device_status_word());
-  return cuda_status(cudaGetLastError(), "network weight gradient");
+  return cuda_status(launch_dependent(wgrad1_kernel, nch, Wg1::THREADS, Wg1::SMEM, s, tx, td, part, B, kLgIn[0],
+                                      kLgOut[0], kStride[0], per, device_status_word()),
+                     "network weight gradient");
 }
 
 struct Bufs {
@@ -1101,11 +1125,11 @@ Bufs bufs(void *ws_v, const Work &Wk) {
   return b;
 }
 
-int pack(const float *params, const Layout &L, const Bufs &b, cudaStream_t s) {
-  pack_kernel<<<grid_for(L.total + kPack0 + 3 * kPack), 256, 0, s>>>(params, b.wq, (int)L.total, b.wf[0], b.wf[1],
-                                                                    b.wd[1], b.wf[2], b.wd[2], b.wf[3], b.wd[3],
-                                                                    L.w[0], L.w[1], L.w[2], L.w[3]);
-  return cuda_status(cudaGetLastError(), "network weight packing");
+int pack(const float *params, const Layout &L, const Bufs &b, cudaStream_t s, float *loss = nullptr) {
+  return cuda_status(launch_dependent(pack_kernel, grid_for(L.total + kPack0 + 3 * kPack), 256, 0, s, params, b.wq,
+                                      (int)L.total, b.wf[0], b.wf[1], b.wd[1], b.wf[2], b.wd[2], b.wf[3], b.wd[3],
+                                      L.w[0], L.w[1], L.w[2], L.w[3], loss),
+                     "network weight packing");
 }
 
 // x -> act[0..3] -> pooled -> out (parameters already packed)
@@ -1116,9 +1140,9 @@ int forward(const float *x, const Layout &L, const Bufs &b, int B, int n_out, fl
     st = conv_tma<kFwd>(b.act[li - 1], 1 << kLgIn[li], b.wf[li], b.wq + L.b[li], nullptr, b.act[li], B, kLgOut[li],
                         kStride[li], nsm, s);
   if (st != SVK_OK) return st;
-  pool_fc_kernel<<<B, 64, 0, s>>>(b.act[kLayers - 1], b.wq + L.fcw, b.wq + L.fcb, b.pooled, out, n_out, target,
-                                  b.dout, loss, B);
-  return cuda_status(cudaGetLastError(), "network pooling");
+  return cuda_status(launch_dependent(pool_fc_kernel, B, 64, 0, s, b.act[kLayers - 1], b.wq + L.fcw, b.wq + L.fcb,
+                                      b.pooled, out, n_out, target, b.dout, loss, B),
+                     "network pooling");
 }
 
 int check_ws(void *ws, size_t ws_bytes, int B, int n_out) {
@@ -1235,14 +1259,13 @@ int cnn_gradient(const float *params, const float *x, const float *target, int B
   const Layout L = param_layout(n_out);
   const Bufs b = bufs(ws, work_layout(B, n_out));
   const int nsm = sm_count();
-  if ((st = pack(params, L, b, s)) != SVK_OK) return st;
-  cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), s);
-  if (e != cudaSuccess) return cuda_status(e, "loss reset");
+  if ((st = pack(params, L, b, s, loss)) != SVK_OK) return st;
   if ((st = forward(x, L, b, B, n_out, b.out, nsm, s, target, loss)) != SVK_OK) return st;
-  fc_grad_kernel<<<n_out + (B * kCh + 255) / 256, 256, 0, s>>>(b.dout, b.pooled, b.wq + L.fcw, b.act[kLayers - 1],
-                                                                grad + L.fcw, grad + L.fcb, b.dz[kLayers - 1], B,
-                                                                n_out);
-  if ((st = cuda_status(cudaGetLastError(), "network output gradient")) != SVK_OK) return st;
+  st = cuda_status(launch_dependent(fc_grad_kernel, n_out + (B * kCh + 255) / 256, 256, 0, s, b.dout, b.pooled,
+                                    b.wq + L.fcw, b.act[kLayers - 1], grad + L.fcw, grad + L.fcb, b.dz[kLayers - 1],
+                                    B, n_out),
+                   "network output gradient");
+  if (st != SVK_OK) return st;
   for (int li = kLayers - 1; li >= 1; --li) {
     st = wgrad_tma(b.act[li - 1], 1 << kLgIn[li], b.dz[li], b.part[li], B, kLgOut[li], kStride[li], s);
     if (st == SVK_OK)
@@ -1261,21 +1284,23 @@ int cnn_gradient(const float *params, const float *x, const float *target, int B
     set.nchunks[li] = wg_nchunks(B * kHout[li] * kHout[li], kCin[li]);
     set.row0[li + 1] = set.row0[li] + wg_rows(kCin[li]);
   }
-  wgrad_reduce_kernel<<<set.row0[kLayers], kRedSlices * kCh, 0, s>>>(set);
-  return cuda_status(cudaGetLastError(), "network weight-gradient reduction");
+  return cuda_status(launch_dependent(wgrad_reduce_kernel, set.row0[kLayers], kRedSlices * kCh, 0, s, set),
+                     "network weight-gradient reduction");
 }
 
 int cnn_adam(float *params, float *m, float *v, const float *grad, int n, int step, float lr, float b1, float b2,
              float eps, cudaStream_t s) {
   const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
-  adam_kernel<<<grid_for(n), 256, 0, s>>>(params, m, v, grad, n, lr, b1, b2, eps, c1, c2);
-  return cuda_status(cudaGetLastError(), "adam");
+  return cuda_status(launch_dependent(adam_kernel, grid_for(n), 256, 0, s, params, m, v, grad, n, lr, b1, b2, eps, c1,
+                                      c2),
+                     "adam");
 }
 
 int cnn_adam_device_step(float *params, float *m, float *v, const float *grad, int n, const int *step, float lr,
                          float b1, float b2, float eps, cudaStream_t s) {
-  adam_dstep_kernel<<<grid_for(n), 256, 0, s>>>(params, m, v, grad, n, step, lr, b1, b2, eps);
-  return cuda_status(cudaGetLastError(), "adam");
+  return cuda_status(launch_dependent(adam_dstep_kernel, grid_for(n), 256, 0, s, params, m, v, grad, n, step, lr, b1,
+                                      b2, eps),
+                     "adam");
 }
 
 }  // namespace svk

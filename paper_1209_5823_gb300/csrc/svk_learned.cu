@@ -2,7 +2,8 @@
 // images and normalised for its input, standardisation of its targets and outputs, the
 // residual check that decides whether its coefficients are kept or handed to the FP64 fit,
 // and the pieces of a training step that run on the device (batch draw, row gather, step
-// bookkeeping), so a captured training step is library kernels only.
+// bookkeeping), so a captured training step is library kernels only.  The training-step
+// kernels are launched as programmatic dependents (launch_dependent), like the network's.
 #include "svk_common.cuh"
 #include "svk_internal.h"
 
@@ -106,6 +107,8 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
 // SplitMix64, reduced to the range by a 32 x 32 -> 64-bit multiply of its high word.
 __global__ void draw_batch_kernel(uint64_t seed, const int *__restrict__ step, int n, int batch,
                                   long long *__restrict__ idx) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= batch) return;
   const uint64_t ctr = seed + (uint64_t)(uint32_t)(*step) * (uint64_t)batch + (uint64_t)i;
@@ -116,6 +119,8 @@ __global__ void draw_batch_kernel(uint64_t seed, const int *__restrict__ step, i
 // dst row i = src row idx[i] (rows of `words` 32-bit words).
 __global__ void gather_rows_kernel(const uint32_t *__restrict__ src, long long words, const long long *__restrict__ idx,
                                    int n, uint32_t *__restrict__ dst) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const int r = blockIdx.y;
   if (r >= n) return;
   const uint32_t *s = src + (size_t)idx[r] * words;
@@ -126,6 +131,8 @@ __global__ void gather_rows_kernel(const uint32_t *__restrict__ src, long long w
 
 __global__ void step_end_kernel(const float *__restrict__ loss, int *__restrict__ step, float *__restrict__ hist,
                                 int len) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const int s = *step;
   hist[(unsigned)s % (unsigned)len] = *loss;
   *step = s + 1;
@@ -165,21 +172,21 @@ int launch_standardise(const float *in, long long rows, int cols, const float *m
 }
 
 int launch_draw_batch(unsigned long long seed, const int *step, int n, int batch, long long *idx, cudaStream_t s) {
-  draw_batch_kernel<<<(batch + 255) / 256, 256, 0, s>>>((uint64_t)seed, step, n, batch, idx);
-  return cuda_status(cudaGetLastError(), "draw_batch_kernel launch");
+  return cuda_status(launch_dependent(draw_batch_kernel, (batch + 255) / 256, 256, 0, s, (uint64_t)seed, step, n, batch,
+                                      idx),
+                     "draw_batch_kernel launch");
 }
 
 int launch_gather_rows(const void *src, long long row_bytes, const long long *idx, int n, void *dst, cudaStream_t s) {
   const long long words = row_bytes / 4;
   const int bx = (int)((words + 255) / 256 < 64 ? (words + 255) / 256 : 64);
-  gather_rows_kernel<<<dim3(bx, n), 256, 0, s>>>(static_cast<const uint32_t *>(src), words, idx, n,
-                                                 static_cast<uint32_t *>(dst));
-  return cuda_status(cudaGetLastError(), "gather_rows_kernel launch");
+  return cuda_status(launch_dependent(gather_rows_kernel, dim3(bx, n), 256, 0, s, static_cast<const uint32_t *>(src),
+                                      words, idx, n, static_cast<uint32_t *>(dst)),
+                     "gather_rows_kernel launch");
 }
 
 int launch_step_end(const float *loss, int *step, float *hist, int len, cudaStream_t s) {
-  step_end_kernel<<<1, 1, 0, s>>>(loss, step, hist, len);
-  return cuda_status(cudaGetLastError(), "step_end_kernel launch");
+  return cuda_status(launch_dependent(step_end_kernel, 1, 1, 0, s, loss, step, hist, len), "step_end_kernel launch");
 }
 
 }  // namespace svk

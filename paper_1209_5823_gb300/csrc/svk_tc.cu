@@ -153,6 +153,7 @@ static bool make_plan(int N, int L, int prec, int G, int NS, int stream, Plan *p
     q.srows = q.nrows;
   }
   q.smem_tab_bytes = (size_t)q.nKG * q.srows * 16;
+
   size_t o = 0;
   q.off_tab_hi = o;
   o += q.smem_tab_bytes;
@@ -322,6 +323,34 @@ __global__ void tc_prep_table(const float *__restrict__ basis, Plan pl, float bs
   if (tl) tl[idx] = b;
 }
 
+// The epilogue's dot products for one pixel and output row: s[p] = sum over the slots of
+// alpha[p][slot] * C[slot] for the powers p < NPOW of xt (the others are zero), the slots
+// taken four at a time (q < NQ) as packed f32x2 pairs: P[p] accumulates slots 4q, 4q+2 in
+// its low half and 4q+1, 4q+3 in its high half.  The coefficients are broadcast
+// shared-memory loads (four wavefronts per 16 bytes), so slots and powers that carry
+// nothing are not read.
+template <int NPOW, int NQ>
+__device__ __forceinline__ void slot_dots(const uint32_t (&v)[64], const float *ag, float (&s)[4]) {
+  uint64_t P[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const uint64_t c01 = f2_pack(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]));
+    const uint64_t c23 = f2_pack(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+#pragma unroll
+    for (int p = 0; p < NPOW; ++p) {
+      const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(ag + 64 * p + 4 * q);
+      P[p] = f2_fma(A.x, c01, P[p]);
+      P[p] = f2_fma(A.y, c23, P[p]);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    float l = 0.0f, u = 0.0f;
+    if (p < NPOW) f2_unpack(P[p], l, u);
+    s[p] = l + u;
+  }
+}
+
 // ----------------------------------------------------------------- main kernel
 // STREAM: the plan streams its basis slices (pl.stream); a template parameter, so the
 // resident-table kernel carries none of the streamed bookkeeping in its issuing loop
@@ -343,6 +372,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   float *alpha = reinterpret_cast<float *>(sm + pl.off_alpha);
   float *alphaS = reinterpret_cast<float *>(sm + pl.off_alphaS);
   const bool fast = (N >= 16 && N <= 64);
+  // 49..52 stamps (the 49 of three Gaussians of degrees 6, 4, 2 among them): slot k carries
+  // column k, loaded as three 16-column loads and one 4-column load (slots N..51 read
+  // columns of the next group or the MMA padding, with zero coefficients), when those
+  // columns lie inside the accumulator buffer; other stamp counts use four 16-column loads
+  const bool exact = N >= 49 && N <= 52 && (G - 1) * N + 52 <= kAccStride;
   int b_begin, b_end;
   cta_block_range(fs, b_begin, b_end);
 
@@ -724,7 +758,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           a3 = ck[9];
         }
         *reinterpret_cast<float4 *>(alpha + (size_t)e * 4) = make_float4(a0, a1, a2, a3);
-        if (fast) {
+        if (exact) {  // the same coefficients at slot k
+          float *as = alphaS + (size_t)g * 256 + k;  // [g][power of xt][slot]
+          as[0] = a0;
+          as[64] = a1;
+          as[128] = a2;
+          as[192] = a3;
+        } else if (fast) {
           // the same coefficients at the TMEM-load slot that carries column k
           // (load i covers columns min(16 i, N - 16) .. + 15; each column used once)
 #pragma unroll
@@ -767,45 +807,37 @@ __global__ void __launch_bounds__(kThreads, 1)
         // products over the accumulator columns, then Horner in xt
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
         if (fast) {
-          // 16 <= N <= 64: four 16-column loads (the last one moved back to end at column
-          // N - 1) and one wait; coefficients in load-slot order, zeros in repeated slots
+          // 16 <= N <= 64, one wait for all loads.  Exact slots: columns 0..51.  Otherwise
+          // four 16-column loads, the last one moved back to end at column N - 1, zeros at
+          // its repeated slots.
           uint32_t v[64];
+          if (exact) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int st = 16 * i < N ? min(16 * i, N - 16) : 0;  // unused slots re-read chunk 0
-            if (SVK_CHECK((G - 1 - g) * N + st + 16 <= kAccStride, status, 4)) tmem_ld16p(c0 + (uint32_t)st, &v[16 * i]);
+            for (int i = 0; i < 3; ++i)
+              if (SVK_CHECK((G - 1 - g) * N + 16 * i + 16 <= kAccStride, status, 4))
+                tmem_ld16p(c0 + (uint32_t)(16 * i), &v[16 * i]);
+            if (SVK_CHECK((G - 1 - g) * N + 52 <= kAccStride, status, 4)) tmem_ld4p(c0 + 48u, &v[48]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int st = 16 * i < N ? min(16 * i, N - 16) : 0;  // unused slots re-read chunk 0
+              if (SVK_CHECK((G - 1 - g) * N + st + 16 <= kAccStride, status, 4)) tmem_ld16p(c0 + (uint32_t)st, &v[16 * i]);
+            }
           }
           tmem_ld_wait();
-          // packed pairs of slots: P_i accumulates slots 4q, 4q+2 in its low half and 4q+1,
-          // 4q+3 in its high half (one fma.rn.f32x2 per pair and power of xt)
           const float *ag = alphaS + (size_t)g * 256;
-          uint64_t P0 = 0, P1 = 0, P2 = 0, P3 = 0;
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const uint64_t c01 = f2_pack(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]));
-            const uint64_t c23 = f2_pack(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
-            const ulonglong2 A0 = *reinterpret_cast<const ulonglong2 *>(ag + 4 * q);
-            const ulonglong2 A1 = *reinterpret_cast<const ulonglong2 *>(ag + 64 + 4 * q);
-            const ulonglong2 A2 = *reinterpret_cast<const ulonglong2 *>(ag + 128 + 4 * q);
-            const ulonglong2 A3 = *reinterpret_cast<const ulonglong2 *>(ag + 192 + 4 * q);
-            P0 = f2_fma(A0.x, c01, P0);
-            P1 = f2_fma(A1.x, c01, P1);
-            P2 = f2_fma(A2.x, c01, P2);
-            P3 = f2_fma(A3.x, c01, P3);
-            P0 = f2_fma(A0.y, c23, P0);
-            P1 = f2_fma(A1.y, c23, P1);
-            P2 = f2_fma(A2.y, c23, P2);
-            P3 = f2_fma(A3.y, c23, P3);
+          float sv[4];
+          if (exact) {
+            if (degree >= 3) slot_dots<4, 13>(v, ag, sv);
+            else slot_dots<3, 13>(v, ag, sv);  // degree <= 2: no xt^3 term
+          } else {
+            if (degree >= 3) slot_dots<4, 16>(v, ag, sv);
+            else slot_dots<3, 16>(v, ag, sv);
           }
-          float l, u;
-          f2_unpack(P0, l, u);
-          s0 = l + u;
-          f2_unpack(P1, l, u);
-          s1 = l + u;
-          f2_unpack(P2, l, u);
-          s2 = l + u;
-          f2_unpack(P3, l, u);
-          s3 = l + u;
+          s0 = sv[0];
+          s1 = sv[1];
+          s2 = sv[2];
+          s3 = sv[3];
         } else {
           const float4 *a4 = reinterpret_cast<const float4 *>(alpha) + (size_t)g * N;
           const int nfull = N >> 4, tail = N & 15;

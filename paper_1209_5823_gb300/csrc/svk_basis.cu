@@ -22,24 +22,38 @@ __device__ double ipow_d(double x, int n) {
   return r;
 }
 
-// Block-wide FP64 sum (blockDim.x multiple of 32, <= 1024).
-__device__ double block_sum(double v, double *scratch) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// Block-wide FP64 sums of two values at once (blockDim.x a multiple of 32, <= 1024).
+__device__ void block_sum2(double &a, double &b, double (*scratch)[32]) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
-  if (l == 0) scratch[w] = v;
+  if (l == 0) {
+    scratch[0][w] = a;
+    scratch[1][w] = b;
+  }
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += scratch[i];
-  return s;
+  a = 0.0;
+  b = 0.0;
+  for (int i = 0; i < nw; ++i) {
+    a += scratch[0][i];
+    b += scratch[1][i];
+  }
 }
 
-// One CTA per stamp k.  For SVK_NORM_ALARD every CTA also rebuilds B_0 to make the
-// even-even stamps zero-sum, so no CTA depends on another.
-__global__ void gauss_basis_kernel(int L, GaussList gl, int normalize, float *out) {
-  extern __shared__ double sm[];
+constexpr int kBasisThreads = 256, kBasisPer = 4;  // 4 x 256 >= 31 x 31 taps
+
+// One CTA per stamp k, the stamp's taps in registers (tap i = threadIdx.x + 256 j).  For
+// SVK_NORM_ALARD every CTA also evaluates B_0 (its sum normalises B_0 and makes the
+// even-even stamps zero-sum), so no CTA depends on another; two block reductions: the sums
+// of B_0 and B_k, then the squared norm of the corrected B_k.
+__global__ void __launch_bounds__(kBasisThreads) gauss_basis_kernel(int L, GaussList gl, int normalize, float *out) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
+  __shared__ double red[2][32];
   const int LL = L * L, h = (L - 1) / 2;
-  double *b0 = sm, *bk = sm + LL, *red = sm + 2 * LL;
   const int k = blockIdx.x;
   int g = 0, p = 0, q = 0, idx = k;
   for (g = 0; g < gl.n; ++g) {
@@ -56,42 +70,56 @@ __global__ void gauss_basis_kernel(int L, GaussList gl, int normalize, float *ou
     idx -= nq;
   }
   const double s0 = 2.0 * gl.sigma[0] * gl.sigma[0], sg = 2.0 * gl.sigma[g] * gl.sigma[g];
-  for (int i = threadIdx.x; i < LL; i += blockDim.x) {
-    const int u = i % L - h, v = i / L - h;
-    const double r2 = (double)(u * u + v * v);
-    b0[i] = exp(-r2 / s0);
-    bk[i] = exp(-r2 / sg) * ipow_d((double)u, p) * ipow_d((double)v, q);
+  double b0[kBasisPer], bk[kBasisPer];
+  double sum0 = 0.0, sumk = 0.0;
+#pragma unroll
+  for (int j = 0; j < kBasisPer; ++j) {
+    const int i = threadIdx.x + kBasisThreads * j;
+    b0[j] = 0.0;
+    bk[j] = 0.0;
+    if (i < LL) {
+      const int u = i % L - h, v = i / L - h;
+      const double r2 = (double)(u * u + v * v);
+      b0[j] = exp(-r2 / s0);
+      bk[j] = exp(-r2 / sg) * ipow_d((double)u, p) * ipow_d((double)v, q);
+    }
+    sum0 += b0[j];
+    sumk += bk[j];
   }
-  __syncthreads();
   if (normalize == SVK_NORM_ALARD) {
-    double part = 0.0;
-    for (int i = threadIdx.x; i < LL; i += blockDim.x) part += b0[i];
-    const double sum0 = block_sum(part, red);
-    for (int i = threadIdx.x; i < LL; i += blockDim.x) b0[i] = b0[i] / sum0;
-    __syncthreads();
+    block_sum2(sum0, sumk, red);
+    const double inv0 = 1.0 / sum0;
     if (k == 0) {
-      for (int i = threadIdx.x; i < LL; i += blockDim.x) out[i] = (float)b0[i];
+#pragma unroll
+      for (int j = 0; j < kBasisPer; ++j) {
+        const int i = threadIdx.x + kBasisThreads * j;
+        if (i < LL) out[i] = (float)(b0[j] * inv0);
+      }
       return;
     }
-    if ((p % 2) == 0 && (q % 2) == 0) {
-      part = 0.0;
-      for (int i = threadIdx.x; i < LL; i += blockDim.x) part += bk[i];
-      const double sk = block_sum(part, red);
-      for (int i = threadIdx.x; i < LL; i += blockDim.x) bk[i] -= sk * b0[i];
-      __syncthreads();
+    const bool even = (p % 2) == 0 && (q % 2) == 0;
+    double n2 = 0.0, unused = 0.0;
+#pragma unroll
+    for (int j = 0; j < kBasisPer; ++j) {
+      if (even) bk[j] -= sumk * (b0[j] * inv0);
+      n2 += bk[j] * bk[j];
     }
-    part = 0.0;
-    for (int i = threadIdx.x; i < LL; i += blockDim.x) part += bk[i] * bk[i];
-    const double n2 = block_sum(part, red);
+    block_sum2(n2, unused, red);
     const double nrm = sqrt(n2);
-    if (nrm > 0.0)
-      for (int i = threadIdx.x; i < LL; i += blockDim.x) bk[i] /= nrm;
-    __syncthreads();
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 1.0;
+#pragma unroll
+    for (int j = 0; j < kBasisPer; ++j) bk[j] *= inv;
   }
-  for (int i = threadIdx.x; i < LL; i += blockDim.x) out[(size_t)k * LL + i] = (float)bk[i];
+#pragma unroll
+  for (int j = 0; j < kBasisPer; ++j) {
+    const int i = threadIdx.x + kBasisThreads * j;
+    if (i < LL) out[(size_t)k * LL + i] = (float)bk[j];
+  }
 }
 
 __global__ void delta_basis_kernel(int L, int normalize, float *out) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const int LL = L * L, c = (LL - 1) / 2;
   const size_t n = (size_t)LL * LL;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -109,8 +137,8 @@ int launch_build_basis(int kind, int L, int n_gauss, const double *sigma, const 
   if (kind == SVK_BASIS_DELTA) {
     const size_t n = (size_t)L * L * L * L;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    delta_basis_kernel<<<blocks, 256, 0, s>>>(L, normalize, basis_out);
-    return cuda_status(cudaGetLastError(), "delta_basis_kernel launch");
+    return cuda_status(launch_dependent(delta_basis_kernel, blocks, 256, 0, s, L, normalize, basis_out),
+                       "delta_basis_kernel launch");
   }
   GaussList gl{};
   gl.n = n_gauss;
@@ -118,11 +146,9 @@ int launch_build_basis(int kind, int L, int n_gauss, const double *sigma, const 
     gl.sigma[g] = sigma[g];
     gl.deg[g] = deg[g];
   }
-  const size_t smem = (size_t)(2 * L * L + 32) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(gauss_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_status(e, "gauss_basis_kernel smem attribute");
-  gauss_basis_kernel<<<N, 256, smem, s>>>(L, gl, normalize, basis_out);
-  return cuda_status(cudaGetLastError(), "gauss_basis_kernel launch");
+  if (L * L > kBasisThreads * kBasisPer) return set_error(SVK_ERR_ARG, "basis size %d above %d taps", L, 31);
+  return cuda_status(launch_dependent(gauss_basis_kernel, N, kBasisThreads, 0, s, L, gl, normalize, basis_out),
+                     "gauss_basis_kernel launch");
 }
 
 }  // namespace svk

@@ -297,6 +297,8 @@ struct RowIt {
 // P = rho / N (kernel row v = h + G - 1 - P); zero outside the kernel or the slices.
 template <int PREC>
 __global__ void tc_prep_table(const float *__restrict__ basis, Plan pl, float bscale, uint4 *th, uint4 *tl) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= pl.nKG * pl.nrows) return;
   const int j = idx / pl.nrows, rho = idx % pl.nrows;
@@ -371,6 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float *coef = reinterpret_cast<float *>(sm + pl.off_coef);
   float *alpha = reinterpret_cast<float *>(sm + pl.off_alpha);
   float *alphaS = reinterpret_cast<float *>(sm + pl.off_alphaS);
+  dep_trigger();  // launched by launch_dependent: the next kernel may start launching
   const bool fast = (N >= 16 && N <= 64);
   // 49..52 stamps (the 49 of three Gaussians of degrees 6, 4, 2 among them): slot k carries
   // column k, loaded as three 16-column loads and one 4-column load (slots N..51 read
@@ -407,6 +410,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // set-up done (shared memory and TMEM only); global memory from here on, once the
+  // kernel before this one in the stream has completed
+  dep_wait();
 
   if (warp == kIdleWarp) {
     goto done;
@@ -963,8 +969,11 @@ int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *w
     } else {
       uint4 *th = reinterpret_cast<uint4 *>(ws + (size_t)ntab * pl.table_bytes * 2);
       uint4 *tl = reinterpret_cast<uint4 *>(ws + (size_t)ntab * pl.table_bytes * 2 + pl.table_bytes);
-      if (prep)
-        tc_prep_table<P><<<(nrow_items + 255) / 256, 256, 0, s>>>(fr[i].basis, pl, bscale, th, pl.parts == 2 ? tl : nullptr);
+      if (prep) {
+        const cudaError_t pe = launch_dependent(tc_prep_table<P>, (nrow_items + 255) / 256, 256, 0, s, fr[i].basis, pl,
+                                                bscale, th, pl.parts == 2 ? tl : nullptr);
+        if (pe != cudaSuccess) return cuda_status(pe, "tc_prep_table launch");
+      }
       d.tab_hi = th;
       d.tab_lo = tl;
       ++ntab;
@@ -982,8 +991,8 @@ int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *w
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int grid = blocks < nsm ? blocks : nsm;
-  if (grid > 0) kern<<<grid, kThreads, pl.smem, s>>>(fs, pl, status);
-  return cuda_status(cudaGetLastError(), "tc_basis_kernel launch");
+  if (grid > 0) return cuda_status(launch_dependent(kern, grid, kThreads, pl.smem, s, fs, pl, status), "tc_basis_kernel launch");
+  return SVK_OK;
 }
 
 // rows: per frame the output rows [rows[2i], rows[2i+1]) (multiples of G apart from the

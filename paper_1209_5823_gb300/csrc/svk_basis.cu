@@ -22,7 +22,9 @@ __device__ double ipow_d(double x, int n) {
   return r;
 }
 
-// Block-wide FP64 sums of two values at once (blockDim.x a multiple of 32, <= 1024).
+// Block-wide FP64 sums of two values at once (blockDim.x a multiple of 32, <= 1024): a
+// shuffle tree in each warp, the warps' partials added by a shuffle tree in warp 0 (short
+// dependent chains: FP64 adds are slow on this part), the result broadcast.
 __device__ void block_sum2(double &a, double &b, double (*scratch)[32]) {
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -35,12 +37,22 @@ __device__ void block_sum2(double &a, double &b, double (*scratch)[32]) {
     scratch[1][w] = b;
   }
   __syncthreads();
-  a = 0.0;
-  b = 0.0;
-  for (int i = 0; i < nw; ++i) {
-    a += scratch[0][i];
-    b += scratch[1][i];
+  if (w == 0) {
+    double x = l < nw ? scratch[0][l] : 0.0, y = l < nw ? scratch[1][l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    __syncwarp();
+    if (l == 0) {
+      scratch[0][0] = x;
+      scratch[1][0] = y;
+    }
   }
+  __syncthreads();
+  a = scratch[0][0];
+  b = scratch[1][0];
+  __syncthreads();  // the scratch is reused by the next call
 }
 
 constexpr int kBasisThreads = 256, kBasisPer = 4;  // 4 x 256 >= 31 x 31 taps
@@ -69,7 +81,23 @@ __global__ void __launch_bounds__(kBasisThreads) gauss_basis_kernel(int L, Gauss
     }
     idx -= nq;
   }
-  const double s0 = 2.0 * gl.sigma[0] * gl.sigma[0], sg = 2.0 * gl.sigma[g] * gl.sigma[g];
+  // the stamps are separable, exp(-(u^2 + v^2) / s) u^p v^q = fu(u) fv(v): one FP64 exp per
+  // offset and Gaussian, and per tap two multiplies (FP64 is GB300's slow pipe)
+  __shared__ double e0[32], fu[32], fv[32];
+  if (threadIdx.x < 64) {  // warp 0 the first Gaussian, warp 1 the stamp's (in parallel)
+    const int t = threadIdx.x & 31;
+    if (t < L) {
+      const double u = (double)(t - h);
+      if (threadIdx.x < 32) {
+        e0[t] = exp(-(u * u) / (2.0 * gl.sigma[0] * gl.sigma[0]));
+      } else {
+        const double eg = exp(-(u * u) / (2.0 * gl.sigma[g] * gl.sigma[g]));
+        fu[t] = eg * ipow_d(u, p);
+        fv[t] = eg * ipow_d(u, q);
+      }
+    }
+  }
+  __syncthreads();
   double b0[kBasisPer], bk[kBasisPer];
   double sum0 = 0.0, sumk = 0.0;
 #pragma unroll
@@ -78,10 +106,9 @@ __global__ void __launch_bounds__(kBasisThreads) gauss_basis_kernel(int L, Gauss
     b0[j] = 0.0;
     bk[j] = 0.0;
     if (i < LL) {
-      const int u = i % L - h, v = i / L - h;
-      const double r2 = (double)(u * u + v * v);
-      b0[j] = exp(-r2 / s0);
-      bk[j] = exp(-r2 / sg) * ipow_d((double)u, p) * ipow_d((double)v, q);
+      const int iu = i % L, iv = i / L;
+      b0[j] = e0[iu] * e0[iv];
+      bk[j] = fu[iu] * fv[iv];
     }
     sum0 += b0[j];
     sumk += bk[j];

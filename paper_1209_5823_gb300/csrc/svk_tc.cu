@@ -1091,14 +1091,29 @@ int tc_rows_per_block(int N, int L, int precision) {
 
 namespace {
 // K_t = sum_k c[k][t] B_k (FP64 sums, stored FP32) and the T x T identity coefficients
-// that make the epilogue's polynomial sum_t m_t C_t.
+// that make the epilogue's polynomial sum_t m_t C_t.  Blocks of 64 threads: each thread's
+// sum is a chain of N dependent FP64 multiply-adds, so the outputs are spread over many
+// SMs rather than sharing a few SMs' FP64 pipes.
 __global__ void tform_combine_kernel(const float *__restrict__ basis, const float *__restrict__ coeffs, int N, int T,
                                      int LL, float *__restrict__ Kt, float *__restrict__ ident) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < T * LL) {
     const int t = idx / LL, i = idx % LL;
     double acc = 0.0;
-    for (int k = 0; k < N; ++k) acc += (double)coeffs[(size_t)k * T + t] * (double)basis[(size_t)k * LL + i];
+    // eight stamps' loads in flight at a time (a plain loop waits for each load in turn);
+    // the sum is taken in the same order
+    for (int k0 = 0; k0 < N; k0 += 8) {
+      float cv[8], bv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int k = k0 + j;
+        cv[j] = k < N ? coeffs[(size_t)k * T + t] : 0.0f;
+        bv[j] = k < N ? basis[(size_t)k * LL + i] : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (k0 + j < N) acc += (double)cv[j] * (double)bv[j];
+    }
     Kt[idx] = (float)acc;
   }
   if (idx < T * T) ident[idx] = (idx / T == idx % T) ? 1.0f : 0.0f;
@@ -1127,7 +1142,7 @@ int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W
     float *Kt = static_cast<float *>(ws);
     float *ident = Kt + (size_t)T * L * L;
     const int n = T * L * L > T * T ? T * L * L : T * T;
-    if (prep) tform_combine_kernel<<<(n + 255) / 256, 256, 0, s>>>(basis, coeffs, N, T, L * L, Kt, ident);
+    if (prep) tform_combine_kernel<<<(n + 63) / 64, 64, 0, s>>>(basis, coeffs, N, T, L * L, Kt, ident);
     return launch_tform_fp32(R, pitch_R, I, pitch_I, W, H, Kt, T, L, out, pitch_out, s, y_begin,
                              y_end < 0 ? H : y_end, r_begin, r_end);
   }
@@ -1140,7 +1155,7 @@ int launch_tform(const float *R, int pitch_R, const float *I, int pitch_I, int W
   float *Kt = reinterpret_cast<float *>(w);
   float *ident = Kt + (size_t)T * L * L;
   const int n = T * L * L > T * T ? T * L * L : T * T;
-  if (prep) tform_combine_kernel<<<(n + 255) / 256, 256, 0, s>>>(basis, coeffs, N, T, L * L, Kt, ident);
+  if (prep) tform_combine_kernel<<<(n + 63) / 64, 64, 0, s>>>(basis, coeffs, N, T, L * L, Kt, ident);
   svk_frame f{};
   f.R = R;
   f.pitch_R = pitch_R;

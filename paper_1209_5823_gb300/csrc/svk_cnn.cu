@@ -1155,41 +1155,77 @@ int check_ws(void *ws, size_t ws_bytes, int B, int n_out) {
 
 // Field fit of local coefficient predictions: for each stamp k-vector a_s at position
 // (x_s, y_s), least squares for c[k][t] in a_k(x_s, y_s) = sum_t c[k][t] m_t(xt_s, yt_s):
-// one T x T FP64 normal matrix shared by every k, Cholesky in shared memory, then N solves.
-__global__ void field_fit_kernel(const float *__restrict__ local, const int *__restrict__ xy, const float *__restrict__ wts,
-                                 int S, int N, int W, int H, int degree, double *__restrict__ coeffs, int *info) {
-  __shared__ double A[10][10];
+// one T x T FP64 normal matrix shared by every k, Cholesky, then N solves.  Block j solves
+// stamps' coefficient sets k = kFfPerBlock j .. + kFfPerBlock - 1; every block forms the
+// normal matrix itself (it is small) so no block waits for another.  The stamps pass in
+// chunks: their monomials and weights go to shared memory once, and each sum (a normal-
+// matrix entry, or a right-hand side entry (k, t)) is taken by one warp, lanes striding
+// over the chunk's stamps, then a shuffle tree, then added to its running total in chunk
+// order (deterministic).
+constexpr int kFfThreads = 256, kFfChunk = 256, kFfPerBlock = 4;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kFfThreads) field_fit_kernel(const float *__restrict__ local, const int *__restrict__ xy,
+                                                              const float *__restrict__ wts, int S, int N, int W, int H,
+                                                              int degree, double *__restrict__ coeffs, int *info) {
+  __shared__ double mono[kFfChunk][10];
+  __shared__ double wt[kFfChunk];
+  __shared__ double Asum[55], bsum[kFfPerBlock * 10];
   __shared__ double Gc[10][10];
   __shared__ int bad;
-  const int T = (degree + 1) * (degree + 2) / 2;
-  auto mono = [&](int s, double *m) {
-    const double xt = W > 1 ? (2.0 * xy[2 * s] - (W - 1)) / (double)(W - 1) : 0.0;
-    const double yt = H > 1 ? (2.0 * xy[2 * s + 1] - (H - 1)) / (double)(H - 1) : 0.0;
-    int t = 0;
-    double xi = 1.0;
-    for (int i = 0; i <= degree; ++i) {
-      double yj = 1.0;
-      for (int j = 0; j <= degree - i; ++j) {
-        m[t++] = xi * yj;
-        yj *= yt;
-      }
-      xi *= xt;
-    }
-  };
-  if (threadIdx.x < T * T) {
-    const int r = threadIdx.x / T, c = threadIdx.x % T;
-    double acc = 0.0, m[10];
-    for (int s = 0; s < S; ++s) {
-      mono(s, m);
-      acc += (wts ? (double)wts[s] : 1.0) * m[r] * m[c];
-    }
-    A[r][c] = acc;
-  }
+  const int T = (degree + 1) * (degree + 2) / 2, P = T * (T + 1) / 2;
+  const int k0 = blockIdx.x * kFfPerBlock, nk = min(kFfPerBlock, N - k0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kFfThreads / 32;
+  for (int i = threadIdx.x; i < P; i += kFfThreads) Asum[i] = 0.0;
+  for (int i = threadIdx.x; i < nk * T; i += kFfThreads) bsum[i] = 0.0;
   if (threadIdx.x == 0) bad = -1;
+  for (int s0 = 0; s0 < S; s0 += kFfChunk) {
+    const int cs = min(kFfChunk, S - s0);
+    __syncthreads();  // the previous chunk's sums are done with mono and wt
+    for (int i = threadIdx.x; i < cs; i += kFfThreads) {
+      const int s = s0 + i;
+      const double xt = W > 1 ? (2.0 * xy[2 * s] - (W - 1)) / (double)(W - 1) : 0.0;
+      const double yt = H > 1 ? (2.0 * xy[2 * s + 1] - (H - 1)) / (double)(H - 1) : 0.0;
+      int t = 0;
+      double xi = 1.0;
+      for (int p = 0; p <= degree; ++p) {
+        double yj = 1.0;
+        for (int q = 0; q <= degree - p; ++q) {
+          mono[i][t++] = xi * yj;
+          yj *= yt;
+        }
+        xi *= xt;
+      }
+      wt[i] = wts ? (double)wts[s] : 1.0;
+    }
+    __syncthreads();
+    // normal-matrix entries r <= c (pair e = c (c + 1) / 2 + r), then right-hand sides
+    for (int e = warp; e < P + nk * T; e += nw) {
+      double acc = 0.0;
+      if (e < P) {
+        int c = 0;
+        while ((c + 1) * (c + 2) / 2 <= e) ++c;
+        const int r = e - c * (c + 1) / 2;
+        for (int i = lane; i < cs; i += 32) acc += wt[i] * mono[i][r] * mono[i][c];
+      } else {
+        const int kk = (e - P) / T, t = (e - P) % T;
+        for (int i = lane; i < cs; i += 32) acc += mono[i][t] * wt[i] * (double)local[(size_t)(s0 + i) * N + k0 + kk];
+      }
+      acc = warp_sum_d(acc);
+      if (lane == 0) {
+        if (e < P) Asum[e] += acc;
+        else bsum[e - P] += acc;
+      }
+    }
+  }
   __syncthreads();
   if (threadIdx.x == 0) {  // T <= 10: serial textbook Cholesky
     for (int j = 0; j < T && bad < 0; ++j) {
-      double d = A[j][j];
+      double d = Asum[j * (j + 1) / 2 + j];
       for (int k = 0; k < j; ++k) d -= Gc[j][k] * Gc[j][k];
       if (!(d > 0.0)) {
         bad = j;
@@ -1197,37 +1233,33 @@ __global__ void field_fit_kernel(const float *__restrict__ local, const int *__r
       }
       Gc[j][j] = sqrt(d);
       for (int i = j + 1; i < T; ++i) {
-        double v = A[i][j];
+        double v = Asum[i * (i + 1) / 2 + j];
         for (int k = 0; k < j; ++k) v -= Gc[i][k] * Gc[j][k];
         Gc[i][j] = v / Gc[j][j];
       }
     }
-    *info = bad;
+    if (blockIdx.x == 0) *info = bad;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    double b[10], y[10], m[10];
-    for (int t = 0; t < T; ++t) b[t] = 0.0;
-    for (int s = 0; s < S; ++s) {
-      mono(s, m);
-      const double a = (wts ? (double)wts[s] : 1.0) * (double)local[(size_t)s * N + k];
-      for (int t = 0; t < T; ++t) b[t] += m[t] * a;
-    }
+  if ((int)threadIdx.x < nk) {
+    const int kk = threadIdx.x, k = k0 + kk;
+    double b[10], y[10];
+    for (int t = 0; t < T; ++t) b[t] = bsum[kk * T + t];
     if (bad >= 0) {
       for (int t = 0; t < T; ++t) coeffs[(size_t)k * T + t] = 0.0;
-      continue;
+    } else {
+      for (int i = 0; i < T; ++i) {
+        double v = b[i];
+        for (int q = 0; q < i; ++q) v -= Gc[i][q] * y[q];
+        y[i] = v / Gc[i][i];
+      }
+      for (int i = T - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int q = i + 1; q < T; ++q) v -= Gc[q][i] * b[q];
+        b[i] = v / Gc[i][i];
+      }
+      for (int t = 0; t < T; ++t) coeffs[(size_t)k * T + t] = b[t];
     }
-    for (int i = 0; i < T; ++i) {
-      double v = b[i];
-      for (int q = 0; q < i; ++q) v -= Gc[i][q] * y[q];
-      y[i] = v / Gc[i][i];
-    }
-    for (int i = T - 1; i >= 0; --i) {
-      double v = y[i];
-      for (int q = i + 1; q < T; ++q) v -= Gc[q][i] * b[q];
-      b[i] = v / Gc[i][i];
-    }
-    for (int t = 0; t < T; ++t) coeffs[(size_t)k * T + t] = b[t];
   }
 }
 
@@ -1235,7 +1267,8 @@ __global__ void field_fit_kernel(const float *__restrict__ local, const int *__r
 
 int cnn_field_fit(const float *local, const int *xy, const float *wts, int S, int N, int W, int H, int degree,
                   double *coeffs, int *info, cudaStream_t s) {
-  field_fit_kernel<<<1, 128, 0, s>>>(local, xy, wts, S, N, W, H, degree, coeffs, info);
+  field_fit_kernel<<<(N + kFfPerBlock - 1) / kFfPerBlock, kFfThreads, 0, s>>>(local, xy, wts, S, N, W, H, degree,
+                                                                               coeffs, info);
   return cuda_status(cudaGetLastError(), "field fit");
 }
 

@@ -131,6 +131,36 @@ def test_field_fit_recovers_polynomial():
     np.testing.assert_allclose(co.cpu().numpy(), c, rtol=0, atol=2e-5)
 
 
+@pytest.mark.parametrize("S,N,d,weighted", [(700, 49, 3, True), (257, 49, 2, False), (1, 3, 0, False),
+                                              (600, 130, 1, True)])
+def test_field_fit_matches_weighted_least_squares(S, N, d, weighted):
+    # several stamp chunks and coefficient blocks; weighted normal equations against
+    # numpy's least squares on sqrt(w)-scaled rows (FP64)
+    W, H = 2048, 4096
+    g = starfield.rng(40 + S + N)
+    xy = np.stack([g.integers(0, W, S), g.integers(0, H, S)], 1).astype(np.int32)
+    xt = (2.0 * xy[:, 0] - (W - 1)) / (W - 1)
+    yt = (2.0 * xy[:, 1] - (H - 1)) / (H - 1)
+    mono = np.stack([xt ** p * yt ** q for p in range(d + 1) for q in range(d + 1 - p)], 1)
+    local = g.normal(0, 1, (S, N)).astype(np.float32)
+    w = g.uniform(0.5, 2.0, S).astype(np.float32) if weighted else np.ones(S, np.float32)
+    co, info = svk.svk_cnn_field_fit(torch.from_numpy(local).cuda(), torch.from_numpy(xy).cuda(), W, H, d,
+                                     weights=torch.from_numpy(w).cuda() if weighted else None)
+    assert int(info.item()) == -1
+    sw = np.sqrt(w.astype(np.float64))[:, None]
+    ref = np.linalg.lstsq(mono * sw, local.astype(np.float64) * sw, rcond=None)[0].T  # [N][T]
+    np.testing.assert_allclose(co.cpu().numpy(), ref, rtol=0, atol=1e-9 * max(1.0, np.abs(ref).max()))
+
+
+def test_field_fit_reports_a_singular_system():
+    # every stamp at the frame centre (xt = yt = 0): only the constant term is determined
+    xy = np.tile(np.array([[500, 500]], np.int32), (50, 1))
+    local = np.ones((50, 7), np.float32)
+    co, info = svk.svk_cnn_field_fit(torch.from_numpy(local).cuda(), torch.from_numpy(xy).cuda(), 1001, 1001, 2)
+    assert int(info.item()) >= 0
+    assert not co.abs().sum().item()
+
+
 def _field(W, H, seed):
     g = starfield.rng(seed)
     cat = starfield.star_catalog(W, H, int(W * H * 0.0024), g)

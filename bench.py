@@ -367,17 +367,21 @@ def _fit_timing(svk, torch, dev, R, I, fp64_peak, reps=3):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    # FP64 moment accumulation: (N+2)(N+3)/2 column pairs x (1 product + 28 monomial FMAs)
-    # per stamp pixel (N = 49, monomials of degree <= 6)
+    # FP64 moment accumulation as the moment kernel does it, per column pair ((N+2)(N+3)/2
+    # of them, N = 49): per stamp pixel one product and 7 multiply-adds into the sums of its
+    # row (w E xt^i, i <= 6), per stamp row 28 multiply-adds and 6 products folding those
+    # sums into the moments of degree <= 6 (forming all 28 moments at every pixel instead
+    # would take 57 FLOP per pixel and pair)
     px = n_sel * 41 * 41
-    flop64 = px * (51 * 52 // 2) * (1 + 2 * 28)
+    pairs = 51 * 52 // 2
+    flop64 = px * pairs * (1 + 2 * 7) + n_sel * 41 * pairs * (2 * 28 + 6)
     return {"ms": ms, "unknowns": 49 * 10 + 1, "stamp_pixels": px, "info": int(info.item()),
             "workload": "fit_500x41x41_L25_N49_d3_bg0",
             "stamps": {"selected": n_sel, "peaks": n_peaks, "select_ms": sel_ms, "rule": sel},
             "roofline": {"bound": "fp64", "achieved": flop64 / (ms / 1e3) / 1e12, "peak": fp64_peak / 1e12,
                          "unit": "TFLOP/s", "frac": flop64 / (ms / 1e3) / fp64_peak,
-                         "note": "FP64 moment FLOP over the whole fit time (selection excluded); peak = "
-                                 "measured DFMA throughput"}}
+                         "note": "FP64 moment FLOP (row-factored form) over the whole fit time (selection "
+                                 "excluded); peak = measured DFMA throughput"}}
 
 
 def _precision_table(svk, torch, dev):
@@ -674,6 +678,8 @@ def main():
     ap.add_argument("--workload", default="ccd_2048x4096_L19_d2", choices=["ccd_2048x4096_L19_d2", "ccd_4096x4096_L25_d3"],
                     help="the frame the step times (the default is the metric's; the other one profiles a "
                          "25-tap kernel)")
+    ap.add_argument("--fit-only", action="store_true",
+                    help="only the stamp selection and OIS fit measurement (one JSON object)")
     ap.add_argument("--learned-only", action="store_true",
                     help="only the coefficient-network measurement (its own JSON line; for profiling)")
     ap.add_argument("--learned-steps", type=int, default=10000, help="training steps of that measurement")
@@ -700,6 +706,11 @@ def main():
     dev = torch.device("cuda", local_rank)
     prec = {"bf16x3": svk.SVK_PREC_BF16X3, "fp16x3": svk.SVK_PREC_FP16X3, "bf16": svk.SVK_PREC_BF16}[args.precision]
     spec, R, I, c = _frame(rank)
+    if args.fit_only:
+        res = _fit_timing(svk, torch, dev, R, I, svk.svk_measure_fma_peak(svk.SVK_FMA_FP64))
+        if rank == 0:
+            print(json.dumps({"fit": res}), flush=True)
+        return
     if args.learned_only:
         res = _learned(svk, torch, dev, R, I, steps=args.learned_steps)
         if rank == 0:

@@ -126,11 +126,22 @@ __global__ void __launch_bounds__(kCkThreads) fit_ck_kernel(const float *__restr
 // S[(e1 * NE + e2) * n_mu + mu] += sum over this CTA's pixels of w E_e1 E_e2 mu(p)
 // (e1 <= e2).  Thread = one column pair; CTA = one pixel range x one pair tile.  Pixels
 // outside the frame, or outside the rows [r0, r1) the buffers hold, add nothing.
+// The monomials mu = xt^i yt^j factor by rows: consecutive stamp pixels of one frame row
+// share yt, so each thread sums R_i = sum w E xt^i over the pixels of the current row
+// (D + 1 multiply-adds per pixel) and adds R_i yt^j into the (i, j) moments when the row
+// changes (once per run of pixels): about D + 2 FP64 operations per pixel and pair instead
+// of the n_mu + 1 of forming every moment at every pixel.  The accumulators are indexed
+// for the largest degree (kMaxDeg) so that they stay in registers.
+constexpr int kMaxDeg = 6;  // moment degree 2 max(d, bd)
+__host__ __device__ constexpr int idx6(int i, int j) { return i * (kMaxDeg + 1) - i * (i - 1) / 2 + j; }
+
 __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__ C, const float *__restrict__ I,
                                                        const float *__restrict__ weight, const int *stamp_xy, FitDims f,
                                                        int px_per_cta, double *__restrict__ S) {
-  __shared__ double Es[kChunk][66];         // extended columns of the staged pixels (NE <= 66), widened once
-  __shared__ double Ms[kChunk][kMaxMu];     // w * mu(p)
+  __shared__ double Es[kChunk][66];           // extended columns of the staged pixels (NE <= 66), widened once
+  __shared__ double WX[kChunk][kMaxDeg + 1];  // w xt^i (zero for i > D)
+  __shared__ double Yt[kChunk];               // yt of the pixel's row
+  __shared__ int Yv[kChunk];                  // its frame row, -1 for a pixel that adds nothing
   const int npairs = f.NE * (f.NE + 1) / 2;
   const int pair = blockIdx.y * blockDim.x + threadIdx.x;
   int e1 = 0, e2 = 0;
@@ -143,9 +154,24 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
     }
     e2 = e1 + rem;
   }
-  double acc[kMaxMu];
+  double acc[kMaxMu], rr[kMaxDeg + 1];
 #pragma unroll
   for (int m = 0; m < kMaxMu; ++m) acc[m] = 0.0;
+#pragma unroll
+  for (int i = 0; i <= kMaxDeg; ++i) rr[i] = 0.0;
+  int cur_y = -1;
+  double cur_yt = 0.0;
+  auto flush = [&]() {  // the current row's sums into the moments
+    double yj = 1.0;
+#pragma unroll
+    for (int j = 0; j <= kMaxDeg; ++j) {
+#pragma unroll
+      for (int i = 0; i + j <= kMaxDeg; ++i) acc[idx6(i, j)] = fma(rr[i], yj, acc[idx6(i, j)]);
+      yj *= cur_yt;
+    }
+#pragma unroll
+    for (int i = 0; i <= kMaxDeg; ++i) rr[i] = 0.0;
+  };
   const int p0 = blockIdx.x * px_per_cta, p1 = min(f.P, p0 + px_per_cta);
   for (int pc = p0; pc < p1; pc += kChunk) {
     __syncthreads();
@@ -167,6 +193,7 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
     for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
       const int p = pc + q;
       double w = 0.0, xt = 0.0, yt = 0.0;
+      int yv = -1;
       if (p < p1) {
         int x, y;
         stamp_pixel(f, stamp_xy, p, x, y);
@@ -174,34 +201,43 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
           w = weight ? (double)weight[(size_t)(y - f.r0) * f.pitch + x] : 1.0;
           xt = norm_coord(x, f.W);
           yt = norm_coord(y, f.H);
+          yv = y;
         }
       }
-      double xi = w;
-      for (int i = 0; i <= f.D; ++i) {
-        double v = xi;
-        for (int j = 0; j <= f.D - i; ++j) {
-          Ms[q][mono_index(i, j, f.D)] = v;
-          v *= yt;
-        }
-        xi *= xt;
+      double v = w;
+      for (int i = 0; i <= kMaxDeg; ++i) {
+        WX[q][i] = i <= f.D ? v : 0.0;
+        v *= xt;
       }
+      Yt[q] = yt;
+      Yv[q] = yv;
     }
     __syncthreads();
     if (pair < npairs) {
       const int nq = min(kChunk, p1 - pc);
       for (int q = 0; q < nq; ++q) {
+        const int yv = Yv[q];  // the same for every thread: uniform branches
+        if (yv < 0) continue;
+        if (yv != cur_y) {
+          flush();
+          cur_y = yv;
+          cur_yt = Yt[q];
+        }
         const double e = Es[q][e1] * Es[q][e2];
 #pragma unroll
-        for (int m = 0; m < kMaxMu; ++m)
-          if (m < f.n_mu) acc[m] = fma(e, Ms[q][m], acc[m]);
+        for (int i = 0; i <= kMaxDeg; ++i)
+          if (i <= f.D) rr[i] = fma(e, WX[q][i], rr[i]);
       }
     }
   }
   if (pair < npairs) {
+    flush();
     double *dst = S + ((size_t)e1 * f.NE + e2) * f.n_mu;
 #pragma unroll
-    for (int m = 0; m < kMaxMu; ++m)
-      if (m < f.n_mu) atomicAdd(dst + m, acc[m]);
+    for (int i = 0; i <= kMaxDeg; ++i)
+#pragma unroll
+      for (int j = 0; i + j <= kMaxDeg; ++j)
+        if (i + j <= f.D) atomicAdd(dst + mono_index(i, j, f.D), acc[idx6(i, j)]);
   }
 }
 
@@ -374,40 +410,32 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double *A, int M, int 
 // CTA: row i's dot product is split over the threads, reduced per warp and across warps.
 __global__ void __launch_bounds__(256) fit_solve_kernel(const double *G, const double *b, int M, const int *info,
                                                         double *x) {
-  __shared__ double y[1024];
-  __shared__ double part[8];
+  // Column-oriented substitutions: thread t owns the entries k = t, t + 256, ..., so each
+  // step is one division by the owner of entry i, one barrier, and one multiply-add per
+  // owned entry (no reduction tree on the critical path).
+  __shared__ double v[1024];
   if (*info >= 0) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) x[i] = 0.0;
     return;
   }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  for (int i = 0; i < M; ++i) {  // forward: G y = b
-    double s = 0.0;
-    for (int k = threadIdx.x; k < i; k += blockDim.x) s = fma(G[(size_t)i * M + k], y[k], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (l == 0) part[w] = s;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) v[k] = b[k];
+  __syncthreads();
+  for (int i = 0; i < M; ++i) {  // forward: G y = b; v[k] = b_k - sum_{j < i} G_kj y_j
+    if ((i & (blockDim.x - 1)) == threadIdx.x) v[i] = v[i] / G[(size_t)i * M + i];  // y_i
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int v = 0; v < 8; ++v) t += part[v];
-      y[i] = (b[i] - t) / G[(size_t)i * M + i];
-    }
-    __syncthreads();
+    const double yi = v[i];
+    for (int k = threadIdx.x; k < M; k += blockDim.x)
+      if (k > i) v[k] = fma(-G[(size_t)k * M + i], yi, v[k]);
   }
-  for (int i = M - 1; i >= 0; --i) {  // backward: G^T x = y (column i of G below the diagonal)
-    double s = 0.0;
-    for (int k = i + 1 + threadIdx.x; k < M; k += blockDim.x) s = fma(G[(size_t)k * M + i], y[k], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (l == 0) part[w] = s;
+  __syncthreads();
+  for (int i = M - 1; i >= 0; --i) {  // backward: G^T x = y; row i of G gives column i of G^T
+    if ((i & (blockDim.x - 1)) == threadIdx.x) v[i] = v[i] / G[(size_t)i * M + i];  // x_i
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int v = 0; v < 8; ++v) t += part[v];
-      y[i] = (y[i] - t) / G[(size_t)i * M + i];
-    }
-    __syncthreads();
+    const double xi = v[i];
+    for (int k = threadIdx.x; k < i; k += blockDim.x) v[k] = fma(-G[(size_t)i * M + k], xi, v[k]);
   }
-  for (int i = threadIdx.x; i < M; i += blockDim.x) x[i] = y[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) x[i] = v[i];
 }
 
 __global__ void fit_chi2_kernel(const float *__restrict__ C, const float *__restrict__ I, const float *__restrict__ weight,
@@ -420,18 +448,30 @@ __global__ void fit_chi2_kernel(const float *__restrict__ C, const float *__rest
     stamp_pixel(f, stamp_xy, p, x, y);
     if (x >= 0 && x < f.W && y >= 0 && y < f.H) {
       const double xt = norm_coord(x, f.W), yt = norm_coord(y, f.H);
-      double model = 0.0;
-      for (int k = 0; k < f.N; ++k) {
-        double ak = 0.0, xi = 1.0;
+      // the pixel's monomials once (registers: T <= 10), then per stamp its polynomial
+      // a_k = sum_t c[k][t] m_t and the model's term a_k C_k
+      double m[10];
+      {
         int t = 0;
+        double xi = 1.0;
         for (int i = 0; i <= f.d; ++i) {
           double yj = 1.0;
           for (int j = 0; j <= f.d - i; ++j, ++t) {
-            ak = fma(coef[k * f.T + t], xi * yj, ak);
+#pragma unroll
+            for (int u = 0; u < 10; ++u)
+              if (u == t) m[u] = xi * yj;
             yj *= yt;
           }
           xi *= xt;
         }
+      }
+      double model = 0.0;
+      for (int k = 0; k < f.N; ++k) {
+        const double *ck = coef + (size_t)k * f.T;
+        double ak = 0.0;
+#pragma unroll
+        for (int t = 0; t < 10; ++t)
+          if (t < f.T) ak = fma(ck[t], m[t], ak);
         model = fma(ak, (double)C[(size_t)p * f.N + k], model);
       }
       double xi = 1.0;

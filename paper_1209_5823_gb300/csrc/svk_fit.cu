@@ -18,6 +18,8 @@
 //                      pivot is reported in info and the solve is skipped.
 // 5. fit_solve         forward / backward substitution (one CTA).
 // 6. fit_chi2_kernel   chi^2 = sum w (model - I)^2 at the solution, a direct second pass.
+#include <algorithm>
+
 #include "svk_common.cuh"
 #include "svk_internal.h"
 
@@ -25,7 +27,7 @@ namespace svk {
 namespace {
 
 constexpr int kMaxMu = 28;  // monomials of degree <= 6
-constexpr int kChunk = 32;  // pixels staged per step in the moment kernel
+constexpr int kChunk = 64;  // pixels staged per step in the moment kernel
 
 __host__ __device__ inline int mono_index(int i, int j, int D) {  // (i outer, j inner)
   return i * (D + 1) - i * (i - 1) / 2 + j;
@@ -127,21 +129,41 @@ __global__ void __launch_bounds__(kCkThreads) fit_ck_kernel(const float *__restr
 // (e1 <= e2).  Thread = one column pair; CTA = one pixel range x one pair tile.  Pixels
 // outside the frame, or outside the rows [r0, r1) the buffers hold, add nothing.
 // The monomials mu = xt^i yt^j factor by rows: consecutive stamp pixels of one frame row
-// share yt, so each thread sums R_i = sum w E xt^i over the pixels of the current row
-// (D + 1 multiply-adds per pixel) and adds R_i yt^j into the (i, j) moments when the row
-// changes (once per run of pixels): about D + 2 FP64 operations per pixel and pair instead
-// of the n_mu + 1 of forming every moment at every pixel.  The accumulators are indexed
-// for the largest degree (kMaxDeg) so that they stay in registers.
+// share yt, so each thread sums R_i = sum w E xt^i over the pixels of the current row and
+// adds R_i yt^j into the (i, j) moments (FP64) when the row changes (once per run of at
+// most a stamp width of pixels).  The short row sums run on the FP32 pipe in double-float
+// arithmetic (value = hi + lo, about 48 significant bits; GB300's FP64 rate is about
+// 1/60 of its FP32 rate): E_e1 E_e2 is a product of two float32 values, exact as hi + lo
+// with one FMA (Dekker/Knuth two-product), w xt^i is split into hi + lo once per pixel,
+// and each row sum adds its terms with an error-free two-sum (Knuth), the rounding errors
+// gathered in the lo part.  The row sums, converted to FP64, enter the FP64 moments.
+// The accumulators are indexed for the largest degree (kMaxDeg) so that they stay in
+// registers.
 constexpr int kMaxDeg = 6;  // moment degree 2 max(d, bd)
 __host__ __device__ constexpr int idx6(int i, int j) { return i * (kMaxDeg + 1) - i * (i - 1) / 2 + j; }
+
+// (h, l) += (eh + el) (wh + wl), the el wl term (about 2^-48 of the product) dropped
+__device__ __forceinline__ void df_madd(float &h, float &l, float eh, float el, float wh, float wl) {
+  const float th = eh * wh;
+  float tl = fmaf(eh, wh, -th);
+  tl = fmaf(eh, wl, tl);
+  tl = fmaf(el, wh, tl);
+  const float sum = h + th;           // two-sum of h and th
+  const float bv = sum - h;
+  const float err = (h - (sum - bv)) + (th - bv);
+  l += err + tl;
+  h = sum;
+}
 
 __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__ C, const float *__restrict__ I,
                                                        const float *__restrict__ weight, const int *stamp_xy, FitDims f,
                                                        int px_per_cta, double *__restrict__ S) {
-  __shared__ double Es[kChunk][66];           // extended columns of the staged pixels (NE <= 66), widened once
-  __shared__ double WX[kChunk][kMaxDeg + 1];  // w xt^i (zero for i > D)
+  __shared__ float Es[kChunk][66];            // extended columns of the staged pixels (NE <= 66)
+  __shared__ float WXh[kChunk][kMaxDeg + 1];  // w xt^i = hi + lo (zero for i > D)
+  __shared__ float WXl[kChunk][kMaxDeg + 1];
   __shared__ double Yt[kChunk];               // yt of the pixel's row
   __shared__ int Yv[kChunk];                  // its frame row, -1 for a pixel that adds nothing
+  __shared__ int Ix[kChunk];                  // offset of its I value, -1 outside
   const int npairs = f.NE * (f.NE + 1) / 2;
   const int pair = blockIdx.y * blockDim.x + threadIdx.x;
   int e1 = 0, e2 = 0;
@@ -154,14 +176,21 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
     }
     e2 = e1 + rem;
   }
-  double acc[kMaxMu], rr[kMaxDeg + 1];
+  double acc[kMaxMu];
+  float rh[kMaxDeg + 1], rl[kMaxDeg + 1];  // the current row's sums, double-float
 #pragma unroll
   for (int m = 0; m < kMaxMu; ++m) acc[m] = 0.0;
 #pragma unroll
-  for (int i = 0; i <= kMaxDeg; ++i) rr[i] = 0.0;
+  for (int i = 0; i <= kMaxDeg; ++i) rh[i] = rl[i] = 0.0f;
   int cur_y = -1;
   double cur_yt = 0.0;
   auto flush = [&]() {  // the current row's sums into the moments
+    double rr[kMaxDeg + 1];
+#pragma unroll
+    for (int i = 0; i <= kMaxDeg; ++i) {
+      rr[i] = (double)rh[i] + (double)rl[i];
+      rh[i] = rl[i] = 0.0f;
+    }
     double yj = 1.0;
 #pragma unroll
     for (int j = 0; j <= kMaxDeg; ++j) {
@@ -169,36 +198,21 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
       for (int i = 0; i + j <= kMaxDeg; ++i) acc[idx6(i, j)] = fma(rr[i], yj, acc[idx6(i, j)]);
       yj *= cur_yt;
     }
-#pragma unroll
-    for (int i = 0; i <= kMaxDeg; ++i) rr[i] = 0.0;
   };
   const int p0 = blockIdx.x * px_per_cta, p1 = min(f.P, p0 + px_per_cta);
   for (int pc = p0; pc < p1; pc += kChunk) {
     __syncthreads();
-    for (int i = threadIdx.x; i < kChunk * f.NE; i += blockDim.x) {
-      const int q = i / f.NE, e = i % f.NE, p = pc + q;
-      float v = 0.0f;
-      if (p < p1) {
-        int x, y;
-        stamp_pixel(f, stamp_xy, p, x, y);
-        const bool inside = x >= 0 && x < f.W && y >= f.r0 && y < f.r1;
-        if (inside) {
-          if (e < f.N) v = C[(size_t)p * f.N + e];
-          else if (e == f.N) v = I[(size_t)(y - f.r0) * f.pitch + x];
-          else v = 1.0f;
-        }
-      }
-      Es[q][e] = (double)v;
-    }
+    // per pixel once: position, weight and monomial factors; then the columns
     for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
       const int p = pc + q;
       double w = 0.0, xt = 0.0, yt = 0.0;
-      int yv = -1;
+      int yv = -1, ix = -1;
       if (p < p1) {
         int x, y;
         stamp_pixel(f, stamp_xy, p, x, y);
         if (x >= 0 && x < f.W && y >= f.r0 && y < f.r1) {
-          w = weight ? (double)weight[(size_t)(y - f.r0) * f.pitch + x] : 1.0;
+          ix = (y - f.r0) * f.pitch + x;
+          w = weight ? (double)weight[ix] : 1.0;
           xt = norm_coord(x, f.W);
           yt = norm_coord(y, f.H);
           yv = y;
@@ -206,11 +220,26 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
       }
       double v = w;
       for (int i = 0; i <= kMaxDeg; ++i) {
-        WX[q][i] = i <= f.D ? v : 0.0;
+        const double wx = i <= f.D ? v : 0.0;
+        const float hi = (float)wx;
+        WXh[q][i] = hi;
+        WXl[q][i] = (float)(wx - (double)hi);
         v *= xt;
       }
       Yt[q] = yt;
       Yv[q] = yv;
+      Ix[q] = ix;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kChunk * f.NE; i += blockDim.x) {
+      const int q = i / f.NE, e = i % f.NE, ix = Ix[q];
+      float v = 0.0f;
+      if (ix >= 0) {
+        if (e < f.N) v = C[(size_t)(pc + q) * f.N + e];
+        else if (e == f.N) v = I[ix];
+        else v = 1.0f;
+      }
+      Es[q][e] = v;
     }
     __syncthreads();
     if (pair < npairs) {
@@ -223,10 +252,11 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
           cur_y = yv;
           cur_yt = Yt[q];
         }
-        const double e = Es[q][e1] * Es[q][e2];
+        const float a = Es[q][e1], c = Es[q][e2];
+        const float eh = a * c, el = fmaf(a, c, -eh);  // E_e1 E_e2 = eh + el exactly
 #pragma unroll
         for (int i = 0; i <= kMaxDeg; ++i)
-          if (i <= f.D) rr[i] = fma(e, WX[q][i], rr[i]);
+          if (i <= f.D) df_madd(rh[i], rl[i], eh, el, WXh[q][i], WXl[q][i]);
       }
     }
   }
@@ -553,10 +583,20 @@ int queue_moments(const float *R, const float *I, const float *weight, const Fit
   if ((e = cudaFuncSetAttribute(fit_ck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ck_smem)) != cudaSuccess)
     return cuda_status(e, "fit_ck_kernel smem attribute");
   fit_ck_kernel<<<dim3(f.n_stamps, (f.S + ty - 1) / ty), kCkThreads, ck_smem, s>>>(R, basis, stamp_xy, f, ty, C);
+  // Tiles of column pairs as even as whole warps allow (1326 pairs: 6 tiles of 224, not
+  // 5 of 256 and one of 46), and pixel ranges in a multiple of the SM count, so the CTAs
+  // (two per SM at this kernel's registers) fill whole waves.
   const int npairs = f.NE * (f.NE + 1) / 2;
-  const int px_per_cta = 4096;
-  dim3 ggrid((f.P + px_per_cta - 1) / px_per_cta, (npairs + 255) / 256);
-  fit_gram_kernel<<<ggrid, 256, 0, s>>>(C, I, weight, stamp_xy, f, px_per_cta, S);
+  const int ytiles = (npairs + 255) / 256;
+  const int tpb = ((npairs + ytiles - 1) / ytiles + 31) / 32 * 32;
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int xtiles = (int)(((long long)f.P + (long long)nsm * 4096 - 1) / ((long long)nsm * 4096)) * nsm;
+  xtiles = std::min(xtiles, (f.P + kChunk - 1) / kChunk);
+  const int px_per_cta = (f.P + xtiles - 1) / xtiles;
+  dim3 ggrid((f.P + px_per_cta - 1) / px_per_cta, ytiles);
+  fit_gram_kernel<<<ggrid, tpb, 0, s>>>(C, I, weight, stamp_xy, f, px_per_cta, S);
   return cuda_status(cudaGetLastError(), "fit moment kernels launch");
 }
 

@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(kCkThreads) fit_ck_kernel(const float *__restr
 // The accumulators are indexed for the largest degree (kMaxDeg) so that they stay in
 // registers.
 constexpr int kMaxDeg = 6;  // moment degree 2 max(d, bd)
+constexpr int kGramThreads = 224;  // column pairs per CTA at most (1326 pairs = 6 x 221)
 __host__ __device__ constexpr int idx6(int i, int j) { return i * (kMaxDeg + 1) - i * (i - 1) / 2 + j; }
 
 // (h, l) += (eh + el) (wh + wl), the el wl term (about 2^-48 of the product) dropped
@@ -155,7 +156,7 @@ __device__ __forceinline__ void df_madd(float &h, float &l, float eh, float el, 
   h = sum;
 }
 
-__global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__ C, const float *__restrict__ I,
+__global__ void __launch_bounds__(kGramThreads) fit_gram_kernel(const float *__restrict__ C, const float *__restrict__ I,
                                                        const float *__restrict__ weight, const int *stamp_xy, FitDims f,
                                                        int px_per_cta, double *__restrict__ S) {
   __shared__ float Es[kChunk][66];            // extended columns of the staged pixels (NE <= 66)
@@ -164,6 +165,9 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
   __shared__ double Yt[kChunk];               // yt of the pixel's row
   __shared__ int Yv[kChunk];                  // its frame row, -1 for a pixel that adds nothing
   __shared__ int Ix[kChunk];                  // offset of its I value, -1 outside
+  // the thread's FP64 moments (touched once per row): [moment][thread], so a warp's
+  // accesses are consecutive
+  __shared__ double accS[kMaxMu][kGramThreads];
   const int npairs = f.NE * (f.NE + 1) / 2;
   const int pair = blockIdx.y * blockDim.x + threadIdx.x;
   int e1 = 0, e2 = 0;
@@ -176,26 +180,28 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
     }
     e2 = e1 + rem;
   }
-  double acc[kMaxMu];
-  float rh[kMaxDeg + 1], rl[kMaxDeg + 1];  // the current row's sums, double-float
+  double *acc = &accS[0][threadIdx.x];  // moment m at acc[m * kGramThreads]
 #pragma unroll
-  for (int m = 0; m < kMaxMu; ++m) acc[m] = 0.0;
+  for (int m = 0; m < kMaxMu; ++m) acc[m * kGramThreads] = 0.0;
+  // the current row's sums, double-float, in two independent sets (alternate pixels of a
+  // row), so consecutive pixels' additions do not wait for each other
+  float rh0[kMaxDeg + 1], rl0[kMaxDeg + 1], rh1[kMaxDeg + 1], rl1[kMaxDeg + 1];
 #pragma unroll
-  for (int i = 0; i <= kMaxDeg; ++i) rh[i] = rl[i] = 0.0f;
+  for (int i = 0; i <= kMaxDeg; ++i) rh0[i] = rl0[i] = rh1[i] = rl1[i] = 0.0f;
   int cur_y = -1;
   double cur_yt = 0.0;
   auto flush = [&]() {  // the current row's sums into the moments
     double rr[kMaxDeg + 1];
 #pragma unroll
     for (int i = 0; i <= kMaxDeg; ++i) {
-      rr[i] = (double)rh[i] + (double)rl[i];
-      rh[i] = rl[i] = 0.0f;
+      rr[i] = ((double)rh0[i] + (double)rl0[i]) + ((double)rh1[i] + (double)rl1[i]);
+      rh0[i] = rl0[i] = rh1[i] = rl1[i] = 0.0f;
     }
     double yj = 1.0;
 #pragma unroll
     for (int j = 0; j <= kMaxDeg; ++j) {
 #pragma unroll
-      for (int i = 0; i + j <= kMaxDeg; ++i) acc[idx6(i, j)] = fma(rr[i], yj, acc[idx6(i, j)]);
+      for (int i = 0; i + j <= kMaxDeg; ++i) acc[idx6(i, j) * kGramThreads] = fma(rr[i], yj, acc[idx6(i, j) * kGramThreads]);
       yj *= cur_yt;
     }
   };
@@ -244,9 +250,12 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
     __syncthreads();
     if (pair < npairs) {
       const int nq = min(kChunk, p1 - pc);
-      for (int q = 0; q < nq; ++q) {
+      for (int q = 0; q < nq;) {
         const int yv = Yv[q];  // the same for every thread: uniform branches
-        if (yv < 0) continue;
+        if (yv < 0) {
+          ++q;
+          continue;
+        }
         if (yv != cur_y) {
           flush();
           cur_y = yv;
@@ -254,9 +263,22 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
         }
         const float a = Es[q][e1], c = Es[q][e2];
         const float eh = a * c, el = fmaf(a, c, -eh);  // E_e1 E_e2 = eh + el exactly
+        if (q + 1 < nq && Yv[q + 1] == yv) {  // two pixels of the row, one per set
+          const float a1 = Es[q + 1][e1], c1 = Es[q + 1][e2];
+          const float eh1 = a1 * c1, el1 = fmaf(a1, c1, -eh1);
 #pragma unroll
-        for (int i = 0; i <= kMaxDeg; ++i)
-          if (i <= f.D) df_madd(rh[i], rl[i], eh, el, WXh[q][i], WXl[q][i]);
+          for (int i = 0; i <= kMaxDeg; ++i)
+            if (i <= f.D) {
+              df_madd(rh0[i], rl0[i], eh, el, WXh[q][i], WXl[q][i]);
+              df_madd(rh1[i], rl1[i], eh1, el1, WXh[q + 1][i], WXl[q + 1][i]);
+            }
+          q += 2;
+        } else {
+#pragma unroll
+          for (int i = 0; i <= kMaxDeg; ++i)
+            if (i <= f.D) df_madd(rh0[i], rl0[i], eh, el, WXh[q][i], WXl[q][i]);
+          ++q;
+        }
       }
     }
   }
@@ -267,7 +289,7 @@ __global__ void __launch_bounds__(256) fit_gram_kernel(const float *__restrict__
     for (int i = 0; i <= kMaxDeg; ++i)
 #pragma unroll
       for (int j = 0; i + j <= kMaxDeg; ++j)
-        if (i + j <= f.D) atomicAdd(dst + mono_index(i, j, f.D), acc[idx6(i, j)]);
+        if (i + j <= f.D) atomicAdd(dst + mono_index(i, j, f.D), acc[idx6(i, j) * kGramThreads]);
   }
 }
 
@@ -583,11 +605,10 @@ int queue_moments(const float *R, const float *I, const float *weight, const Fit
   if ((e = cudaFuncSetAttribute(fit_ck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ck_smem)) != cudaSuccess)
     return cuda_status(e, "fit_ck_kernel smem attribute");
   fit_ck_kernel<<<dim3(f.n_stamps, (f.S + ty - 1) / ty), kCkThreads, ck_smem, s>>>(R, basis, stamp_xy, f, ty, C);
-  // Tiles of column pairs as even as whole warps allow (1326 pairs: 6 tiles of 224, not
-  // 5 of 256 and one of 46), and pixel ranges in a multiple of the SM count, so the CTAs
-  // (two per SM at this kernel's registers) fill whole waves.
+  // Tiles of column pairs as even as whole warps allow (1326 pairs: 6 tiles of 224), and
+  // pixel ranges in a multiple of the SM count, so the CTAs fill whole waves.
   const int npairs = f.NE * (f.NE + 1) / 2;
-  const int ytiles = (npairs + 255) / 256;
+  const int ytiles = (npairs + kGramThreads - 1) / kGramThreads;
   const int tpb = ((npairs + ytiles - 1) / ytiles + 31) / 32 * 32;
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);

@@ -356,7 +356,7 @@ __device__ double block_sum_d(double v, double *red) {
 //   chol_diag_kernel    factors the kPanel x kPanel diagonal block in shared memory (one
 //                       CTA) and reports the first non-positive pivot in *info;
 //   chol_trsm_kernel    A[i][panel] <- A[i][panel] L_pp^-T for the rows below (one row per
-//                       thread);
+//                       warp);
 //   chol_update_kernel  A[i][j] -= sum_{k in panel} A[i][k] A[j][k] for the trailing lower
 //                       triangle (32 x 32 tiles).
 // Every kernel returns at once when *info >= 0 (an earlier pivot failed).
@@ -398,8 +398,12 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(double *A, int M, int p,
   if (threadIdx.x == 0 && fail >= 0) *info = fail;
 }
 
-__global__ void __launch_bounds__(64) chol_trsm_kernel(double *A, int M, int p, const int *info) {
+__global__ void __launch_bounds__(256) chol_trsm_kernel(double *A, int M, int p, const int *info) {
+  // One warp per row below the panel: x L_pp^T = a, column by column; lane l holds x[l] and
+  // x[l + 32].  Step c: the owner's entry times 1 / L_cc is x_c (broadcast by a shuffle),
+  // then every later entry k takes its -x_c L_kc (a multiply-add per lane, no reduction).
   __shared__ double Ls[kPanel][kPanel + 1];
+  __shared__ double inv[kPanel];
   if (*info >= 0) return;
   const int b = min(kPanel, M - p);
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
@@ -407,24 +411,24 @@ __global__ void __launch_bounds__(64) chol_trsm_kernel(double *A, int M, int p, 
     Ls[r][c] = c <= r ? A[(size_t)(p + r) * M + p + c] : 0.0;
   }
   __syncthreads();
-  const int i = p + b + blockIdx.x * blockDim.x + threadIdx.x;
+  for (int c = threadIdx.x; c < b; c += blockDim.x) inv[c] = 1.0 / Ls[c][c];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int i = p + b + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= M) return;
-  double x[kPanel];
   double *row = A + (size_t)i * M + p;
-#pragma unroll
-  for (int c = 0; c < kPanel; ++c) x[c] = c < b ? row[c] : 0.0;
-#pragma unroll
-  for (int c = 0; c < kPanel; ++c) {
-    if (c < b) {
-      double s = x[c];
-#pragma unroll
-      for (int k = 0; k < c; ++k) s = fma(-x[k], Ls[c][k], s);
-      x[c] = s / Ls[c][c];
+  double v0 = lane < b ? row[lane] : 0.0, v1 = lane + 32 < b ? row[lane + 32] : 0.0;
+  for (int c = 0; c < b; ++c) {
+    const double xc = __shfl_sync(0xffffffffu, c < 32 ? v0 : v1, c & 31) * inv[c];
+    if (lane == (c & 31)) {
+      if (c < 32) v0 = xc;
+      else v1 = xc;
     }
+    if (lane > c && lane < b) v0 = fma(-xc, Ls[lane][c], v0);
+    if (lane + 32 > c && lane + 32 < b) v1 = fma(-xc, Ls[lane + 32][c], v1);
   }
-#pragma unroll
-  for (int c = 0; c < kPanel; ++c)
-    if (c < b) row[c] = x[c];
+  if (lane < b) row[lane] = v0;
+  if (lane + 32 < b) row[lane + 32] = v1;
 }
 
 __global__ void __launch_bounds__(256) chol_update_kernel(double *A, int M, int p, const int *info) {
@@ -463,17 +467,21 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double *A, int M, int 
 __global__ void __launch_bounds__(256) fit_solve_kernel(const double *G, const double *b, int M, const int *info,
                                                         double *x) {
   // Column-oriented substitutions: thread t owns the entries k = t, t + 256, ..., so each
-  // step is one division by the owner of entry i, one barrier, and one multiply-add per
-  // owned entry (no reduction tree on the critical path).
-  __shared__ double v[1024];
+  // step is one multiply by the owner of entry i (the diagonal's reciprocals formed in
+  // parallel first: FP64 division is slow on this part), one barrier, and one multiply-add
+  // per owned entry (no reduction tree on the critical path).
+  __shared__ double v[1024], inv[1024];
   if (*info >= 0) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) x[i] = 0.0;
     return;
   }
-  for (int k = threadIdx.x; k < M; k += blockDim.x) v[k] = b[k];
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    v[k] = b[k];
+    inv[k] = 1.0 / G[(size_t)k * M + k];
+  }
   __syncthreads();
   for (int i = 0; i < M; ++i) {  // forward: G y = b; v[k] = b_k - sum_{j < i} G_kj y_j
-    if ((i & (blockDim.x - 1)) == threadIdx.x) v[i] = v[i] / G[(size_t)i * M + i];  // y_i
+    if ((i & (blockDim.x - 1)) == threadIdx.x) v[i] *= inv[i];  // y_i
     __syncthreads();
     const double yi = v[i];
     for (int k = threadIdx.x; k < M; k += blockDim.x)
@@ -481,7 +489,7 @@ __global__ void __launch_bounds__(256) fit_solve_kernel(const double *G, const d
   }
   __syncthreads();
   for (int i = M - 1; i >= 0; --i) {  // backward: G^T x = y; row i of G gives column i of G^T
-    if ((i & (blockDim.x - 1)) == threadIdx.x) v[i] = v[i] / G[(size_t)i * M + i];  // x_i
+    if ((i & (blockDim.x - 1)) == threadIdx.x) v[i] *= inv[i];  // x_i
     __syncthreads();
     const double xi = v[i];
     for (int k = threadIdx.x; k < i; k += blockDim.x) v[k] = fma(-G[(size_t)i * M + k], xi, v[k]);
@@ -631,7 +639,7 @@ int queue_solve(const double *S, const FitDims &f, double *A, double *b, double 
     chol_diag_kernel<<<1, 256, 0, s>>>(A, f.M, p, info);
     const int rest = f.M - p - kPanel;
     if (rest > 0) {
-      chol_trsm_kernel<<<(rest + 63) / 64, 64, 0, s>>>(A, f.M, p, info);
+      chol_trsm_kernel<<<(rest + 7) / 8, 256, 0, s>>>(A, f.M, p, info);
       const int nt = (rest + 31) / 32;
       chol_update_kernel<<<nt * (nt + 1) / 2, 256, 0, s>>>(A, f.M, p, info);
     }

@@ -130,15 +130,15 @@ __global__ void __launch_bounds__(kCkThreads) fit_ck_kernel(const float *__restr
 // outside the frame, or outside the rows [r0, r1) the buffers hold, add nothing.
 // The monomials mu = xt^i yt^j factor by rows: consecutive stamp pixels of one frame row
 // share yt, so each thread sums R_i = sum w E xt^i over the pixels of the current row and
-// adds R_i yt^j into the (i, j) moments (FP64) when the row changes (once per run of at
-// most a stamp width of pixels).  The short row sums run on the FP32 pipe in double-float
-// arithmetic (value = hi + lo, about 48 significant bits; GB300's FP64 rate is about
-// 1/60 of its FP32 rate): E_e1 E_e2 is a product of two float32 values, exact as hi + lo
-// with one FMA (Dekker/Knuth two-product), w xt^i is split into hi + lo once per pixel,
-// and each row sum adds its terms with an error-free two-sum (Knuth), the rounding errors
-// gathered in the lo part.  The row sums, converted to FP64, enter the FP64 moments.
-// The accumulators are indexed for the largest degree (kMaxDeg) so that they stay in
-// registers.
+// adds R_i yt^j into the (i, j) moments when the row changes (once per run of at most a
+// stamp width of pixels).  Everything runs on the FP32 pipe in double-float arithmetic
+// (value = hi + lo, about 48 significant bits; GB300's FP64 rate is about 1/60 of its
+// FP32 rate): E_e1 E_e2 is a product of two float32 values, exact as hi + lo with one FMA
+// (Dekker/Knuth two-product); w xt^i and yt are split into hi + lo once per pixel; every
+// addition is an error-free two-sum (Knuth), the rounding errors gathered in the lo part.
+// Each CTA's moments (sums over a few dozen rows) are converted to FP64 for the atomic
+// additions across CTAs.  The row sums are indexed for the largest degree (kMaxDeg) so
+// that they stay in registers; the moments, touched once per row, sit in shared memory.
 constexpr int kMaxDeg = 6;  // moment degree 2 max(d, bd)
 constexpr int kGramThreads = 224;  // column pairs per CTA at most (1326 pairs = 6 x 221)
 __host__ __device__ constexpr int idx6(int i, int j) { return i * (kMaxDeg + 1) - i * (i - 1) / 2 + j; }
@@ -162,12 +162,12 @@ __global__ void __launch_bounds__(kGramThreads) fit_gram_kernel(const float *__r
   __shared__ float Es[kChunk][66];            // extended columns of the staged pixels (NE <= 66)
   __shared__ float WXh[kChunk][kMaxDeg + 1];  // w xt^i = hi + lo (zero for i > D)
   __shared__ float WXl[kChunk][kMaxDeg + 1];
-  __shared__ double Yt[kChunk];               // yt of the pixel's row
+  __shared__ float Yth[kChunk], Ytl[kChunk];  // yt of the pixel's row, hi + lo
   __shared__ int Yv[kChunk];                  // its frame row, -1 for a pixel that adds nothing
   __shared__ int Ix[kChunk];                  // offset of its I value, -1 outside
-  // the thread's FP64 moments (touched once per row): [moment][thread], so a warp's
-  // accesses are consecutive
-  __shared__ double accS[kMaxMu][kGramThreads];
+  // the thread's moments, double-float (touched once per row): [moment][thread], so a
+  // warp's accesses are consecutive
+  __shared__ float accH[kMaxMu][kGramThreads], accL[kMaxMu][kGramThreads];
   const int npairs = f.NE * (f.NE + 1) / 2;
   const int pair = blockIdx.y * blockDim.x + threadIdx.x;
   int e1 = 0, e2 = 0;
@@ -180,29 +180,41 @@ __global__ void __launch_bounds__(kGramThreads) fit_gram_kernel(const float *__r
     }
     e2 = e1 + rem;
   }
-  double *acc = &accS[0][threadIdx.x];  // moment m at acc[m * kGramThreads]
+  float *aH = &accH[0][threadIdx.x], *aL = &accL[0][threadIdx.x];  // moment m at [m * kGramThreads]
 #pragma unroll
-  for (int m = 0; m < kMaxMu; ++m) acc[m * kGramThreads] = 0.0;
+  for (int m = 0; m < kMaxMu; ++m) aH[m * kGramThreads] = aL[m * kGramThreads] = 0.0f;
   // the current row's sums, double-float, in two independent sets (alternate pixels of a
   // row), so consecutive pixels' additions do not wait for each other
   float rh0[kMaxDeg + 1], rl0[kMaxDeg + 1], rh1[kMaxDeg + 1], rl1[kMaxDeg + 1];
 #pragma unroll
   for (int i = 0; i <= kMaxDeg; ++i) rh0[i] = rl0[i] = rh1[i] = rl1[i] = 0.0f;
   int cur_y = -1;
-  double cur_yt = 0.0;
-  auto flush = [&]() {  // the current row's sums into the moments
-    double rr[kMaxDeg + 1];
+  float cur_yh = 0.0f, cur_yl = 0.0f;
+  auto flush = [&]() {  // the current row's sums R_i into the moments: M_ij += R_i yt^j
+    float rh[kMaxDeg + 1], rl[kMaxDeg + 1];
 #pragma unroll
-    for (int i = 0; i <= kMaxDeg; ++i) {
-      rr[i] = ((double)rh0[i] + (double)rl0[i]) + ((double)rh1[i] + (double)rl1[i]);
+    for (int i = 0; i <= kMaxDeg; ++i) {  // the two sets added (two-sum), renormalised
+      const float sum = rh0[i] + rh1[i], bv = sum - rh0[i];
+      const float lo = ((rh0[i] - (sum - bv)) + (rh1[i] - bv)) + (rl0[i] + rl1[i]);
+      rh[i] = sum + lo;
+      rl[i] = lo - (rh[i] - sum);
       rh0[i] = rl0[i] = rh1[i] = rl1[i] = 0.0f;
     }
-    double yj = 1.0;
+    float yh = 1.0f, yl = 0.0f;  // yt^j, double-float
 #pragma unroll
     for (int j = 0; j <= kMaxDeg; ++j) {
 #pragma unroll
-      for (int i = 0; i + j <= kMaxDeg; ++i) acc[idx6(i, j) * kGramThreads] = fma(rr[i], yj, acc[idx6(i, j) * kGramThreads]);
-      yj *= cur_yt;
+      for (int i = 0; i + j <= kMaxDeg; ++i) {
+        const int m = idx6(i, j) * kGramThreads;
+        float h = aH[m], l = aL[m];
+        df_madd(h, l, rh[i], rl[i], yh, yl);
+        aH[m] = h;
+        aL[m] = l;
+      }
+      const float ph = yh * cur_yh;  // yt^(j+1) = yt^j yt
+      const float pl = fmaf(yh, cur_yl, fmaf(yl, cur_yh, fmaf(yh, cur_yh, -ph)));
+      yh = ph + pl;
+      yl = pl - (yh - ph);
     }
   };
   const int p0 = blockIdx.x * px_per_cta, p1 = min(f.P, p0 + px_per_cta);
@@ -232,7 +244,8 @@ __global__ void __launch_bounds__(kGramThreads) fit_gram_kernel(const float *__r
         WXl[q][i] = (float)(wx - (double)hi);
         v *= xt;
       }
-      Yt[q] = yt;
+      Yth[q] = (float)yt;
+      Ytl[q] = (float)(yt - (double)(float)yt);
       Yv[q] = yv;
       Ix[q] = ix;
     }
@@ -259,7 +272,8 @@ __global__ void __launch_bounds__(kGramThreads) fit_gram_kernel(const float *__r
         if (yv != cur_y) {
           flush();
           cur_y = yv;
-          cur_yt = Yt[q];
+          cur_yh = Yth[q];
+          cur_yl = Ytl[q];
         }
         const float a = Es[q][e1], c = Es[q][e2];
         const float eh = a * c, el = fmaf(a, c, -eh);  // E_e1 E_e2 = eh + el exactly
@@ -289,7 +303,9 @@ __global__ void __launch_bounds__(kGramThreads) fit_gram_kernel(const float *__r
     for (int i = 0; i <= kMaxDeg; ++i)
 #pragma unroll
       for (int j = 0; i + j <= kMaxDeg; ++j)
-        if (i + j <= f.D) atomicAdd(dst + mono_index(i, j, f.D), acc[idx6(i, j) * kGramThreads]);
+        if (i + j <= f.D)
+          atomicAdd(dst + mono_index(i, j, f.D),
+                    (double)aH[idx6(i, j) * kGramThreads] + (double)aL[idx6(i, j) * kGramThreads]);
   }
 }
 

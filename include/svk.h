@@ -360,8 +360,12 @@ SVK_API size_t svk_fit_workspace_size(int n_stamps, int stamp_size, int N, int L
  * on Eq. 1 over isolated-star stamps, K decomposed on the basis).  Model at a stamp
  * pixel:  sum_k sum_t c[k][t] m_t(xt,yt) C_k(x,y) + sum_j g_j m_j(xt,yt),  with
  * C_k = R (x) B_k (computed in FP32 on the device); minimise
- * sum w (model - I)^2 through the normal equations A c = b, accumulated in FP64, and
- * solve them by an FP64 Cholesky factorisation on the device.
+ * sum w (model - I)^2 through the normal equations A c = b, and solve them by an FP64
+ * Cholesky factorisation on the device.  A and b are FP64; their sums over the stamp
+ * pixels are taken in double-float arithmetic (pairs of float32, about 48 significant
+ * bits, error-free two-sums) within each run of pixels a CTA handles and in FP64 across
+ * them (the order of the FP64 additions across CTAs is not fixed, so repeated calls may
+ * differ in the last bits).
  *   R, I       device float32 [H][pitch] (same pitch)
  *   stamp_xy   device int32 [n_stamps][2] = (x, y) centres; stamps are
  *              stamp_size x stamp_size (odd); pixels outside the frame are skipped

@@ -408,24 +408,32 @@ def _precision_table(svk, torch, dev):
     ref = oracle.convolve_points(R.astype(np.float64), B.cpu().numpy().astype(np.float64), c.astype(np.float64),
                                  spec.degree, px, py)
     scale = np.abs(ref).max()
+    # the same basis rounded so that 1024 B is FP16-exact, for SVK_PREC_FP16X2 (its errors
+    # against the oracle on that rounded basis)
+    Br = svk.svk_round_basis_fp16(B.clone())
+    ref_r = oracle.convolve_points(R.astype(np.float64), Br.cpu().numpy().astype(np.float64), c.astype(np.float64),
+                                   spec.degree, px, py)
     out = {"workload": spec.name, "sample": "2000 random pixels + 200 brightest star centres", "paths": {}}
-    for name, method, prec in (("basis_bf16x3", svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3),
-                               ("basis_fp16x3", svk.SVK_METHOD_BASIS, svk.SVK_PREC_FP16X3),
-                               ("basis_bf16", svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16),
-                               ("direct_fp32", svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32)):
-        o = svk.svk_convolve(Rt, B, ct, spec.degree, method=method, precision=prec)
+    for name, method, prec, Bx, refx in (("basis_bf16x3", svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16X3, B, ref),
+                                         ("basis_fp16x3", svk.SVK_METHOD_BASIS, svk.SVK_PREC_FP16X3, B, ref),
+                                         ("basis_bf16", svk.SVK_METHOD_BASIS, svk.SVK_PREC_BF16, B, ref),
+                                         ("basis_fp16x2_fp16_exact_basis", svk.SVK_METHOD_BASIS,
+                                          svk.SVK_PREC_FP16X2, Br, ref_r),
+                                         ("direct_fp32", svk.SVK_METHOD_DIRECT, svk.SVK_PREC_FP32, B, ref)):
+        B_, ref_ = Bx, refx
+        o = svk.svk_convolve(Rt, B_, ct, spec.degree, method=method, precision=prec)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 3
         e0.record()
         for _ in range(reps):
-            svk.svk_convolve(Rt, B, ct, spec.degree, method=method, precision=prec, out=o)
+            svk.svk_convolve(Rt, B_, ct, spec.degree, method=method, precision=prec, out=o)
         e1.record()
         torch.cuda.synchronize()
         got = o[torch.from_numpy(py).to(dev).long(), torch.from_numpy(px).to(dev).long()].double().cpu().numpy()
         ms = e0.elapsed_time(e1) / reps
-        out["paths"][name] = {"max_rel_err": float(np.abs(got - ref).max() / scale),
-                              "rms_rel_err": float(np.sqrt(((got - ref) ** 2).mean()) / scale),
+        out["paths"][name] = {"max_rel_err": float(np.abs(got - ref_).max() / scale),
+                              "rms_rel_err": float(np.sqrt(((got - ref_) ** 2).mean()) / scale),
                               "ms": ms, "mpixel_s": spec.W * spec.H / (ms / 1e3) / 1e6}
     return out
 

@@ -84,6 +84,11 @@ extern "C" {
                           /* FP32 accumulation                                            */
 #define SVK_PREC_FP16X3 2 /* BASIS, TFORM: the same split in FP16 (power-of-two prescaled) */
 #define SVK_PREC_BF16 3   /* BASIS, TFORM: plain BF16 operands, FP32 accumulation (one MMA) */
+#define SVK_PREC_FP16X2 4 /* BASIS: R split hi + lo in FP16 (power-of-two prescaled), the     */
+                          /* basis taken as FP16-exact (its values x 1024 rounded to FP16),  */
+                          /* hi*B + lo*B: two MMAs; FP32-level accuracy for a basis that      */
+                          /* svk_round_basis_fp16 made exact (otherwise the convolution is    */
+                          /* with that rounding of the basis)                                  */
 
 #define SVK_EDGE_ZERO 0 /* R is zero outside the frame (the only mode)                    */
 
@@ -115,6 +120,16 @@ SVK_API int svk_gauss_basis_count(int n_gauss, const int *deg);
  */
 SVK_API int svk_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg,
                     int normalize, float *basis_out, int *n_basis_out, void *stream);
+
+/*
+ * Round n basis values in place so that 1024 b is exactly an FP16 value:
+ * b <- fp16_rn(1024 b) / 1024.  A basis so rounded is a basis like any other (any B_k
+ * defines Eq. 2's kernel family); SVK_PREC_FP16X2 then multiplies it without a low part
+ * (two MMAs per K step instead of three) at the accuracy of the x3 splits.  Values beyond
+ * +-64 saturate to FP16's range.  basis: device float32, n >= 0.  Asynchronous on
+ * `stream`; SVK_ERR_ARG on a NULL pointer with n > 0.
+ */
+SVK_API int svk_round_basis_fp16(float *basis, long long n, void *stream);
 
 /*
  * Bytes of device workspace that svk_convolve / svk_difference need for this request.

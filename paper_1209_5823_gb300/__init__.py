@@ -32,6 +32,7 @@ SVK_PREC_FP32 = 0
 SVK_PREC_BF16X3 = 1
 SVK_PREC_FP16X3 = 2
 SVK_PREC_BF16 = 3
+SVK_PREC_FP16X2 = 4
 SVK_FMA_FP32 = 0
 SVK_FMA_FP64 = 1
 SVK_FMA_FP32X2 = 2
@@ -49,7 +50,7 @@ EXPORTS = (
     "svk_device_status", "svk_fit_moments_count", "svk_fit_moments_workspace_size", "svk_fit_moments",
     "svk_fit_solve_workspace_size", "svk_fit_solve", "svk_band_rows", "svk_difference_rows", "svk_cut_stamps",
     "svk_stamp_residual_workspace_size", "svk_stamp_residual", "svk_cnn_standardise", "svk_cnn_draw_batch",
-    "svk_gather_rows", "svk_cnn_step_end", "svk_tc_plan", "svk_set_plan",
+    "svk_gather_rows", "svk_cnn_step_end", "svk_tc_plan", "svk_set_plan", "svk_round_basis_fp16",
 )
 
 
@@ -97,6 +98,7 @@ def load_library(path: str | None = None):
         "svk_autotune": (i, [i, i, i, i, i, i, vp, vp, vp]),
         "svk_tc_plan": (i, [i, i, i, vp, vp, vp]),
         "svk_set_plan": (i, [i, i, i, i, i, i]),
+        "svk_round_basis_fp16": (i, [vp, ctypes.c_longlong, vp]),
         "svk_cnn_param_count": (i, [i]),
         "svk_cnn_workspace_size": (sz, [i, i]),
         "svk_cnn_forward": (i, [vp, vp, i, i, vp, vp, sz, vp]),
@@ -196,6 +198,12 @@ def svk_build_basis(kind: int, L: int, sigma=(0.7, 1.5, 2.5), deg=(6, 4, 2), nor
     _check(lib.svk_build_basis(int(kind), int(L), len(sigma), sg, dg, int(normalize), _ptr(out),
                                ctypes.byref(nb), _stream(stream)))
     return out
+
+
+def svk_round_basis_fp16(basis, stream=None):
+    """Round a device float32 basis in place so that 1024 b is FP16-exact (SVK_PREC_FP16X2)."""
+    _check(load_library().svk_round_basis_fp16(_ptr(basis), int(basis.numel()), _stream(stream)))
+    return basis
 
 
 def svk_workspace_size(method: int, precision: int, W: int, H: int, N: int, L: int, degree: int) -> int:

@@ -199,7 +199,8 @@ static int check_conv_args(const float *R, int pitch_R, const float *I, int pitc
     if (precision != SVK_PREC_FP32)
       return set_error(SVK_ERR_UNSUPPORTED, "the direct method computes in FP32 only");
   } else if (method == SVK_METHOD_BASIS || method == SVK_METHOD_TFORM) {
-    const bool tc = precision == SVK_PREC_BF16X3 || precision == SVK_PREC_FP16X3 || precision == SVK_PREC_BF16;
+    const bool tc = precision == SVK_PREC_BF16X3 || precision == SVK_PREC_FP16X3 || precision == SVK_PREC_BF16 ||
+                    (precision == SVK_PREC_FP16X2 && method == SVK_METHOD_BASIS);
     if (!tc && !(method == SVK_METHOD_TFORM && precision == SVK_PREC_FP32))
       return set_error(SVK_ERR_UNSUPPORTED, "precision %d not built for method %d", precision, method);
     if (method == SVK_METHOD_BASIS && N > 256)
@@ -249,6 +250,12 @@ int svk_gauss_basis_count(int n_gauss, const int *deg) {
     n += (deg[g] + 1) * (deg[g] + 2) / 2;
   }
   return n;
+}
+
+int svk_round_basis_fp16(float *basis, long long n, void *stream) {
+  CallRange range("svk_round_basis_fp16");
+  if (n < 0 || (n > 0 && !basis)) return set_error(SVK_ERR_ARG, "bad basis rounding arguments");
+  return launch_round_basis_fp16(basis, n, static_cast<cudaStream_t>(stream));
 }
 
 int svk_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg, int normalize,
@@ -335,7 +342,8 @@ int svk_difference_batch(const svk_frame *frames, int n_frames, int precision, v
 
 int svk_autotune(int N, int L, int degree, int precision, int W, int H, int *G_out, int *stages_out, void *stream) {
   CallRange range("svk_autotune");
-  if (precision != SVK_PREC_BF16X3 && precision != SVK_PREC_FP16X3 && precision != SVK_PREC_BF16)
+  if (precision != SVK_PREC_BF16X3 && precision != SVK_PREC_FP16X3 && precision != SVK_PREC_BF16 &&
+      precision != SVK_PREC_FP16X2)
     return set_error(SVK_ERR_UNSUPPORTED, "autotune covers the tensor-core precisions only");
   if (N < 1 || N > 256 || L < 1 || L > 31 || (L % 2) == 0 || degree < 0 || degree > 3 || W < 1 || H < 1 ||
       W > 65535 || H > 65535)
@@ -344,7 +352,8 @@ int svk_autotune(int N, int L, int degree, int precision, int W, int H, int *G_o
 }
 
 static bool tc_plan_args(int N, int L, int precision) {
-  return (precision == SVK_PREC_BF16X3 || precision == SVK_PREC_FP16X3 || precision == SVK_PREC_BF16) && N >= 1 &&
+  return (precision == SVK_PREC_BF16X3 || precision == SVK_PREC_FP16X3 || precision == SVK_PREC_BF16 ||
+          precision == SVK_PREC_FP16X2) && N >= 1 &&
          N <= 256 && L >= 1 && L <= 31 && (L % 2) == 1;
 }
 

@@ -2,6 +2,8 @@
 // arithmetic, float32 storage): the Gaussian function basis (Gaussian x monomial
 // stamps, Alard & Lupton) and the Dirac delta function basis (one stamp per kernel
 // pixel, Miller et al.), Sec. 2.
+#include <cuda_fp16.h>
+
 #include "svk_common.cuh"
 #include "svk_internal.h"
 
@@ -55,7 +57,7 @@ __device__ void block_sum2(double &a, double &b, double (*scratch)[32]) {
   __syncthreads();  // the scratch is reused by the next call
 }
 
-constexpr int kBasisThreads = 256, kBasisPer = 4;  // 4 x 256 >= 31 x 31 taps
+constexpr int kBasisThreads = 256, kBasisPer = 16;  // 16 x 256 >= 63 x 63 taps
 
 // One CTA per stamp k, the stamp's taps in registers (tap i = threadIdx.x + 256 j).  For
 // SVK_NORM_ALARD every CTA also evaluates B_0 (its sum normalises B_0 and makes the
@@ -83,12 +85,12 @@ __global__ void __launch_bounds__(kBasisThreads) gauss_basis_kernel(int L, Gauss
   }
   // the stamps are separable, exp(-(u^2 + v^2) / s) u^p v^q = fu(u) fv(v): one FP64 exp per
   // offset and Gaussian, and per tap two multiplies (FP64 is GB300's slow pipe)
-  __shared__ double e0[32], fu[32], fv[32];
-  if (threadIdx.x < 64) {  // warp 0 the first Gaussian, warp 1 the stamp's (in parallel)
-    const int t = threadIdx.x & 31;
+  __shared__ double e0[64], fu[64], fv[64];
+  if (threadIdx.x < 128) {  // warps 0-1 the first Gaussian, warps 2-3 the stamp's (in parallel)
+    const int t = threadIdx.x & 63;
     if (t < L) {
       const double u = (double)(t - h);
-      if (threadIdx.x < 32) {
+      if (threadIdx.x < 64) {
         e0[t] = exp(-(u * u) / (2.0 * gl.sigma[0] * gl.sigma[0]));
       } else {
         const double eg = exp(-(u * u) / (2.0 * gl.sigma[g] * gl.sigma[g]));
@@ -157,7 +159,20 @@ __global__ void delta_basis_kernel(int L, int normalize, float *out) {
   }
 }
 
+// v <- fp16(1024 v) / 1024 (round to nearest even), so that 1024 v is exactly an FP16 value.
+__global__ void round_basis_fp16_kernel(float *__restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = __half2float(__float2half_rn(b[i] * 1024.0f)) * (1.0f / 1024.0f);
+}
+
 }  // namespace
+
+int launch_round_basis_fp16(float *basis, long long n, cudaStream_t s) {
+  if (n <= 0) return SVK_OK;
+  const long long blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  round_basis_fp16_kernel<<<(unsigned)blocks, 256, 0, s>>>(basis, n);
+  return cuda_status(cudaGetLastError(), "round_basis_fp16_kernel launch");
+}
 
 int launch_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg, int normalize,
                        float *basis_out, int N, cudaStream_t s) {
@@ -173,7 +188,7 @@ int launch_build_basis(int kind, int L, int n_gauss, const double *sigma, const 
     gl.sigma[g] = sigma[g];
     gl.deg[g] = deg[g];
   }
-  if (L * L > kBasisThreads * kBasisPer) return set_error(SVK_ERR_ARG, "basis size %d above %d taps", L, 31);
+  if (L * L > kBasisThreads * kBasisPer) return set_error(SVK_ERR_ARG, "basis size %d above %d taps", L, 63);
   return cuda_status(launch_dependent(gauss_basis_kernel, N, kBasisThreads, 0, s, L, gl, normalize, basis_out),
                      "gauss_basis_kernel launch");
 }

@@ -30,6 +30,7 @@ int launch_tform_fp32(const float *R, int pitch_R, const float *I, int pitch_I, 
                       int r_begin = 0, int r_end = -1);
 
 // Basis tabulation (svk_basis.cu).
+int launch_round_basis_fp16(float *basis, long long n, cudaStream_t s);
 int launch_build_basis(int kind, int L, int n_gauss, const double *sigma, const int *deg,
                        int normalize, float *basis_out, int N, cudaStream_t s);
 

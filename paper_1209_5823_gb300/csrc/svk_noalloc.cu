@@ -41,7 +41,8 @@ extern "C" int svk_difference_noalloc(const float *R, int pitch_R, const float *
                                       const float *basis, int N, int L, const float *coeffs, int degree,
                                       int precision, int edge, float *D, int pitch_D, void *stream) {
   using namespace svk;
-  if (precision != SVK_PREC_BF16X3 && precision != SVK_PREC_FP16X3 && precision != SVK_PREC_BF16)
+  if (precision != SVK_PREC_BF16X3 && precision != SVK_PREC_FP16X3 && precision != SVK_PREC_BF16 &&
+      precision != SVK_PREC_FP16X2)
     return set_error(SVK_ERR_UNSUPPORTED, "svk_difference_noalloc runs the tensor-core basis form only (precision %d)",
                      precision);
   const size_t need = svk_workspace_size(SVK_METHOD_BASIS, precision, W, H, N, L, degree);

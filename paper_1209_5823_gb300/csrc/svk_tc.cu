@@ -93,7 +93,9 @@ struct Plan {
   size_t stage_bytes;      // one pipeline stage (hi [+ lo] Hankel tiles)
   int seglen;              // staged row length (elements) = 8 S + 8
   int NP, nrows;           // table slices, table rows per K group (global tables)
-  int parts;               // 2 for split precision, 1 for plain BF16
+  int parts;               // Hankel (A) parts: 2 for split precisions, 1 for plain BF16
+  int tparts;              // basis-table (B) parts: 2 for the x3 splits, 1 for plain BF16
+                           // and FP16x2 (whose basis is taken as FP16-exact)
   int NS;                  // Hankel pipeline stages
   int rpg, epg;            // rows per `full` group (NS / 2: two groups in flight, NS / 4 when
                            // streamed) and per `empty` group (4, or rpg when smaller)
@@ -122,6 +124,7 @@ static bool make_plan(int N, int L, int prec, int G, int NS, int stream, Plan *p
   q.rpg = stream ? NS / 4 : NS / 2;
   q.epg = q.rpg < 4 ? q.rpg : 4;
   q.parts = (prec == SVK_PREC_BF16) ? 1 : 2;
+  q.tparts = (prec == SVK_PREC_BF16 || prec == SVK_PREC_FP16X2) ? 1 : 2;
   q.nmma = rup(G * N, 16);
   if (q.nmma > 256 || q.nmma < 16) return false;
   q.nG = (L + 7) / 8;
@@ -158,7 +161,7 @@ static bool make_plan(int N, int L, int prec, int G, int NS, int stream, Plan *p
   q.off_tab_hi = o;
   o += q.smem_tab_bytes;
   q.off_tab_lo = o;
-  if (q.parts == 2) o += q.smem_tab_bytes;
+  if (q.tparts == 2) o += q.smem_tab_bytes;
   o = rup((int)o, 128);
   q.off_stage = o;
   o += (size_t)NS * q.stage_bytes;
@@ -215,7 +218,7 @@ __device__ __forceinline__ bool epi_bar_any(bool v) {
 // Split x into hi + lo 16-bit floats; returns the two bit patterns.
 template <int PREC>
 __device__ __forceinline__ void split16(float x, uint16_t &hi, uint16_t &lo) {
-  if (PREC == SVK_PREC_FP16X3) {
+  if (PREC == SVK_PREC_FP16X3 || PREC == SVK_PREC_FP16X2) {
     const __half a = __float2half_rn(x);
     const __half b = __float2half_rn(x - __half2float(a));
     hi = __half_as_ushort(a);
@@ -361,8 +364,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_basis_kernel(const __grid_constant__ FrameSet fs, const Plan pl, uint32_t *status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  // Hankel (A) parts and basis-table (B) parts: the x3 splits multiply Ah Bh + Ah Bl + Al Bh,
+  // FP16x2 (an FP16-exact basis) Ah B + Al B, plain BF16 A B
   constexpr int kParts = (PREC == SVK_PREC_BF16) ? 1 : 2;
-  constexpr int kFmt = (PREC == SVK_PREC_FP16X3) ? 0 : 1;
+  constexpr int kPartsB = (PREC == SVK_PREC_BF16 || PREC == SVK_PREC_FP16X2) ? 1 : 2;
+  constexpr int kFmt = (PREC == SVK_PREC_FP16X3 || PREC == SVK_PREC_FP16X2) ? 0 : 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = pl.N, G = pl.G, h = pl.h, NS = pl.NS;
 
@@ -402,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // the ring starts as zeros: slots a window reads beyond its slices (the MMA columns
     // past G*N, the partner window of an odd last row, whose A tile is zero) always hold
     // finite values
-    for (size_t o = (size_t)threadIdx.x * 16; o < pl.smem_tab_bytes * kParts; o += (size_t)kThreads * 16)
+    for (size_t o = (size_t)threadIdx.x * 16; o < pl.smem_tab_bytes * kPartsB; o += (size_t)kThreads * 16)
       *reinterpret_cast<uint4 *>(sm + pl.off_tab_hi + o) = make_uint4(0u, 0u, 0u, 0u);
     fence_proxy_async_smem();
   }
@@ -521,16 +527,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         // part, and again into the mirror slot; the row's arrival then also waits for those
         // bytes
         const int t = it.r_lo - it.y0 + h + it.i;
-        const int ncopy = t < pl.NP ? kParts * pl.nKG * ((int)stage < pl.M ? 2 : 1) : 0;
+        const int ncopy = t < pl.NP ? kPartsB * pl.nKG * ((int)stage < pl.M ? 2 : 1) : 0;
         if (lane == 0) {
           if (ncopy) mbar_arrive_expect_tx(&full[grp], (uint32_t)(ncopy * N * 16));
           else mbar_arrive(&full[grp]);
         }
         __syncwarp();
         if (lane < ncopy) {
-          const int c = lane % (kParts * pl.nKG), part = c / pl.nKG, kg = c % pl.nKG;
+          const int c = lane % (kPartsB * pl.nKG), part = c / pl.nKG, kg = c % pl.nKG;
           const uint4 *src = (part ? fs.fr[it.f].tab_lo : fs.fr[it.f].tab_hi) + (size_t)kg * pl.nrows + (size_t)t * N;
-          const size_t slot = lane < kParts * pl.nKG ? stage : stage + NS;  // copy 2: the mirror
+          const size_t slot = lane < kPartsB * pl.nKG ? stage : stage + NS;  // copy 2: the mirror
           const size_t dst = (part ? pl.off_tab_lo : pl.off_tab_hi) + ((size_t)kg * pl.srows + slot * N) * 16;
           if (SVK_CHECK(dst + (size_t)N * 16 <= (part ? pl.off_tab_lo : pl.off_tab_hi) + pl.smem_tab_bytes &&
                             (slot + 1) * N <= (size_t)pl.srows && ((size_t)t + 1) * N <= (size_t)pl.nrows,
@@ -583,8 +589,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!mbar_wait_bounded(drain_bar, drain_phase, status)) return false;
             drain_phase ^= 1;
           }
-          mbar_arrive_expect_tx(tab_bar, (uint32_t)(pl.table_bytes * kParts));
-          for (int part = 0; part < kParts; ++part) {
+          mbar_arrive_expect_tx(tab_bar, (uint32_t)(pl.table_bytes * kPartsB));
+          for (int part = 0; part < kPartsB; ++part) {
             const unsigned char *src = reinterpret_cast<const unsigned char *>(part ? fd.tab_lo : fd.tab_hi);
             unsigned char *dst = sm + (part ? pl.off_tab_lo : pl.off_tab_hi);
             for (size_t o = 0; o < pl.table_bytes; o += 32768) {
@@ -601,9 +607,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         // basis window starts at descriptor b
         auto row_mmas = [&](uint64_t a, uint64_t b, int nsteps) {
           for (int ks = 0; ks < nsteps; ++ks, a += oKs_a, b += oKs_b) {
-            if (kParts == 2) {  // A hi read once for its two products
+            if (kParts == 2 && kPartsB == 2) {  // A hi read once for its two products
               umma_f16_fill(d_tmem, a, b, idesc, acc);
               umma_f16_lastuse(d_tmem, a, b + oBl, idesc, 1);
+              umma_f16(d_tmem, a + oAl, b, idesc, 1);
+            } else if (kParts == 2) {  // FP16x2: A hi and lo against the one B
+              umma_f16(d_tmem, a, b, idesc, acc);
               umma_f16(d_tmem, a + oAl, b, idesc, 1);
             } else {
               umma_f16(d_tmem, a, b, idesc, acc);
@@ -672,9 +681,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (pl.nG & 1) {
                 const uint64_t ax = dAx + (uint64_t)sa * oStage;
                 const uint64_t bx = bx0 + (uint64_t)(STREAM ? sa : (uint32_t)i) * oSlice;
-                if (kParts == 2) {
+                if (kParts == 2 && kPartsB == 2) {
                   umma_f16_fill(d_tmem, ax, bx, idesc, acc);
                   umma_f16_lastuse(d_tmem, ax, bx + oBl, idesc, 1);
+                  umma_f16(d_tmem, ax + oAl, bx, idesc, 1);
+                } else if (kParts == 2) {
+                  umma_f16(d_tmem, ax, bx, idesc, acc);
                   umma_f16(d_tmem, ax + oAl, bx, idesc, 1);
                 } else {
                   umma_f16(d_tmem, ax, bx, idesc, acc);
@@ -910,7 +922,7 @@ bool plan_for(int N, int L, int prec, Plan *pl) {
 void prec_scales(int prec, float &bscale, float &rscale) {
   bscale = 1.0f;
   rscale = 1.0f;
-  if (prec == SVK_PREC_FP16X3) {
+  if (prec == SVK_PREC_FP16X3 || prec == SVK_PREC_FP16X2) {
     bscale = 1024.0f;       // basis values are O(1e-3 .. 1)
     rscale = 1.0f / 16.0f;  // counts up to ~1e6 stay below 65504
   }
@@ -971,7 +983,7 @@ int launch_set_prec(const svk_frame *fr, int n, const Plan &pl, unsigned char *w
       uint4 *tl = reinterpret_cast<uint4 *>(ws + (size_t)ntab * pl.table_bytes * 2 + pl.table_bytes);
       if (prep) {
         const cudaError_t pe = launch_dependent(tc_prep_table<P>, (nrow_items + 255) / 256, 256, 0, s, fr[i].basis, pl,
-                                                bscale, th, pl.parts == 2 ? tl : nullptr);
+                                                bscale, th, pl.tparts == 2 ? tl : nullptr);
         if (pe != cudaSuccess) return cuda_status(pe, "tc_prep_table launch");
       }
       d.tab_hi = th;
@@ -1006,6 +1018,7 @@ int launch_set(const svk_frame *fr, int n, int prec, const Plan &pl, void *ws, s
   unsigned char *w = static_cast<unsigned char *>(ws);
   if (prec == SVK_PREC_BF16X3) return launch_set_prec<SVK_PREC_BF16X3>(fr, n, pl, w, rows, held, prep, s);
   if (prec == SVK_PREC_FP16X3) return launch_set_prec<SVK_PREC_FP16X3>(fr, n, pl, w, rows, held, prep, s);
+  if (prec == SVK_PREC_FP16X2) return launch_set_prec<SVK_PREC_FP16X2>(fr, n, pl, w, rows, held, prep, s);
   return launch_set_prec<SVK_PREC_BF16>(fr, n, pl, w, rows, held, prep, s);
 }
 

@@ -71,7 +71,8 @@ def test_direct_delta_basis_identity_and_dfb():
 
 @pytest.mark.parametrize("kind,norm,L", [
     (svk.SVK_BASIS_GAUSS, svk.SVK_NORM_ALARD, 11), (svk.SVK_BASIS_GAUSS, svk.SVK_NORM_NONE, 19),
-    (svk.SVK_BASIS_GAUSS, svk.SVK_NORM_ALARD, 31), (svk.SVK_BASIS_DELTA, svk.SVK_NORM_ALARD, 5),
+    (svk.SVK_BASIS_GAUSS, svk.SVK_NORM_ALARD, 31), (svk.SVK_BASIS_GAUSS, svk.SVK_NORM_ALARD, 63),
+    (svk.SVK_BASIS_GAUSS, svk.SVK_NORM_NONE, 1), (svk.SVK_BASIS_DELTA, svk.SVK_NORM_ALARD, 5),
     (svk.SVK_BASIS_DELTA, svk.SVK_NORM_NONE, 3),
 ])
 def test_build_basis_matches_oracle(kind, norm, L):

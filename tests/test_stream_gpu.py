@@ -1,7 +1,8 @@
 """Tensor-core plans whose basis slices stream through a shared-memory ring (large kernels,
 where resident tables leave room only for narrow blocks): parity with the FP64 oracle,
 bit-identity with the resident-table plan of the same block height, row bands, batches of
-frames with distinct bases, and the plan rules of svk_set_plan."""
+frames with distinct bases, and the plan rules of svk_set_plan.  Also the FP16x2 precision
+(an FP16-exact basis, two MMAs per K step) on resident and streamed plans."""
 import numpy as np
 import pytest
 import torch
@@ -19,7 +20,7 @@ def _default_plans():
     """Plans are per process: every test leaves the defaults behind."""
     yield
     for L in range(1, 32, 2):
-        for p in (svk.SVK_PREC_BF16X3, svk.SVK_PREC_FP16X3, svk.SVK_PREC_BF16):
+        for p in (svk.SVK_PREC_BF16X3, svk.SVK_PREC_FP16X3, svk.SVK_PREC_BF16, svk.SVK_PREC_FP16X2):
             svk.svk_set_plan(49, L, p, 0)
 
 
@@ -165,3 +166,61 @@ def test_set_plan_rules():
     assert svk.svk_band_rows(svk.SVK_METHOD_BASIS, p, 49, 31, 2) == 2
     svk.svk_set_plan(49, 31, p, 0)
     assert svk.svk_tc_plan(49, 31, p) == (5, 16, 1)
+
+
+# ---------------------------------------------------------------- FP16x2 (FP16-exact basis)
+
+def test_round_basis_fp16_is_exact_and_idempotent():
+    B = svk.svk_build_basis(svk.SVK_BASIS_GAUSS, 19)
+    Br = svk.svk_round_basis_fp16(B.clone())
+    v = Br.cpu().numpy().astype(np.float64) * 1024.0
+    assert np.array_equal(v.astype(np.float16).astype(np.float64), v)  # 1024 b is an FP16 value
+    assert np.abs(Br.cpu().numpy() - B.cpu().numpy()).max() <= 2.0 ** -11 * np.abs(B.cpu().numpy()).max()
+    assert torch.equal(svk.svk_round_basis_fp16(Br.clone()), Br)
+
+
+@pytest.mark.parametrize("W,H,L,d", [
+    (300, 77, 19, 2),    # paired last tap groups (3 groups)
+    (260, 40, 25, 3),    # streamed slices
+    (130, 23, 31, 2),
+    (129, 37, 15, 1),
+    (47, 38, 7, 3),
+    (1, 1, 11, 2),
+])
+def test_fp16x2_matches_oracle_on_a_rounded_basis(W, H, L, d):
+    R, I, B, c = _frame(W, H, L, d, 17)
+    B = svk.svk_round_basis_fp16(B)
+    D = svk.svk_difference(_dev(R), _dev(I), B, _dev(c), d, method=svk.SVK_METHOD_BASIS,
+                           precision=svk.SVK_PREC_FP16X2)
+    ref = oracle_conv(R, B.cpu().numpy(), c, d)
+    assert rel_err(D.cpu().numpy() + I, ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("L,G", [(31, 5), (25, 5), (21, 4)])
+def test_fp16x2_streamed_equals_resident(L, G):
+    p = svk.SVK_PREC_FP16X2
+    R, _, B, c = _frame(220, 41, L, 2, 23)
+    B = svk.svk_round_basis_fp16(B)
+    res = {}
+    for sm, stages in ((1, [16]), (0, [16, 8, 4])):
+        for st in stages:
+            try:
+                svk.svk_set_plan(49, L, p, G, st, sm)
+                break
+            except svk.SvkError:
+                continue
+        else:
+            continue  # no resident plan of this height: the streamed one alone is checked below
+        res[sm] = _conv(R, B, c, 2, p)
+    if 0 in res:
+        assert torch.equal(res[0], res[1])
+    ref = oracle_conv(R, B.cpu().numpy(), c, 2)
+    assert rel_err(res[1].cpu().numpy(), ref) <= TOL_FP32
+
+
+def test_fp16x2_is_the_basis_form_only():
+    R, _, B, c = _frame(64, 32, 11, 1, 29)
+    with pytest.raises(svk.SvkError):
+        svk.svk_convolve(_dev(R), B, _dev(c), 1, method=svk.SVK_METHOD_TFORM, precision=svk.SVK_PREC_FP16X2)
+    with pytest.raises(svk.SvkError):
+        svk.svk_convolve(_dev(R), B, _dev(c), 1, method=svk.SVK_METHOD_DIRECT, precision=svk.SVK_PREC_FP16X2)

@@ -13,15 +13,17 @@
 // Four steps on the stream, none of which needs the host to know a count:
 //   1. peak_kernel     one thread per pixel: peak map (1 byte/pixel), selectable-position
 //                      candidates appended to a list (order of arrival is irrelevant);
-//   2. isolate_kernel  one thread per candidate: scans its window of the peak map and
-//                      appends a 64-bit sort key (inverted order-preserving bits of R(p),
-//                      then the index) for each isolated one;
+//   2. isolate_kernel  one warp per candidate: its lanes scan the window of the peak map
+//                      and it appends a 64-bit sort key (inverted order-preserving bits of
+//                      R(p), then the index) for each isolated one;
 //   3. bitonic sort of the keys, padded to the next power of two of their count read on
 //      the device; the host launches the passes for the largest possible count and the
 //      passes beyond the actual count return at once;
 //   4. output_kernel   the first max_stamps keys -> (x, y), and the counts.
 // Capacity: two peaks are never 8-neighbours, so a frame holds at most
-// ceil(W/2) * ceil(H/2) peaks; every buffer is sized for that.
+// ceil(W/2) * ceil(H/2) peaks; every buffer is sized for that.  The kernels are launched as
+// programmatic dependents, so the sort's passes beyond the actual count, which return at
+// once, cost little more than their launch.
 #include "svk_common.cuh"
 #include "svk_internal.h"
 
@@ -71,6 +73,8 @@ __device__ __forceinline__ uint32_t dev_next_pow2(uint32_t v) {
 
 __global__ void peak_kernel(const float *__restrict__ R, int W, int H, int pitch, float sky, float thr, float sat,
                             int margin, unsigned char *__restrict__ pk, int *__restrict__ cand, int *cnt) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= W) return;
   const float v = R[(size_t)y * pitch + x];
@@ -97,30 +101,44 @@ __device__ __forceinline__ unsigned long long sort_key(float v, uint32_t idx) {
 __global__ void isolate_kernel(const float *__restrict__ R, int W, int H, int pitch, float sky, float frac, int rad,
                                const unsigned char *__restrict__ pk, const int *__restrict__ cand, int *cnt,
                                unsigned long long *__restrict__ keys) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const int n = cnt[kCand];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  // one warp per candidate: the lanes take the window's pixels in row-major order (runs of
+  // a row are consecutive bytes of the peak map), the warp stops at the first hit
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
     const int idx = cand[i], y = idx / W, x = idx % W;
     const float v = R[(size_t)y * pitch + x];
     const float bar = __fmul_rn(frac, __fsub_rn(v, sky));
-    bool iso = true;
     const int y0 = max(0, y - rad), y1 = min(H - 1, y + rad), x0 = max(0, x - rad), x1 = min(W - 1, x + rad);
-    for (int yy = y0; yy <= y1 && iso; ++yy)
-      for (int xx = x0; xx <= x1; ++xx)
-        if (pk[(size_t)yy * W + xx] && (yy != y || xx != x) && __fsub_rn(R[(size_t)yy * pitch + xx], sky) >= bar) {
-          iso = false;
-          break;
-        }
-    if (iso) keys[atomicAdd(&cnt[kSel], 1)] = sort_key(v, (uint32_t)idx);
+    const int wx = x1 - x0 + 1, total = (y1 - y0 + 1) * wx;
+    bool hit = false;
+    for (int e0 = 0; e0 < total; e0 += 32) {
+      const int e = e0 + lane;
+      if (e < total) {
+        const int yy = y0 + e / wx, xx = x0 + e % wx;
+        hit = pk[(size_t)yy * W + xx] && (yy != y || xx != x) && __fsub_rn(R[(size_t)yy * pitch + xx], sky) >= bar;
+      }
+      if (__any_sync(0xffffffffu, hit)) break;
+    }
+    const bool any_hit = __any_sync(0xffffffffu, hit);  // every lane votes
+    if (lane == 0 && !any_hit) keys[atomicAdd(&cnt[kSel], 1)] = sort_key(v, (uint32_t)idx);
+    __syncwarp();
   }
 }
 
 __global__ void pad_kernel(unsigned long long *keys, const int *cnt) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const uint32_t n = (uint32_t)cnt[kSel], np2 = dev_next_pow2(n);
   for (uint32_t i = n + blockIdx.x * blockDim.x + threadIdx.x; i < np2; i += gridDim.x * blockDim.x) keys[i] = ~0ull;
 }
 
 // One compare-exchange stage (k, j) of the bitonic network over the padded keys.
 __global__ void bitonic_global(unsigned long long *keys, const int *cnt, uint32_t k, uint32_t j) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const uint32_t np2 = dev_next_pow2((uint32_t)cnt[kSel]);
   if (k > np2) return;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np2; i += gridDim.x * blockDim.x) {
@@ -139,6 +157,8 @@ __global__ void bitonic_global(unsigned long long *keys, const int *cnt, uint32_
 // holds one kLocalSort-key segment (pairs (i, i ^ j) never leave it for j < kLocalSort).
 __global__ void __launch_bounds__(kLocalSort / 2) bitonic_local(unsigned long long *keys, const int *cnt,
                                                                 uint32_t k_lo, uint32_t k_hi) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   __shared__ unsigned long long s[kLocalSort];
   const uint32_t np2 = dev_next_pow2((uint32_t)cnt[kSel]);
   const uint32_t base = blockIdx.x * kLocalSort;
@@ -166,6 +186,8 @@ __global__ void __launch_bounds__(kLocalSort / 2) bitonic_local(unsigned long lo
 
 __global__ void output_kernel(const unsigned long long *keys, const int *cnt, int W, int max_stamps, int *xy,
                               int *counts) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
   const int n = min(cnt[kSel], max_stamps);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t idx = (uint32_t)(keys[i] & 0xFFFFFFFFull);
@@ -194,18 +216,22 @@ int launch_select(const float *R, int W, int H, int pitch, float sky, float thre
   unsigned long long *keys = reinterpret_cast<unsigned long long *>(w + l.off_keys);
   int st = cuda_status(cudaMemsetAsync(cnt, 0, 16, s), "clear counters");
   if (st != SVK_OK) return st;
-  peak_kernel<<<dim3((W + 255) / 256, H), 256, 0, s>>>(R, W, H, pitch, sky, threshold, saturation, margin, pk, cand,
-                                                       cnt);
-  isolate_kernel<<<kGridStride, 256, 0, s>>>(R, W, H, pitch, sky, iso_frac, iso_radius, pk, cand, cnt, keys);
-  pad_kernel<<<kGridStride, 256, 0, s>>>(keys, cnt);
+  cudaError_t e = launch_dependent(peak_kernel, dim3((W + 255) / 256, H), 256, 0, s, R, W, H, pitch, sky, threshold,
+                                   saturation, margin, pk, cand, cnt);
+  if (e == cudaSuccess)
+    e = launch_dependent(isolate_kernel, kGridStride, 256, 0, s, R, W, H, pitch, sky, iso_frac, iso_radius, pk, cand,
+                         cnt, keys);
+  if (e == cudaSuccess) e = launch_dependent(pad_kernel, kGridStride, 256, 0, s, keys, cnt);
   const uint32_t P = (uint32_t)l.cap_p2, nloc = P / kLocalSort;
-  bitonic_local<<<nloc, kLocalSort / 2, 0, s>>>(keys, cnt, 2u, (uint32_t)kLocalSort);
-  for (uint32_t k = 2 * kLocalSort; k <= P; k <<= 1) {
-    for (uint32_t j = k >> 1; j >= (uint32_t)kLocalSort; j >>= 1) bitonic_global<<<kGridStride, 256, 0, s>>>(keys, cnt, k, j);
-    bitonic_local<<<nloc, kLocalSort / 2, 0, s>>>(keys, cnt, k, k);
+  if (e == cudaSuccess) e = launch_dependent(bitonic_local, nloc, kLocalSort / 2, 0, s, keys, cnt, 2u, (uint32_t)kLocalSort);
+  for (uint32_t k = 2 * kLocalSort; k <= P && e == cudaSuccess; k <<= 1) {
+    for (uint32_t j = k >> 1; j >= (uint32_t)kLocalSort && e == cudaSuccess; j >>= 1)
+      e = launch_dependent(bitonic_global, kGridStride, 256, 0, s, keys, cnt, k, j);
+    if (e == cudaSuccess) e = launch_dependent(bitonic_local, nloc, kLocalSort / 2, 0, s, keys, cnt, k, k);
   }
-  output_kernel<<<kGridStride / 8, 256, 0, s>>>(keys, cnt, W, max_stamps, xy, counts);
-  return cuda_status(cudaGetLastError(), "stamp selection launch");
+  if (e == cudaSuccess)
+    e = launch_dependent(output_kernel, kGridStride / 8, 256, 0, s, keys, (const int *)cnt, W, max_stamps, xy, counts);
+  return cuda_status(e, "stamp selection launch");
 }
 
 }  // namespace svk

@@ -479,6 +479,12 @@ def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=10000):
     gbuf, lbuf = torch.empty_like(net.params), torch.empty(1, device=dev)
     grad_ms = _time(torch, lambda: svk.svk_cnn_gradient(net.params, xb, zb, grad=gbuf, loss=lbuf, workspace=net.ws),
                     reps=50)
+    # the same call at batch 1024 (the network's kernels are latency-bound at 256)
+    xb4 = x[:1024].contiguous()
+    zb4 = svk.svk_cnn_standardise(a[:1024], prior.mean(dev), prior.std(dev))
+    ws4 = torch.empty(svk.svk_cnn_workspace_size(1024, N), dtype=torch.uint8, device=dev)
+    grad1024_ms = _time(torch, lambda: svk.svk_cnn_gradient(net.params, xb4, zb4, grad=gbuf, loss=lbuf, workspace=ws4),
+                        reps=20)
     xf = x[:4096].contiguous()
     fout = torch.empty((4096, N), device=dev)
     fws = torch.empty(svk.svk_cnn_workspace_size(4096, N), dtype=torch.uint8, device=dev)
@@ -542,6 +548,8 @@ def _learned(svk, torch, dev, R, I_unused, n_pairs=100000, steps=10000):
             "forward_stamps_per_s": 4096 / (1e-3 * fwd_ms), "flop_per_stamp_forward": f_fwd,
             "flop_per_stamp_train": f_train, "gradient_tflops": f_train * net.batch / (1e-3 * grad_ms) / 1e12,
             "forward_tflops": f_fwd * 4096 / (1e-3 * fwd_ms) / 1e12,
+            "gradient_1024_ms": grad1024_ms,
+            "gradient_1024_tflops": f_train * 1024 / (1e-3 * grad1024_ms) / 1e12,
             "loss_first100": float(losses[:100].mean()), "loss_last100": float(losses[-100:].mean()),
             "heldout_mse_std_units": float(err.mean()), "heldout_mse_a0": float(err[0]), "prior_mse_std_units": 1.0,
             "frames": frames, "fallback_rule": fallback_rule}

@@ -356,6 +356,83 @@ __device__ __forceinline__ void slot_dots(const uint32_t (&v)[64], const float *
   }
 }
 
+// The same dot products with one output row's columns spread over four lanes.  The
+// 16x256b TMEM loads start on a multiple of 8 columns, so the row's columns c0 .. c0+N-1
+// are read from ca = c0 rounded down, in NREP = ceil((c0 - ca + N) / 8) repetitions of 8
+// (slot s = column ca + s; the coefficients of stamp k sit at slot k + c0 - ca, zeros
+// elsewhere).  Lane t gets slots 8r + 2(t%4), 8r + 2(t%4) + 1 (r < NREP) of the four
+// pixels t/4 + 8j (j < 4) of its warp's lane quarter, so it reads 2 NREP coefficients per
+// power instead of all 52 (8-byte loads, the warp's four distinct pairs in one wavefront),
+// and the four lanes of a pixel group add their partial sums in two shuffle steps, after
+// which lane t holds the sums of pixel t/4 + 8(t%4).  The pixels come in two halves (TMEM
+// lanes 0..15 and 16..31 of the quarter, pixels j = 2hh, 2hh + 1), one load and wait
+// each, so only one half's columns are live at a time.
+template <int NPOW, int NREP>
+__device__ __forceinline__ void quad_dots(uint32_t ca, bool in_range, const float *ag, int q, float (&s)[4]) {
+  float K[2][NPOW];
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    uint32_t v[4 * NREP];
+    if (in_range) {
+      const uint32_t ta = ca + ((uint32_t)(16 * hh) << 16);
+      tmem_ld256x4(ta, &v[0]);
+      if (NREP == 8) {
+        tmem_ld256x4(ta + 32u, &v[16]);
+      } else {
+        tmem_ld256x2(ta + 32u, &v[16]);
+        tmem_ld256x1(ta + 48u, &v[24]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4 * NREP; ++i) v[i] = 0u;
+    }
+    tmem_ld_wait();
+    uint64_t P[2][NPOW];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int p = 0; p < NPOW; ++p) P[j][p] = 0;
+#pragma unroll
+    for (int r = 0; r < NREP; ++r) {
+      uint64_t A[NPOW];
+#pragma unroll
+      for (int p = 0; p < NPOW; ++p) A[p] = *reinterpret_cast<const uint64_t *>(ag + 64 * p + 8 * r + 2 * q);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint64_t c = f2_pack(__uint_as_float(v[4 * r + 2 * j]), __uint_as_float(v[4 * r + 2 * j + 1]));
+#pragma unroll
+        for (int p = 0; p < NPOW; ++p) P[j][p] = f2_fma(A[p], c, P[j][p]);
+      }
+    }
+    // lanes q and q^1 swap the pixel of this half they do not keep (pixel parity q & 1)
+#pragma unroll
+    for (int p = 0; p < NPOW; ++p) {
+      float l0, u0, l1, u1;
+      f2_unpack(P[0][p], l0, u0);
+      f2_unpack(P[1][p], l1, u1);
+      const float s0 = l0 + u0, s1 = l1 + u1;
+      const float mine = (q & 1) ? s1 : s0, other = (q & 1) ? s0 : s1;
+      K[hh][p] = mine + __shfl_xor_sync(0xffffffffu, other, 1);
+    }
+  }
+  // then lanes q and q^2 (half q >> 1): lane q ends with pixel j = q summed over its lanes
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    s[p] = 0.0f;
+    if (p < NPOW) {
+      const float mine = (q >> 1) ? K[1][p] : K[0][p];
+      const float other = (q >> 1) ? K[0][p] : K[1][p];
+      s[p] = mine + __shfl_xor_sync(0xffffffffu, other, 2);
+    }
+  }
+}
+
+// First column of output row g's accumulators, its offset from the 8-column boundary
+// below, and the 8-column repetitions that cover its N columns from that boundary.
+__host__ __device__ inline int quad_col(int G, int N, int g) { return (G - 1 - g) * N; }
+__host__ __device__ inline int quad_off(int G, int N, int g) { return quad_col(G, N, g) & 7; }
+__host__ __device__ inline int quad_reps(int G, int N, int g) { return (quad_off(G, N, g) + N + 7) >> 3; }
+
 // ----------------------------------------------------------------- main kernel
 // STREAM: the plan streams its basis slices (pl.stream); a template parameter, so the
 // resident-table kernel carries none of the streamed bookkeeping in its issuing loop
@@ -386,6 +463,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   // columns of the next group or the MMA padding, with zero coefficients), when those
   // columns lie inside the accumulator buffer; other stamp counts use four 16-column loads
   const bool exact = N >= 49 && N <= 52 && (G - 1) * N + 52 <= kAccStride;
+  // Streamed plans (whose slice copies add to the shared-memory traffic) with 49..56
+  // stamps whose output rows' column windows (from the 8-column boundary at or below the
+  // row's first column, 7 or 8 repetitions of 8) lie inside the MMA's columns (those past
+  // G*N hold exact zeros, products of the table's zero rows): the four-lane form of the dot
+  // products (quad_dots), a quarter of the coefficient reads for about 45 % more epilogue
+  // instructions.  Measured per 2048^2 frame: 2-4 % faster at L = 25 and 31 (streamed),
+  // 3 % slower at L = 19 with resident tables, where the epilogue warps that share the
+  // MMA-issuing thread's scheduler delay it.
+  bool quad = STREAM && N >= 49 && N <= 56;
+  for (int g = 0; g < G && quad; ++g)
+    quad = (quad_col(G, N, g) & ~7) + 8 * quad_reps(G, N, g) <= pl.nmma;
   int b_begin, b_end;
   cta_block_range(fs, b_begin, b_end);
 
@@ -716,7 +804,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     // output rows g of parity w / 4, so two warps share each scheduler and one's TMEM
     // wait overlaps the other's arithmetic.
     const int et = threadIdx.x;  // 0 .. 255
-    const int m = (warp & 3) * 32 + lane, par = warp >> 2;
+    // m: the pixel (TMEM lane) whose output this thread writes; in the four-lane form the
+    // lane that ends with pixel t/4 + 8(t%4) of the quarter
+    const int m = (warp & 3) * 32 + (quad ? (lane >> 2) + 8 * (lane & 3) : lane), par = warp >> 2;
     const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
     uint32_t blk_seq = 0;
     int f = 0, coef_frame = -1;
@@ -776,8 +866,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           a3 = ck[9];
         }
         *reinterpret_cast<float4 *>(alpha + (size_t)e * 4) = make_float4(a0, a1, a2, a3);
-        if (exact) {  // the same coefficients at slot k
-          float *as = alphaS + (size_t)g * 256 + k;  // [g][power of xt][slot]
+        if (exact || quad) {  // the same coefficients at slot k (four-lane form: k + row offset)
+          float *as = alphaS + (size_t)g * 256 + k + (quad ? quad_off(G, N, g) : 0);  // [g][power of xt][slot]
           as[0] = a0;
           as[64] = a1;
           as[128] = a2;
@@ -824,7 +914,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         // sum_k a_k C_k = sum_i xt^i (sum_k alpha[g][k][i] C_k): four independent dot
         // products over the accumulator columns, then Horner in xt
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        if (fast) {
+        if (quad) {
+          // the row's columns from the 8-column boundary below c0, TMEM lanes 0..15 and
+          // 16..31 of the quarter
+          const float *ag = alphaS + (size_t)g * 256;
+          const int off = quad_off(G, N, g), nrep = quad_reps(G, N, g);
+          const uint32_t ca = c0 - (uint32_t)off;
+          const bool in_range = SVK_CHECK((quad_col(G, N, g) - off) % 8 == 0 && quad_col(G, N, g) - off + 8 * nrep <= pl.nmma &&
+                                              off + N <= 8 * nrep && nrep <= 8,
+                                          status, 4);
+          float sv[4];
+          if (nrep == 8) {
+            if (degree >= 3) quad_dots<4, 8>(ca, in_range, ag, lane & 3, sv);
+            else quad_dots<3, 8>(ca, in_range, ag, lane & 3, sv);  // degree <= 2: no xt^3 term
+          } else {
+            if (degree >= 3) quad_dots<4, 7>(ca, in_range, ag, lane & 3, sv);
+            else quad_dots<3, 7>(ca, in_range, ag, lane & 3, sv);
+          }
+          s0 = sv[0];
+          s1 = sv[1];
+          s2 = sv[2];
+          s3 = sv[3];
+        } else if (fast) {
           // 16 <= N <= 64, one wait for all loads.  Exact slots: columns 0..51.  Otherwise
           // four 16-column loads, the last one moved back to end at column N - 1, zeros at
           // its repeated slots.

@@ -56,6 +56,17 @@ def test_split_precision_matches_oracle(W, H, L, d, N, prec):
 
 
 @pytest.mark.parametrize("prec", SPLIT)
+@pytest.mark.parametrize("N,L,d", [
+    (50, 9, 2),    # 5-row blocks, 52 exact accumulator slots per output row
+    (52, 11, 3),   # 4-row blocks, 52 exact slots
+    (53, 13, 1),   # four 16-column loads per output row
+    (56, 9, 3),
+])
+def test_stamp_counts_50_to_56(N, L, d, prec):
+    assert _run(230, 47, L, d, N, prec, seed=N, kind=svk.SVK_BASIS_DELTA) <= TOL_FP32
+
+
+@pytest.mark.parametrize("prec", SPLIT)
 @pytest.mark.parametrize("N", [100, 121])
 def test_wide_delta_basis(N, prec):
     # 100 / 121 stamps of an 11 x 11 delta basis: 2-row and 1-row blocks

@@ -382,8 +382,9 @@ def _fit_timing(svk, torch, dev, R, I, fp64_peak, reps=3):
             "roofline": {"bound": "latency", "achieved": flop_def / (ms / 1e3) / 1e12,
                          "unit": "TFLOP/s (moments as defined, FP64-equivalent)",
                          "fp64_peak": fp64_peak / 1e12, "vs_fp64_peak": flop_def / (ms / 1e3) / fp64_peak,
-                         "note": "whole fit time (selection excluded); moments by double-float row sums on the "
-                                 "FP32 pipe and FP64 row folds"}}
+                         "note": "whole fit time (selection excluded); moments by double-float row sums and "
+                                 "row folds on the FP32 pipe (FP64 for the sums across CTAs), chi-square pass "
+                                 "in double-float"}}
 
 
 def _precision_table(svk, torch, dev):

@@ -17,7 +17,8 @@
 // 4. chol_*            FP64 blocked Cholesky over the whole GPU; the first non-positive
 //                      pivot is reported in info and the solve is skipped.
 // 5. fit_solve         forward / backward substitution (one CTA).
-// 6. fit_chi2_kernel   chi^2 = sum w (model - I)^2 at the solution, a direct second pass.
+// 6. fit_chi2_kernel   chi^2 = sum w (model - I)^2 at the solution, a direct second pass
+//                      in double-float arithmetic.
 #include <algorithm>
 
 #include "svk_common.cuh"
@@ -379,38 +380,46 @@ __device__ double block_sum_d(double v, double *red) {
 constexpr int kPanel = 64;
 
 __global__ void __launch_bounds__(256) chol_diag_kernel(double *A, int M, int p, int *info) {
+  // Right-looking, one column per step: thread 0 takes the pivot's square root and its
+  // reciprocal (one FP64 division per column, not one per thread), the threads scale the
+  // column, then update the trailing lower triangle on a 16 x 16 thread grid (rows ty + 16a,
+  // columns tx + 16c: no index divisions).
   __shared__ double Ls[kPanel][kPanel + 1];
+  __shared__ double pinv;
   __shared__ int fail;
   if (*info >= 0) return;
   const int b = min(kPanel, M - p);
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int r = e / b, c = e % b;
-    Ls[r][c] = c <= r ? A[(size_t)(p + r) * M + p + c] : 0.0;
-  }
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int r = ty; r < b; r += 16)
+    for (int c = tx; c < b; c += 16) Ls[r][c] = c <= r ? A[(size_t)(p + r) * M + p + c] : 0.0;
   if (threadIdx.x == 0) fail = -1;
   __syncthreads();
   for (int j = 0; j < b; ++j) {
     if (threadIdx.x == 0) {
       const double d = Ls[j][j];
-      if (!(d > 0.0)) fail = p + j;
-      else Ls[j][j] = sqrt(d);
+      if (!(d > 0.0)) {
+        fail = p + j;
+      } else {
+        const double sd = sqrt(d);
+        Ls[j][j] = sd;
+        pinv = 1.0 / sd;
+      }
     }
     __syncthreads();
     if (fail >= 0) break;
-    const double inv = 1.0 / Ls[j][j];
+    const double inv = pinv;
     for (int i = j + 1 + threadIdx.x; i < b; i += blockDim.x) Ls[i][j] *= inv;
     __syncthreads();
-    const int n = b - j - 1;  // trailing triangle of the block
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int r = j + 1 + e / n, c = j + 1 + e % n;
-      if (c <= r) Ls[r][c] = fma(-Ls[r][j], Ls[c][j], Ls[r][c]);
+    // rows r > j, columns j < c <= r
+    const int r0 = j + 1 + ty, c0 = j + 1 + tx;
+    for (int r = r0; r < b; r += 16) {
+      const double lr = Ls[r][j];
+      for (int c = c0; c <= r; c += 16) Ls[r][c] = fma(-lr, Ls[c][j], Ls[r][c]);
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int r = e / b, c = e % b;
-    if (c <= r) A[(size_t)(p + r) * M + p + c] = Ls[r][c];
-  }
+  for (int r = ty; r < b; r += 16)
+    for (int c = tx; c <= r; c += 16) A[(size_t)(p + r) * M + p + c] = Ls[r][c];
   if (threadIdx.x == 0 && fail >= 0) *info = fail;
 }
 
@@ -482,90 +491,247 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double *A, int M, int 
 // CTA: row i's dot product is split over the threads, reduced per warp and across warps.
 __global__ void __launch_bounds__(256) fit_solve_kernel(const double *G, const double *b, int M, const int *info,
                                                         double *x) {
-  // Column-oriented substitutions: thread t owns the entries k = t, t + 256, ..., so each
-  // step is one multiply by the owner of entry i (the diagonal's reciprocals formed in
-  // parallel first: FP64 division is slow on this part), one barrier, and one multiply-add
-  // per owned entry (no reduction tree on the critical path).
-  __shared__ double v[1024], inv[1024];
+  // Column-oriented substitutions: thread t owns the entries k = t + 256 q (q < 4, M <=
+  // 1024), kept in registers; each step is one multiply by the owner of entry i (the
+  // diagonal's reciprocals formed in parallel first: FP64 division is slow on this part),
+  // its value passed through shared memory with one barrier, and one multiply-add per owned
+  // entry.  The entries of G a step needs do not depend on the solution, so each thread
+  // loads the next step's while this one runs (an L2 read is not on the step's path).
+  constexpr int kOwn = 4;
+  __shared__ double inv[1024], val[2];
   if (*info >= 0) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) x[i] = 0.0;
     return;
   }
-  for (int k = threadIdx.x; k < M; k += blockDim.x) {
-    v[k] = b[k];
-    inv[k] = 1.0 / G[(size_t)k * M + k];
+  const int t = threadIdx.x;
+  double v[kOwn], g[kOwn], gn[kOwn];
+#pragma unroll
+  for (int q = 0; q < kOwn; ++q) {
+    const int k = t + 256 * q;
+    v[q] = k < M ? b[k] : 0.0;
+  }
+  for (int k = t; k < M; k += blockDim.x) inv[k] = 1.0 / G[(size_t)k * M + k];
+  // forward: G y = b; v_k <- v_k - G_ki y_i for k > i (column i of G).  Steps i in
+  // [256 qo, 256 qo + 256) are owned through v[qo] (qo unrolled: no indexed register array)
+#pragma unroll
+  for (int q = 0; q < kOwn; ++q) {
+    const int k = t + 256 * q;
+    g[q] = (k > 0 && k < M) ? G[(size_t)k * M] : 0.0;
   }
   __syncthreads();
-  for (int i = 0; i < M; ++i) {  // forward: G y = b; v[k] = b_k - sum_{j < i} G_kj y_j
-    if ((i & (blockDim.x - 1)) == threadIdx.x) v[i] *= inv[i];  // y_i
-    __syncthreads();
-    const double yi = v[i];
-    for (int k = threadIdx.x; k < M; k += blockDim.x)
-      if (k > i) v[k] = fma(-G[(size_t)k * M + i], yi, v[k]);
+#pragma unroll
+  for (int qo = 0; qo < kOwn; ++qo) {
+    const int i_end = min(M, 256 * (qo + 1));
+    for (int i = 256 * qo; i < i_end; ++i) {
+#pragma unroll
+      for (int q = 0; q < kOwn; ++q) {
+        const int k = t + 256 * q;
+        gn[q] = (i + 1 < M && k > i + 1 && k < M) ? G[(size_t)k * M + i + 1] : 0.0;
+      }
+      if ((i & 255) == t) {
+        v[qo] *= inv[i];  // y_i
+        val[i & 1] = v[qo];
+      }
+      __syncthreads();
+      const double yi = val[i & 1];
+#pragma unroll
+      for (int q = 0; q < kOwn; ++q) {
+        const int k = t + 256 * q;
+        if (k > i && k < M) v[q] = fma(-g[q], yi, v[q]);
+        g[q] = gn[q];
+      }
+    }
+  }
+  // backward: G^T x = y; v_k <- v_k - G_ik x_i for k < i (row i of G)
+#pragma unroll
+  for (int q = 0; q < kOwn; ++q) {
+    const int k = t + 256 * q;
+    g[q] = (k < M - 1) ? G[(size_t)(M - 1) * M + k] : 0.0;
   }
   __syncthreads();
-  for (int i = M - 1; i >= 0; --i) {  // backward: G^T x = y; row i of G gives column i of G^T
-    if ((i & (blockDim.x - 1)) == threadIdx.x) v[i] *= inv[i];  // x_i
-    __syncthreads();
-    const double xi = v[i];
-    for (int k = threadIdx.x; k < i; k += blockDim.x) v[k] = fma(-G[(size_t)i * M + k], xi, v[k]);
+#pragma unroll
+  for (int qo = kOwn - 1; qo >= 0; --qo) {
+    for (int i = min(M, 256 * (qo + 1)) - 1; i >= 256 * qo; --i) {
+#pragma unroll
+      for (int q = 0; q < kOwn; ++q) {
+        const int k = t + 256 * q;
+        gn[q] = (i >= 1 && k < i - 1) ? G[(size_t)(i - 1) * M + k] : 0.0;
+      }
+      if ((i & 255) == t) {
+        v[qo] *= inv[i];  // x_i
+        val[i & 1] = v[qo];
+      }
+      __syncthreads();
+      const double xi = val[i & 1];
+#pragma unroll
+      for (int q = 0; q < kOwn; ++q) {
+        const int k = t + 256 * q;
+        if (k < i) v[q] = fma(-g[q], xi, v[q]);
+        g[q] = gn[q];
+      }
+    }
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < M; i += blockDim.x) x[i] = v[i];
+#pragma unroll
+  for (int q = 0; q < kOwn; ++q) {
+    const int k = t + 256 * q;
+    if (k < M) x[k] = v[q];
+  }
 }
 
-__global__ void fit_chi2_kernel(const float *__restrict__ C, const float *__restrict__ I, const float *__restrict__ weight,
-                                const int *stamp_xy, FitDims f, const double *coef, const int *info, double *chi2) {
+// (h, l) += e (wh + wl) for a float e: the double-float multiply-add above with el = 0
+__device__ __forceinline__ void df_madd1(float &h, float &l, float e, float wh, float wl) {
+  const float th = e * wh;
+  float tl = fmaf(e, wh, -th);
+  tl = fmaf(e, wl, tl);
+  const float sum = h + th;
+  const float bv = sum - h;
+  const float err = (h - (sum - bv)) + (th - bv);
+  l += err + tl;
+  h = sum;
+}
+
+// (ah + al)(bh + bl) as a normalised double-float (the al bl term dropped)
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &h, float &l) {
+  const float ph = ah * bh;
+  float pl = fmaf(ah, bh, -ph);
+  pl = fmaf(ah, bl, pl);
+  pl = fmaf(al, bh, pl);
+  h = ph + pl;
+  l = pl - (h - ph);
+}
+
+// (2 x - (n - 1)) / (n - 1) as hi + lo floats (Dekker: the float quotient, then the exact
+// remainder divided once more); 0 for n = 1.  Integer frame sizes < 2^24 are exact floats.
+__device__ __forceinline__ void df_norm_coord(int x, int n, float &h, float &l) {
+  if (n <= 1) {
+    h = 0.0f;
+    l = 0.0f;
+    return;
+  }
+  const float a = (float)(2 * x - (n - 1)), den = (float)(n - 1);
+  const float q1 = a / den;
+  const float r = fmaf(-q1, den, a);  // exact: a - q1 den
+  const float q2 = r / den;
+  h = q1 + q2;
+  l = q2 - (h - q1);
+}
+
+// chi^2 = sum w (model - I)^2 at the solution, a direct second pass.  Double-float
+// arithmetic on the FP32 pipe (FP64 runs at about 1/60 of its rate here): per pixel
+// G_t = sum_k c[k][t] C_k (C_k is a float, c[k][t] split into hi + lo once per CTA), then
+// model = sum_t m_t G_t + the background polynomial, the monomials xt^i yt^j in double-float;
+// the residual and w r^2 in FP64.  CTA = kChiPix stamp pixels, their C rows staged in
+// shared memory by coalesced loads.
+constexpr int kChiPix = 128;
+
+__global__ void __launch_bounds__(kChiPix) fit_chi2_kernel(const float *__restrict__ C, const float *__restrict__ I,
+                                                           const float *__restrict__ weight, const int *stamp_xy,
+                                                           FitDims f, const double *coef, const int *info,
+                                                           double *chi2) {
+  __shared__ float Cs[kChiPix * 64];                // N <= 64
+  __shared__ float ch[64 * 10 + 10], cl[64 * 10 + 10];  // M = N T + Tb <= 650
   __shared__ double red[32];
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (*info >= 0) return;  // no solution: chi^2 stays 0
+  const int p0 = blockIdx.x * kChiPix, np = min(kChiPix, f.P - p0);
+  for (int i = threadIdx.x; i < f.M; i += kChiPix) {
+    const double c = coef[i];
+    const float hi = (float)c;
+    ch[i] = hi;
+    cl[i] = (float)(c - (double)hi);
+  }
+  {
+    const float *src = C + (size_t)p0 * f.N;
+    const int n = np * f.N;
+    for (int i = threadIdx.x; i < n; i += kChiPix) Cs[i] = __ldg(src + i);
+  }
+  __syncthreads();
   double r2 = 0.0;
-  if (p < f.P && *info < 0) {
+  const int t = threadIdx.x;
+  if (t < np) {
     int x, y;
-    stamp_pixel(f, stamp_xy, p, x, y);
+    stamp_pixel(f, stamp_xy, p0 + t, x, y);
     if (x >= 0 && x < f.W && y >= 0 && y < f.H) {
-      const double xt = norm_coord(x, f.W), yt = norm_coord(y, f.H);
-      // the pixel's monomials once (registers: T <= 10), then per stamp its polynomial
-      // a_k = sum_t c[k][t] m_t and the model's term a_k C_k
-      double m[10];
+      // monomials xt^i yt^j of degree <= D = max(d, bd), index mono_index(i, j, D)
+      const int D = f.d > f.bd ? f.d : f.bd;
+      float xh, xl, yh, yl;
+      df_norm_coord(x, f.W, xh, xl);
+      df_norm_coord(y, f.H, yh, yl);
+      float mh[10], ml[10];
       {
-        int t = 0;
-        double xi = 1.0;
-        for (int i = 0; i <= f.d; ++i) {
-          double yj = 1.0;
-          for (int j = 0; j <= f.d - i; ++j, ++t) {
+        float pih = 1.0f, pil = 0.0f;  // xt^i
+        int u = 0;
 #pragma unroll
-            for (int u = 0; u < 10; ++u)
-              if (u == t) m[u] = xi * yj;
-            yj *= yt;
+        for (int i = 0; i <= 3; ++i) {
+          float qh = pih, ql = pil;  // xt^i yt^j
+#pragma unroll
+          for (int j = 0; j <= 3 - i; ++j) {
+            if (i + j <= D) {
+#pragma unroll
+              for (int v = 0; v < 10; ++v)
+                if (v == u) {
+                  mh[v] = qh;
+                  ml[v] = ql;
+                }
+              ++u;
+            }
+            df_mul(qh, ql, yh, yl, qh, ql);
           }
-          xi *= xt;
+          df_mul(pih, pil, xh, xl, pih, pil);
         }
       }
-      double model = 0.0;
-      for (int k = 0; k < f.N; ++k) {
-        const double *ck = coef + (size_t)k * f.T;
-        double ak = 0.0;
+      // G_t = sum_k c[k][t] C_k
+      float gh[10], gl[10];
 #pragma unroll
-        for (int t = 0; t < 10; ++t)
-          if (t < f.T) ak = fma(ck[t], m[t], ak);
-        model = fma(ak, (double)C[(size_t)p * f.N + k], model);
+      for (int u = 0; u < 10; ++u) gh[u] = gl[u] = 0.0f;
+      const float *crow = Cs + t * f.N;
+      for (int k = 0; k < f.N; ++k) {
+        const float ck = crow[k];
+        const float *h = ch + k * f.T, *l = cl + k * f.T;
+#pragma unroll
+        for (int u = 0; u < 10; ++u)
+          if (u < f.T) df_madd1(gh[u], gl[u], ck, h[u], l[u]);
       }
-      double xi = 1.0;
-      int t = 0;
-      for (int i = 0; i <= f.bd; ++i) {
-        double yj = 1.0;
-        for (int j = 0; j <= f.bd - i; ++j, ++t) {
-          model = fma(coef[f.N * f.T + t], xi * yj, model);
-          yj *= yt;
-        }
-        xi *= xt;
+      // model = sum_t m_t G_t (t = (i, j), i + j <= d) + sum over the background terms
+      float mdh = 0.0f, mdl = 0.0f;
+      {
+        int u = 0;
+        for (int i = 0; i <= f.d; ++i)
+          for (int j = 0; j <= f.d - i; ++j, ++u) {
+            const int mi = mono_index(i, j, D);
+            float a_h = 0.f, a_l = 0.f, b_h = 0.f, b_l = 0.f;
+#pragma unroll
+            for (int v = 0; v < 10; ++v) {
+              if (v == u) {
+                a_h = gh[v];
+                a_l = gl[v];
+              }
+              if (v == mi) {
+                b_h = mh[v];
+                b_l = ml[v];
+              }
+            }
+            df_madd(mdh, mdl, a_h, a_l, b_h, b_l);
+          }
+        int q = f.N * f.T;
+        for (int i = 0; i <= f.bd; ++i)
+          for (int j = 0; j <= f.bd - i; ++j, ++q) {
+            const int mi = mono_index(i, j, D);
+            float b_h = 0.f, b_l = 0.f;
+#pragma unroll
+            for (int v = 0; v < 10; ++v)
+              if (v == mi) {
+                b_h = mh[v];
+                b_l = ml[v];
+              }
+            df_madd(mdh, mdl, b_h, b_l, ch[q], cl[q]);
+          }
       }
-      const double r = model - (double)I[(size_t)y * f.pitch + x];
+      const double r = ((double)mdh + (double)mdl) - (double)I[(size_t)y * f.pitch + x];
       r2 = (weight ? (double)weight[(size_t)y * f.pitch + x] : 1.0) * r * r;
     }
   }
-  const double s = block_sum_d(r2, red);
-  if (threadIdx.x == 0) atomicAdd(chi2, s);
+  const double sum = block_sum_d(r2, red);
+  if (threadIdx.x == 0) atomicAdd(chi2, sum);
 }
 
 FitDims dims(int W, int H, int pitch, int n_stamps, int S, int N, int L, int d, int bd) {
@@ -695,7 +861,9 @@ int launch_fit(const float *R, const float *I, int W, int H, int pitch, const in
   int st = queue_moments(R, I, weight, f, stamp_xy, basis, C, S, s);
   if (st == SVK_OK) st = queue_solve(S, f, A, b, coeffs_out, info_out, s);
   if (st != SVK_OK) return st;
-  if (chi2_out) fit_chi2_kernel<<<(f.P + 255) / 256, 256, 0, s>>>(C, I, weight, stamp_xy, f, coeffs_out, info_out, chi2_out);
+  if (chi2_out)
+    fit_chi2_kernel<<<(f.P + kChiPix - 1) / kChiPix, kChiPix, 0, s>>>(C, I, weight, stamp_xy, f, coeffs_out, info_out,
+                                                                    chi2_out);
   return cuda_status(cudaGetLastError(), "fit kernels launch");
 }
 

@@ -677,7 +677,7 @@ static int check_host_frames(const svk_frame *frames, int n, int method, int pre
     int st = check_conv_args(F.R, F.pitch_R, F.I, F.pitch_I, F.W, F.H, F.basis, F.N, F.L, F.coeffs, F.degree, method,
                              precision, SVK_EDGE_ZERO, F.D, F.pitch_D, true);
     if (st != SVK_OK) {
-      char msg[256];
+      char msg[sizeof(g_err)];  // the message is rewritten into g_err below
       snprintf(msg, sizeof(msg), "%s", last_error());
       return set_error(st, "frame %d: %s", f, msg);
     }

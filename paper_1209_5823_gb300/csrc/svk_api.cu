@@ -115,7 +115,7 @@ ScopedWorkspace::~ScopedWorkspace() {
 // cannot be read.  Ids are unique for the life of the process: a context destroyed (by
 // cudaDeviceReset, for instance) and created again gets a new id even where the driver
 // hands out the same handle.
-static unsigned long long current_context_id() {
+unsigned long long current_context_id() {
   static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
   static PFN_cuCtxGetId_v12000 get_id = nullptr;
   static std::once_flag once;

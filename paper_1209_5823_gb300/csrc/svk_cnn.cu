@@ -26,6 +26,8 @@
 //                order, so the gradient is deterministic), N = 32 outputs.
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "svk_common.cuh"
 #include "svk_internal.h"
 #include "svk_umma.cuh"
@@ -1285,6 +1287,43 @@ int cnn_forward(const float *params, const float *x, int B, int n_out, float *ou
   return forward(x, L, b, B, n_out, out, sm_count(), s);
 }
 
+// A second stream per device for the weight gradients of the 32-channel layers: the one of
+// layer l needs only dz[l] and act[l-1], so it runs beside the data gradient of layer l
+// (which the chain below waits for), and the reduction joins the two streams.  A weight-
+// gradient CTA and a data-gradient CTA fit in one SM's shared memory together.  Created
+// once per device and context; the mutex is held while a call enqueues its fork and join
+// (the stream and events are shared).
+struct WgradSide {
+  unsigned long long ctx = 0;
+  cudaStream_t ss = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kSideDevices = 64;
+std::mutex g_side_mutex;
+WgradSide g_side[kSideDevices];
+
+int wgrad_side(WgradSide **out) {
+  int dev = 0;
+  int st = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+  if (st != SVK_OK) return st;
+  if (dev < 0 || dev >= kSideDevices) return set_error(SVK_ERR_UNSUPPORTED, "device %d out of range", dev);
+  WgradSide &w = g_side[dev];
+  const unsigned long long id = current_context_id();
+  if (!w.ss || id == 0 || id != w.ctx) {  // first use, or the context was created again
+    w = WgradSide{};
+    st = cuda_status(cudaStreamCreateWithFlags(&w.ss, cudaStreamNonBlocking), "weight-gradient stream");
+    if (st == SVK_OK) st = cuda_status(cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming), "event");
+    if (st == SVK_OK) st = cuda_status(cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming), "event");
+    if (st != SVK_OK) {
+      w = WgradSide{};
+      return st;
+    }
+    w.ctx = id;
+  }
+  *out = &w;
+  return SVK_OK;
+}
+
 int cnn_gradient(const float *params, const float *x, const float *target, int B, int n_out, float *grad, float *loss,
                  void *ws, size_t ws_bytes, cudaStream_t s) {
   int st = check_ws(ws, ws_bytes, B, n_out);
@@ -1299,14 +1338,24 @@ int cnn_gradient(const float *params, const float *x, const float *target, int B
                                     B, n_out),
                    "network output gradient");
   if (st != SVK_OK) return st;
+  std::lock_guard<std::mutex> lock(g_side_mutex);
+  WgradSide *side = nullptr;
+  if ((st = wgrad_side(&side)) != SVK_OK) return st;
   for (int li = kLayers - 1; li >= 1; --li) {
-    st = wgrad_tma(b.act[li - 1], 1 << kLgIn[li], b.dz[li], b.part[li], B, kLgOut[li], kStride[li], s);
+    // dz[li] is written (by the output gradient or the data gradient above): fork
+    st = cuda_status(cudaEventRecord(side->fork, s), "fork record");
+    if (st == SVK_OK) st = cuda_status(cudaStreamWaitEvent(side->ss, side->fork, 0), "fork wait");
+    if (st == SVK_OK)
+      st = wgrad_tma(b.act[li - 1], 1 << kLgIn[li], b.dz[li], b.part[li], B, kLgOut[li], kStride[li], side->ss);
     if (st == SVK_OK)
       st = conv_tma<kDgrad>(b.dz[li], 1 << kLgOut[li], b.wd[li], nullptr, b.act[li - 1], b.dz[li - 1], B, kLgIn[li],
                             kStride[li], nsm, s);
     if (st != SVK_OK) return st;
   }
   if ((st = wgrad1(x, b.dz[0], b.part[0], B, s)) != SVK_OK) return st;
+  st = cuda_status(cudaEventRecord(side->join, side->ss), "join record");
+  if (st == SVK_OK) st = cuda_status(cudaStreamWaitEvent(s, side->join, 0), "join wait");
+  if (st != SVK_OK) return st;
   WgradSet set{};
   set.row0[0] = 0;
   for (int li = 0; li < kLayers; ++li) {

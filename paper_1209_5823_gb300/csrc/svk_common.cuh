@@ -52,6 +52,10 @@ enum DeviceStatus : uint32_t { kDevOk = 0, kDevTimeout = 1, kDevIndex = 2 };
 // kernels' status pointer), or NULL if it cannot be resolved.
 uint32_t *device_status_word();
 
+// The driver's id of the calling thread's current context (unique for the life of the
+// process), or 0 when there is none or it cannot be read.
+unsigned long long current_context_id();
+
 // Device addresses of a file-scope __device__ variable, one per device ordinal, each
 // remembered with the context it was looked up in.  In host code such a variable's name
 // is only a host-side stand-in, so its device address comes from cudaGetSymbolAddress

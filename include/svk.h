@@ -276,7 +276,10 @@ SVK_API size_t svk_cnn_workspace_size(int batch, int n_out);
 SVK_API int svk_cnn_forward(const float *params, const float *x, int batch, int n_out, float *out, void *workspace,
                             size_t ws_bytes, void *stream);
 /* Mean squared error against target [batch][n_out] into *loss (device float) and its
- * gradient with respect to every parameter into grad (device float [param_count]). */
+ * gradient with respect to every parameter into grad (device float [param_count]).  The
+ * weight gradients of the 32-channel layers run on a library stream forked from and joined
+ * back into `stream` within the call (events; capturable in a CUDA graph once a first call
+ * has run outside the capture), so all of the call's work is ordered on `stream`. */
 SVK_API int svk_cnn_gradient(const float *params, const float *x, const float *target, int batch, int n_out,
                              float *grad, float *loss, void *workspace, size_t ws_bytes, void *stream);
 /* One Adam step (bias-corrected, step >= 1) on the FP32 parameters with moments m, v. */

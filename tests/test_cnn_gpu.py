@@ -105,6 +105,46 @@ def test_gradient_is_deterministic():
     assert torch.equal(g1, g2)
 
 
+def test_gradient_calls_from_two_threads():
+    # the weight gradients run on a library stream forked from and joined back into the
+    # caller's stream; two host threads on their own streams (and workspaces) must each get
+    # exactly the single-threaded result while their calls interleave
+    import threading
+    n_out, B = 49, 256
+    p = torch.from_numpy(starfield.cnn_init_params(n_out, 5)).cuda()
+    data = [tuple(torch.from_numpy(a).cuda() for a in _data(B, n_out, 40 + i)) for i in range(2)]
+    ref = [svk.svk_cnn_gradient(p, x, t)[0].clone() for x, t in data]
+    torch.cuda.synchronize()
+    nbytes = svk.svk_cnn_workspace_size(B, n_out)
+    out = [[], []]
+    errors = []
+
+    def worker(i):
+        try:
+            s = torch.cuda.Stream()
+            ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            x, t = data[i]
+            with torch.cuda.stream(s):
+                for _ in range(20):
+                    g = torch.empty_like(p)
+                    svk.svk_cnn_gradient(p, x, t, grad=g, workspace=ws, stream=s)
+                    out[i].append(g)
+            s.synchronize()
+        except Exception as e:  # reported below, on the main thread
+            errors.append(e)
+
+    th = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+    for t_ in th:
+        t_.start()
+    for t_ in th:
+        t_.join()
+    assert not errors, errors
+    for i in range(2):
+        assert len(out[i]) == 20
+        for g in out[i]:
+            assert torch.equal(g, ref[i])
+
+
 def test_adam_step():
     n = 1000
     g = starfield.rng(3)

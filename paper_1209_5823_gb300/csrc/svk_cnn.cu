@@ -1309,7 +1309,7 @@ int wgrad_side(WgradSide **out) {
   if (dev < 0 || dev >= kSideDevices) return set_error(SVK_ERR_UNSUPPORTED, "device %d out of range", dev);
   WgradSide &w = g_side[dev];
   const unsigned long long id = current_context_id();
-  if (!w.ss || id == 0 || id != w.ctx) {  // first use, or the context was created again
+  if (!w.ss || (id != 0 && id != w.ctx)) {  // first use, or the context was created again
     w = WgradSide{};
     st = cuda_status(cudaStreamCreateWithFlags(&w.ss, cudaStreamNonBlocking), "weight-gradient stream");
     if (st == SVK_OK) st = cuda_status(cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming), "event");

@@ -16,9 +16,12 @@
 //   2. isolate_kernel  one warp per candidate: its lanes scan the window of the peak map
 //                      and it appends a 64-bit sort key (inverted order-preserving bits of
 //                      R(p), then the index) for each isolated one;
-//   3. bitonic sort of the keys, padded to the next power of two of their count read on
-//      the device; the host launches the passes for the largest possible count and the
-//      passes beyond the actual count return at once;
+//   3. the keys, padded to the next power of two of their count read on the device, in
+//      order: when at most kLocalSort stamps are wanted, a bitonic top-k -- chunks of
+//      kLocalSort keys sorted in shared memory, then rounds that merge pairs of chunks
+//      keeping the smaller half (one launch per round, log2 of the chunk capacity rounds);
+//      otherwise a full bitonic sort.  The host launches the passes or rounds for the
+//      largest possible count, and those beyond the actual count return at once;
 //   4. output_kernel   the first max_stamps keys -> (x, y), and the counts.
 // Capacity: two peaks are never 8-neighbours, so a frame holds at most
 // ceil(W/2) * ceil(H/2) peaks; every buffer is sized for that.  The kernels are launched as
@@ -155,8 +158,10 @@ __global__ void bitonic_global(unsigned long long *keys, const int *cnt, uint32_
 
 // Stages k = k_lo .. k_hi (doubling) with j < kLocalSort, in shared memory: each block
 // holds one kLocalSort-key segment (pairs (i, i ^ j) never leave it for j < kLocalSort).
+// chunk_dir: every segment ascending (directions from the index within the segment; the
+// top-k path), else the directions of the whole-array network.
 __global__ void __launch_bounds__(kLocalSort / 2) bitonic_local(unsigned long long *keys, const int *cnt,
-                                                                uint32_t k_lo, uint32_t k_hi) {
+                                                                uint32_t k_lo, uint32_t k_hi, int chunk_dir) {
   dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
   dep_wait();
   __shared__ unsigned long long s[kLocalSort];
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(kLocalSort / 2) bitonic_local(unsigned long lo
         const uint32_t l = t ^ j;
         if (l > t && l < len) {
           const unsigned long long a = s[t], b = s[l];
-          const bool up = ((base + t) & k) == 0;
+          const bool up = ((chunk_dir ? t : base + t) & k) == 0;
           if ((a > b) == up) {
             s[t] = b;
             s[l] = a;
@@ -182,6 +187,42 @@ __global__ void __launch_bounds__(kLocalSort / 2) bitonic_local(unsigned long lo
       __syncthreads();
     }
   for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) keys[base + t] = s[t];
+}
+
+// Round r of the top-k: block b merges the ascending chunks c = b 2^r and c + 2^(r-1) (in
+// chunks of kLocalSort keys).  C_i = min(A_i, B_{m-1-i}) are the m smallest keys of the two
+// and form a bitonic sequence (the first stage of Batcher's bitonic merge of A with B
+// reversed); the rest of that merge sorts them ascending into chunk c.  A chunk without a
+// partner (or beyond the padded count) stays as it is.
+__global__ void __launch_bounds__(kLocalSort / 2) topk_merge(unsigned long long *keys, const int *cnt, uint32_t r) {
+  dep_trigger();  // launched by launch_dependent: wait for the previous kernel first
+  dep_wait();
+  __shared__ unsigned long long s[kLocalSort];
+  const uint32_t np2 = dev_next_pow2((uint32_t)cnt[kSel]);
+  const uint32_t nch = np2 <= (uint32_t)kLocalSort ? 1u : np2 / kLocalSort;
+  const uint32_t c = blockIdx.x << r, pc = c + (1u << (r - 1));
+  if (pc >= nch) return;
+  unsigned long long *A = keys + (size_t)c * kLocalSort;
+  const unsigned long long *Bc = keys + (size_t)pc * kLocalSort;
+  for (uint32_t t = threadIdx.x; t < (uint32_t)kLocalSort; t += blockDim.x) {
+    const unsigned long long a = A[t], b = Bc[kLocalSort - 1 - t];
+    s[t] = a < b ? a : b;
+  }
+  __syncthreads();
+  for (uint32_t j = kLocalSort / 2; j > 0; j >>= 1) {
+    for (uint32_t t = threadIdx.x; t < (uint32_t)kLocalSort; t += blockDim.x) {
+      const uint32_t l = t ^ j;
+      if (l > t) {
+        const unsigned long long a = s[t], b = s[l];
+        if (a > b) {
+          s[t] = b;
+          s[l] = a;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (uint32_t t = threadIdx.x; t < (uint32_t)kLocalSort; t += blockDim.x) A[t] = s[t];
 }
 
 __global__ void output_kernel(const unsigned long long *keys, const int *cnt, int W, int max_stamps, int *xy,
@@ -223,11 +264,19 @@ int launch_select(const float *R, int W, int H, int pitch, float sky, float thre
                          cnt, keys);
   if (e == cudaSuccess) e = launch_dependent(pad_kernel, kGridStride, 256, 0, s, keys, cnt);
   const uint32_t P = (uint32_t)l.cap_p2, nloc = P / kLocalSort;
-  if (e == cudaSuccess) e = launch_dependent(bitonic_local, nloc, kLocalSort / 2, 0, s, keys, cnt, 2u, (uint32_t)kLocalSort);
-  for (uint32_t k = 2 * kLocalSort; k <= P && e == cudaSuccess; k <<= 1) {
-    for (uint32_t j = k >> 1; j >= (uint32_t)kLocalSort && e == cudaSuccess; j >>= 1)
-      e = launch_dependent(bitonic_global, kGridStride, 256, 0, s, keys, cnt, k, j);
-    if (e == cudaSuccess) e = launch_dependent(bitonic_local, nloc, kLocalSort / 2, 0, s, keys, cnt, k, k);
+  if (max_stamps <= kLocalSort) {  // top-k: log2(nloc) merge rounds instead of the full network
+    if (e == cudaSuccess)
+      e = launch_dependent(bitonic_local, nloc, kLocalSort / 2, 0, s, keys, cnt, 2u, (uint32_t)kLocalSort, 1);
+    for (uint32_t r = 1; (nloc >> r) >= 1 && e == cudaSuccess; ++r)
+      e = launch_dependent(topk_merge, nloc >> r, kLocalSort / 2, 0, s, keys, (const int *)cnt, r);
+  } else {
+    if (e == cudaSuccess)
+      e = launch_dependent(bitonic_local, nloc, kLocalSort / 2, 0, s, keys, cnt, 2u, (uint32_t)kLocalSort, 0);
+    for (uint32_t k = 2 * kLocalSort; k <= P && e == cudaSuccess; k <<= 1) {
+      for (uint32_t j = k >> 1; j >= (uint32_t)kLocalSort && e == cudaSuccess; j >>= 1)
+        e = launch_dependent(bitonic_global, kGridStride, 256, 0, s, keys, cnt, k, j);
+      if (e == cudaSuccess) e = launch_dependent(bitonic_local, nloc, kLocalSort / 2, 0, s, keys, cnt, k, k, 0);
+    }
   }
   if (e == cudaSuccess)
     e = launch_dependent(output_kernel, kGridStride / 8, 256, 0, s, keys, (const int *)cnt, W, max_stamps, xy, counts);

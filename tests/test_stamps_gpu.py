@@ -55,6 +55,15 @@ def test_parity_full_size_frame():
     assert len(want) == 500
 
 
+@pytest.mark.parametrize("max_stamps", [1500, 2048, 2049])
+def test_top_k_and_full_sort_over_many_candidates(max_stamps):
+    # thousands of isolated peaks: up to 2048 stamps come from the top-k merge rounds over
+    # chunks of 2048 keys, more from the full sort; both must give the oracle's list
+    R = _field(1536, 1024, 9000, 11)
+    want = _check(R, SKY, 150.0, 1e9, 4, 2, 0.5, max_stamps)
+    assert len(want) == max_stamps
+
+
 def test_constructed_frame_on_device():
     cat = starfield.Catalog(x=np.array([20.0, 60.0, 40.0, 46.0, 80.0, 86.0, 100.0, 106.0, 3.0]),
                             y=np.array([20.0, 30.0, 60.0, 60.0, 70.0, 70.0, 20.0, 20.0, 50.0]),

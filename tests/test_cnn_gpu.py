@@ -231,27 +231,30 @@ def test_training_learns_and_network_path_is_faster_with_fallback():
     # predicting the prior mean scores 1.0 (+- 0.01 over 500 x 49 held-out values)
     assert err_net < 0.95
 
-    # a frame whose kernel has spatially varying coefficients: network path vs FP64 fit
+    # a frame whose kernel has spatially varying coefficients: network path vs FP64 fit, both
+    # for the cubic 49 x 10 field (the fit's moments grow with the degree, the network's
+    # cost does not; with few stamps the fit can be the faster one)
     W = H = 1024
-    c_true = torch.from_numpy(starfield.planted_coeffs(N, 1, starfield.rng(8)).astype(np.float32)).cuda()
-    I = svk.svk_convolve(Rf, basis, c_true, 1, method=svk.SVK_METHOD_BASIS, precision=svk.SVK_PREC_BF16X3)
+    D = 3
+    c_true = torch.from_numpy(starfield.planted_coeffs(N, D, starfield.rng(8)).astype(np.float32)).cuda()
+    I = svk.svk_convolve(Rf, basis, c_true, D, method=svk.SVK_METHOD_BASIS, precision=svk.SVK_PREC_BF16X3)
     I = I + 30.0 * torch.randn(I.shape, device=dev, generator=gen)
     st = torch.stack([cx[:300], cy[:300]], 1).to(torch.int32)
-    learned.apply_to_frame(net, Rf, I, st, basis, 1, 30.0, fallback_ratio=1e9, reference_noise_sigma=0.0)  # warm both paths
-    svk.svk_fit_coeffs(Rf, I, st, 41, basis, 1, bg_degree=0)
+    learned.apply_to_frame(net, Rf, I, st, basis, D, 30.0, fallback_ratio=1e9, reference_noise_sigma=0.0)  # warm both paths
+    svk.svk_fit_coeffs(Rf, I, st, 41, basis, D, bg_degree=0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = learned.apply_to_frame(net, Rf, I, st, basis, 1, 30.0, fallback_ratio=1e9, reference_noise_sigma=0.0)
+    res = learned.apply_to_frame(net, Rf, I, st, basis, D, 30.0, fallback_ratio=1e9, reference_noise_sigma=0.0)
     torch.cuda.synchronize()
     t_net = time.perf_counter() - t0
     t0 = time.perf_counter()
-    svk.svk_fit_coeffs(Rf, I, st, 41, basis, 1, bg_degree=0)
+    svk.svk_fit_coeffs(Rf, I, st, 41, basis, D, bg_degree=0)
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     assert res["source"] == "network" and t_net < t_fit
     # garbage weights: the residual check hands the frame to the fit
     bad = learned.CoefficientNetwork(torch.zeros_like(net.params), learned.CoeffPrior(N, mean0=0.0), batch=128)
-    res2 = learned.apply_to_frame(bad, Rf, I, st, basis, 1, 30.0, fallback_ratio=2.0, reference_noise_sigma=0.0)
+    res2 = learned.apply_to_frame(bad, Rf, I, st, basis, D, 30.0, fallback_ratio=2.0, reference_noise_sigma=0.0)
     assert res2["source"] == "fit"
 
 

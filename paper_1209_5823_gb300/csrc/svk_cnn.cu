@@ -24,6 +24,9 @@
 //   weight grad  rows = 9 taps x input channels (+ a row of ones for the bias),
 //                K = output pixels (split over CTAs, partial sums reduced in a fixed
 //                order, so the gradient is deterministic), N = 32 outputs.
+// Every kernel is launched as a programmatic dependent of the one before; the weight
+// gradients of the 32-channel layers run on a second stream beside the data gradients
+// (cnn_gradient).
 #include <cuda_bf16.h>
 
 #include <mutex>

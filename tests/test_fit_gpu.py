@@ -48,6 +48,25 @@ def test_fit_recovers_planted_and_matches_oracle():
     np.testing.assert_allclose(co, c.reshape(-1), rtol=0, atol=2e-5)
 
 
+@pytest.mark.parametrize("d,bd", [(0, 2), (1, 3)])
+def test_fit_background_above_kernel_degree(d, bd):
+    # a background polynomial of higher degree than the kernel's: the monomials of both
+    # (degree max(d, bd)) and their moments (degree 2 max(d, bd)) index past the kernel terms'
+    W, H, L, S, sig = 128, 96, 9, 13, 10.0
+    R, I, B, c, st = _setup(W, H, L, S, d, 30, (0.8, 1.6), (2, 1), 70 + bd, noise=sig, bg=(12.0, -3.0, 5.0))
+    w = np.full((H, W), 1.0 / sig ** 2, np.float32)  # A is then the inverse covariance
+    ref = oracle.fit(R.astype(np.float64), I.astype(np.float64), st, S, B.astype(np.float64), d, bg_degree=bd,
+                     weight=w.astype(np.float64))
+    co, chi2, info = svk.svk_fit_coeffs(_dev(R), _dev(I), _dev(st), S, _dev(B), d, bg_degree=bd, weight=_dev(w),
+                                        sync=True)
+    assert int(info.item()) == -1 and ref["status"] == 0
+    assert abs(float(chi2.item()) - ref["chi2"]) <= 1e-4 * ref["chi2"]
+    # coefficients agree to a small fraction of their statistical uncertainty
+    cov = np.linalg.inv(ref["A"])
+    z = (co.cpu().numpy() - ref["coeffs"]) / np.sqrt(np.diag(cov))
+    assert np.abs(z).max() < 1e-2
+
+
 def test_fit_background_weights_noise_chi2():
     W, H, L, S, d, bd = 128, 96, 9, 13, 2, 1
     sig = 30.0

@@ -1344,20 +1344,24 @@ int cnn_gradient(const float *params, const float *x, const float *target, int B
   std::lock_guard<std::mutex> lock(g_side_mutex);
   WgradSide *side = nullptr;
   if ((st = wgrad_side(&side)) != SVK_OK) return st;
-  for (int li = kLayers - 1; li >= 1; --li) {
+  bool forked = false;
+  for (int li = kLayers - 1; li >= 1 && st == SVK_OK; --li) {
     // dz[li] is written (by the output gradient or the data gradient above): fork
     st = cuda_status(cudaEventRecord(side->fork, s), "fork record");
     if (st == SVK_OK) st = cuda_status(cudaStreamWaitEvent(side->ss, side->fork, 0), "fork wait");
+    forked = forked || st == SVK_OK;
     if (st == SVK_OK)
       st = wgrad_tma(b.act[li - 1], 1 << kLgIn[li], b.dz[li], b.part[li], B, kLgOut[li], kStride[li], side->ss);
     if (st == SVK_OK)
       st = conv_tma<kDgrad>(b.dz[li], 1 << kLgOut[li], b.wd[li], nullptr, b.act[li - 1], b.dz[li - 1], B, kLgIn[li],
                             kStride[li], nsm, s);
-    if (st != SVK_OK) return st;
   }
-  if ((st = wgrad1(x, b.dz[0], b.part[0], B, s)) != SVK_OK) return st;
-  st = cuda_status(cudaEventRecord(side->join, side->ss), "join record");
-  if (st == SVK_OK) st = cuda_status(cudaStreamWaitEvent(s, side->join, 0), "join wait");
+  if (st == SVK_OK) st = wgrad1(x, b.dz[0], b.part[0], B, s);
+  if (forked) {  // joined on every path once forked (a capture must not end with the fork open)
+    int js = cuda_status(cudaEventRecord(side->join, side->ss), "join record");
+    if (js == SVK_OK) js = cuda_status(cudaStreamWaitEvent(s, side->join, 0), "join wait");
+    if (st == SVK_OK) st = js;
+  }
   if (st != SVK_OK) return st;
   WgradSet set{};
   set.row0[0] = 0;
